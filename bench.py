@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the L-HWENO hot path: M point-updates/s per SSP-RK3 step.
+
+Workload (default): the ragged batch of 2048 1D Euler Riemann problems
+(gamma = 1.4, outflow, x in [0, 1], N per instance drawn from
+{200, 400, 800, 1600, 3200}, 2.54 M points, seeded), FP64. One step is one
+hweno_step over the whole batch: wave-speed reduction, three fused stage
+kernels (ghosts, splitting, characteristic HWENO fluxes, linear derivative
+fluxes, differences, limiter, RK combination) and the time update. A
+point-update is one grid point advanced through one full step; instances
+that have reached t_end do not count.
+
+Prints one JSON line (rank 0). Timing: W warm-up steps, then K timed steps,
+each bracketed by CUDA events on the library's stream with a 256 MiB write
+(larger than the 129 MB L2) between steps outside the events; barrier and
+synchronize on both sides; max over ranks. Under torchrun each rank runs its
+own seeded batch (weak scaling, no collective on the data path).
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoint-updates/s per RK step"
+# Algorithmic operations per grid point of one SSP-RK3 step (+ - * / sqrt count
+# one; abs and max zero), counted by the oracle's op-counting scalar on the
+# scheme as the paper states it; tests/test_bench_constants.py re-derives them.
+ALGO_FLOPS_PER_POINT_STEP = {
+    ("euler", 1): 5068.4,
+    ("burgers", 1): 1198.05,
+    ("euler", 2): 15092.06,
+    ("burgers", 2): 2484.84,
+}
+# Compulsory state traffic per point-step and component (words): 1D reads
+# U^n,V^n / U1,V1,U^n,V~^n / U2,V2,U^n,V~^n and writes U1,V1,V~^n / U2,V2 /
+# U^{n+1},V^{n+1}: 10 + 7 = 17.
+ALGO_WORDS_PER_COMPONENT = {1: 17, 2: 26}
+# ALU peaks (the recipe's nominal figures; no FP64/FP32 entry is measured in
+# MEASURED_PEAKS.json): FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flop
+# x 2.07 GHz.
+PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
+# DRAM bytes per point and launch of the fused stage kernel from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum / points); None until
+# taken for the current kernel.
+MEASURED_STAGE_TRAFFIC_PER_POINT = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--instances", type=int, default=2048)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e, fp32 and cpu_baseline legs")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r for r in self.rows if len(r) >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of the batch a rank runs (each rank its own batch: weak scaling)."""
+    return 20220711 + rank
+
+
+def reduce_over_ranks(ms: float, point_updates: float, device) -> tuple:
+    """Job time = max over ranks; job work = sum over ranks."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms, point_updates], dtype=torch.float64, device=device)
+    mx, sm = tt.clone(), tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, dev_index):
+    import torch
+    from paper_2207_05258_gb300 import hweno
+    from paper_2207_05258_gb300 import workloads as W
+
+    torch.cuda.set_device(dev_index)
+    w = W.riemann_batch(count=args.instances, seed=rank_seed(rank))
+    nx = torch.tensor(w.nx, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(precision, K, Wm, profile):
+        s = hweno.Solver.from_workload(w, precision=precision)
+        dt_t = torch.float64 if precision == "fp64" else torch.float32
+        U = torch.from_numpy(w.U).to("cuda", dt_t)
+        V = torch.from_numpy(w.V).to("cuda", dt_t)
+        t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+        hist = torch.zeros(K, w.batch, dtype=torch.float64, device="cuda")
+        for _ in range(Wm):
+            s.step(U, V, None, t, w.t_end)
+        s.sync_status()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        if profile:
+            s.profile_start(K * 5 + 8)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()
+            ev[i][0].record()
+            s.step(U, V, None, t, w.t_end, hist[i])
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        s.sync_status()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        prof = s.profile_read() if profile else None
+        pu = float(((hist > 0).double() * nx[None, :]).sum().item())
+        launches = s.launches_last_call * K
+        s.close()
+        return ms, pu, prof, launches
+
+    with ClockSampler(dev_index) as clk:
+        ms, pu, prof, launches = timed(args.precision, args.steps, args.warmup, True)
+    clocks = clk.summary()
+
+    if world > 1:
+        ms, pu = reduce_over_ranks(ms, pu, "cuda")
+    value = pu / (ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (the fused stage kernel)
+    stage_ms, stage_n = prof["stage"]
+    pts_per_stage = (pu / world) / args.steps  # units per launch (this rank)
+    flop_stage = ALGO_FLOPS_PER_POINT_STEP[("euler", 1)] / 3.0
+    achieved = flop_stage * pts_per_stage / (stage_ms / stage_n * 1e-3) / 1e12
+    peak = PEAK_TFLOPS[args.precision]
+    traffic = MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
+    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": None if traffic is None else traffic * pts_per_stage,
+            "kernel": "k_stage_1d<euler,%s>" % args.precision,
+            "kernel_share_of_step": round(stage_ms / sum(v[0] for v in prof.values()), 4),
+            "flops_per_point_stage": round(flop_stage, 2),
+            "peak_source": "nominal (recipe): FP64 1.25 TFLOP/s; FP32 = 152 SM x 128 x 2 x 2.07 GHz",
+            "hbm_achieved_gbs": round(ALGO_WORDS_PER_COMPONENT[1] / 3.0 * 3 *
+                                      (8 if args.precision == "fp64" else 4) * pts_per_stage /
+                                      (stage_ms / stage_n * 1e-3) / 1e9, 1)}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": "Mpoint-updates/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+           "config": {"workload": "riemann_batch: %d x 1D Euler Riemann problems, N in "
+                                  "{200,400,800,1600,3200}, %d points, t_end 0.15, outflow"
+                                  % (w.batch, w.points),
+                      "instances": w.batch, "points": w.points, "precision": args.precision,
+                      "l2": "flushed between timed steps (256 MiB write, L2 129 MB)",
+                      "parallelism": "replicas (one seeded batch per rank)"},
+           "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+           "point_updates_timed": pu}
+
+    if not args.no_extras:
+        # FP32 variant of the same workload (state and reconstruction in FP32)
+        if args.precision == "fp64":
+            ms32, pu32, prof32, _ = timed("fp32", args.steps, args.warmup, True)
+            out["fp32"] = {"value": round(pu32 / (ms32 * 1e-3) / 1e6, 3),
+                           "ms_per_step": round(ms32 / args.steps, 4),
+                           "stage_kernel_ms": round(prof32["stage"][0] / prof32["stage"][1], 4)}
+        out["e2e"] = run_e2e(args, w, hweno, torch)
+        if rank == 0:
+            out["cpu_baseline"] = cpu_baseline(w, budget_s=12.0)
+    return out, rank
+
+
+def run_e2e(args, w, hweno, torch):
+    """Same metric through the C ABI's host-buffer entry point: every step
+    copies U, V, t from pinned host memory and the result back."""
+    s = hweno.Solver.from_workload(w, precision=args.precision)
+    dt_t = torch.float64 if args.precision == "fp64" else torch.float32
+    U = torch.from_numpy(w.U).to(dt_t).pin_memory()
+    V = torch.from_numpy(w.V).to(dt_t).pin_memory()
+    t = torch.zeros(w.batch, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        s.step_host(U, V, None, t, w.t_end, 1)
+    K = max(3, args.steps // 2)
+    pts = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        active = (t.numpy() < w.t_end)
+        pts += int(np.sum(np.array(w.nx)[active]))
+        s.step_host(U, V, None, t, w.t_end, 1)
+    el = time.perf_counter() - t0
+    s.close()
+    b = (U.numel() + V.numel()) * U.element_size() + t.numel() * 8
+    return {"value": round(pts / el / 1e6, 3), "unit": "Mpoint-updates/s",
+            "h2d_bytes_per_step": b, "d2h_bytes_per_step": b, "steps": K}
+
+
+def cpu_baseline(w, budget_s=12.0, sample=128):
+    """The oracle as it stands, single-threaded on the host, on a bounded
+    sample: one SSP-RK3 step of the first `sample` instances, repeated until
+    `budget_s` seconds have passed."""
+    import oracle as O
+    bcs = {"outflow": O.BC_OUTFLOW, "periodic": O.BC_PERIODIC}
+    probs = [O.problem(O.EQ_EULER, 1, w.nx[k], 1, w.x0, w.x1, gas_gamma=w.gas_gamma,
+                       bc=(bcs[w.bc[0]], bcs[w.bc[1]])) for k in range(sample)]
+    states = [w.instance(k) for k in range(sample)]
+    O.step(probs[0], states[0][0], states[0][1], None, 0.0, w.t_end)  # load + warm
+    pts, t0 = 0, time.perf_counter()
+    while True:
+        for k in range(sample):
+            O.step(probs[k], states[k][0], states[k][1], None, 0.0, w.t_end)
+            pts += w.nx[k]
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(pts / el / 1e6, 5), "unit": "Mpoint-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "one SSP-RK3 step of the first %d instances (%d points), repeated for "
+                      "%.1f s, single thread" % (sample, sum(w.nx[:sample]), el)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2207_05258_gb300 import workloads as W
+    import oracle as O
+    w = W.riemann_batch(count=args.instances, seed=rank_seed(0))
+    sample = 32
+    bcs = {"outflow": O.BC_OUTFLOW}
+    probs = [O.problem(O.EQ_EULER, 1, w.nx[k], 1, w.x0, w.x1, gas_gamma=w.gas_gamma,
+                       bc=(bcs[w.bc[0]], bcs[w.bc[1]])) for k in range(sample)]
+    st = [[*w.instance(k), 0.0] for k in range(sample)]
+
+    def one_step():
+        n = 0
+        for k in range(sample):
+            U, V, _, tk, _ = O.step(probs[k], st[k][0], st[k][1], None, st[k][2], w.t_end)
+            st[k] = [U, V, tk]
+            n += w.nx[k]
+        return n
+
+    for _ in range(args.warmup):
+        one_step()
+    pts, t0 = 0, time.perf_counter()
+    for _ in range(args.steps):
+        pts += one_step()
+    el = time.perf_counter() - t0
+    v = pts / el / 1e6
+    pts_sample = sum(w.nx[:sample])
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 5),
+            "unit": "Mpoint-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "riemann_batch: first %d of %d 1D Euler Riemann problems "
+                                   "(%d points) per step" % (sample, w.batch, pts_sample),
+                       "instances": sample, "points": pts_sample, "precision": "fp64"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(v, 5),
+                             "unit": "Mpoint-updates/s",
+                             "sample": "one SSP-RK3 step of the first %d instances per timed step"
+                                       % sample},
+            "e2e": {"value": round(v, 5), "unit": "Mpoint-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    out, rank = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * hweno.h - C ABI of the GB300 (sm_103a) L-HWENO library.
+ *
+ * The library advances u_t + f(u)_x (+ g(u)_y) = 0 together with its
+ * derivative equations v = u_x (and w = u_y) by the fifth-order
+ * finite-difference HWENO scheme with limiter of Zhang & Zhao,
+ * arXiv:2207.05258 (Sec. 2): global Lax-Friedrichs flux splitting, the
+ * nonlinear HWENO reconstruction of the governing-equation flux (one quintic
+ * and two quadratics, Sec. 2.1; characteristic-wise for Euler, remarks of
+ * Sec. 2.1 and 2.2), the linear p_0' fluxes of the derivative equations, the
+ * central mixed-derivative fluxes (Eq. mixed), the HWENO limiter that
+ * modifies the derivatives used only in time stepping (Sec. 2.2) and the
+ * SSP-RK3 stages of the fully discrete scheme.
+ *
+ * Conventions for every call:
+ *  - Arrays named U, V, W, dU, ... are DEVICE pointers owned by the caller,
+ *    laid out [instance][component][j][i] with i contiguous, interior points
+ *    only (ghost values are produced inside the library from the boundary
+ *    conditions). Elements are double (HWENO_FP64) or float (HWENO_FP32) as
+ *    chosen at create time. Components: Burgers m = 1 (u); Euler 1D m = 3
+ *    (rho, rho u, E); Euler 2D m = 4 (rho, rho u, rho v, E). Instance k of a
+ *    1D batch starts at element m * sum_{l<k} nx[l]. V is u_x, W is u_y (2D).
+ *  - Times t are DEVICE arrays of `batch` doubles (one time per instance).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy stream); all
+ *    work is enqueued on it and the calls return without synchronising,
+ *    except hweno_sync_status and hweno_step_host.
+ *  - The library allocates all of its scratch (stage buffers, the stored
+ *    limited derivative, per-instance wave speeds and time steps, a status
+ *    word) in hweno_create and frees it in hweno_destroy; no other call
+ *    allocates device memory.
+ *  - Every call returns an int status: HWENO_OK (0) or a negative code; a
+ *    readable message is kept in the context (hweno_last_error). Errors the
+ *    device detects (a non-finite wave speed) are latched into the context's
+ *    device status word and returned by hweno_sync_status (which
+ *    hweno_step_host calls). No call aborts the process or throws across the
+ *    ABI.
+ */
+#ifndef HWENO_H
+#define HWENO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define HWENO_OK 0
+#define HWENO_EINVAL (-1)     /* invalid argument: grid, BC, option, pointer */
+#define HWENO_ENOMEM (-2)     /* device or host allocation failed */
+#define HWENO_ECUDA (-3)      /* a CUDA runtime call failed */
+#define HWENO_ENONFINITE (-4) /* a wave speed (alpha) became NaN or Inf */
+#define HWENO_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define HWENO_ENOTSUP (-6)    /* not implemented for this configuration */
+
+/* Equations (Sec. 3: Burgers, Eq. 1dbugers / 2dbugers; Euler, Eq. euler1 /
+ * euler2 with E = p/(gamma-1) + rho |u|^2 / 2). */
+#define HWENO_BURGERS 0
+#define HWENO_EULER 1
+
+/* Precision of state arrays and of the reconstruction arithmetic. Wave
+ * speeds, time steps and times are always FP64. */
+#define HWENO_FP64 0
+#define HWENO_FP32 1
+
+/* Boundary conditions (Sec. 3). Ghost derivatives: periodic wraps; outflow
+ * copies U and its derivatives; reflective mirrors U with the normal momentum
+ * odd (Burgers: u odd), the normal derivative of opposite parity and the
+ * tangential one of the same parity; imposed states carry zero derivatives.
+ * HWENO_BC_DMR_BOTTOM (y-low only): imposed state `inflow` for x < dmr_x0,
+ * reflective wall beyond; HWENO_BC_DMR_TOP (y-high only): `inflow` left of the
+ * exact shock position x_s(y, t) = dmr_x0 + y / tan(dmr_angle)
+ * + dmr_speed t / sin(dmr_angle), `pre` right of it (Example 3.11). */
+#define HWENO_BC_PERIODIC 0
+#define HWENO_BC_OUTFLOW 1
+#define HWENO_BC_REFLECTIVE 2
+#define HWENO_BC_INFLOW 3
+#define HWENO_BC_DMR_BOTTOM 4
+#define HWENO_BC_DMR_TOP 5
+
+typedef struct hweno_bc {
+  int xlo, xhi, ylo, yhi; /* HWENO_BC_* per side (y sides ignored in 1D) */
+  double inflow[4];       /* imposed conserved state (inflow, DMR post-shock) */
+  double pre[4];          /* DMR pre-shock conserved state */
+  double dmr_x0;          /* DMR: x where the shock meets y = 0 at t = 0 */
+  double dmr_speed;       /* DMR: normal speed of the shock */
+  double dmr_angle;       /* DMR: angle of the shock to the x axis, radians */
+} hweno_bc;
+
+/* Uniform cell-centred grid (Sec. 2.1: x_i the centre of I_i,
+ * dx = (x1 - x0) / nx). A 1D batch holds `batch` independent instances on
+ * the same [x0, x1] with nx_per_instance[k] points each (host array, read
+ * only during hweno_create; NULL means nx for all). 2D requires batch = 1.
+ * Every nx, ny must be >= 4. */
+typedef struct hweno_grid {
+  int dim;                    /* 1 or 2 */
+  int nx, ny;                 /* points per direction (ny ignored in 1D) */
+  double x0, x1, y0, y1;      /* domain */
+  int batch;                  /* number of instances, >= 1 */
+  const int* nx_per_instance; /* host, [batch], or NULL */
+  int precision;              /* HWENO_FP64 or HWENO_FP32 */
+} hweno_grid;
+
+/* Scheme options. hweno_default_options fills the paper's values (Sec. 3):
+ * lin_w = lim_d = {0.98, 0.01, 0.01}, eps = 1e-6, cfl = 0.6,
+ * dt_mode = 0, limiter = 1, eig_avg = 0. */
+typedef struct hweno_options {
+  double lin_w[3]; /* gamma_0..2 of the reconstruction: > 0, sum 1 (Sec. 2.1) */
+  double lim_d[3]; /* d_0..2 of the limiter: > 0, sum 1 (Sec. 2.2) */
+  double eps;      /* epsilon of the nonlinear weights, > 0 */
+  double cfl;      /* CFL number, > 0 */
+  int dt_mode;     /* 0: dt = cfl / sum(alpha_d / h_d) with h = dx;
+                      1: h = dx^{5/3} (accuracy runs); 2: dt = dt_fixed.
+                      The last step of a run is clipped to land on t_end. */
+  double dt_fixed;
+  int limiter;     /* 0: off; 1: on characteristic variables (eigenvectors at
+                      U_i of the sweep direction); 2: component-wise */
+  int eig_avg;     /* eigenvectors at x_{i+1/2}: 0 Roe average of U_i, U_{i+1};
+                      1 arithmetic mean */
+} hweno_options;
+
+typedef struct hweno_ctx hweno_ctx; /* opaque, library-owned */
+
+/* Fill *opt with the paper's defaults (Sec. 3). */
+int hweno_default_options(hweno_options* opt);
+
+/* Create a solver for `equation` (HWENO_BURGERS / HWENO_EULER) on `grid`
+ * with ratio of specific heats `gamma` (Euler; ignored for Burgers) and
+ * boundary conditions `bc` (the problem statement of Sec. 2.1 and Sec. 3).
+ * Allocates all device scratch on the current device. On success *out holds
+ * the context and HWENO_OK is returned; on failure *out is NULL and the code
+ * says why: HWENO_EINVAL for an invalid grid, equation, gamma or boundary
+ * set (nx, ny < 4; batch < 1; 2D with batch > 1; periodic on one side only;
+ * DMR kinds outside y-low/y-high or with Burgers), HWENO_ENOMEM / HWENO_ECUDA
+ * for allocation or runtime failures. Options start at hweno_default_options. */
+int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double gamma,
+                 const hweno_bc* bc);
+
+/* Replace the scheme options (validated; HWENO_EINVAL leaves them unchanged). */
+int hweno_set_options(hweno_ctx* ctx, const hweno_options* opt);
+
+/* Spatial operator of one stage (Eq. odeH in 1D, Eq. ode2H in 2D):
+ * dU = L^1(U, V[, W]), dV = L^2, dW = L^3 (2D), each -(flux difference)/h,
+ * with alpha the maximum of |f'(u)| (Euler: |u| + c per direction) over each
+ * instance's grid and boundary data at time t[k]. Vlim / Wlim (nullable)
+ * receive the limited derivatives of Sec. 2.2. W, dW, Wlim must be NULL in
+ * 1D. All array arguments are device pointers of the state's size. */
+int hweno_rhs(hweno_ctx* ctx, const void* U, const void* V, const void* W, void* dU,
+              void* dV, void* dW, void* Vlim, void* Wlim, const double* t, void* stream);
+
+/* One SSP-RK3 step of the fully discrete scheme (Sec. 2.2) in place on
+ * U, V (, W): stage k evaluates L at the unlimited stage state and combines
+ * with the limited derivatives. dt per instance from the wave speed of U^n
+ * (dt_mode), clipped so that t lands on t_end; instances with t >= t_end
+ * are left unchanged. t (device, [batch]) is advanced; dt_used (device,
+ * [batch], nullable) receives each instance's dt (0 when inactive). */
+int hweno_step(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
+               double* dt_used, void* stream);
+
+/* As hweno_step with HOST arrays: copies U, V (, W) and t (host, [batch]) to
+ * library-owned device buffers, takes `nsteps` steps, copies them back and
+ * synchronises the stream. Pinned host memory makes the copies asynchronous. */
+int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
+                    int nsteps, void* stream);
+
+/* Discrete adjoint of hweno_step (reverse of the three stages with the
+ * wave speed, time step and weight branches frozen). Not built yet:
+ * returns HWENO_ENOTSUP. */
+int hweno_adjoint_step(hweno_ctx* ctx, const void* U, const void* V, const void* W,
+                       double dt, void* lamU, void* lamV, void* lamW, void* stream);
+
+/* Synchronise `stream`, read the device status word and return the latched
+ * device error (HWENO_OK if none); clears the latch. */
+int hweno_sync_status(hweno_ctx* ctx, void* stream);
+
+/* Number of grid points summed over instances (-1 for a NULL context). */
+long long hweno_num_points(const hweno_ctx* ctx);
+
+/* Number of instances with t < t_end after the last hweno_step enqueued on
+ * `stream` (synchronises the stream; negative on error). */
+int hweno_active_instances(hweno_ctx* ctx, void* stream);
+
+/* Kernel launches enqueued by the most recent hweno_step / hweno_rhs call. */
+int hweno_launches_last_call(const hweno_ctx* ctx);
+
+/* Kernel timing for measurement. hweno_profile_start(ctx, capacity) makes the
+ * following hweno_step / hweno_rhs calls bracket each kernel launch with CUDA
+ * events on the call's stream, for up to `capacity` launches (0 stops it).
+ * hweno_profile_read synchronises `stream` and writes, per kernel kind
+ * (0: wave-speed reduction, 1: fused stage, 2: step finalisation), the summed
+ * device time in milliseconds ms[3] and the launch count n[3] recorded since
+ * the start; it then clears the record. Events are host-side objects created
+ * in hweno_profile_start; no device memory is allocated. */
+int hweno_profile_start(hweno_ctx* ctx, int capacity);
+int hweno_profile_read(hweno_ctx* ctx, double* ms, int* n, void* stream);
+
+/* Message describing the last error on this context ("" if none). */
+const char* hweno_last_error(const hweno_ctx* ctx);
+
+/* Free all device and host resources of the context (NULL is a no-op). */
+int hweno_destroy(hweno_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWENO_H */

@@ -127,6 +127,13 @@ struct Face {
   R beta[3], tau, omega[3];
 };
 
+// p_0'(x_{i+1/2}) of the quintic on T0 (Sec. 2.1): the linear flux of the
+// derivative equation.
+template <class R>
+R p0_prime(const R f[3], const R h[3], double dx) {
+  return (f[0] - 8.0 * f[1] + 7.0 * f[2]) / (4.0 * dx) + (h[0] - 2.0 * h[1] - 5.0 * h[2]) / 12.0;
+}
+
 template <class R>
 Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
                    double eps) {
@@ -139,8 +146,7 @@ Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
            (dx / 20.0) * (hm + 10.0 * h0 - hp);
   o.p[1] = (1.0 / 6.0) * fm + (5.0 / 6.0) * f0 + (2.0 / 3.0) * dx * h0;
   o.p[2] = (5.0 / 6.0) * f0 + (1.0 / 6.0) * fp + (1.0 / 3.0) * dx * h0;
-  o.dp0 = (fm - 8.0 * f0 + 7.0 * fp) / (4.0 * dx) +
-          (hm - 2.0 * h0 - 5.0 * hp) / 12.0;
+  o.dp0 = p0_prime(f, h, dx);
 
   // a_1..a_5 and the smoothness indicators (Eq. GHYZP).
   const R a1 = dx * ((19.0 / 192.0) * hm + (79.0 / 48.0) * h0 + (19.0 / 192.0) * hp) +
@@ -471,14 +477,14 @@ void sweep_line(const or_problem& P, int dir, int n, double dx, R alpha,
         fchar[s] = a.fhat + b.fhat;
       }
       matvec(m, Rm, fchar, fh);
-      // derivative flux: linear p_0', component by component
+      // derivative flux: linear p_0', component by component; the "-" side
+      // is the mirror image (reversed stencil, negated h, negated result)
       for (int c = 0; c < m; ++c) {
         const R f3p[3] = {fp[c][gi - 1], fp[c][gi], fp[c][gi + 1]};
         const R h3p[3] = {hp[c][gi - 1], hp[c][gi], hp[c][gi + 1]};
-        const R f3m[3] = {fmn[c][gi], fmn[c][gi + 1], fmn[c][gi + 2]};
-        const R h3m[3] = {hmn[c][gi], hmn[c][gi + 1], hmn[c][gi + 2]};
-        hh[c] = hweno_plus(f3p, h3p, dx, gw, P.eps).hhat +
-                hweno_minus(f3m, h3m, dx, gw, P.eps).hhat;
+        const R f3r[3] = {fmn[c][gi + 2], fmn[c][gi + 1], fmn[c][gi]};
+        const R h3r[3] = {-hmn[c][gi + 2], -hmn[c][gi + 1], -hmn[c][gi]};
+        hh[c] = p0_prime(f3p, h3p, dx) + (-p0_prime(f3r, h3r, dx));
       }
     }
     for (int c = 0; c < m; ++c) { fhat[c][j] = fh[c]; hhat[c][j] = hh[c]; }

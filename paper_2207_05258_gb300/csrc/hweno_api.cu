@@ -1,0 +1,517 @@
+// Host side of the C ABI declared in include/hweno.h: argument checking,
+// ownership of all device scratch, the tile tables of ragged batches, and the
+// launch sequence of one SSP-RK3 step (Sec. 2.2 of Zhang & Zhao,
+// arXiv:2207.05258):
+//
+//   memset(alpha slots, active counter)
+//   alpha(U^n)                         -> slot 0            (per instance)
+//   stage 1: U^n, V^n    -> U1, V1, V~^n;  alpha(U1) -> slot 1; dt from slot 0
+//   stage 2: U1, V1      -> U2, V2;        alpha(U2) -> slot 2
+//   stage 3: U2, V2      -> U^{n+1}, V^{n+1} (in place; reads U^n, V~^n pointwise)
+//   finalize: t += dt (landing exactly on t_end), active count, status
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hweno.h"
+#include "internal.h"
+
+using namespace hweno;
+
+struct hweno_ctx {
+  int eq = 0, dim = 1, m = 1, batch = 1;
+  bool fp32 = false;
+  std::vector<int> nx;
+  int ny = 1;
+  double x0 = 0, x1 = 1, y0 = 0, y1 = 1, gamma = 1.4;
+  hweno_bc bc{};
+  hweno_options opt{};
+  long long npts = 0;
+  size_t elems = 0, esize = 8;
+  // 1D batch tables
+  int ntiles = 0;
+  int* d_tile_inst = nullptr;
+  int* d_tile_start = nullptr;
+  int* d_inst_n = nullptr;
+  long long* d_inst_off = nullptr;
+  double* d_inst_dx = nullptr;
+  double* d_inst_hx = nullptr;
+  std::vector<double> inst_dx;
+  // per-instance scalars
+  unsigned long long* d_alpha = nullptr;  // 3 slots x batch (x 2 directions in 2D)
+  double* d_dt = nullptr;
+  int* d_lands = nullptr;
+  int* d_active = nullptr;
+  unsigned* d_status = nullptr;
+  // stage scratch
+  void* d_U1 = nullptr; void* d_V1 = nullptr; void* d_W1 = nullptr;
+  void* d_U2 = nullptr; void* d_V2 = nullptr; void* d_W2 = nullptr;
+  void* d_Vt0 = nullptr; void* d_Wt0 = nullptr;
+  // device copies for the host-buffer entry point
+  void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
+  double* d_ht = nullptr;
+  int launches = 0;
+  // kernel timing (hweno_profile_start / hweno_profile_read)
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  int ev_used = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(hweno_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(hweno_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, HWENO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool weights_ok(const double* w) {
+  return w[0] > 0 && w[1] > 0 && w[2] > 0 && std::fabs(w[0] + w[1] + w[2] - 1.0) <= 1e-12;
+}
+
+int check_options(const hweno_options* o, std::string& why) {
+  if (!weights_ok(o->lin_w)) { why = "lin_w must be positive and sum to 1"; return HWENO_EINVAL; }
+  if (!weights_ok(o->lim_d)) { why = "lim_d must be positive and sum to 1"; return HWENO_EINVAL; }
+  if (!(o->eps > 0)) { why = "eps must be > 0"; return HWENO_EINVAL; }
+  if (!(o->cfl > 0)) { why = "cfl must be > 0"; return HWENO_EINVAL; }
+  if (o->dt_mode < 0 || o->dt_mode > 2) { why = "dt_mode must be 0, 1 or 2"; return HWENO_EINVAL; }
+  if (o->dt_mode == 2 && !(o->dt_fixed > 0)) { why = "dt_fixed must be > 0"; return HWENO_EINVAL; }
+  if (o->limiter < 0 || o->limiter > 2) { why = "limiter must be 0, 1 or 2"; return HWENO_EINVAL; }
+  if (o->eig_avg < 0 || o->eig_avg > 1) { why = "eig_avg must be 0 or 1"; return HWENO_EINVAL; }
+  return HWENO_OK;
+}
+
+bool bc_ok_1d(int b) { return b >= HWENO_BC_PERIODIC && b <= HWENO_BC_INFLOW; }
+
+template <class T>
+int dalloc(hweno_ctx* c, T** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, e == cudaErrorMemoryAllocation ? HWENO_ENOMEM : HWENO_ECUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return HWENO_OK;
+}
+
+void free_all(hweno_ctx* c) {
+  void* ptrs[] = {c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
+                  c->d_inst_hx, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
+                  c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
+                  c->d_hU, c->d_hV, c->d_hW, c->d_ht};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+SchemeParams scheme_params(const hweno_ctx* c) {
+  SchemeParams sp{};
+  for (int i = 0; i < 3; ++i) { sp.lin_w[i] = c->opt.lin_w[i]; sp.lim_d[i] = c->opt.lim_d[i]; }
+  sp.eps = c->opt.eps;
+  sp.cfl = c->opt.cfl;
+  sp.dt_fixed = c->opt.dt_fixed;
+  sp.dt_mode = c->opt.dt_mode;
+  sp.limiter = c->opt.limiter;
+  sp.eig_avg = c->opt.eig_avg;
+  sp.gas_gamma = c->gamma;
+  sp.bc[0] = c->bc.xlo; sp.bc[1] = c->bc.xhi; sp.bc[2] = c->bc.ylo; sp.bc[3] = c->bc.yhi;
+  for (int i = 0; i < 4; ++i) { sp.inflow[i] = c->bc.inflow[i]; sp.pre[i] = c->bc.pre[i]; }
+  sp.dmr_x0 = c->bc.dmr_x0;
+  sp.dmr_speed = c->bc.dmr_speed;
+  sp.dmr_angle = c->bc.dmr_angle;
+  return sp;
+}
+
+// Per-instance h of the time-step rule (dx, or dx^{5/3} for dt_mode 1).
+int upload_hx(hweno_ctx* c) {
+  std::vector<double> hx(c->batch);
+  for (int k = 0; k < c->batch; ++k)
+    hx[k] = c->opt.dt_mode == 1 ? std::pow(c->inst_dx[k], 5.0 / 3.0) : c->inst_dx[k];
+  const cudaError_t e = cudaMemcpy(c->d_inst_hx, hx.data(), sizeof(double) * c->batch,
+                                   cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? HWENO_OK : cuda_fail(c, e, "upload hx");
+}
+
+Args1D base_args_1d(const hweno_ctx* c) {
+  Args1D a{};
+  a.tile_inst = c->d_tile_inst;
+  a.tile_start = c->d_tile_start;
+  a.inst_n = c->d_inst_n;
+  a.inst_off = c->d_inst_off;
+  a.inst_dx = c->d_inst_dx;
+  a.inst_hx = c->d_inst_hx;
+  a.status = c->d_status;
+  a.sp = scheme_params(c);
+  return a;
+}
+
+// Event bracket around one launch when profiling is on (kind 0 alpha, 1 stage,
+// 2 finalize).
+void prof_begin(hweno_ctx* c, cudaStream_t s) {
+  if (c->ev_used + 2 <= (int)c->ev.size()) cudaEventRecord(c->ev[c->ev_used], s);
+}
+void prof_end(hweno_ctx* c, cudaStream_t s, int kind) {
+  if (c->ev_used + 2 <= (int)c->ev.size()) {
+    cudaEventRecord(c->ev[c->ev_used + 1], s);
+    c->ev_kind[c->ev_used / 2] = kind;
+    c->ev_used += 2;
+  }
+}
+
+void destroy_events(hweno_ctx* c) {
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  c->ev_kind.clear();
+  c->ev_used = 0;
+}
+
+unsigned long long* slot(hweno_ctx* c, int k) { return c->d_alpha + (size_t)k * c->batch; }
+const double* slotd(hweno_ctx* c, int k) {
+  return reinterpret_cast<const double*>(c->d_alpha + (size_t)k * c->batch);
+}
+
+int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_used,
+            cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)) ||
+      (e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)))
+    return cuda_fail(c, e, "memset");
+  Args1D a = base_args_1d(c);
+  a.t = t;
+  a.t_end = t_end;
+  a.skip_done = 1;
+  a.dt = c->d_dt;
+  a.lands = c->d_lands;
+  // alpha(U^n)
+  a.U = U;
+  a.alpha_out = slot(c, 0);
+  prof_begin(c, s);
+  if ((e = launch_alpha_1d(c->eq, c->fp32, a, c->ntiles, s))) return cuda_fail(c, e, "alpha");
+  prof_end(c, s, 0);
+  // stage 1
+  a.U = U; a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
+  a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
+  prof_begin(c, s);
+  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_STAGE1, a, c->ntiles, s)))
+    return cuda_fail(c, e, "stage 1");
+  prof_end(c, s, 1);
+  // stage 2
+  a.U = c->d_U1; a.V = c->d_V1; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = c->d_U2; a.Vout = c->d_V2;
+  a.Vt0out = nullptr;
+  a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
+  prof_begin(c, s);
+  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_STAGE2, a, c->ntiles, s)))
+    return cuda_fail(c, e, "stage 2");
+  prof_end(c, s, 1);
+  // stage 3 (in place)
+  a.U = c->d_U2; a.V = c->d_V2; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = U; a.Vout = V;
+  a.alpha_in = slotd(c, 2); a.alpha_out = nullptr;
+  prof_begin(c, s);
+  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_STAGE3, a, c->ntiles, s)))
+    return cuda_fail(c, e, "stage 3");
+  prof_end(c, s, 1);
+  prof_begin(c, s);
+  if ((e = launch_finalize(c->batch, c->d_dt, c->d_lands, t, t_end, dt_used, slotd(c, 0),
+                           c->d_active, c->d_status, s)))
+    return cuda_fail(c, e, "finalize");
+  prof_end(c, s, 2);
+  c->launches = 5;
+  return HWENO_OK;
+}
+
+int rhs_1d(hweno_ctx* c, const void* U, const void* V, void* dU, void* dV, void* Vlim,
+           const double* t, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * c->batch, s)))
+    return cuda_fail(c, e, "memset");
+  Args1D a = base_args_1d(c);
+  a.t = t;
+  a.t_end = 0.0;
+  a.skip_done = 0;
+  a.U = U;
+  a.alpha_out = slot(c, 0);
+  prof_begin(c, s);
+  if ((e = launch_alpha_1d(c->eq, c->fp32, a, c->ntiles, s))) return cuda_fail(c, e, "alpha");
+  prof_end(c, s, 0);
+  a.V = V; a.L1 = dU; a.L2 = dV; a.Vlim = Vlim;
+  a.alpha_in = slotd(c, 0); a.alpha_out = nullptr;
+  prof_begin(c, s);
+  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_RHS, a, c->ntiles, s)))
+    return cuda_fail(c, e, "rhs");
+  prof_end(c, s, 1);
+  c->launches = 2;
+  return HWENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hweno_default_options(hweno_options* o) {
+  if (!o) return HWENO_EINVAL;
+  std::memset(o, 0, sizeof *o);
+  o->lin_w[0] = 0.98; o->lin_w[1] = 0.01; o->lin_w[2] = 0.01;
+  o->lim_d[0] = 0.98; o->lim_d[1] = 0.01; o->lim_d[2] = 0.01;
+  o->eps = 1e-6;
+  o->cfl = 0.6;
+  o->dt_mode = 0;
+  o->dt_fixed = 0.0;
+  o->limiter = 1;
+  o->eig_avg = 0;
+  return HWENO_OK;
+}
+
+int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double gamma,
+                 const hweno_bc* bc) {
+  if (!out) return HWENO_EINVAL;
+  *out = nullptr;
+  if (!grid || !bc) return HWENO_EINVAL;
+  hweno_ctx* c = new (std::nothrow) hweno_ctx();
+  if (!c) return HWENO_ENOMEM;
+  auto bad = [&](const char* why) {
+    delete c;
+    (void)why;
+    return HWENO_EINVAL;
+  };
+  if (equation != HWENO_BURGERS && equation != HWENO_EULER) return bad("equation");
+  if (grid->dim != 1 && grid->dim != 2) return bad("dim");
+  if (grid->precision != HWENO_FP64 && grid->precision != HWENO_FP32) return bad("precision");
+  if (!(grid->x1 > grid->x0)) return bad("x range");
+  if (grid->batch < 1) return bad("batch");
+  if (grid->dim == 2 && (grid->batch != 1 || !(grid->y1 > grid->y0) || grid->ny < 4))
+    return bad("2D grid");
+  if (equation == HWENO_EULER && !(gamma > 1.0)) return bad("gamma");
+  c->eq = equation;
+  c->dim = grid->dim;
+  c->m = equation == HWENO_BURGERS ? 1 : (grid->dim == 1 ? 3 : 4);
+  c->batch = grid->batch;
+  c->fp32 = grid->precision == HWENO_FP32;
+  c->esize = c->fp32 ? 4 : 8;
+  c->ny = grid->dim == 2 ? grid->ny : 1;
+  c->x0 = grid->x0; c->x1 = grid->x1; c->y0 = grid->y0; c->y1 = grid->y1;
+  c->gamma = gamma;
+  c->bc = *bc;
+  hweno_default_options(&c->opt);
+  c->nx.resize(c->batch);
+  for (int k = 0; k < c->batch; ++k) {
+    c->nx[k] = grid->nx_per_instance ? grid->nx_per_instance[k] : grid->nx;
+    if (c->nx[k] < 4) return bad("nx < 4");
+  }
+  // boundary conditions
+  const int sides[4] = {bc->xlo, bc->xhi, bc->ylo, bc->yhi};
+  if (grid->dim == 1) {
+    if (!bc_ok_1d(bc->xlo) || !bc_ok_1d(bc->xhi)) return bad("bc");
+    if ((bc->xlo == HWENO_BC_PERIODIC) != (bc->xhi == HWENO_BC_PERIODIC)) return bad("periodic");
+  } else {
+    for (int i = 0; i < 4; ++i)
+      if (sides[i] < HWENO_BC_PERIODIC || sides[i] > HWENO_BC_DMR_TOP) return bad("bc");
+    if (bc->xlo >= HWENO_BC_DMR_BOTTOM || bc->xhi >= HWENO_BC_DMR_BOTTOM) return bad("bc x");
+    if (bc->ylo == HWENO_BC_DMR_TOP || bc->yhi == HWENO_BC_DMR_BOTTOM) return bad("bc dmr side");
+    if ((bc->xlo == HWENO_BC_PERIODIC) != (bc->xhi == HWENO_BC_PERIODIC)) return bad("periodic x");
+    if ((bc->ylo == HWENO_BC_PERIODIC) != (bc->yhi == HWENO_BC_PERIODIC)) return bad("periodic y");
+    if ((bc->ylo == HWENO_BC_DMR_BOTTOM || bc->yhi == HWENO_BC_DMR_TOP) &&
+        (equation != HWENO_EULER || !(std::sin(bc->dmr_angle) > 0) || !(std::tan(bc->dmr_angle) > 0)))
+      return bad("dmr");
+  }
+  if (grid->dim == 2) {
+    delete c;
+    return HWENO_ENOTSUP;
+  }
+
+  // sizes and tile tables
+  std::vector<int> tinst, tstart;
+  std::vector<long long> off(c->batch);
+  c->inst_dx.resize(c->batch);
+  long long acc = 0;
+  for (int k = 0; k < c->batch; ++k) {
+    off[k] = acc;
+    acc += c->nx[k];
+    c->inst_dx[k] = (c->x1 - c->x0) / c->nx[k];
+    for (int s = 0; s < c->nx[k]; s += kTile1D) { tinst.push_back(k); tstart.push_back(s); }
+  }
+  c->npts = acc;
+  c->elems = (size_t)c->m * (size_t)acc;
+  c->ntiles = (int)tinst.size();
+
+  int rc = HWENO_OK;
+  const size_t fb = c->elems * c->esize;
+  const size_t B = (size_t)c->batch;
+  if ((rc = dalloc(c, &c->d_tile_inst, sizeof(int) * tinst.size())) ||
+      (rc = dalloc(c, &c->d_tile_start, sizeof(int) * tstart.size())) ||
+      (rc = dalloc(c, &c->d_inst_n, sizeof(int) * B)) ||
+      (rc = dalloc(c, &c->d_inst_off, sizeof(long long) * B)) ||
+      (rc = dalloc(c, &c->d_inst_dx, sizeof(double) * B)) ||
+      (rc = dalloc(c, &c->d_inst_hx, sizeof(double) * B)) ||
+      (rc = dalloc(c, &c->d_alpha, sizeof(unsigned long long) * 3 * B * 2)) ||
+      (rc = dalloc(c, &c->d_dt, sizeof(double) * B)) ||
+      (rc = dalloc(c, &c->d_lands, sizeof(int) * B)) ||
+      (rc = dalloc(c, &c->d_active, sizeof(int))) ||
+      (rc = dalloc(c, &c->d_status, sizeof(unsigned))) ||
+      (rc = dalloc(c, &c->d_U1, fb)) || (rc = dalloc(c, &c->d_V1, fb)) ||
+      (rc = dalloc(c, &c->d_U2, fb)) || (rc = dalloc(c, &c->d_V2, fb)) ||
+      (rc = dalloc(c, &c->d_Vt0, fb)) || (rc = dalloc(c, &c->d_hU, fb)) ||
+      (rc = dalloc(c, &c->d_hV, fb)) || (rc = dalloc(c, &c->d_ht, sizeof(double) * B))) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  const bool copy_failed =
+      cudaMemcpy(c->d_tile_inst, tinst.data(), sizeof(int) * tinst.size(), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_tile_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_inst_n, c->nx.data(), sizeof(int) * B, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_inst_off, off.data(), sizeof(long long) * B, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_inst_dx, c->inst_dx.data(), sizeof(double) * B, cudaMemcpyHostToDevice) ||
+      cudaMemset(c->d_status, 0, sizeof(unsigned));
+  if (copy_failed) {
+    free_all(c);
+    delete c;
+    return HWENO_ECUDA;
+  }
+  if ((rc = upload_hx(c)) != HWENO_OK) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return HWENO_OK;
+}
+
+int hweno_set_options(hweno_ctx* c, const hweno_options* o) {
+  if (!c || !o) return HWENO_EINVAL;
+  std::string why;
+  if (check_options(o, why) != HWENO_OK) return fail(c, HWENO_EINVAL, why);
+  const hweno_options old = c->opt;
+  c->opt = *o;
+  const int rc = upload_hx(c);
+  if (rc != HWENO_OK) c->opt = old;
+  return rc;
+}
+
+int hweno_rhs(hweno_ctx* c, const void* U, const void* V, const void* W, void* dU, void* dV,
+              void* dW, void* Vlim, void* Wlim, const double* t, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!U || !V || !dU || !dV || !t) return fail(c, HWENO_EINVAL, "null array");
+  if (c->dim == 1 && (W || dW || Wlim)) return fail(c, HWENO_EINVAL, "W given in 1D");
+  c->err.clear();
+  return rhs_1d(c, U, V, dU, dV, Vlim, t, static_cast<cudaStream_t>(stream));
+}
+
+int hweno_step(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
+               double* dt_used, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!U || !V || !t) return fail(c, HWENO_EINVAL, "null array");
+  if (c->dim == 1 && W) return fail(c, HWENO_EINVAL, "W given in 1D");
+  if (!std::isfinite(t_end)) return fail(c, HWENO_EINVAL, "t_end not finite");
+  c->err.clear();
+  return step_1d(c, U, V, t, t_end, dt_used, static_cast<cudaStream_t>(stream));
+}
+
+int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
+                    int nsteps, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!U || !V || !t || nsteps < 0) return fail(c, HWENO_EINVAL, "bad argument");
+  if (c->dim == 1 && W) return fail(c, HWENO_EINVAL, "W given in 1D");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t fb = c->elems * c->esize, tb = sizeof(double) * c->batch;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->d_hU, U, fb, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(c->d_hV, V, fb, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(c->d_ht, t, tb, cudaMemcpyHostToDevice, s)))
+    return cuda_fail(c, e, "copy in");
+  for (int i = 0; i < nsteps; ++i) {
+    const int rc = hweno_step(c, c->d_hU, c->d_hV, nullptr, c->d_ht, t_end, nullptr, stream);
+    if (rc != HWENO_OK) return rc;
+  }
+  if ((e = cudaMemcpyAsync(U, c->d_hU, fb, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(V, c->d_hV, fb, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(t, c->d_ht, tb, cudaMemcpyDeviceToHost, s)))
+    return cuda_fail(c, e, "copy out");
+  return hweno_sync_status(c, stream);
+}
+
+int hweno_adjoint_step(hweno_ctx* c, const void*, const void*, const void*, double, void*, void*,
+                       void*, void*) {
+  if (!c) return HWENO_EINVAL;
+  return fail(c, HWENO_ENOTSUP, "adjoint step not built");
+}
+
+int hweno_sync_status(hweno_ctx* c, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  unsigned st = 0;
+  if ((e = cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost)))
+    return cuda_fail(c, e, "read status");
+  if (st) {
+    cudaMemset(c->d_status, 0, sizeof(unsigned));
+    if (st & STATUS_NONFINITE) return fail(c, HWENO_ENONFINITE, "non-finite wave speed");
+  }
+  return HWENO_OK;
+}
+
+long long hweno_num_points(const hweno_ctx* c) { return c ? c->npts : -1; }
+
+int hweno_active_instances(hweno_ctx* c, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  int n = 0;
+  if ((e = cudaMemcpy(&n, c->d_active, sizeof n, cudaMemcpyDeviceToHost)))
+    return cuda_fail(c, e, "read active");
+  return n;
+}
+
+int hweno_launches_last_call(const hweno_ctx* c) { return c ? c->launches : -1; }
+
+int hweno_profile_start(hweno_ctx* c, int capacity) {
+  if (!c || capacity < 0) return HWENO_EINVAL;
+  destroy_events(c);
+  c->ev.resize(2 * (size_t)capacity);
+  c->ev_kind.assign(capacity, 0);
+  for (size_t i = 0; i < c->ev.size(); ++i) {
+    const cudaError_t e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+      c->ev.resize(i);
+      destroy_events(c);
+      return cuda_fail(c, e, "cudaEventCreate");
+    }
+  }
+  return HWENO_OK;
+}
+
+int hweno_profile_read(hweno_ctx* c, double* ms, int* n, void* stream) {
+  if (!c || !ms || !n) return HWENO_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  for (int k = 0; k < 3; ++k) { ms[k] = 0.0; n[k] = 0; }
+  for (int i = 0; i + 1 < c->ev_used; i += 2) {
+    float t = 0.f;
+    if ((e = cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1])) != cudaSuccess)
+      return cuda_fail(c, e, "cudaEventElapsedTime");
+    const int kind = c->ev_kind[i / 2];
+    ms[kind] += t;
+    n[kind] += 1;
+  }
+  c->ev_used = 0;
+  return HWENO_OK;
+}
+
+const char* hweno_last_error(const hweno_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int hweno_destroy(hweno_ctx* c) {
+  if (!c) return HWENO_OK;
+  destroy_events(c);
+  free_all(c);
+  delete c;
+  return HWENO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,222 @@
+// Device arithmetic of the L-HWENO scheme (Zhang & Zhao, arXiv:2207.05258).
+//
+// Formulation used on the GPU (same mathematics as the paper, arranged for an
+// FP64 pipe that is the bottleneck on sm_103a):
+//  * Derivative data enter pre-scaled by the mesh width: H = dx * h, so the
+//    reconstruction formulas of Sec. 2.1 and the limiter of Sec. 2.2 carry no
+//    dx; the derivative flux is returned as D = dx * p_0'(x_{i+1/2}).
+//  * The nonlinear weights w_l = g_l (1 + tau / (beta_l + eps)) / S are never
+//    formed one by one. In FP64 both sides of an interface are brought over
+//    the common denominator b_0 b_1 b_2 (b_l = beta_l + eps), which leaves one
+//    division per interface and field; in FP32 the per-side form with three
+//    divisions is kept because the products can exceed the float range.
+//  * The "-" flux at x_{i+1/2} is the mirror image of the "+" one: the "+"
+//    procedure applied to the stencil {i+2, i+1, i} with the derivative data
+//    negated, and the derivative flux negated back (Sec. 2.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <type_traits>
+
+namespace hweno {
+
+template <class Real>
+struct Weights {
+  Real g0, g1, g2;       // linear weights gamma_l (Sec. 2.1)
+  Real d0, d1, d2;       // limiter linear weights d_l (Sec. 2.2)
+  Real eps;
+  Real ig0, id0;         // 1/gamma_0, 1/d_0
+};
+
+// Quantities of one "+" reconstruction (Sec. 2.1) from f^+ and H = dx h^+ on
+// the stencil {i-1, i, i+1}: the three candidate values at x_{i+1/2}, the
+// smoothness indicators and the scaled derivative flux D = dx p_0'.
+template <class Real>
+struct Cand {
+  Real p0, p1, p2;
+  Real b0, b1, b2;  // beta_l + eps
+  Real tau;
+  Real D;
+};
+
+template <class Real>
+__device__ __forceinline__ Cand<Real> candidates(Real fm, Real f0, Real fp, Real Hm, Real H0,
+                                                 Real Hp, Real eps) {
+  Cand<Real> c;
+  const Real sHp = Hm + Hp, dHp = Hm - Hp;
+  const Real lap = fm - Real(2) * f0 + fp;  // f_{i-1} - 2 f_i + f_{i+1}
+  const Real dif = fm - fp;
+  c.p0 = Real(11.0 / 60.0) * (fm + fp) + Real(19.0 / 30.0) * f0 + Real(0.05) * dHp + Real(0.5) * H0;
+  c.p1 = Real(1.0 / 6.0) * fm + Real(5.0 / 6.0) * f0 + Real(2.0 / 3.0) * H0;
+  c.p2 = Real(5.0 / 6.0) * f0 + Real(1.0 / 6.0) * fp + Real(1.0 / 3.0) * H0;
+  c.D = Real(0.25) * (fm - Real(8) * f0 + Real(7) * fp) +
+        Real(1.0 / 12.0) * (Hm - Real(2) * H0 - Real(5) * Hp);
+  // a_1..a_5 of Eq. GHYZP (dx absorbed into H)
+  const Real a1 = Real(19.0 / 192.0) * sHp + Real(79.0 / 48.0) * H0 + Real(27.0 / 64.0) * dif;
+  const Real a2 = Real(0.375) * dHp + Real(1.25) * lap;
+  const Real a3 = -(Real(11.0 / 24.0) * sHp + Real(17.0 / 6.0) * H0) - Real(1.875) * dif;
+  const Real a4 = Real(-0.25) * dHp - Real(0.5) * lap;
+  const Real a5 = Real(0.25) * sHp + H0 + Real(0.75) * dif;
+  const Real e1 = a1 + Real(0.25) * a3 + Real(0.0625) * a5;
+  const Real e2 = a2 + Real(63.0 / 130.0) * a4;
+  const Real e3 = a3 + Real(8825.0 / 10934.0) * a5;
+  const Real beta0 = e1 * e1 + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * e3 * e3 +
+                     Real(1421461.0 / 2275.0) * a4 * a4 +
+                     Real(21520059541.0 / 1377684.0) * a5 * a5;
+  const Real s1 = H0 - f0 + fm, s2 = H0 + f0 - fp;  // beta_2 uses f_{i+1}
+  const Real h2 = H0 * H0;
+  const Real beta1 = h2 + Real(13.0 / 3.0) * s1 * s1;
+  const Real beta2 = h2 + Real(13.0 / 3.0) * s2 * s2;
+  const Real t = fabs(beta0 - beta1) + fabs(beta0 - beta2);
+  c.tau = Real(0.25) * t * t;
+  c.b0 = beta0 + eps;
+  c.b1 = beta1 + eps;
+  c.b2 = beta2 + eps;
+  return c;
+}
+
+// Numerator and denominator of f-hat over the common factor b0 b1 b2:
+// f-hat = num / den, num = (b0+tau) b1 b2 (p0 - g1 p1 - g2 p2)
+//   + g1 (b1+tau) b0 b2 p1 + g2 (b2+tau) b0 b1 p2, den = g0 (b0+tau) b1 b2 + ...
+template <class Real>
+__device__ __forceinline__ void combine_nd(const Cand<Real>& c, const Weights<Real>& w, Real& num,
+                                           Real& den) {
+  const Real b12 = c.b1 * c.b2, b02 = c.b0 * c.b2, b01 = c.b0 * c.b1;
+  const Real W0 = (c.b0 + c.tau) * b12;
+  const Real W1 = w.g1 * (c.b1 + c.tau) * b02;
+  const Real W2 = w.g2 * (c.b2 + c.tau) * b01;
+  num = W0 * (c.p0 - w.g1 * c.p1 - w.g2 * c.p2) + W1 * c.p1 + W2 * c.p2;
+  den = w.g0 * W0 + W1 + W2;
+}
+
+// f-hat of one side in the per-weight form (used for FP32).
+template <class Real>
+__device__ __forceinline__ Real combine_direct(const Cand<Real>& c, const Weights<Real>& w) {
+  const Real o0 = w.g0 + w.g0 * c.tau / c.b0;
+  const Real o1 = w.g1 + w.g1 * c.tau / c.b1;
+  const Real o2 = w.g2 + w.g2 * c.tau / c.b2;
+  const Real num = o0 * w.ig0 * (c.p0 - w.g1 * c.p1 - w.g2 * c.p2) + o1 * c.p1 + o2 * c.p2;
+  return num / (o0 + o1 + o2);
+}
+
+// Full interface flux of one (characteristic) field: f-hat = f-hat^+ + f-hat^-
+// from f^+ at i-1..i+1, f^- at i..i+2 and the scaled derivative data.
+template <class Real>
+__device__ __forceinline__ Real interface_flux(Real fpm, Real fp0, Real fpp, Real Hpm, Real Hp0,
+                                               Real Hpp, Real fm0, Real fm1, Real fm2, Real Hm0,
+                                               Real Hm1, Real Hm2, const Weights<Real>& w) {
+  const Cand<Real> a = candidates(fpm, fp0, fpp, Hpm, Hp0, Hpp, w.eps);
+  const Cand<Real> b = candidates(fm2, fm1, fm0, -Hm2, -Hm1, -Hm0, w.eps);  // mirror
+  if constexpr (std::is_same<Real, double>::value) {
+    Real na, da, nb, db;
+    combine_nd(a, w, na, da);
+    combine_nd(b, w, nb, db);
+    return (na * db + nb * da) / (da * db);
+  } else {
+    return combine_direct(a, w) + combine_direct(b, w);
+  }
+}
+
+// Scaled derivative flux D = dx (h-hat^+ + h-hat^-) = dx (p_0'^+ + p_0'^-),
+// linear (Sec. 2.1, h-hat = p_0'(x_{i+1/2}); the "-" side mirrored).
+template <class Real>
+__device__ __forceinline__ Real derivative_flux(Real fpm, Real fp0, Real fpp, Real Hpm, Real Hp0,
+                                                Real Hpp, Real fm0, Real fm1, Real fm2, Real Hm0,
+                                                Real Hm1, Real Hm2) {
+  const Real Dp = Real(0.25) * (fpm - Real(8) * fp0 + Real(7) * fpp) +
+                  Real(1.0 / 12.0) * (Hpm - Real(2) * Hp0 - Real(5) * Hpp);
+  // mirror: -(0.25 (f2 - 8 f1 + 7 f0) + (-H2 + 2 H1 + 5 H0)/12)
+  const Real Dm = Real(-0.25) * (fm2 - Real(8) * fm1 + Real(7) * fm0) +
+                  Real(1.0 / 12.0) * (Hm2 - Real(2) * Hm1 - Real(5) * Hm0);
+  return Dp + Dm;
+}
+
+// HWENO limiter (Sec. 2.2) in scaled form: point values um, u0, up and
+// Vm = dx v_{i-1}, Vp = dx v_{i+1}; returns dx * v-tilde_i.
+template <class Real>
+__device__ __forceinline__ Real limited_derivative(Real um, Real u0, Real up, Real Vm, Real Vp,
+                                                   const Weights<Real>& w) {
+  const Real sV = Vm + Vp, dV = Vm - Vp;
+  const Real lap = um - Real(2) * u0 + up;
+  const Real q0 = Real(0.75) * (up - um) - Real(0.25) * sV;  // dx q_0'(x_i) = a_1
+  const Real q1 = u0 - um;                                    // dx q_1'
+  const Real q2 = up - u0;                                    // dx q_2'
+  const Real a2 = Real(0.25) * dV + lap;
+  const Real a3 = Real(0.25) * sV - Real(0.25) * (up - um);
+  const Real a4 = Real(-0.25) * dV - Real(0.5) * lap;
+  const Real e1 = q0 + Real(0.25) * a3;
+  const Real e2 = a2 + Real(63.0 / 130.0) * a4;
+  const Real beta0 = e1 * e1 + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * a3 * a3 +
+                     Real(1421461.0 / 2275.0) * a4 * a4;
+  const Real beta1 = q1 * q1, beta2 = q2 * q2;
+  const Real t = fabs(beta0 - beta1) + fabs(beta0 - beta2);
+  const Real tau = Real(0.25) * t * t;
+  const Real b0 = beta0 + w.eps, b1 = beta1 + w.eps, b2 = beta2 + w.eps;
+  if constexpr (std::is_same<Real, double>::value) {
+    const Real b12 = b1 * b2, b02 = b0 * b2, b01 = b0 * b1;
+    const Real L0 = (b0 + tau) * b12;
+    const Real L1 = w.d1 * (b1 + tau) * b02;
+    const Real L2 = w.d2 * (b2 + tau) * b01;
+    const Real num = L0 * (q0 - w.d1 * q1 - w.d2 * q2) + L1 * q1 + L2 * q2;
+    return num / (w.d0 * L0 + L1 + L2);
+  } else {
+    const Real l0 = w.d0 + w.d0 * tau / b0;
+    const Real l1 = w.d1 + w.d1 * tau / b1;
+    const Real l2 = w.d2 + w.d2 * tau / b2;
+    const Real num = l0 * w.id0 * (q0 - w.d1 * q1 - w.d2 * q2) + l1 * q1 + l2 * q2;
+    return num / (l0 + l1 + l2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Euler eigen-systems in direction `dir` at a state given by velocity (u, v),
+// enthalpy H and sound speed c (standard right/left eigenvectors of the flux
+// Jacobian; eigenvalue order u-c, u, [shear], u+c). m = 3 (1D) or 4 (2D).
+// Only what the projections need is formed: the left matrix row by row and
+// the right matrix column by column.
+// ---------------------------------------------------------------------------
+template <class Real, int M>
+struct Eigen {
+  Real L[M][M];
+  Real R[M][M];
+};
+
+template <class Real, int M>
+__device__ __forceinline__ void euler_eigen(int dir, Real u, Real v, Real H, Real c, Real gm1,
+                                            Eigen<Real, M>& e) {
+  const Real ic = Real(1) / c;
+  const Real b1 = gm1 * ic * ic;
+  if constexpr (M == 3) {
+    const Real q = Real(0.5) * u * u;
+    const Real b2 = b1 * q;
+    const Real uc = u * ic;
+    e.L[0][0] = Real(0.5) * (b2 + uc); e.L[0][1] = Real(-0.5) * (b1 * u + ic); e.L[0][2] = Real(0.5) * b1;
+    e.L[1][0] = Real(1) - b2;          e.L[1][1] = b1 * u;                     e.L[1][2] = -b1;
+    e.L[2][0] = Real(0.5) * (b2 - uc); e.L[2][1] = Real(-0.5) * (b1 * u - ic); e.L[2][2] = Real(0.5) * b1;
+    e.R[0][0] = Real(1); e.R[0][1] = Real(1); e.R[0][2] = Real(1);
+    e.R[1][0] = u - c;   e.R[1][1] = u;       e.R[1][2] = u + c;
+    e.R[2][0] = H - u * c; e.R[2][1] = q;     e.R[2][2] = H + u * c;
+  } else {
+    const Real q = Real(0.5) * (u * u + v * v);
+    const Real b2 = b1 * q;
+    // normal / tangential velocity and their component slots
+    const Real un = dir == 0 ? u : v, ut = dir == 0 ? v : u;
+    const int kn = dir == 0 ? 1 : 2, kt = dir == 0 ? 2 : 1;
+    const Real unc = un * ic;
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 4; ++k) { e.L[r][k] = Real(0); e.R[r][k] = Real(0); }
+    e.L[0][0] = Real(0.5) * (b2 + unc); e.L[0][kn] = Real(-0.5) * (b1 * un + ic);
+    e.L[0][kt] = Real(-0.5) * b1 * ut;  e.L[0][3] = Real(0.5) * b1;
+    e.L[1][0] = Real(1) - b2; e.L[1][kn] = b1 * un; e.L[1][kt] = b1 * ut; e.L[1][3] = -b1;
+    e.L[2][0] = -ut; e.L[2][kt] = Real(1);
+    e.L[3][0] = Real(0.5) * (b2 - unc); e.L[3][kn] = Real(-0.5) * (b1 * un - ic);
+    e.L[3][kt] = Real(-0.5) * b1 * ut;  e.L[3][3] = Real(0.5) * b1;
+    // columns: (1, un-c, ut, H - un c), (1, un, ut, q), (0, 0, 1, ut), (1, un+c, ut, H + un c)
+    e.R[0][0] = Real(1); e.R[kn][0] = un - c; e.R[kt][0] = ut; e.R[3][0] = H - un * c;
+    e.R[0][1] = Real(1); e.R[kn][1] = un;     e.R[kt][1] = ut; e.R[3][1] = q;
+    e.R[kt][2] = Real(1); e.R[3][2] = ut;
+    e.R[0][3] = Real(1); e.R[kn][3] = un + c; e.R[kt][3] = ut; e.R[3][3] = H + un * c;
+  }
+}
+
+}  // namespace hweno

@@ -1,0 +1,69 @@
+// Internal interface between the host side of the library (hweno_api.cu) and
+// its kernels (stage1d.cu, stage2d.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hweno {
+
+// Status-word bits written by kernels (read by hweno_sync_status).
+enum : unsigned { STATUS_NONFINITE = 1u };
+
+enum Mode { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE2 = 2, MODE_STAGE3 = 3 };
+
+// 1D tiles: one CTA handles up to kTile1D consecutive points of one instance.
+constexpr int kTile1D = 128;
+constexpr int kThreads1D = 128;
+
+struct SchemeParams {
+  double lin_w[3], lim_d[3], eps, cfl, dt_fixed;
+  int dt_mode, limiter, eig_avg;
+  double gas_gamma;
+  int bc[4];
+  double inflow[4], pre[4];
+  double dmr_x0, dmr_speed, dmr_angle;
+};
+
+// Arguments of one 1D launch (all instances of the batch).
+struct Args1D {
+  // stage input state (u^{(k-1)}, v^{(k-1)}) and, for stages 2-3, u^n, v~^n
+  const void* U;
+  const void* V;
+  const void* U0;
+  const void* Vt0;
+  // outputs: stage state, the stored v~^n (stage 1) or L^1, L^2, v~ (rhs)
+  void* Uout;
+  void* Vout;
+  void* Vt0out;
+  void* L1;
+  void* L2;
+  void* Vlim;
+  // batch tables (device)
+  const int* tile_inst;
+  const int* tile_start;
+  const int* inst_n;
+  const long long* inst_off;  // first point of each instance
+  const double* inst_dx;
+  const double* inst_hx;      // dx or dx^{5/3} per dt_mode
+  // per-instance scalars (device)
+  const double* t;
+  double t_end;
+  int skip_done;              // instances with t >= t_end do nothing
+  const double* alpha_in;     // wave speed of the stage input
+  unsigned long long* alpha_out;  // max wave speed of the stage output (bits)
+  double* dt;                 // per-instance time step (written in stage 1)
+  int* lands;                 // dt was clipped to t_end (stage 1)
+  unsigned* status;
+  SchemeParams sp;
+};
+
+// Launchers (stage1d.cu). eq: 0 Burgers, 1 Euler; fp32: precision.
+cudaError_t launch_alpha_1d(int eq, bool fp32, const Args1D& a, int ntiles, cudaStream_t s);
+cudaError_t launch_stage_1d(int eq, bool fp32, int mode, const Args1D& a, int ntiles,
+                            cudaStream_t s);
+cudaError_t launch_finalize(int batch, const double* dt, const int* lands, double* t,
+                            double t_end, double* dt_used, const double* alpha,
+                            int* active_count, unsigned* status, cudaStream_t s);
+
+}  // namespace hweno

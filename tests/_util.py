@@ -41,3 +41,26 @@ def load_table(name):
             p = line.split()
             rows.append((int(p[0]), float(p[1]), float(p[3])))
     return {n: (l1, li) for n, l1, li in rows}
+
+
+def header_functions():
+    """Names of the functions declared in include/hweno.h."""
+    import re
+    root = os.path.dirname(GOLDEN[:-len("/golden")])
+    src = open(os.path.join(root, "include", "hweno.h")).read()
+    return sorted(set(re.findall(r"^(?:int|long long|const char\*)\s+(hweno_\w+)\s*\(", src, re.M)))
+
+
+def scales_1d(w, U, k=None):
+    """(U_scale, F_scale) of one 1D instance: max|U| and max over points of
+    |f(U)| + alpha |U| (the size of the split fluxes)."""
+    import oracle as O
+    P = oracle_problem(w, nx=U.shape[1])
+    us = float(np.max(np.abs(U)))
+    al = max(O.wave_speed(P, 0, U[:, i]) for i in range(U.shape[1]))
+    fs = max(float(np.max(np.abs(O.flux(P, 0, U[:, i])))) for i in range(U.shape[1]))
+    return us, fs + al * us
+
+
+def max_err(a, b):
+    return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64))))

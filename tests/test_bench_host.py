@@ -1,0 +1,54 @@
+"""Host-side pieces of bench.py: the algorithmic flop constants equal the
+oracle's operation count, and the multi-rank reduction (max time, summed
+work) over world_size 2 with the gloo backend on CPU."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+import oracle as O
+from paper_2207_05258_gb300 import workloads as W
+from _util import oracle_problem
+
+
+@pytest.mark.parametrize("key,make", [
+    (("euler", 1), lambda: W.euler1d_smooth(1000, dt_mode="cfl")),
+    (("burgers", 1), lambda: W.burgers1d_sine(1000)),
+    (("euler", 2), lambda: W.euler2d_smooth(64)),
+    (("burgers", 2), lambda: W.burgers2d_sine(64)),
+])
+def test_flop_constants_match_oracle_count(key, make):
+    w = make()
+    n = O.flops_per_point_step(oracle_problem(w), w.U, w.V, w.W)
+    assert abs(n - bench.ALGO_FLOPS_PER_POINT_STEP[key]) <= 1e-3 * n
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, pu = bench.reduce_over_ranks(10.0 + rank, 100.0 * (rank + 1), "cpu")
+    q.put((rank, ms, pu, bench.rank_seed(rank)))
+    dist.destroy_process_group()
+
+
+def test_reduce_over_two_gloo_ranks():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [11.0, 11.0]
+    assert [o[2] for o in out] == [300.0, 300.0]
+    assert out[0][3] != out[1][3]

@@ -1,0 +1,83 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports
+every entry point that include/hweno.h declares, and the binding declares
+them all; argument checks that precede any CUDA call return HWENO_EINVAL."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+import torch
+
+from _util import header_functions
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hw():
+    from paper_2207_05258_gb300 import build
+    build.build()
+    from paper_2207_05258_gb300 import hweno
+    return hweno
+
+
+def test_library_exports_every_declared_function(hw):
+    names = header_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(hw.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", hw.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert set(names) <= exported
+    assert set(hw.SIGNATURES) == set(names)
+
+
+def test_default_options_are_the_papers(hw):
+    o = hw.default_options()
+    assert list(o.lin_w) == [0.98, 0.01, 0.01] and list(o.lim_d) == [0.98, 0.01, 0.01]
+    assert o.eps == 1e-6 and o.cfl == 0.6 and o.limiter == 1 and o.eig_avg == 0
+
+
+def _create(hw, eq=0, dim=1, nx=16, ny=16, batch=1, nxs=None, prec=0, bc=(0, 0, 0, 0),
+            gamma=1.4, y1=1.0):
+    arr = (ctypes.c_int * len(nxs))(*nxs) if nxs else None
+    g = hw.Grid(dim, nx, ny, 0.0, 1.0, 0.0, y1, batch,
+                ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)) if arr else None, prec)
+    b = hw.Bc(*bc)
+    h = ctypes.c_void_p()
+    rc = hw.lib.hweno_create(ctypes.byref(h), eq, ctypes.byref(g), gamma, ctypes.byref(b))
+    if rc == 0:
+        hw.lib.hweno_destroy(h)
+    return rc, h
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=3), dict(nx=0), dict(batch=0), dict(batch=2, nxs=[16, 2]), dict(eq=2), dict(dim=3),
+    dict(prec=5), dict(bc=(0, 1, 0, 0)), dict(bc=(4, 1, 0, 0)), dict(bc=(9, 9, 0, 0)),
+    dict(eq=1, gamma=1.0), dict(dim=2, batch=2), dict(dim=2, ny=3), dict(dim=2, y1=0.0),
+    dict(dim=2, bc=(1, 1, 5, 4)), dict(dim=2, eq=0, bc=(1, 1, 4, 5)),
+])
+def test_create_rejects_invalid_problems(hw, kw):
+    rc, h = _create(hw, **kw)
+    assert rc == hw.EINVAL and not h.value
+
+
+def test_null_arguments(hw):
+    assert hw.lib.hweno_create(None, 0, None, 1.4, None) == hw.EINVAL
+    assert hw.lib.hweno_destroy(None) == 0
+    assert hw.lib.hweno_last_error(None) == b"null context"
+    assert hw.lib.hweno_step(None, None, None, None, None, 1.0, None, None) == hw.EINVAL
+    assert hw.lib.hweno_num_points(None) == -1
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU failure path")
+def test_valid_create_without_gpu_fails_cleanly(hw):
+    rc, h = _create(hw, nx=64)
+    assert rc in (hw.ECUDA, hw.ENOMEM) and not h.value
+
+
+def test_binding_refuses_cpu_tensors(hw):
+    with pytest.raises(ValueError):
+        hw._ptr(torch.zeros(4))

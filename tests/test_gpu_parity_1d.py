@@ -1,0 +1,309 @@
+"""GPU parity of the 1D path (C ABI through the binding) against the oracle.
+
+Tolerances come from the arithmetic: both sides compute the same formulas in
+FP64 in a different order (the GPU folds the weight divisions and contracts
+FMAs), so interface fluxes agree to a few ulps of the split-flux size F.
+The flux differences divide that by dx (L^1) and the derivative equation's
+by dx^2 (L^2 differences p_0' values that are themselves differences over
+dx); the limited derivative is a difference of point values over dx. Hence
+per-field scales F/dx, F/dx^2 and U/dx with a relative factor TOL = 1e-13.
+Full runs use the stated bounds: relative L-inf 1e-10 smooth, 1e-8 shocked.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2207_05258_gb300 import workloads as W
+from _util import max_err, oracle_problem, scales_1d
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def hw():
+    from paper_2207_05258_gb300 import build
+    build.build()
+    from paper_2207_05258_gb300 import hweno
+    return hweno
+
+
+def dev(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to("cuda", dtype)
+
+
+def host(x):
+    return x.double().cpu().numpy()
+
+
+def euler_batch(sizes, seed, kind, bc=("outflow", "outflow")):
+    """Ragged batch of 1D Euler instances on [0, 1]: 'riemann' (a jump at
+    x = 0.5, V = 0) or 'smooth' (random smooth waves, exact V)."""
+    rng = W.SplitMix64(seed)
+    Us, Vs = [], []
+    for n in sizes:
+        if kind == "riemann":
+            left = (rng.uniform(0.1, 1), rng.uniform(-0.5, 0.5), rng.uniform(0.1, 1))
+            right = (rng.uniform(0.1, 1), rng.uniform(-0.5, 0.5), rng.uniform(0.1, 1))
+            w = W.riemann1d(n, left, right)
+            Us.append(w.U); Vs.append(w.V)
+        else:
+            x = W.centers(0, 1, n)
+            ph, a = rng.uniform(0, 6.28), rng.uniform(0.05, 0.3)
+            rho = 1 + a * np.sin(2 * np.pi * x + ph)
+            drho = 2 * np.pi * a * np.cos(2 * np.pi * x + ph)
+            u = 0.3 + 0.2 * np.cos(2 * np.pi * x)
+            du = -0.4 * np.pi * np.sin(2 * np.pi * x)
+            p = 1 + 0.1 * np.sin(2 * np.pi * x)
+            dp = 0.2 * np.pi * np.cos(2 * np.pi * x)
+            U = W.euler_conserved(rho, u, p, 1.4)
+            V = np.stack([drho, drho * u + rho * du,
+                          dp / 0.4 + 0.5 * drho * u * u + rho * u * du])
+            Us.append(U.ravel()); Vs.append(V.ravel())
+    w = W.Workload("batch", "euler", 1, list(sizes), 1, 0.0, 1.0, 0.0, 1.0, 0.15,
+                   (bc[0], bc[1], "periodic", "periodic"), np.concatenate(Us),
+                   np.concatenate(Vs), inflow=(1.0, 0.2, 2.6, 0.0))
+    return w
+
+
+def burgers_batch(sizes, seed, bc):
+    rng = np.random.default_rng(seed)
+    Us, Vs = [], []
+    for n in sizes:
+        x = W.centers(0, 2, n)
+        Us.append(0.3 + np.sin(np.pi * x + rng.uniform(0, 6)) + 0.2 * rng.standard_normal(n))
+        Vs.append(3 * rng.standard_normal(n))
+    return W.Workload("bb", "burgers", 1, list(sizes), 1, 0.0, 2.0, 0.0, 1.0, 1.0,
+                      (bc, bc, "periodic", "periodic"), np.concatenate(Us), np.concatenate(Vs),
+                      inflow=(0.7, 0, 0, 0))
+
+
+def oracle_rhs(w, **opts):
+    L1, L2, Vt = [], [], []
+    for k in range(w.batch):
+        U, V = w.instance(k)
+        r = O.rhs(oracle_problem(w, nx=w.nx[k], **opts), U, V)
+        L1.append(r["L1"]); L2.append(r["L2"]); Vt.append(r["Vt"])
+    return L1, L2, Vt
+
+
+def split(w, flat):
+    out, off = [], 0
+    for n in w.nx:
+        out.append(flat[off:off + w.m * n].reshape(w.m, n))
+        off += w.m * n
+    return out
+
+
+def check_rhs(hw, w, **opts):
+    s = hw.Solver.from_workload(w, **opts)
+    r = s.rhs(dev(w.U), dev(w.V))
+    torch.cuda.synchronize()
+    s.sync_status()
+    L1, L2, Vt = (split(w, host(r[k])) for k in ("L1", "L2", "Vt"))
+    R1, R2, Rt = oracle_rhs(w, **opts)
+    for k in range(w.batch):
+        U, _ = w.instance(k)
+        us, fs = scales_1d(w, U)
+        dx = (w.x1 - w.x0) / w.nx[k]
+        e1, e2, et = max_err(L1[k], R1[k]), max_err(L2[k], R2[k]), max_err(Vt[k], Rt[k])
+        assert e1 <= TOL * fs / dx, (k, w.nx[k], e1, fs / dx)
+        assert e2 <= TOL * fs / dx ** 2, (k, w.nx[k], e2, fs / dx ** 2)
+        assert et <= TOL * us / dx, (k, w.nx[k], et, us / dx)
+    s.close()
+
+
+SIZES = [4, 5, 31, 127, 128, 129, 255, 257, 400]
+
+
+def test_rhs_burgers_config1(hw):
+    check_rhs(hw, W.burgers1d_sine(400))
+
+
+@pytest.mark.parametrize("bc", ["periodic", "outflow", "reflective", "inflow"])
+def test_rhs_burgers_rough_ragged(hw, bc):
+    check_rhs(hw, burgers_batch(SIZES, 3, bc))
+
+
+@pytest.mark.parametrize("kind", ["riemann", "smooth"])
+@pytest.mark.parametrize("bc", ["outflow", "periodic", "reflective", "inflow"])
+def test_rhs_euler_ragged(hw, kind, bc):
+    check_rhs(hw, euler_batch(SIZES, 11, kind, (bc, bc)))
+
+
+@pytest.mark.parametrize("opts", [dict(eig_avg=1), dict(limiter=0), dict(limiter=2),
+                                  dict(lin_w=(0.6, 0.3, 0.1), lim_d=(1 / 3, 1 / 3, 1 / 3)),
+                                  dict(eps=1e-3)])
+def test_rhs_euler_options(hw, opts):
+    check_rhs(hw, euler_batch([64, 129, 300], 5, "riemann"), **opts)
+
+
+def gpu_run(hw, w, t_end, steps=None, precision="fp64", **opts):
+    s = hw.Solver.from_workload(w, precision=precision, **opts)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    U, V = dev(w.U, dt), dev(w.V, dt)
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    if steps is None:
+        s.run(U, V, None, t, t_end)
+    else:
+        for _ in range(steps):
+            s.step(U, V, None, t, t_end)
+        s.sync_status()
+    out = host(U), host(V), t.cpu().numpy()
+    s.close()
+    return out
+
+
+def oracle_run(w, t_end, steps=None, **opts):
+    Us, Vs, ts = [], [], []
+    for k in range(w.batch):
+        U, V = w.instance(k)
+        U2, V2, _, t, _ = O.run(oracle_problem(w, nx=w.nx[k], **opts), U, V, None, 0.0, t_end,
+                                max_steps=steps if steps is not None else 1 << 40)
+        Us.append(U2); Vs.append(V2); ts.append(t)
+    return Us, Vs, np.array(ts)
+
+
+def compare_runs(w, g, o, rtol_u, rtol_v):
+    GU, GV = split(w, g[0]), split(w, g[1])
+    worst = 0.0
+    for k in range(w.batch):
+        eu = max_err(GU[k], o[0][k]) / np.max(np.abs(o[0][k]))
+        ev = max_err(GV[k], o[1][k]) / max(np.max(np.abs(o[1][k])), 1e-300)
+        worst = max(worst, eu)
+        assert eu <= rtol_u, (k, w.nx[k], eu)
+        assert ev <= rtol_v, (k, w.nx[k], ev)
+    assert np.allclose(g[2], o[2], rtol=1e-14, atol=0)
+    return worst
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(dt_mode=1), dict(dt_mode=2, dt_fixed=1e-3),
+                                  dict(limiter=2, eig_avg=1)])
+def test_one_step_euler(hw, opts):
+    w = euler_batch(SIZES, 21, "riemann")
+    compare_runs(w, gpu_run(hw, w, 1.0, steps=1, **opts), oracle_run(w, 1.0, steps=1, **opts),
+                 1e-13, 1e-12)
+
+
+def test_one_step_burgers(hw):
+    w = burgers_batch(SIZES, 22, "periodic")
+    compare_runs(w, gpu_run(hw, w, 1.0, steps=1), oracle_run(w, 1.0, steps=1), 1e-13, 1e-12)
+
+
+def test_smooth_run_burgers_example_3_1(hw):
+    w = W.burgers1d_sine(160, t_end=0.5 / math.pi, dt_mode="accuracy")
+    compare_runs(w, gpu_run(hw, w, w.t_end), oracle_run(w, w.t_end), 1e-10, 1e-10)
+
+
+def test_smooth_run_euler_example_3_2(hw):
+    w = W.euler1d_smooth(40, t_end=0.5)
+    compare_runs(w, gpu_run(hw, w, w.t_end), oracle_run(w, w.t_end), 1e-10, 1e-10)
+
+
+def test_shocked_run_burgers_n400(hw):
+    """Burgers, u0 = 0.5 + sin(pi x), N = 400, to t = 1.5/pi (a shock forms)."""
+    w = W.burgers1d_sine(400)
+    compare_runs(w, gpu_run(hw, w, w.t_end), oracle_run(w, w.t_end), 1e-8, 1e-8)
+
+
+def test_riemann_batch_subset_to_final_time(hw):
+    full = W.riemann_batch(count=64, seed=20220711)
+    pick = [k for k in range(64) if full.nx[k] <= 400][:10]
+    w = euler_subset(full, pick)
+    compare_runs(w, gpu_run(hw, w, w.t_end), oracle_run(w, w.t_end), 1e-8, 1e-8)
+
+
+def euler_subset(w, pick):
+    Us, Vs = zip(*(w.instance(k) for k in pick))
+    return W.Workload("sub", "euler", 1, [w.nx[k] for k in pick], 1, w.x0, w.x1, w.y0, w.y1,
+                      w.t_end, w.bc, np.concatenate([u.ravel() for u in Us]),
+                      np.concatenate([v.ravel() for v in Vs]), gas_gamma=w.gas_gamma)
+
+
+def test_full_size_batch_sampled(hw):
+    """The 2048-instance workload in the benchmark's launch configuration; 20
+    steps on the GPU, sampled instances re-run one by one on the oracle."""
+    w = W.riemann_batch()
+    g = gpu_run(hw, w, w.t_end, steps=20)
+    GU, GV = split(w, g[0]), split(w, g[1])
+    sizes = np.array(w.nx)
+    pick = [int(np.flatnonzero(sizes == n)[0]) for n in W.RIEMANN_SIZES] + [2047]
+    for k in pick:
+        U, V = w.instance(k)
+        U2, V2, _, t, _ = O.run(oracle_problem(w, nx=w.nx[k]), U, V, None, 0.0, w.t_end,
+                                max_steps=20)
+        assert max_err(GU[k], U2) <= 1e-10 * np.max(np.abs(U2)), k
+        assert max_err(GV[k], V2) <= 1e-10 * max(np.max(np.abs(V2)), 1.0), k
+        assert abs(g[2][k] - t) <= 1e-14 * t
+
+
+def test_finished_instances_are_untouched(hw):
+    w = euler_batch([64, 200, 129], 31, "riemann")
+    s = hw.Solver.from_workload(w)
+    U, V = dev(w.U), dev(w.V)
+    U0, V0 = U.clone(), V.clone()
+    t = torch.tensor([0.15, 0.0, 0.2], dtype=torch.float64, device="cuda")
+    dt = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    s.step(U, V, None, t, 0.15, dt)
+    assert s.active_instances() == 1
+    s.sync_status()
+    GU, GU0 = split(w, host(U)), split(w, host(U0))
+    assert np.array_equal(GU[0], GU0[0]) and np.array_equal(GU[2], GU0[2])
+    assert not np.array_equal(GU[1], GU0[1])
+    d = dt.cpu().numpy()
+    assert d[0] == 0.0 and d[2] == 0.0 and d[1] > 0.0
+    assert s.launches_last_call == 5
+
+
+def test_zero_burgers_state_lands_on_final_time(hw):
+    """alpha = 0: dt is the time left, the state stays zero."""
+    w = W.Workload("z", "burgers", 1, [50], 1, 0.0, 1.0, 0.0, 1.0, 0.3,
+                   ("periodic",) * 4, np.zeros(50), np.zeros(50))
+    g = gpu_run(hw, w, 0.3, steps=2)
+    assert np.all(g[0] == 0.0) and np.all(g[1] == 0.0) and g[2][0] == 0.3
+
+
+def test_nonfinite_state_is_reported(hw):
+    w = euler_batch([64], 41, "riemann")
+    U = w.U.copy()
+    U[10] = np.nan
+    s = hw.Solver.from_workload(w)
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.step(dev(U), dev(w.V), None, t, 1.0)
+    with pytest.raises(hw.HwenoError) as e:
+        s.sync_status()
+    assert e.value.code == hw.ENONFINITE
+    s.sync_status()  # the latch is cleared
+    s.close()
+
+
+def test_host_entry_point_matches_device_path(hw):
+    w = euler_batch([100, 257], 51, "riemann")
+    dev_out = gpu_run(hw, w, 1.0, steps=3)
+    s = hw.Solver.from_workload(w)
+    U = torch.from_numpy(w.U.copy()).pin_memory()
+    V = torch.from_numpy(w.V.copy()).pin_memory()
+    t = torch.zeros(2, dtype=torch.float64).pin_memory()
+    s.step_host(U, V, None, t, 1.0, nsteps=3)
+    assert np.array_equal(U.numpy(), dev_out[0]) and np.array_equal(V.numpy(), dev_out[1])
+    assert np.array_equal(t.numpy(), dev_out[2])
+    s.close()
+
+
+def test_fp32_error_against_fp64_oracle(hw):
+    """FP32 state and reconstruction: error against the FP64 oracle, stated."""
+    w = W.euler1d_smooth(80, t_end=0.5)
+    g = gpu_run(hw, w, w.t_end, precision="fp32")
+    o = oracle_run(w, w.t_end)
+    e = max_err(g[0].reshape(3, 80), o[0][0]) / np.max(np.abs(o[0][0]))
+    assert e < 1e-5, e
+    w = euler_subset(W.riemann_batch(count=16), [0, 1, 2, 3])
+    g = gpu_run(hw, w, 0.05, precision="fp32")
+    o = oracle_run(w, 0.05)
+    GU = split(w, g[0])
+    for k in range(4):
+        l1 = np.mean(np.abs(GU[k][0] - o[0][k][0])) / np.mean(np.abs(o[0][k][0]))
+        assert l1 < 1e-4, (k, l1)
