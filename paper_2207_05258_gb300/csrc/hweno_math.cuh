@@ -89,14 +89,22 @@ __device__ __forceinline__ void combine_nd(const Cand<Real>& c, const Weights<Re
   den = w.g0 * W0 + W1 + W2;
 }
 
+// Quotient used where the FP32 path divides: the fast approximate division
+// (a few ulp) in single precision; the IEEE division in double precision.
+template <class Real>
+__device__ __forceinline__ Real qdiv(Real a, Real b) {
+  if constexpr (std::is_same<Real, float>::value) return __fdividef(a, b);
+  else return a / b;
+}
+
 // f-hat of one side in the per-weight form (used for FP32).
 template <class Real>
 __device__ __forceinline__ Real combine_direct(const Cand<Real>& c, const Weights<Real>& w) {
-  const Real o0 = w.g0 + w.g0 * c.tau / c.b0;
-  const Real o1 = w.g1 + w.g1 * c.tau / c.b1;
-  const Real o2 = w.g2 + w.g2 * c.tau / c.b2;
+  const Real o0 = w.g0 + w.g0 * qdiv(c.tau, c.b0);
+  const Real o1 = w.g1 + w.g1 * qdiv(c.tau, c.b1);
+  const Real o2 = w.g2 + w.g2 * qdiv(c.tau, c.b2);
   const Real num = o0 * w.ig0 * (c.p0 - w.g1 * c.p1 - w.g2 * c.p2) + o1 * c.p1 + o2 * c.p2;
-  return num / (o0 + o1 + o2);
+  return qdiv(num, o0 + o1 + o2);
 }
 
 // Full interface flux of one (characteristic) field: f-hat = f-hat^+ + f-hat^-
@@ -160,11 +168,11 @@ __device__ __forceinline__ Real limited_derivative(Real um, Real u0, Real up, Re
     const Real num = L0 * (q0 - w.d1 * q1 - w.d2 * q2) + L1 * q1 + L2 * q2;
     return num / (w.d0 * L0 + L1 + L2);
   } else {
-    const Real l0 = w.d0 + w.d0 * tau / b0;
-    const Real l1 = w.d1 + w.d1 * tau / b1;
-    const Real l2 = w.d2 + w.d2 * tau / b2;
+    const Real l0 = w.d0 + w.d0 * qdiv(tau, b0);
+    const Real l1 = w.d1 + w.d1 * qdiv(tau, b1);
+    const Real l2 = w.d2 + w.d2 * qdiv(tau, b2);
     const Real num = l0 * w.id0 * (q0 - w.d1 * q1 - w.d2 * q2) + l1 * q1 + l2 * q2;
-    return num / (l0 + l1 + l2);
+    return qdiv(num, l0 + l1 + l2);
   }
 }
 

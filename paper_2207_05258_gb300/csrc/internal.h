@@ -12,9 +12,11 @@ enum : unsigned { STATUS_NONFINITE = 1u };
 
 enum Mode { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE2 = 2, MODE_STAGE3 = 3 };
 
-// 1D tiles: one CTA handles up to kTile1D consecutive points of one instance.
-constexpr int kTile1D = 128;
+// 1D tiles: one CTA of kThreads1D threads handles up to kTile1D consecutive
+// points of one instance, so that each phase takes one pass: kTile1D + 4
+// loaded points, kTile1D + 1 interfaces and kTile1D updates all fit in 128.
 constexpr int kThreads1D = 128;
+constexpr int kTile1D = kThreads1D - 4;
 
 struct SchemeParams {
   double lin_w[3], lim_d[3], eps, cfl, dt_fixed;
