@@ -194,6 +194,32 @@ int hweno_launches_last_call(const hweno_ctx* ctx);
 int hweno_profile_start(hweno_ctx* ctx, int capacity);
 int hweno_profile_read(hweno_ctx* ctx, double* ms, int* n, void* stream);
 
+/* Allocation-free step (this entry point has no counterpart in the paper; it
+ * serves callers that cannot allocate device memory: code inside a host
+ * framework that owns all device allocations through its own pool, code that
+ * must not pay cudaMalloc's implicit synchronisation, plug-ins that are only
+ * handed pre-allocated buffers).
+ *
+ * One SSP-RK3 step, as hweno_step, of a single 1D instance in FP64, with no
+ * context: the problem is passed in full (`opt` NULL = the paper's defaults),
+ * U, V (device, [m][nx]) are advanced in place, t (device, one double)
+ * advances and dt_used (device, one double, nullable) receives the step.
+ * All scratch lives in one fixed device array built into the library (about
+ * 2 MB, enough for nx <= HWENO_NOALLOC_MAX_POINTS points), present on every
+ * GPU that loads the library until the process exits; the call performs no
+ * cudaMalloc, cudaFree or other allocation. The first call on a device looks
+ * up that array's address for the device (with the device current), so make
+ * the first call on each device before any stream capture. The call
+ * synchronises `stream` and returns HWENO_ENONFINITE if a wave speed was not
+ * finite. HWENO_EINVAL: nx outside [4, HWENO_NOALLOC_MAX_POINTS], an invalid
+ * equation, gamma, boundary set or option. Every call shares the one array,
+ * so calls whose GPU work overlaps (other streams, other host threads) race:
+ * serialise them. */
+#define HWENO_NOALLOC_MAX_POINTS 16384
+int hweno_step_1d_noalloc(int equation, int nx, double x0, double x1, double gamma,
+                          const hweno_bc* bc, const hweno_options* opt, double* U, double* V,
+                          double* t, double t_end, double* dt_used, void* stream);
+
 /* Message describing the last error on this context ("" if none). */
 const char* hweno_last_error(const hweno_ctx* ctx);
 

@@ -74,6 +74,10 @@ SIGNATURES = {
     "hweno_launches_last_call": (ctypes.c_int, [_VP]),
     "hweno_profile_start": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hweno_profile_read": (ctypes.c_int, [_VP, _DP, ctypes.POINTER(ctypes.c_int), _VP]),
+    "hweno_step_1d_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.POINTER(Bc),
+                                             ctypes.POINTER(Options), _VP, _VP, _VP,
+                                             ctypes.c_double, _VP, _VP]),
     "hweno_last_error": (ctypes.c_char_p, [_VP]),
     "hweno_destroy": (ctypes.c_int, [_VP]),
 }
