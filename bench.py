@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--instances", type=int, default=2048)
+    ap.add_argument("--workload", default="riemann_batch",
+                    help="riemann_batch (default) | euler2d_smooth:N | double_mach:NXxNY")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, fp32 and cpu_baseline legs")
     return ap.parse_args()
@@ -142,14 +144,38 @@ def reduce_over_ranks(ms: float, point_updates: float, device) -> tuple:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def make_workload(name, rank, instances):
+    """The benchmark workload `name` for a rank (see --workload)."""
+    from paper_2207_05258_gb300 import workloads as W
+    if name == "riemann_batch":
+        return W.riemann_batch(count=instances, seed=rank_seed(rank))
+    kind, _, size = name.partition(":")
+    if kind == "euler2d_smooth":
+        return W.euler2d_smooth(int(size or 2048), dt_mode="cfl")
+    if kind == "double_mach":
+        nx, ny = (int(v) for v in (size or "1920x480").split("x"))
+        return W.double_mach(nx, ny)
+    raise SystemExit("unknown workload %r" % name)
+
+
+def describe(w):
+    if w.name == "riemann_batch":
+        return ("riemann_batch: %d x 1D Euler Riemann problems, N in {200,400,800,1600,3200}, "
+                "%d points, t_end 0.15, outflow" % (w.batch, w.points))
+    if w.name == "euler2d_smooth":
+        return ("euler2d_smooth: 2D Euler periodic [0,2]^2, rho = 1 + 0.2 sin(pi(x+y)), "
+                "u = 0.7, v = 0.3, p = 1, %dx%d" % (w.nx[0], w.ny))
+    return ("double_mach: Mach 10 shock at 60 deg on a wall, [0,4]x[0,1], %dx%d, t_end 0.2"
+            % (w.nx[0], w.ny))
+
+
 def run_ours(args, rank, world, dev_index):
     import torch
     from paper_2207_05258_gb300 import hweno
-    from paper_2207_05258_gb300 import workloads as W
 
     torch.cuda.set_device(dev_index)
-    w = W.riemann_batch(count=args.instances, seed=rank_seed(rank))
-    nx = torch.tensor(w.nx, dtype=torch.float64, device="cuda")
+    w = make_workload(args.workload, rank, args.instances)
+    nx = torch.tensor(w.nx if w.dim == 1 else [w.points], dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def timed(precision, K, Wm, profile):
@@ -157,10 +183,11 @@ def run_ours(args, rank, world, dev_index):
         dt_t = torch.float64 if precision == "fp64" else torch.float32
         U = torch.from_numpy(w.U).to("cuda", dt_t)
         V = torch.from_numpy(w.V).to("cuda", dt_t)
+        Wd = torch.from_numpy(w.W).to("cuda", dt_t) if w.dim == 2 else None
         t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
         hist = torch.zeros(K, w.batch, dtype=torch.float64, device="cuda")
         for _ in range(Wm):
-            s.step(U, V, None, t, w.t_end)
+            s.step(U, V, Wd, t, w.t_end)
         s.sync_status()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(K)]
@@ -173,7 +200,7 @@ def run_ours(args, rank, world, dev_index):
         for i in range(K):
             flush.zero_()
             ev[i][0].record()
-            s.step(U, V, None, t, w.t_end, hist[i])
+            s.step(U, V, Wd, t, w.t_end, hist[i])
             ev[i][1].record()
         torch.cuda.synchronize()
         if world > 1:
@@ -196,30 +223,33 @@ def run_ours(args, rank, world, dev_index):
 
     # roofline of the dominant kernel (the fused stage kernel)
     stage_ms, stage_n = prof["stage"]
-    pts_per_stage = (pu / world) / args.steps  # units per launch (this rank)
-    flop_stage = ALGO_FLOPS_PER_POINT_STEP[("euler", 1)] / 3.0
-    achieved = flop_stage * pts_per_stage / (stage_ms / stage_n * 1e-3) / 1e12
+    pts_per_stage = (pu / world) / args.steps  # points per stage (this rank)
+    flop_stage = ALGO_FLOPS_PER_POINT_STEP[(w.equation, w.dim)] / 3.0
+    # a 2D stage is two launches (x- and y-sweep): time per stage = 2 launches
+    launches_per_stage = 1 if w.dim == 1 else 2
+    stage_time = stage_ms / stage_n * launches_per_stage * 1e-3
+    achieved = flop_stage * pts_per_stage / stage_time / 1e12
     peak = PEAK_TFLOPS[args.precision]
-    traffic = MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
+    traffic = (MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
+               if args.workload == "riemann_batch" else None)
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
             "traffic": None if traffic is None else traffic * pts_per_stage,
-            "kernel": "k_stage_1d<euler,%s>" % args.precision,
+            "kernel": ("k_stage_1d<%s,%s>" % (w.equation, args.precision) if w.dim == 1 else
+                       "k_xsweep_2d + k_ysweep_2d <%s,%s>" % (w.equation, args.precision)),
             "kernel_share_of_step": round(stage_ms / sum(v[0] for v in prof.values()), 4),
             "flops_per_point_stage": round(flop_stage, 2),
             "peak_source": "nominal (recipe): FP64 1.25 TFLOP/s; FP32 = 152 SM x 128 x 2 x 2.07 GHz",
-            "hbm_achieved_gbs": round(ALGO_WORDS_PER_COMPONENT[1] / 3.0 * 3 *
+            "hbm_achieved_gbs": round(ALGO_WORDS_PER_COMPONENT[w.dim] / 3.0 * w.m *
                                       (8 if args.precision == "fp64" else 4) * pts_per_stage /
-                                      (stage_ms / stage_n * 1e-3) / 1e9, 1)}
+                                      stage_time / 1e9, 1)}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": "Mpoint-updates/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-           "config": {"workload": "riemann_batch: %d x 1D Euler Riemann problems, N in "
-                                  "{200,400,800,1600,3200}, %d points, t_end 0.15, outflow"
-                                  % (w.batch, w.points),
+           "config": {"workload": describe(w),
                       "instances": w.batch, "points": w.points, "precision": args.precision,
                       "l2": "flushed between timed steps (256 MiB write, L2 129 MB)",
                       "parallelism": "replicas (one seeded batch per rank)"},
@@ -234,7 +264,7 @@ def run_ours(args, rank, world, dev_index):
                            "ms_per_step": round(ms32 / args.steps, 4),
                            "stage_kernel_ms": round(prof32["stage"][0] / prof32["stage"][1], 4)}
         out["e2e"] = run_e2e(args, w, hweno, torch)
-        if rank == 0:
+        if rank == 0 and w.name == "riemann_batch":
             out["cpu_baseline"] = cpu_baseline(w, budget_s=12.0)
     return out, rank
 
@@ -246,20 +276,23 @@ def run_e2e(args, w, hweno, torch):
     dt_t = torch.float64 if args.precision == "fp64" else torch.float32
     U = torch.from_numpy(w.U).to(dt_t).pin_memory()
     V = torch.from_numpy(w.V).to(dt_t).pin_memory()
+    Wd = torch.from_numpy(w.W).to(dt_t).pin_memory() if w.dim == 2 else None
     t = torch.zeros(w.batch, dtype=torch.float64).pin_memory()
+    sizes = np.array(w.nx if w.dim == 1 else [w.points])
     for _ in range(2):
-        s.step_host(U, V, None, t, w.t_end, 1)
+        s.step_host(U, V, Wd, t, w.t_end, 1)
     K = max(3, args.steps // 2)
     pts = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(K):
         active = (t.numpy() < w.t_end)
-        pts += int(np.sum(np.array(w.nx)[active]))
-        s.step_host(U, V, None, t, w.t_end, 1)
+        pts += int(np.sum(sizes[active]))
+        s.step_host(U, V, Wd, t, w.t_end, 1)
     el = time.perf_counter() - t0
     s.close()
-    b = (U.numel() + V.numel()) * U.element_size() + t.numel() * 8
+    b = (U.numel() + V.numel() + (Wd.numel() if Wd is not None else 0)) * U.element_size() \
+        + t.numel() * 8
     return {"value": round(pts / el / 1e6, 3), "unit": "Mpoint-updates/s",
             "h2d_bytes_per_step": b, "d2h_bytes_per_step": b, "steps": K}
 

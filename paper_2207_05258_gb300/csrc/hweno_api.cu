@@ -50,6 +50,7 @@ struct hweno_ctx {
   void* d_U1 = nullptr; void* d_V1 = nullptr; void* d_W1 = nullptr;
   void* d_U2 = nullptr; void* d_V2 = nullptr; void* d_W2 = nullptr;
   void* d_Vt0 = nullptr; void* d_Wt0 = nullptr;
+  void* d_LX = nullptr; void* d_VT = nullptr;  // 2D: x-sweep results
   // device copies for the host-buffer entry point
   void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
   double* d_ht = nullptr;
@@ -106,7 +107,7 @@ void free_all(hweno_ctx* c) {
   void* ptrs[] = {c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
                   c->d_inst_hx, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
-                  c->d_hU, c->d_hV, c->d_hW, c->d_ht};
+                  c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -126,6 +127,8 @@ SchemeParams scheme_params(const hweno_ctx* c) {
   sp.dmr_x0 = c->bc.dmr_x0;
   sp.dmr_speed = c->bc.dmr_speed;
   sp.dmr_angle = c->bc.dmr_angle;
+  sp.dmr_tan = std::tan(c->bc.dmr_angle);
+  sp.dmr_sin = std::sin(c->bc.dmr_angle);
   return sp;
 }
 
@@ -226,6 +229,106 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
   return HWENO_OK;
 }
 
+double step_h(const hweno_ctx* c, double h) {
+  return c->opt.dt_mode == 1 ? std::pow(h, 5.0 / 3.0) : h;
+}
+
+Args2D base_args_2d(const hweno_ctx* c) {
+  Args2D a{};
+  a.nx = c->nx[0];
+  a.ny = c->ny;
+  a.dx = (c->x1 - c->x0) / c->nx[0];
+  a.dy = (c->y1 - c->y0) / c->ny;
+  a.hx = step_h(c, a.dx);
+  a.hy = step_h(c, a.dy);
+  a.x0 = c->x0;
+  a.y0 = c->y0;
+  a.status = c->d_status;
+  a.dt = c->d_dt;
+  a.lands = c->d_lands;
+  a.LX = c->d_LX;
+  a.sp = scheme_params(c);
+  return a;
+}
+
+// One SSP-RK3 step in 2D: alpha(U^n); per stage an x-sweep (x parts of L and
+// v~ into scratch) and a y-sweep (y parts, w~, RK combination, next alpha).
+int step_2d(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end, double* dt_used,
+            cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 6, s)) ||
+      (e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)))
+    return cuda_fail(c, e, "memset");
+  Args2D a = base_args_2d(c);
+  a.t = t;
+  a.t_end = t_end;
+  a.skip_done = 1;
+  a.U = U;
+  a.alpha_out = c->d_alpha;
+  prof_begin(c, s);
+  if ((e = launch_alpha_2d(c->eq, c->fp32, a, s))) return cuda_fail(c, e, "alpha");
+  prof_end(c, s, 0);
+  struct Stage { const void *u, *v, *w; void *uo, *vo, *wo, *vt; int slot_in; double sc; };
+  const Stage st[3] = {
+      {U, V, W, c->d_U1, c->d_V1, c->d_W1, c->d_Vt0, 0, 0.0},
+      {c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_VT, 1, 1.0},
+      {c->d_U2, c->d_V2, c->d_W2, U, V, W, c->d_VT, 2, 0.5}};
+  for (int k = 0; k < 3; ++k) {
+    const int mode = MODE_STAGE1 + k;
+    a.U = st[k].u; a.V = st[k].v; a.W = st[k].w;
+    a.U0 = U; a.Vt0 = c->d_Vt0; a.Wt0 = c->d_Wt0;
+    a.Uout = st[k].uo; a.Vout = st[k].vo; a.Wout = st[k].wo;
+    a.Wt0out = k == 0 ? c->d_Wt0 : nullptr;
+    a.VT = st[k].vt;
+    a.stage_c = st[k].sc;
+    a.alpha_in = reinterpret_cast<const double*>(c->d_alpha + 2 * st[k].slot_in);
+    a.alpha_out = k < 2 ? c->d_alpha + 2 * (k + 1) : nullptr;
+    prof_begin(c, s);
+    if ((e = launch_xsweep_2d(c->eq, c->fp32, mode, a, s))) return cuda_fail(c, e, "x-sweep");
+    prof_end(c, s, 1);
+    prof_begin(c, s);
+    if ((e = launch_ysweep_2d(c->eq, c->fp32, mode, a, s))) return cuda_fail(c, e, "y-sweep");
+    prof_end(c, s, 1);
+  }
+  prof_begin(c, s);
+  if ((e = launch_finalize(1, c->d_dt, c->d_lands, t, t_end, dt_used,
+                           reinterpret_cast<const double*>(c->d_alpha), c->d_active,
+                           c->d_status, s)))
+    return cuda_fail(c, e, "finalize");
+  prof_end(c, s, 2);
+  c->launches = 8;
+  return HWENO_OK;
+}
+
+int rhs_2d(hweno_ctx* c, const void* U, const void* V, const void* W, void* dU, void* dV,
+           void* dW, void* Vlim, void* Wlim, const double* t, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 2, s)))
+    return cuda_fail(c, e, "memset");
+  Args2D a = base_args_2d(c);
+  a.t = t;
+  a.t_end = 0.0;
+  a.skip_done = 0;
+  a.U = U; a.V = V; a.W = W;
+  a.alpha_out = c->d_alpha;
+  prof_begin(c, s);
+  if ((e = launch_alpha_2d(c->eq, c->fp32, a, s))) return cuda_fail(c, e, "alpha");
+  prof_end(c, s, 0);
+  a.alpha_in = reinterpret_cast<const double*>(c->d_alpha);
+  a.alpha_out = nullptr;
+  a.VT = Vlim ? Vlim : c->d_VT;
+  a.L1 = dU; a.L2 = dV; a.L3 = dW; a.Wlim = Wlim;
+  a.stage_c = 0.0;
+  prof_begin(c, s);
+  if ((e = launch_xsweep_2d(c->eq, c->fp32, MODE_RHS, a, s))) return cuda_fail(c, e, "x-sweep");
+  prof_end(c, s, 1);
+  prof_begin(c, s);
+  if ((e = launch_ysweep_2d(c->eq, c->fp32, MODE_RHS, a, s))) return cuda_fail(c, e, "y-sweep");
+  prof_end(c, s, 1);
+  c->launches = 3;
+  return HWENO_OK;
+}
+
 int rhs_1d(hweno_ctx* c, const void* U, const void* V, void* dU, void* dV, void* Vlim,
            const double* t, cudaStream_t s) {
   cudaError_t e;
@@ -320,12 +423,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
         (equation != HWENO_EULER || !(std::sin(bc->dmr_angle) > 0) || !(std::tan(bc->dmr_angle) > 0)))
       return bad("dmr");
   }
-  if (grid->dim == 2) {
-    delete c;
-    return HWENO_ENOTSUP;
-  }
-
-  // sizes and tile tables
+  // sizes and (1D) tile tables
   std::vector<int> tinst, tstart;
   std::vector<long long> off(c->batch);
   c->inst_dx.resize(c->batch);
@@ -334,7 +432,13 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
     off[k] = acc;
     acc += c->nx[k];
     c->inst_dx[k] = (c->x1 - c->x0) / c->nx[k];
-    for (int s = 0; s < c->nx[k]; s += kTile1D) { tinst.push_back(k); tstart.push_back(s); }
+    if (grid->dim == 1)
+      for (int s = 0; s < c->nx[k]; s += kTile1D) { tinst.push_back(k); tstart.push_back(s); }
+  }
+  if (grid->dim == 2) {
+    acc = (long long)c->nx[0] * c->ny;
+    tinst.push_back(0);
+    tstart.push_back(0);
   }
   c->npts = acc;
   c->elems = (size_t)c->m * (size_t)acc;
@@ -357,7 +461,11 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       (rc = dalloc(c, &c->d_U1, fb)) || (rc = dalloc(c, &c->d_V1, fb)) ||
       (rc = dalloc(c, &c->d_U2, fb)) || (rc = dalloc(c, &c->d_V2, fb)) ||
       (rc = dalloc(c, &c->d_Vt0, fb)) || (rc = dalloc(c, &c->d_hU, fb)) ||
-      (rc = dalloc(c, &c->d_hV, fb)) || (rc = dalloc(c, &c->d_ht, sizeof(double) * B))) {
+      (rc = dalloc(c, &c->d_hV, fb)) || (rc = dalloc(c, &c->d_ht, sizeof(double) * B)) ||
+      (c->dim == 2 &&
+       ((rc = dalloc(c, &c->d_W1, fb)) || (rc = dalloc(c, &c->d_W2, fb)) ||
+        (rc = dalloc(c, &c->d_Wt0, fb)) || (rc = dalloc(c, &c->d_LX, 3 * fb)) ||
+        (rc = dalloc(c, &c->d_VT, fb)) || (rc = dalloc(c, &c->d_hW, fb))))) {
     free_all(c);
     delete c;
     return rc;
@@ -399,7 +507,10 @@ int hweno_rhs(hweno_ctx* c, const void* U, const void* V, const void* W, void* d
   if (!c) return HWENO_EINVAL;
   if (!U || !V || !dU || !dV || !t) return fail(c, HWENO_EINVAL, "null array");
   if (c->dim == 1 && (W || dW || Wlim)) return fail(c, HWENO_EINVAL, "W given in 1D");
+  if (c->dim == 2 && (!W || !dW)) return fail(c, HWENO_EINVAL, "W and dW required in 2D");
   c->err.clear();
+  if (c->dim == 2)
+    return rhs_2d(c, U, V, W, dU, dV, dW, Vlim, Wlim, t, static_cast<cudaStream_t>(stream));
   return rhs_1d(c, U, V, dU, dV, Vlim, t, static_cast<cudaStream_t>(stream));
 }
 
@@ -408,8 +519,10 @@ int hweno_step(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
   if (!c) return HWENO_EINVAL;
   if (!U || !V || !t) return fail(c, HWENO_EINVAL, "null array");
   if (c->dim == 1 && W) return fail(c, HWENO_EINVAL, "W given in 1D");
+  if (c->dim == 2 && !W) return fail(c, HWENO_EINVAL, "W required in 2D");
   if (!std::isfinite(t_end)) return fail(c, HWENO_EINVAL, "t_end not finite");
   c->err.clear();
+  if (c->dim == 2) return step_2d(c, U, V, W, t, t_end, dt_used, static_cast<cudaStream_t>(stream));
   return step_1d(c, U, V, t, t_end, dt_used, static_cast<cudaStream_t>(stream));
 }
 
@@ -418,19 +531,23 @@ int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t
   if (!c) return HWENO_EINVAL;
   if (!U || !V || !t || nsteps < 0) return fail(c, HWENO_EINVAL, "bad argument");
   if (c->dim == 1 && W) return fail(c, HWENO_EINVAL, "W given in 1D");
+  if (c->dim == 2 && !W) return fail(c, HWENO_EINVAL, "W required in 2D");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t fb = c->elems * c->esize, tb = sizeof(double) * c->batch;
   cudaError_t e;
   if ((e = cudaMemcpyAsync(c->d_hU, U, fb, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(c->d_hV, V, fb, cudaMemcpyHostToDevice, s)) ||
+      (c->dim == 2 && (e = cudaMemcpyAsync(c->d_hW, W, fb, cudaMemcpyHostToDevice, s))) ||
       (e = cudaMemcpyAsync(c->d_ht, t, tb, cudaMemcpyHostToDevice, s)))
     return cuda_fail(c, e, "copy in");
   for (int i = 0; i < nsteps; ++i) {
-    const int rc = hweno_step(c, c->d_hU, c->d_hV, nullptr, c->d_ht, t_end, nullptr, stream);
+    const int rc = hweno_step(c, c->d_hU, c->d_hV, c->dim == 2 ? c->d_hW : nullptr, c->d_ht,
+                              t_end, nullptr, stream);
     if (rc != HWENO_OK) return rc;
   }
   if ((e = cudaMemcpyAsync(U, c->d_hU, fb, cudaMemcpyDeviceToHost, s)) ||
       (e = cudaMemcpyAsync(V, c->d_hV, fb, cudaMemcpyDeviceToHost, s)) ||
+      (c->dim == 2 && (e = cudaMemcpyAsync(W, c->d_hW, fb, cudaMemcpyDeviceToHost, s))) ||
       (e = cudaMemcpyAsync(t, c->d_ht, tb, cudaMemcpyDeviceToHost, s)))
     return cuda_fail(c, e, "copy out");
   return hweno_sync_status(c, stream);

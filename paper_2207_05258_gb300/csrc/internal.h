@@ -25,6 +25,7 @@ struct SchemeParams {
   int bc[4];
   double inflow[4], pre[4];
   double dmr_x0, dmr_speed, dmr_angle;
+  double dmr_tan, dmr_sin;  // tan and sin of dmr_angle, evaluated on the host
 };
 
 // Arguments of one 1D launch (all instances of the batch).
@@ -59,6 +60,51 @@ struct Args1D {
   unsigned* status;
   SchemeParams sp;
 };
+
+// 2D tiles. x-sweep: one CTA per row segment of kTileX2D points (like 1D).
+// y-sweep: one CTA per block of kColsY2D columns x kRowsY2D rows, so that
+// (kRowsY2D + 1) x kColsY2D interfaces = kThreads2D.
+constexpr int kThreads2D = 128;
+constexpr int kTileX2D = kThreads2D - 4;
+constexpr int kColsY2D = 16;
+constexpr int kRowsY2D = kThreads2D / kColsY2D - 1;
+
+// Arguments of the 2D launches (one instance).
+struct Args2D {
+  const void* U;  // stage input
+  const void* V;
+  const void* W;
+  const void* U0;  // u^n, v~^n, w~^n (stages 2-3)
+  const void* Vt0;
+  const void* Wt0;
+  void* Uout;
+  void* Vout;
+  void* Wout;
+  void* Wt0out;  // stage 1: w~^n
+  void* LX;      // x-sweep result [3m][ny][nx]: x parts of L^1, L^2, L^3
+  void* VT;      // x-sweep limited derivative v~ [m][ny][nx]
+  void* L1;      // rhs outputs
+  void* L2;
+  void* L3;
+  void* Wlim;
+  int nx, ny;
+  double dx, dy, hx, hy;  // mesh widths; h of the time-step rule
+  double x0, y0;
+  const double* t;
+  double t_end;
+  int skip_done;
+  double stage_c;  // boundary time of the stage: t + stage_c * dt
+  const double* alpha_in;          // [2]: alpha_x, alpha_y of the stage input
+  unsigned long long* alpha_out;   // [2]: of the stage output (bits)
+  double* dt;
+  int* lands;
+  unsigned* status;
+  SchemeParams sp;
+};
+
+cudaError_t launch_alpha_2d(int eq, bool fp32, const Args2D& a, cudaStream_t s);
+cudaError_t launch_xsweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
+cudaError_t launch_ysweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
 
 // Launchers (stage1d.cu). eq: 0 Burgers, 1 Euler; fp32: precision.
 cudaError_t launch_alpha_1d(int eq, bool fp32, const Args1D& a, int ntiles, cudaStream_t s);

@@ -1,0 +1,745 @@
+// Two-dimensional L-HWENO stage (Zhang & Zhao, arXiv:2207.05258, Eq. ode2H
+// with the mixed-derivative fluxes of Eq. mixed and the dimension-by-
+// dimension limiter), as two kernels per Runge-Kutta stage:
+//
+//  x-sweep  one CTA per row segment (kTileX2D points): loads U, V, W with
+//           x-ghosts, forms f, h = A_x V, eta = A_x W and the split f^{+-},
+//           dx h^{+-}; per x-interface the characteristic HWENO f-hat
+//           (eigenvectors of A_x at the Roe average), the linear h-hat and
+//           the central eta-hat; per point the x parts of L^1, L^2, L^3 and
+//           the x-limited derivative v~. Writes them to scratch.
+//  y-sweep  one CTA per kColsY2D x kRowsY2D block: the same in y with
+//           g, theta = A_y W, xi = A_y V (ghosts from the y boundary
+//           conditions, including the double-Mach wall and the exact shock
+//           motion), adds the x parts, forms the y-limited w~, combines the
+//           SSP-RK3 stage and reduces the wave speeds of the new state.
+//
+// The FP64 pipe bounds both kernels; the scratch round trip between them is
+// a few percent of the HBM time budget and keeps each tile's shared memory
+// small enough for several CTAs per SM.
+#include <algorithm>
+#include <cfloat>
+
+#include "hweno.h"
+#include "hweno_math.cuh"
+#include "internal.h"
+
+namespace hweno {
+namespace {
+
+template <int EQ>
+struct Dim2 { static constexpr int M = EQ == HWENO_BURGERS ? 1 : 4; };
+
+// Primitive quantities of a 2D Euler state.
+template <class Real>
+struct Prim2 {
+  Real ir, u, v, p, Ep;
+};
+
+template <class Real>
+__device__ __forceinline__ Prim2<Real> prim2(const Real* U, Real gm1) {
+  Prim2<Real> q;
+  q.ir = Real(1) / U[0];
+  q.u = U[1] * q.ir;
+  q.v = U[2] * q.ir;
+  q.p = gm1 * (U[3] - Real(0.5) * (U[1] * q.u + U[2] * q.v));
+  q.Ep = U[3] + q.p;
+  return q;
+}
+
+// Flux in direction DIR and the Jacobian-vector product A_DIR D (Eq. EQ3:
+// h = f'(u) u_x, xi = g'(u) u_x, eta = f'(u) u_y, theta = g'(u) u_y).
+template <int EQ, int DIR, class Real>
+__device__ __forceinline__ void flux2(const Real* U, const Prim2<Real>& q, Real* F) {
+  if constexpr (EQ == HWENO_BURGERS) {
+    F[0] = Real(0.5) * U[0] * U[0];
+  } else if constexpr (DIR == 0) {
+    F[0] = U[1]; F[1] = U[1] * q.u + q.p; F[2] = U[1] * q.v; F[3] = q.Ep * q.u;
+  } else {
+    F[0] = U[2]; F[1] = U[2] * q.u; F[2] = U[2] * q.v + q.p; F[3] = q.Ep * q.v;
+  }
+}
+
+template <int EQ, int DIR, class Real>
+__device__ __forceinline__ void jvp2(const Real* U, const Prim2<Real>& q, const Real* D, Real gm1,
+                                     Real* out) {
+  if constexpr (EQ == HWENO_BURGERS) {
+    out[0] = U[0] * D[0];
+  } else {
+    const Real du = (D[1] - q.u * D[0]) * q.ir;
+    const Real dv = (D[2] - q.v * D[0]) * q.ir;
+    const Real dp = gm1 * (D[3] - (q.u * D[1] + q.v * D[2]) + Real(0.5) * (q.u * q.u + q.v * q.v) * D[0]);
+    if constexpr (DIR == 0) {
+      out[0] = D[1];
+      out[1] = D[1] * q.u + U[1] * du + dp;
+      out[2] = D[1] * q.v + U[1] * dv;
+      out[3] = (D[3] + dp) * q.u + q.Ep * du;
+    } else {
+      out[0] = D[2];
+      out[1] = D[2] * q.u + U[2] * du;
+      out[2] = D[2] * q.v + U[2] * dv + dp;
+      out[3] = (D[3] + dp) * q.v + q.Ep * dv;
+    }
+  }
+}
+
+template <int EQ, class Real>
+__device__ __forceinline__ void speeds2(const Real* U, Real gam, double& sx, double& sy) {
+  if constexpr (EQ == HWENO_BURGERS) {
+    sx = sy = (double)fabs(U[0]);
+  } else {
+    const Prim2<Real> q = prim2(U, gam - Real(1));
+    const Real c = sqrt(gam * q.p * q.ir);
+    sx = (double)(fabs(q.u) + c);
+    sy = (double)(fabs(q.v) + c);
+  }
+}
+
+// Characteristic system of the 2D Euler flux Jacobian in direction DIR at
+// velocity (u, v), enthalpy H, sound speed c. Rows of L and columns of R in
+// the eigenvalue order un - c, un, shear, un + c; normal velocity un (slot
+// kn = 1 + DIR), tangential ut (slot kt = 2 - DIR). Zeros are skipped.
+template <class Real, int DIR>
+struct Char2 {
+  Real un, ut, H, c, q, b1, b2, ic;
+  __device__ __forceinline__ void init(Real u, Real v, Real H_, Real c_, Real gm1) {
+    un = DIR == 0 ? u : v;
+    ut = DIR == 0 ? v : u;
+    H = H_;
+    c = c_;
+    ic = Real(1) / c_;
+    q = Real(0.5) * (u * u + v * v);
+    b1 = gm1 * ic * ic;
+    b2 = b1 * q;
+  }
+  // row r of L applied to (x0, x1, x2, x3)
+  __device__ __forceinline__ Real left(int r, Real x0, Real x1, Real x2, Real x3) const {
+    const Real xn = DIR == 0 ? x1 : x2, xt = DIR == 0 ? x2 : x1;
+    if (r == 2) return xt - ut * x0;
+    const Real A = Real(0.5) * (b2 * x0 - b1 * un * xn - b1 * ut * xt + b1 * x3);
+    if (r == 1) return x0 - Real(2) * A;
+    const Real B = Real(0.5) * ic * (un * x0 - xn);
+    return r == 0 ? A + B : A - B;
+  }
+  // R s
+  __device__ __forceinline__ void right(const Real* s, Real* out) const {
+    const Real sum = s[0] + s[1] + s[3], dif = s[3] - s[0];
+    const Real on = un * sum + c * dif;
+    const Real ot = ut * sum + s[2];
+    out[0] = sum;
+    out[DIR == 0 ? 1 : 2] = on;
+    out[DIR == 0 ? 2 : 1] = ot;
+    out[3] = H * (s[0] + s[3]) + q * s[1] + ut * s[2] + un * c * dif;
+  }
+};
+
+template <class Real>
+__device__ __forceinline__ Weights<Real> make_weights2(const SchemeParams& sp) {
+  Weights<Real> w;
+  w.g0 = Real(sp.lin_w[0]); w.g1 = Real(sp.lin_w[1]); w.g2 = Real(sp.lin_w[2]);
+  w.d0 = Real(sp.lim_d[0]); w.d1 = Real(sp.lim_d[1]); w.d2 = Real(sp.lim_d[2]);
+  w.eps = Real(sp.eps);
+  w.ig0 = Real(1.0 / sp.lin_w[0]);
+  w.id0 = Real(1.0 / sp.lim_d[0]);
+  return w;
+}
+
+__device__ __forceinline__ double time_step2(const Args2D& a, int& lands) {
+  double dt;
+  if (a.sp.dt_mode == 2) {
+    dt = a.sp.dt_fixed;
+  } else {
+    const double rate = __dadd_rn(__ddiv_rn(a.alpha_in[0], a.hx), __ddiv_rn(a.alpha_in[1], a.hy));
+    dt = rate > 0.0 ? __ddiv_rn(a.sp.cfl, rate) : __longlong_as_double(0x7ff0000000000000LL);
+  }
+  const double rest = a.t_end - a.t[0];
+  lands = dt >= rest;
+  return lands ? rest : dt;
+}
+
+__device__ __forceinline__ double block_max2(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// Ghost handling along one direction. kind: 0 copy, 1 mirror, 2 imposed
+// state (pre = 0: sp.inflow, pre = 1: sp.pre).
+struct Src {
+  int idx;
+  int kind;
+  int pre;
+};
+
+__device__ __forceinline__ double imposed(const SchemeParams& sp, const Src& s, int c) {
+  return s.pre ? sp.pre[c] : sp.inflow[c];
+}
+
+__device__ __forceinline__ Src map_x(int i, int n, const SchemeParams& sp) {
+  Src r{i, 0, 0};
+  if (i >= 0 && i < n) return r;
+  const int b = i < 0 ? sp.bc[0] : sp.bc[1];
+  if (b == HWENO_BC_PERIODIC) r.idx = i < 0 ? i + n : i - n;
+  else if (b == HWENO_BC_OUTFLOW) r.idx = i < 0 ? 0 : n - 1;
+  else if (b == HWENO_BC_REFLECTIVE) { r.kind = 1; r.idx = i < 0 ? -i - 1 : 2 * n - 1 - i; }
+  else r.kind = 2;
+  return r;
+}
+
+// y ghosts of column x (cell centre) at stage time ts; the DMR bottom wall
+// starts at dmr_x0 and the top carries the exact shock position at the
+// ghost's height (reading of Example 3.11).
+__device__ __forceinline__ Src map_y(int j, int n, double x, double y0, double dy, double ts,
+                                     const SchemeParams& sp) {
+  Src r{j, 0, 0};
+  if (j >= 0 && j < n) return r;
+  const int b = j < 0 ? sp.bc[2] : sp.bc[3];
+  if (b == HWENO_BC_PERIODIC) r.idx = j < 0 ? j + n : j - n;
+  else if (b == HWENO_BC_OUTFLOW) r.idx = j < 0 ? 0 : n - 1;
+  else if (b == HWENO_BC_REFLECTIVE ||
+           (b == HWENO_BC_DMR_BOTTOM && !(x < sp.dmr_x0))) {
+    r.kind = 1;
+    r.idx = j < 0 ? -j - 1 : 2 * n - 1 - j;
+  } else if (b == HWENO_BC_DMR_TOP) {
+    const double yg = __dadd_rn(y0, __dmul_rn((double)j + 0.5, dy));
+    const double xs = __dadd_rn(__dadd_rn(sp.dmr_x0, __ddiv_rn(yg, sp.dmr_tan)),
+                                __ddiv_rn(__dmul_rn(sp.dmr_speed, ts), sp.dmr_sin));
+    r.kind = 2;
+    r.pre = x < xs ? 0 : 1;
+  } else {
+    r.kind = 2;  // inflow, or the DMR bottom left of the wall
+  }
+  return r;
+}
+
+// Reflection sign of component c through a wall normal to DIR (Burgers: u
+// odd; Euler: the normal momentum odd).
+template <int EQ, int DIR>
+__device__ __forceinline__ float refl2(int c) {
+  return EQ == HWENO_BURGERS ? -1.f : (c == 1 + DIR ? -1.f : 1.f);
+}
+
+// ---------------------------------------------------------------------------
+template <int EQ, class Real>
+__global__ void __launch_bounds__(256) k_alpha_2d(Args2D a) {
+  constexpr int M = Dim2<EQ>::M;
+  __shared__ double red[8];
+  if (a.skip_done && !(a.t[0] < a.t_end)) return;
+  const long long N = (long long)a.nx * a.ny;
+  const Real* U = static_cast<const Real*>(a.U);
+  const Real gam = Real(a.sp.gas_gamma);
+  double ax = 0.0, ay = 0.0;
+  bool bad = false;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+       q += (long long)gridDim.x * blockDim.x) {
+    Real u[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) u[c] = U[c * N + q];
+    double sx, sy;
+    speeds2<EQ>(u, gam, sx, sy);
+    bad |= !(sx <= DBL_MAX) || !(sy <= DBL_MAX);
+    ax = fmax(ax, sx);
+    ay = fmax(ay, sy);
+  }
+  if (bad) atomicOr(a.status, STATUS_NONFINITE);
+  ax = block_max2(ax, red);
+  if (threadIdx.x == 0) atomicMax(&a.alpha_out[0], (unsigned long long)__double_as_longlong(ax));
+  ay = block_max2(ay, red);
+  if (threadIdx.x == 0) atomicMax(&a.alpha_out[1], (unsigned long long)__double_as_longlong(ay));
+}
+
+// ---------------------------------------------------------------------------
+// x-sweep
+// ---------------------------------------------------------------------------
+template <int EQ, class Real, int MODE>
+__global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(Args2D a) {
+  constexpr int M = Dim2<EQ>::M;
+  constexpr bool EUL = EQ == HWENO_EULER;
+  constexpr int NP = kTileX2D + 4, NF = kTileX2D + 1;
+  __shared__ Real sU[M][NP], sV[M][NP];
+  __shared__ Real sFp[M][NP], sFm[M][NP], sHp[M][NP], sHm[M][NP], sEta[M][NP];
+  __shared__ Real sE[EUL ? 5 : 1][EUL ? NP : 1];  // sqrt(rho), u, v, H, c
+  __shared__ Real sF[M][NF], sD[M][NF], sN[M][NF];
+
+  if (a.skip_done && !(a.t[0] < a.t_end)) return;
+  const int nx = a.nx;
+  const long long N = (long long)nx * a.ny;
+  const int j = blockIdx.y, i0 = blockIdx.x * kTileX2D;
+  const int np = min(kTileX2D, nx - i0);
+  const long long row = (long long)j * nx;
+  const Real dx = Real(a.dx), idx = Real(1.0 / a.dx), idx2 = Real(1.0 / (a.dx * a.dx));
+  const Real alpha = Real(a.alpha_in[0]);
+  const Real gam = Real(a.sp.gas_gamma), gm1 = gam - Real(1);
+  const Weights<Real> w = make_weights2<Real>(a.sp);
+  if constexpr (MODE == MODE_STAGE1) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+      int lands;
+      const double dt = time_step2(a, lands);
+      a.dt[0] = dt;
+      a.lands[0] = lands;
+    }
+  }
+
+  {
+    const Real* U = static_cast<const Real*>(a.U);
+    const Real* V = static_cast<const Real*>(a.V);
+    const Real* W = static_cast<const Real*>(a.W);
+    const Real hdx = Real(0.5) * dx;
+    for (int g = threadIdx.x; g < np + 4; g += blockDim.x) {
+      const Src s = map_x(i0 - 2 + g, nx, a.sp);
+      Real u[M], v[M], ww[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        if (s.kind == 2) {
+          u[c] = Real(imposed(a.sp, s, c)); v[c] = Real(0); ww[c] = Real(0);
+        } else {
+          const long long q = c * N + row + s.idx;
+          u[c] = U[q]; v[c] = V[q]; ww[c] = W[q];
+          if (s.kind == 1) {
+            const Real sg = Real(refl2<EQ, 0>(c));
+            u[c] *= sg; v[c] *= -sg; ww[c] *= sg;
+          }
+        }
+        sU[c][g] = u[c];
+        sV[c][g] = v[c];
+      }
+      Prim2<Real> pq{};
+      if constexpr (EUL) pq = prim2(u, gm1);
+      Real F[M], H[M], E[M];
+      flux2<EQ, 0>(u, pq, F);
+      jvp2<EQ, 0>(u, pq, v, gm1, H);
+      jvp2<EQ, 0>(u, pq, ww, gm1, E);
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
+        sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
+        sHp[c][g] = hdx * (H[c] + alpha * v[c]);
+        sHm[c][g] = hdx * (H[c] - alpha * v[c]);
+        sEta[c][g] = E[c];
+      }
+      if constexpr (EUL) {
+        sE[0][g] = sqrt(u[0]);
+        sE[1][g] = pq.u;
+        sE[2][g] = pq.v;
+        sE[3][g] = pq.Ep * pq.ir;
+        sE[4][g] = sqrt(gam * pq.p * pq.ir);
+      }
+    }
+  }
+  __syncthreads();
+
+  for (int jf = threadIdx.x; jf <= np; jf += blockDim.x) {
+    const int gl = jf + 1;
+    if constexpr (!EUL) {
+      sF[0][jf] = interface_flux(sFp[0][gl - 1], sFp[0][gl], sFp[0][gl + 1], sHp[0][gl - 1],
+                                 sHp[0][gl], sHp[0][gl + 1], sFm[0][gl], sFm[0][gl + 1],
+                                 sFm[0][gl + 2], sHm[0][gl], sHm[0][gl + 1], sHm[0][gl + 2], w);
+    } else {
+      Real uu, vv, HH;
+      if (a.sp.eig_avg == 0) {
+        const Real sl = sE[0][gl], sr = sE[0][gl + 1];
+        const Real is = Real(1) / (sl + sr);
+        uu = (sl * sE[1][gl] + sr * sE[1][gl + 1]) * is;
+        vv = (sl * sE[2][gl] + sr * sE[2][gl + 1]) * is;
+        HH = (sl * sE[3][gl] + sr * sE[3][gl + 1]) * is;
+      } else {
+        Real Um[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Um[c] = Real(0.5) * (sU[c][gl] + sU[c][gl + 1]);
+        const Prim2<Real> pm = prim2(Um, gm1);
+        uu = pm.u; vv = pm.v; HH = pm.Ep * pm.ir;
+      }
+      const Real cc = sqrt(gm1 * (HH - Real(0.5) * (uu * uu + vv * vv)));
+      Char2<Real, 0> e;
+      e.init(uu, vv, HH, cc, gm1);
+      Real fch[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        auto pj = [&](Real (*A)[NP], int g) { return e.left(r, A[0][g], A[1][g], A[2][g], A[3][g]); };
+        fch[r] = interface_flux(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1), pj(sHp, gl - 1),
+                                pj(sHp, gl), pj(sHp, gl + 1), pj(sFm, gl), pj(sFm, gl + 1),
+                                pj(sFm, gl + 2), pj(sHm, gl), pj(sHm, gl + 1), pj(sHm, gl + 2), w);
+      }
+      Real out[4];
+      e.right(fch, out);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sF[c][jf] = out[c];
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      sD[c][jf] = derivative_flux(sFp[c][gl - 1], sFp[c][gl], sFp[c][gl + 1], sHp[c][gl - 1],
+                                  sHp[c][gl], sHp[c][gl + 1], sFm[c][gl], sFm[c][gl + 1],
+                                  sFm[c][gl + 2], sHm[c][gl], sHm[c][gl + 1], sHm[c][gl + 2]);
+      // Eq. mixed: -1/12 eta_{i-1} + 7/12 eta_i + 7/12 eta_{i+1} - 1/12 eta_{i+2}
+      sN[c][jf] = Real(7.0 / 12.0) * (sEta[c][gl] + sEta[c][gl + 1]) -
+                  Real(1.0 / 12.0) * (sEta[c][gl - 1] + sEta[c][gl + 2]);
+    }
+  }
+  __syncthreads();
+
+  Real* LX = static_cast<Real*>(a.LX);
+  Real* VT = static_cast<Real*>(a.VT);
+  for (int ip = threadIdx.x; ip < np; ip += blockDim.x) {
+    const int g = ip + 2;
+    const long long q = row + i0 + ip;
+    Real vt[M];
+    if (a.sp.limiter == 0) {
+#pragma unroll
+      for (int c = 0; c < M; ++c) vt[c] = sV[c][g];
+    } else if (!EUL || a.sp.limiter == 2) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
+                                   dx * sV[c][g + 1], w) * idx;
+    } else if constexpr (EUL) {
+      Char2<Real, 0> e;
+      e.init(sE[1][g], sE[2][g], sE[3][g], sE[4][g], gm1);
+      Real z[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        auto pj = [&](Real (*A)[NP], int gg) { return e.left(r, A[0][gg], A[1][gg], A[2][gg], A[3][gg]); };
+        z[r] = limited_derivative(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1), dx * pj(sV, g - 1),
+                                  dx * pj(sV, g + 1), w);
+      }
+      e.right(z, vt);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) vt[c] *= idx;
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      LX[c * N + q] = -(sF[c][ip + 1] - sF[c][ip]) * idx;
+      LX[(M + c) * N + q] = -(sD[c][ip + 1] - sD[c][ip]) * idx2;
+      LX[(2 * M + c) * N + q] = -(sN[c][ip + 1] - sN[c][ip]) * idx;
+      VT[c * N + q] = vt[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y-sweep + stage combination
+// ---------------------------------------------------------------------------
+template <int EQ, class Real>
+struct YLayout {
+  static constexpr int M = Dim2<EQ>::M;
+  static constexpr bool EUL = EQ == HWENO_EULER;
+  static constexpr int R = kRowsY2D + 4, C = kColsY2D, P = R * C;  // loaded points
+  static constexpr int RF = kRowsY2D + 1;                          // interface rows
+  // per-point arrays: U, W, G+, G-, T+, T-, xi (M each), eigen data (5, Euler)
+  static constexpr int NQ = 7 * M + (EUL ? 5 : 0);
+  static constexpr int NI = 3 * M;                                  // g-hat, theta-hat, xi-hat
+  static constexpr size_t bytes = sizeof(Real) * ((size_t)NQ * P + (size_t)NI * RF * C) + 64;
+};
+
+template <int EQ, class Real, int MODE>
+__global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
+  using Lay = YLayout<EQ, Real>;
+  constexpr int M = Lay::M;
+  constexpr bool EUL = Lay::EUL;
+  constexpr int C = Lay::C, P = Lay::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  // point arrays: index [(q * P) + r * C + col]
+  auto PT = [&](int qty, int c) { return sm + (size_t)(qty * M + c) * P; };
+  Real* sEig = sm + (size_t)7 * M * P;  // 5 x P (Euler)
+  Real* sI = sm + (size_t)Lay::NQ * P;  // interface arrays [3M][RF][C]
+  auto IF = [&](int kind, int c) { return sI + (size_t)(kind * M + c) * Lay::RF * C; };
+  __shared__ double red[kThreads2D / 32];
+
+  if (a.skip_done && !(a.t[0] < a.t_end)) return;
+  const int nx = a.nx, ny = a.ny;
+  const long long N = (long long)nx * ny;
+  const int i0 = blockIdx.x * C, j0 = blockIdx.y * kRowsY2D;
+  const int ncol = min(C, nx - i0), nrow = min(kRowsY2D, ny - j0);
+  const Real dy = Real(a.dy), idy = Real(1.0 / a.dy), idy2 = Real(1.0 / (a.dy * a.dy));
+  const Real alpha = Real(a.alpha_in[1]);
+  const Real gam = Real(a.sp.gas_gamma), gm1 = gam - Real(1);
+  const Weights<Real> w = make_weights2<Real>(a.sp);
+  double dt = 0.0;
+  if constexpr (MODE == MODE_STAGE1) {
+    int lands;
+    dt = time_step2(a, lands);
+  } else if constexpr (MODE != MODE_RHS) {
+    dt = a.dt[0];
+  }
+  const Real rdt = Real(dt);
+  const double ts = __dadd_rn(a.t[0], __dmul_rn(a.stage_c, dt));
+
+  {
+    const Real* U = static_cast<const Real*>(a.U);
+    const Real* V = static_cast<const Real*>(a.V);
+    const Real* W = static_cast<const Real*>(a.W);
+    const Real hdy = Real(0.5) * dy;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+      const int r = k / C, col = k % C;
+      if (col >= ncol || r >= nrow + 4) continue;
+      const int i = i0 + col;
+      const double xc = __dadd_rn(a.x0, __dmul_rn((double)i + 0.5, a.dx));
+      const Src s = map_y(j0 - 2 + r, ny, xc, a.y0, a.dy, ts, a.sp);
+      Real u[M], v[M], ww[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        if (s.kind == 2) {
+          u[c] = Real(imposed(a.sp, s, c)); v[c] = Real(0); ww[c] = Real(0);
+        } else {
+          const long long q = c * N + (long long)s.idx * nx + i;
+          u[c] = U[q]; v[c] = V[q]; ww[c] = W[q];
+          if (s.kind == 1) {
+            const Real sg = Real(refl2<EQ, 1>(c));
+            u[c] *= sg; ww[c] *= -sg; v[c] *= sg;
+          }
+        }
+        PT(0, c)[k] = u[c];
+        PT(1, c)[k] = ww[c];
+      }
+      Prim2<Real> pq{};
+      if constexpr (EUL) pq = prim2(u, gm1);
+      Real G[M], T[M], X[M];
+      flux2<EQ, 1>(u, pq, G);
+      jvp2<EQ, 1>(u, pq, ww, gm1, T);
+      jvp2<EQ, 1>(u, pq, v, gm1, X);
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        PT(2, c)[k] = Real(0.5) * (G[c] + alpha * u[c]);
+        PT(3, c)[k] = Real(0.5) * (G[c] - alpha * u[c]);
+        PT(4, c)[k] = hdy * (T[c] + alpha * ww[c]);
+        PT(5, c)[k] = hdy * (T[c] - alpha * ww[c]);
+        PT(6, c)[k] = X[c];
+      }
+      if constexpr (EUL) {
+        sEig[0 * P + k] = sqrt(u[0]);
+        sEig[1 * P + k] = pq.u;
+        sEig[2 * P + k] = pq.v;
+        sEig[3 * P + k] = pq.Ep * pq.ir;
+        sEig[4 * P + k] = sqrt(gam * pq.p * pq.ir);
+      }
+    }
+  }
+  __syncthreads();
+
+  // interfaces y_{j0+r-1/2}, r = 0..nrow; lower point at loaded row r + 1
+  for (int k = threadIdx.x; k < Lay::RF * C; k += blockDim.x) {
+    const int r = k / C, col = k % C;
+    if (col >= ncol || r > nrow) continue;
+    const int gl = r + 1;
+    auto at = [&](const Real* A, int rr) { return A[rr * C + col]; };
+    if constexpr (!EUL) {
+      IF(0, 0)[k] = interface_flux(at(PT(2, 0), gl - 1), at(PT(2, 0), gl), at(PT(2, 0), gl + 1),
+                                   at(PT(4, 0), gl - 1), at(PT(4, 0), gl), at(PT(4, 0), gl + 1),
+                                   at(PT(3, 0), gl), at(PT(3, 0), gl + 1), at(PT(3, 0), gl + 2),
+                                   at(PT(5, 0), gl), at(PT(5, 0), gl + 1), at(PT(5, 0), gl + 2), w);
+    } else {
+      Real uu, vv, HH;
+      const int kl = gl * C + col, kr = (gl + 1) * C + col;
+      if (a.sp.eig_avg == 0) {
+        const Real sl = sEig[kl], sr = sEig[kr];
+        const Real is = Real(1) / (sl + sr);
+        uu = (sl * sEig[P + kl] + sr * sEig[P + kr]) * is;
+        vv = (sl * sEig[2 * P + kl] + sr * sEig[2 * P + kr]) * is;
+        HH = (sl * sEig[3 * P + kl] + sr * sEig[3 * P + kr]) * is;
+      } else {
+        Real Um[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Um[c] = Real(0.5) * (PT(0, c)[kl] + PT(0, c)[kr]);
+        const Prim2<Real> pm = prim2(Um, gm1);
+        uu = pm.u; vv = pm.v; HH = pm.Ep * pm.ir;
+      }
+      const Real cc = sqrt(gm1 * (HH - Real(0.5) * (uu * uu + vv * vv)));
+      Char2<Real, 1> e;
+      e.init(uu, vv, HH, cc, gm1);
+      Real fch[4];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        auto pj = [&](int qty, int g) {
+          const int kk = g * C + col;
+          return e.left(rr, PT(qty, 0)[kk], PT(qty, 1)[kk], PT(qty, 2)[kk], PT(qty, 3)[kk]);
+        };
+        fch[rr] = interface_flux(pj(2, gl - 1), pj(2, gl), pj(2, gl + 1), pj(4, gl - 1), pj(4, gl),
+                                 pj(4, gl + 1), pj(3, gl), pj(3, gl + 1), pj(3, gl + 2), pj(5, gl),
+                                 pj(5, gl + 1), pj(5, gl + 2), w);
+      }
+      Real out[4];
+      e.right(fch, out);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) IF(0, c)[k] = out[c];
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      IF(1, c)[k] = derivative_flux(at(PT(2, c), gl - 1), at(PT(2, c), gl), at(PT(2, c), gl + 1),
+                                    at(PT(4, c), gl - 1), at(PT(4, c), gl), at(PT(4, c), gl + 1),
+                                    at(PT(3, c), gl), at(PT(3, c), gl + 1), at(PT(3, c), gl + 2),
+                                    at(PT(5, c), gl), at(PT(5, c), gl + 1), at(PT(5, c), gl + 2));
+      IF(2, c)[k] = Real(7.0 / 12.0) * (at(PT(6, c), gl) + at(PT(6, c), gl + 1)) -
+                    Real(1.0 / 12.0) * (at(PT(6, c), gl - 1) + at(PT(6, c), gl + 2));
+    }
+  }
+  __syncthreads();
+
+  double ax = 0.0, ay = 0.0;
+  bool bad = false;
+  const Real* LX = static_cast<const Real*>(a.LX);
+  const Real* VT = static_cast<const Real*>(a.VT);
+  for (int k = threadIdx.x; k < kRowsY2D * C; k += blockDim.x) {
+    const int r = k / C, col = k % C;
+    if (col >= ncol || r >= nrow) continue;
+    const int g = r + 2;
+    const int kc = g * C + col;
+    const long long q = (long long)(j0 + r) * nx + i0 + col;
+    Real l1[M], l2[M], l3[M], vt[M], wt[M], u[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      const int ka = r * C + col, kb = (r + 1) * C + col;
+      l1[c] = LX[c * N + q] - (IF(0, c)[kb] - IF(0, c)[ka]) * idy;
+      l2[c] = LX[(M + c) * N + q] - (IF(2, c)[kb] - IF(2, c)[ka]) * idy;
+      l3[c] = LX[(2 * M + c) * N + q] - (IF(1, c)[kb] - IF(1, c)[ka]) * idy2;
+      vt[c] = VT[c * N + q];
+      u[c] = PT(0, c)[kc];
+    }
+    if (a.sp.limiter == 0) {
+#pragma unroll
+      for (int c = 0; c < M; ++c) wt[c] = PT(1, c)[kc];
+    } else if (!EUL || a.sp.limiter == 2) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        wt[c] = limited_derivative(PT(0, c)[kc - C], u[c], PT(0, c)[kc + C],
+                                   dy * PT(1, c)[kc - C], dy * PT(1, c)[kc + C], w) * idy;
+    } else if constexpr (EUL) {
+      Char2<Real, 1> e;
+      e.init(sEig[P + kc], sEig[2 * P + kc], sEig[3 * P + kc], sEig[4 * P + kc], gm1);
+      Real z[4];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        auto pj = [&](int qty, int kk) {
+          return e.left(rr, PT(qty, 0)[kk], PT(qty, 1)[kk], PT(qty, 2)[kk], PT(qty, 3)[kk]);
+        };
+        z[rr] = limited_derivative(pj(0, kc - C), pj(0, kc), pj(0, kc + C), dy * pj(1, kc - C),
+                                   dy * pj(1, kc + C), w);
+      }
+      e.right(z, wt);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) wt[c] *= idy;
+    }
+    if constexpr (MODE == MODE_RHS) {
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        static_cast<Real*>(a.L1)[c * N + q] = l1[c];
+        static_cast<Real*>(a.L2)[c * N + q] = l2[c];
+        static_cast<Real*>(a.L3)[c * N + q] = l3[c];
+        if (a.Wlim) static_cast<Real*>(a.Wlim)[c * N + q] = wt[c];
+      }
+    } else {
+      Real un[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        const long long qc = c * N + q;
+        Real vn, wn;
+        if constexpr (MODE == MODE_STAGE1) {
+          un[c] = u[c] + rdt * l1[c];
+          vn = vt[c] + rdt * l2[c];
+          wn = wt[c] + rdt * l3[c];
+          static_cast<Real*>(a.Wt0out)[qc] = wt[c];
+        } else {
+          const Real u0 = static_cast<const Real*>(a.U0)[qc];
+          const Real v0 = static_cast<const Real*>(a.Vt0)[qc];
+          const Real w0 = static_cast<const Real*>(a.Wt0)[qc];
+          const Real c0 = MODE == MODE_STAGE2 ? Real(0.75) : Real(1.0 / 3.0);
+          const Real c1 = MODE == MODE_STAGE2 ? Real(0.25) : Real(2.0 / 3.0);
+          un[c] = c0 * u0 + c1 * (u[c] + rdt * l1[c]);
+          vn = c0 * v0 + c1 * (vt[c] + rdt * l2[c]);
+          wn = c0 * w0 + c1 * (wt[c] + rdt * l3[c]);
+        }
+        static_cast<Real*>(a.Uout)[qc] = un[c];
+        static_cast<Real*>(a.Vout)[qc] = vn;
+        static_cast<Real*>(a.Wout)[qc] = wn;
+      }
+      if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
+        double sx, sy;
+        speeds2<EQ>(un, gam, sx, sy);
+        bad |= !(sx <= DBL_MAX) || !(sy <= DBL_MAX);
+        ax = fmax(ax, sx);
+        ay = fmax(ay, sy);
+      }
+    }
+  }
+  if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
+    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    ax = block_max2(ax, red);
+    if (threadIdx.x == 0) atomicMax(&a.alpha_out[0], (unsigned long long)__double_as_longlong(ax));
+    ay = block_max2(ay, red);
+    if (threadIdx.x == 0) atomicMax(&a.alpha_out[1], (unsigned long long)__double_as_longlong(ay));
+  }
+}
+
+template <int EQ, class Real, int MODE>
+cudaError_t ysweep_launch(const Args2D& a, cudaStream_t s) {
+  constexpr size_t bytes = YLayout<EQ, Real>::bytes;
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(k_ysweep_2d<EQ, Real, MODE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const dim3 grid((a.nx + kColsY2D - 1) / kColsY2D, (a.ny + kRowsY2D - 1) / kRowsY2D);
+  k_ysweep_2d<EQ, Real, MODE><<<grid, kThreads2D, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int EQ, class Real>
+cudaError_t ysweep_mode(int mode, const Args2D& a, cudaStream_t s) {
+  switch (mode) {
+    case MODE_RHS: return ysweep_launch<EQ, Real, MODE_RHS>(a, s);
+    case MODE_STAGE1: return ysweep_launch<EQ, Real, MODE_STAGE1>(a, s);
+    case MODE_STAGE2: return ysweep_launch<EQ, Real, MODE_STAGE2>(a, s);
+    default: return ysweep_launch<EQ, Real, MODE_STAGE3>(a, s);
+  }
+}
+
+template <int EQ, class Real>
+cudaError_t xsweep_mode(int mode, const Args2D& a, cudaStream_t s) {
+  const dim3 grid((a.nx + kTileX2D - 1) / kTileX2D, a.ny);
+  if (mode == MODE_STAGE1) k_xsweep_2d<EQ, Real, MODE_STAGE1><<<grid, kThreads2D, 0, s>>>(a);
+  else k_xsweep_2d<EQ, Real, MODE_RHS><<<grid, kThreads2D, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_alpha_2d(int eq, bool fp32, const Args2D& a, cudaStream_t s) {
+  const long long N = (long long)a.nx * a.ny;
+  const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
+  if (eq == HWENO_BURGERS) {
+    if (fp32) k_alpha_2d<HWENO_BURGERS, float><<<blocks, 256, 0, s>>>(a);
+    else k_alpha_2d<HWENO_BURGERS, double><<<blocks, 256, 0, s>>>(a);
+  } else {
+    if (fp32) k_alpha_2d<HWENO_EULER, float><<<blocks, 256, 0, s>>>(a);
+    else k_alpha_2d<HWENO_EULER, double><<<blocks, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// The x-sweep only distinguishes stage 1 (which records dt) from the rest.
+cudaError_t launch_xsweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s) {
+  if (eq == HWENO_BURGERS)
+    return fp32 ? xsweep_mode<HWENO_BURGERS, float>(mode, a, s)
+                : xsweep_mode<HWENO_BURGERS, double>(mode, a, s);
+  return fp32 ? xsweep_mode<HWENO_EULER, float>(mode, a, s)
+              : xsweep_mode<HWENO_EULER, double>(mode, a, s);
+}
+
+cudaError_t launch_ysweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s) {
+  if (eq == HWENO_BURGERS)
+    return fp32 ? ysweep_mode<HWENO_BURGERS, float>(mode, a, s)
+                : ysweep_mode<HWENO_BURGERS, double>(mode, a, s);
+  return fp32 ? ysweep_mode<HWENO_EULER, float>(mode, a, s)
+              : ysweep_mode<HWENO_EULER, double>(mode, a, s);
+}
+
+}  // namespace hweno
