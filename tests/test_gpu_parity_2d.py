@@ -229,7 +229,8 @@ def test_full_size_periodic_translation_and_conservation(hw):
 
 def test_2d_reduces_to_1d_on_gpu(hw):
     """y-independent data with v = 0 and W = 0: the 2D kernels give the 1D
-    kernel's result."""
+    kernel's result (fixed dt: the 2D CFL step also counts the sound speed
+    in y)."""
     n, ny = 200, 9
     w1 = W.riemann1d(n, (1.0, 0.1, 1.0), (0.3, -0.2, 0.4))
     U1, V1 = w1.instance(0)
@@ -237,8 +238,8 @@ def test_2d_reduces_to_1d_on_gpu(hw):
     for c2, c1 in ((0, 0), (1, 1), (3, 2)):
         U2[c2] = U1[c1][None, :]; V2[c2] = V1[c1][None, :]
     w2 = make_w("euler", n, ny, U2, V2, np.zeros_like(U2), bc=("outflow", "outflow", "periodic", "periodic"))
-    g2 = gpu_run(hw, w2, 0.15, steps=5)
-    s = hw.Solver.from_workload(w1)
+    g2 = gpu_run(hw, w2, 0.15, steps=5, dt_mode=2, dt_fixed=1e-3)
+    s = hw.Solver.from_workload(w1, dt_mode=2, dt_fixed=1e-3)
     U, V = dev(w1.U), dev(w1.V)
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
     for _ in range(5):
