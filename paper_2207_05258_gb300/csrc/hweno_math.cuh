@@ -107,22 +107,62 @@ __device__ __forceinline__ Real combine_direct(const Cand<Real>& c, const Weight
   return qdiv(num, o0 + o1 + o2);
 }
 
-// Full interface flux of one (characteristic) field: f-hat = f-hat^+ + f-hat^-
-// from f^+ at i-1..i+1, f^- at i..i+2 and the scaled derivative data.
+// A quotient n / d whose division is deferred, so that the quotients of
+// several fields can share one reciprocal (resolve2). In FP32 the value is
+// already final (d = 1).
 template <class Real>
-__device__ __forceinline__ Real interface_flux(Real fpm, Real fp0, Real fpp, Real Hpm, Real Hp0,
-                                               Real Hpp, Real fm0, Real fm1, Real fm2, Real Hm0,
-                                               Real Hm1, Real Hm2, const Weights<Real>& w) {
+struct Frac {
+  Real n, d;
+};
+
+// n0/d0 and n1/d1 with one division: r = 1/(d0 d1). Both denominators lie in
+// [1e-40, 1e120] for any data the scheme meets (products of smoothness
+// indicators >= eps), so the product stays far inside the FP64 range.
+template <class Real>
+__device__ __forceinline__ void resolve2(const Frac<Real>& a, const Frac<Real>& b, Real& qa,
+                                         Real& qb) {
+  if constexpr (std::is_same<Real, double>::value) {
+    const Real r = Real(1) / (a.d * b.d);
+    qa = a.n * b.d * r;
+    qb = b.n * a.d * r;
+  } else {
+    qa = a.n;
+    qb = b.n;
+  }
+}
+
+template <class Real>
+__device__ __forceinline__ Real resolve1(const Frac<Real>& a) {
+  if constexpr (std::is_same<Real, double>::value) return a.n / a.d;
+  else return a.n;
+}
+
+// Full interface flux of one (characteristic) field: f-hat = f-hat^+ + f-hat^-
+// from f^+ at i-1..i+1, f^- at i..i+2 and the scaled derivative data, as a
+// deferred quotient (FP64: both sides over the common denominator).
+template <class Real>
+__device__ __forceinline__ Frac<Real> interface_flux_frac(Real fpm, Real fp0, Real fpp, Real Hpm,
+                                                          Real Hp0, Real Hpp, Real fm0, Real fm1,
+                                                          Real fm2, Real Hm0, Real Hm1, Real Hm2,
+                                                          const Weights<Real>& w) {
   const Cand<Real> a = candidates(fpm, fp0, fpp, Hpm, Hp0, Hpp, w.eps);
   const Cand<Real> b = candidates(fm2, fm1, fm0, -Hm2, -Hm1, -Hm0, w.eps);  // mirror
   if constexpr (std::is_same<Real, double>::value) {
     Real na, da, nb, db;
     combine_nd(a, w, na, da);
     combine_nd(b, w, nb, db);
-    return (na * db + nb * da) / (da * db);
+    return Frac<Real>{na * db + nb * da, da * db};
   } else {
-    return combine_direct(a, w) + combine_direct(b, w);
+    return Frac<Real>{combine_direct(a, w) + combine_direct(b, w), Real(1)};
   }
+}
+
+template <class Real>
+__device__ __forceinline__ Real interface_flux(Real fpm, Real fp0, Real fpp, Real Hpm, Real Hp0,
+                                               Real Hpp, Real fm0, Real fm1, Real fm2, Real Hm0,
+                                               Real Hm1, Real Hm2, const Weights<Real>& w) {
+  return resolve1(interface_flux_frac(fpm, fp0, fpp, Hpm, Hp0, Hpp, fm0, fm1, fm2, Hm0, Hm1,
+                                      Hm2, w));
 }
 
 // Scaled derivative flux D = dx (h-hat^+ + h-hat^-) = dx (p_0'^+ + p_0'^-),
@@ -140,10 +180,10 @@ __device__ __forceinline__ Real derivative_flux(Real fpm, Real fp0, Real fpp, Re
 }
 
 // HWENO limiter (Sec. 2.2) in scaled form: point values um, u0, up and
-// Vm = dx v_{i-1}, Vp = dx v_{i+1}; returns dx * v-tilde_i.
+// Vm = dx v_{i-1}, Vp = dx v_{i+1}; dx * v-tilde_i as a deferred quotient.
 template <class Real>
-__device__ __forceinline__ Real limited_derivative(Real um, Real u0, Real up, Real Vm, Real Vp,
-                                                   const Weights<Real>& w) {
+__device__ __forceinline__ Frac<Real> limited_derivative_frac(Real um, Real u0, Real up, Real Vm,
+                                                              Real Vp, const Weights<Real>& w) {
   const Real sV = Vm + Vp, dV = Vm - Vp;
   const Real lap = um - Real(2) * u0 + up;
   const Real q0 = Real(0.75) * (up - um) - Real(0.25) * sV;  // dx q_0'(x_i) = a_1
@@ -166,14 +206,35 @@ __device__ __forceinline__ Real limited_derivative(Real um, Real u0, Real up, Re
     const Real L1 = w.d1 * (b1 + tau) * b02;
     const Real L2 = w.d2 * (b2 + tau) * b01;
     const Real num = L0 * (q0 - w.d1 * q1 - w.d2 * q2) + L1 * q1 + L2 * q2;
-    return num / (w.d0 * L0 + L1 + L2);
+    return Frac<Real>{num, w.d0 * L0 + L1 + L2};
   } else {
     const Real l0 = w.d0 + w.d0 * qdiv(tau, b0);
     const Real l1 = w.d1 + w.d1 * qdiv(tau, b1);
     const Real l2 = w.d2 + w.d2 * qdiv(tau, b2);
     const Real num = l0 * w.id0 * (q0 - w.d1 * q1 - w.d2 * q2) + l1 * q1 + l2 * q2;
-    return qdiv(num, l0 + l1 + l2);
+    return Frac<Real>{qdiv(num, l0 + l1 + l2), Real(1)};
   }
+}
+
+template <class Real>
+__device__ __forceinline__ Real limited_derivative(Real um, Real u0, Real up, Real Vm, Real Vp,
+                                                   const Weights<Real>& w) {
+  return resolve1(limited_derivative_frac(um, u0, up, Vm, Vp, w));
+}
+
+// Reciprocal square root (FP64: CUDA's rsqrt, within one ulp; FP32: the
+// hardware approximation).
+template <class Real>
+__device__ __forceinline__ Real rsq(Real x) {
+  if constexpr (std::is_same<Real, double>::value) return rsqrt(x);
+  else return rsqrtf(x);
+}
+
+// c and 1/c from c^2 with one reciprocal square root.
+template <class Real>
+__device__ __forceinline__ void sound_speed(Real c2, Real& c, Real& ic) {
+  ic = rsq(c2);
+  c = c2 * ic;
 }
 
 // ---------------------------------------------------------------------------
@@ -190,9 +251,8 @@ struct Eigen {
 };
 
 template <class Real, int M>
-__device__ __forceinline__ void euler_eigen(int dir, Real u, Real v, Real H, Real c, Real gm1,
-                                            Eigen<Real, M>& e) {
-  const Real ic = Real(1) / c;
+__device__ __forceinline__ void euler_eigen(int dir, Real u, Real v, Real H, Real c, Real ic,
+                                            Real gm1, Eigen<Real, M>& e) {
   const Real b1 = gm1 * ic * ic;
   if constexpr (M == 3) {
     const Real q = Real(0.5) * u * u;

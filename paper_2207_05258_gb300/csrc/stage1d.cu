@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
   constexpr bool EUL = EQ == HWENO_EULER;
   __shared__ Real sU[M][NP], sV[M][NP];
   __shared__ Real sFp[M][NP], sFm[M][NP], sHp[M][NP], sHm[M][NP];
-  __shared__ Real sE[EUL ? 4 : 1][EUL ? NP : 1];  // sqrt(rho), u, H, c
+  __shared__ Real sE[EUL ? 4 : 1][EUL ? NP : 1];  // sqrt(rho), u, H, c^2
   __shared__ Real sF[M][NF], sD[M][NF];
   __shared__ double red[kThreads1D / 32];
 
@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
         F[0] = Real(0.5) * u[0] * u[0];
         H[0] = u[0] * v[0];
       } else {
-        const Real ir = Real(1) / u[0];
+        // 1/rho and sqrt(rho) from one reciprocal square root
+        const Real rr = rsq(u[0]);
+        const Real ir = rr * rr;
         const Real vel = u[1] * ir;
         const Real p = gm1 * (u[2] - Real(0.5) * u[1] * vel);
         const Real Ep = u[2] + p;
@@ -200,10 +202,10 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
         H[0] = v[1];
         H[1] = v[1] * vel + u[1] * dvel + dp;
         H[2] = (v[2] + dp) * vel + Ep * dvel;
-        sE[0][g] = sqrt(u[0]);
+        sE[0][g] = u[0] * rr;
         sE[1][g] = vel;
         sE[2][g] = Ep * ir;
-        sE[3][g] = sqrt(gam * p * ir);
+        sE[3][g] = gam * p * ir;
       }
 #pragma unroll
       for (int c = 0; c < M; ++c) {
@@ -238,21 +240,26 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
         uu = mo * ir;
         HH = (E + gm1 * (E - Real(0.5) * mo * uu)) * ir;
       }
-      cc = sqrt(gm1 * (HH - Real(0.5) * uu * uu));
+      Real ic;
+      sound_speed(gm1 * (HH - Real(0.5) * uu * uu), cc, ic);
       Eigen<Real, 3> e;
-      euler_eigen<Real, 3>(0, uu, Real(0), HH, cc, gm1, e);
-      Real out[3] = {Real(0), Real(0), Real(0)};
+      euler_eigen<Real, 3>(0, uu, Real(0), HH, cc, ic, gm1, e);
+      Frac<Real> fr[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const Real l0 = e.L[q][0], l1 = e.L[q][1], l2 = e.L[q][2];
         auto pj = [&](Real (*A)[NP], int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
-        const Real f = interface_flux(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1),
-                                      pj(sHp, gl - 1), pj(sHp, gl), pj(sHp, gl + 1),
-                                      pj(sFm, gl), pj(sFm, gl + 1), pj(sFm, gl + 2),
-                                      pj(sHm, gl), pj(sHm, gl + 1), pj(sHm, gl + 2), w);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) out[c] += e.R[c][q] * f;
+        fr[q] = interface_flux_frac(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1),
+                                    pj(sHp, gl - 1), pj(sHp, gl), pj(sHp, gl + 1),
+                                    pj(sFm, gl), pj(sFm, gl + 1), pj(sFm, gl + 2),
+                                    pj(sHm, gl), pj(sHm, gl + 1), pj(sHm, gl + 2), w);
       }
+      Real f[3];
+      resolve2(fr[0], fr[1], f[0], f[1]);
+      f[2] = resolve1(fr[2]);
+      Real out[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[c] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
 #pragma unroll
       for (int c = 0; c < 3; ++c) sF[c][j] = out[c];
     }
@@ -284,16 +291,21 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
         vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
                                    dx * sV[c][g + 1], w) * idx;
     } else if constexpr (EUL) {
+      Real cg, icg;
+      sound_speed(sE[3][g], cg, icg);
       Eigen<Real, 3> e;
-      euler_eigen<Real, 3>(0, sE[1][g], Real(0), sE[2][g], sE[3][g], gm1, e);
-      Real z[3];
+      euler_eigen<Real, 3>(0, sE[1][g], Real(0), sE[2][g], cg, icg, gm1, e);
+      Frac<Real> zr[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const Real l0 = e.L[q][0], l1q = e.L[q][1], l2q = e.L[q][2];
         auto pj = [&](Real (*A)[NP], int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
-        z[q] = limited_derivative(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1), dx * pj(sV, g - 1),
-                                  dx * pj(sV, g + 1), w);
+        zr[q] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
+                                        dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
       }
+      Real z[3];
+      resolve2(zr[0], zr[1], z[0], z[1]);
+      z[2] = resolve1(zr[2]);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         vt[c] = (e.R[c][0] * z[0] + e.R[c][1] * z[1] + e.R[c][2] * z[2]) * idx;

@@ -102,12 +102,12 @@ __device__ __forceinline__ void speeds2(const Real* U, Real gam, double& sx, dou
 template <class Real, int DIR>
 struct Char2 {
   Real un, ut, H, c, q, b1, b2, ic;
-  __device__ __forceinline__ void init(Real u, Real v, Real H_, Real c_, Real gm1) {
+  // sound speed from c^2 (one reciprocal square root gives c and 1/c)
+  __device__ __forceinline__ void init(Real u, Real v, Real H_, Real c2, Real gm1) {
     un = DIR == 0 ? u : v;
     ut = DIR == 0 ? v : u;
     H = H_;
-    c = c_;
-    ic = Real(1) / c_;
+    sound_speed(c2, c, ic);
     q = Real(0.5) * (u * u + v * v);
     b1 = gm1 * ic * ic;
     b2 = b1 * q;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(Args2D a) {
   constexpr int NP = kTileX2D + 4, NF = kTileX2D + 1;
   __shared__ Real sU[M][NP], sV[M][NP];
   __shared__ Real sFp[M][NP], sFm[M][NP], sHp[M][NP], sHm[M][NP], sEta[M][NP];
-  __shared__ Real sE[EUL ? 5 : 1][EUL ? NP : 1];  // sqrt(rho), u, v, H, c
+  __shared__ Real sE[EUL ? 5 : 1][EUL ? NP : 1];  // sqrt(rho), u, v, H, c^2
   __shared__ Real sF[M][NF], sD[M][NF], sN[M][NF];
 
   if (a.skip_done && !(a.t[0] < a.t_end)) return;
@@ -325,11 +325,11 @@ __global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(Args2D a) {
         sEta[c][g] = E[c];
       }
       if constexpr (EUL) {
-        sE[0][g] = sqrt(u[0]);
+        sE[0][g] = u[0] * rsq(u[0]);
         sE[1][g] = pq.u;
         sE[2][g] = pq.v;
         sE[3][g] = pq.Ep * pq.ir;
-        sE[4][g] = sqrt(gam * pq.p * pq.ir);
+        sE[4][g] = gam * pq.p * pq.ir;
       }
     }
   }
@@ -356,17 +356,20 @@ __global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(Args2D a) {
         const Prim2<Real> pm = prim2(Um, gm1);
         uu = pm.u; vv = pm.v; HH = pm.Ep * pm.ir;
       }
-      const Real cc = sqrt(gm1 * (HH - Real(0.5) * (uu * uu + vv * vv)));
       Char2<Real, 0> e;
-      e.init(uu, vv, HH, cc, gm1);
-      Real fch[4];
+      e.init(uu, vv, HH, gm1 * (HH - Real(0.5) * (uu * uu + vv * vv)), gm1);
+      Frac<Real> fr[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         auto pj = [&](Real (*A)[NP], int g) { return e.left(r, A[0][g], A[1][g], A[2][g], A[3][g]); };
-        fch[r] = interface_flux(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1), pj(sHp, gl - 1),
-                                pj(sHp, gl), pj(sHp, gl + 1), pj(sFm, gl), pj(sFm, gl + 1),
-                                pj(sFm, gl + 2), pj(sHm, gl), pj(sHm, gl + 1), pj(sHm, gl + 2), w);
+        fr[r] = interface_flux_frac(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1),
+                                    pj(sHp, gl - 1), pj(sHp, gl), pj(sHp, gl + 1), pj(sFm, gl),
+                                    pj(sFm, gl + 1), pj(sFm, gl + 2), pj(sHm, gl),
+                                    pj(sHm, gl + 1), pj(sHm, gl + 2), w);
       }
+      Real fch[4];
+      resolve2(fr[0], fr[1], fch[0], fch[1]);
+      resolve2(fr[2], fr[3], fch[2], fch[3]);
       Real out[4];
       e.right(fch, out);
 #pragma unroll
@@ -401,13 +404,16 @@ __global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(Args2D a) {
     } else if constexpr (EUL) {
       Char2<Real, 0> e;
       e.init(sE[1][g], sE[2][g], sE[3][g], sE[4][g], gm1);
-      Real z[4];
+      Frac<Real> zr[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         auto pj = [&](Real (*A)[NP], int gg) { return e.left(r, A[0][gg], A[1][gg], A[2][gg], A[3][gg]); };
-        z[r] = limited_derivative(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1), dx * pj(sV, g - 1),
-                                  dx * pj(sV, g + 1), w);
+        zr[r] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
+                                        dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
       }
+      Real z[4];
+      resolve2(zr[0], zr[1], z[0], z[1]);
+      resolve2(zr[2], zr[3], z[2], z[3]);
       e.right(z, vt);
 #pragma unroll
       for (int c = 0; c < 4; ++c) vt[c] *= idx;
@@ -513,11 +519,11 @@ __global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
         PT(6, c)[k] = X[c];
       }
       if constexpr (EUL) {
-        sEig[0 * P + k] = sqrt(u[0]);
+        sEig[0 * P + k] = u[0] * rsq(u[0]);
         sEig[1 * P + k] = pq.u;
         sEig[2 * P + k] = pq.v;
         sEig[3 * P + k] = pq.Ep * pq.ir;
-        sEig[4 * P + k] = sqrt(gam * pq.p * pq.ir);
+        sEig[4 * P + k] = gam * pq.p * pq.ir;
       }
     }
   }
@@ -550,20 +556,22 @@ __global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
         const Prim2<Real> pm = prim2(Um, gm1);
         uu = pm.u; vv = pm.v; HH = pm.Ep * pm.ir;
       }
-      const Real cc = sqrt(gm1 * (HH - Real(0.5) * (uu * uu + vv * vv)));
       Char2<Real, 1> e;
-      e.init(uu, vv, HH, cc, gm1);
-      Real fch[4];
+      e.init(uu, vv, HH, gm1 * (HH - Real(0.5) * (uu * uu + vv * vv)), gm1);
+      Frac<Real> fr[4];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         auto pj = [&](int qty, int g) {
           const int kk = g * C + col;
           return e.left(rr, PT(qty, 0)[kk], PT(qty, 1)[kk], PT(qty, 2)[kk], PT(qty, 3)[kk]);
         };
-        fch[rr] = interface_flux(pj(2, gl - 1), pj(2, gl), pj(2, gl + 1), pj(4, gl - 1), pj(4, gl),
-                                 pj(4, gl + 1), pj(3, gl), pj(3, gl + 1), pj(3, gl + 2), pj(5, gl),
-                                 pj(5, gl + 1), pj(5, gl + 2), w);
+        fr[rr] = interface_flux_frac(pj(2, gl - 1), pj(2, gl), pj(2, gl + 1), pj(4, gl - 1),
+                                     pj(4, gl), pj(4, gl + 1), pj(3, gl), pj(3, gl + 1),
+                                     pj(3, gl + 2), pj(5, gl), pj(5, gl + 1), pj(5, gl + 2), w);
       }
+      Real fch[4];
+      resolve2(fr[0], fr[1], fch[0], fch[1]);
+      resolve2(fr[2], fr[3], fch[2], fch[3]);
       Real out[4];
       e.right(fch, out);
 #pragma unroll
@@ -612,15 +620,18 @@ __global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
     } else if constexpr (EUL) {
       Char2<Real, 1> e;
       e.init(sEig[P + kc], sEig[2 * P + kc], sEig[3 * P + kc], sEig[4 * P + kc], gm1);
-      Real z[4];
+      Frac<Real> zr[4];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         auto pj = [&](int qty, int kk) {
           return e.left(rr, PT(qty, 0)[kk], PT(qty, 1)[kk], PT(qty, 2)[kk], PT(qty, 3)[kk]);
         };
-        z[rr] = limited_derivative(pj(0, kc - C), pj(0, kc), pj(0, kc + C), dy * pj(1, kc - C),
-                                   dy * pj(1, kc + C), w);
+        zr[rr] = limited_derivative_frac(pj(0, kc - C), pj(0, kc), pj(0, kc + C),
+                                         dy * pj(1, kc - C), dy * pj(1, kc + C), w);
       }
+      Real z[4];
+      resolve2(zr[0], zr[1], z[0], z[1]);
+      resolve2(zr[2], zr[3], z[2], z[3]);
       e.right(z, wt);
 #pragma unroll
       for (int c = 0; c < 4; ++c) wt[c] *= idy;
