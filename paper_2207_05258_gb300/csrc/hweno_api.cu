@@ -39,6 +39,8 @@ struct hweno_ctx {
   long long* d_inst_off = nullptr;
   double* d_inst_dx = nullptr;
   double* d_inst_hx = nullptr;
+  double* d_inst_geo = nullptr;   // per instance dx, 1/dx, 1/dx^2
+  float* d_inst_geof = nullptr;   // the same in FP32
   std::vector<double> inst_dx;
   // per-instance scalars
   unsigned long long* d_alpha = nullptr;  // 3 slots x batch (x 2 directions in 2D)
@@ -105,7 +107,7 @@ int dalloc(hweno_ctx* c, T** p, size_t bytes) {
 
 void free_all(hweno_ctx* c) {
   void* ptrs[] = {c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
-                  c->d_inst_hx, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
+                  c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
                   c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht};
   for (void* p : ptrs)
@@ -129,6 +131,10 @@ SchemeParams scheme_params(const hweno_ctx* c) {
   sp.dmr_angle = c->bc.dmr_angle;
   sp.dmr_tan = std::tan(c->bc.dmr_angle);
   sp.dmr_sin = std::sin(c->bc.dmr_angle);
+  const double tab[10] = {c->opt.lin_w[0], c->opt.lin_w[1], c->opt.lin_w[2], c->opt.lim_d[0],
+                          c->opt.lim_d[1], c->opt.lim_d[2], c->opt.eps, 1.0 / c->opt.lin_w[0],
+                          1.0 / c->opt.lim_d[0], c->gamma};
+  for (int i = 0; i < 10; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
   return sp;
 }
 
@@ -150,6 +156,8 @@ Args1D base_args_1d(const hweno_ctx* c) {
   a.inst_off = c->d_inst_off;
   a.inst_dx = c->d_inst_dx;
   a.inst_hx = c->d_inst_hx;
+  a.inst_geo = c->d_inst_geo;
+  a.inst_geof = c->d_inst_geof;
   a.status = c->d_status;
   a.sp = scheme_params(c);
   return a;
@@ -241,6 +249,9 @@ Args2D base_args_2d(const hweno_ctx* c) {
   a.dy = (c->y1 - c->y0) / c->ny;
   a.hx = step_h(c, a.dx);
   a.hy = step_h(c, a.dy);
+  const double geo[6] = {a.dx, 1.0 / a.dx, 1.0 / (a.dx * a.dx), a.dy, 1.0 / a.dy,
+                         1.0 / (a.dy * a.dy)};
+  for (int i = 0; i < 6; ++i) { a.geod[i] = geo[i]; a.geof[i] = (float)geo[i]; }
   a.x0 = c->x0;
   a.y0 = c->y0;
   a.status = c->d_status;
@@ -453,6 +464,8 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       (rc = dalloc(c, &c->d_inst_off, sizeof(long long) * B)) ||
       (rc = dalloc(c, &c->d_inst_dx, sizeof(double) * B)) ||
       (rc = dalloc(c, &c->d_inst_hx, sizeof(double) * B)) ||
+      (rc = dalloc(c, &c->d_inst_geo, sizeof(double) * 3 * B)) ||
+      (rc = dalloc(c, &c->d_inst_geof, sizeof(float) * 3 * B)) ||
       (rc = dalloc(c, &c->d_alpha, sizeof(unsigned long long) * 3 * B * 2)) ||
       (rc = dalloc(c, &c->d_dt, sizeof(double) * B)) ||
       (rc = dalloc(c, &c->d_lands, sizeof(int) * B)) ||
@@ -470,7 +483,16 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
     delete c;
     return rc;
   }
+  std::vector<double> geo(3 * B);
+  std::vector<float> geof(3 * B);
+  for (size_t k = 0; k < B; ++k) {
+    const double d = c->inst_dx[k];
+    const double g3[3] = {d, 1.0 / d, 1.0 / (d * d)};
+    for (int i = 0; i < 3; ++i) { geo[3 * k + i] = g3[i]; geof[3 * k + i] = (float)g3[i]; }
+  }
   const bool copy_failed =
+      cudaMemcpy(c->d_inst_geo, geo.data(), sizeof(double) * 3 * B, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_inst_geof, geof.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_tile_inst, tinst.data(), sizeof(int) * tinst.size(), cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_tile_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_n, c->nx.data(), sizeof(int) * B, cudaMemcpyHostToDevice) ||

@@ -28,6 +28,47 @@ struct Weights {
   Real ig0, id0;         // 1/gamma_0, 1/d_0
 };
 
+// Largest finite value of the state precision.
+template <class Real>
+__device__ __forceinline__ constexpr Real real_max() {
+  if constexpr (std::is_same<Real, double>::value) return 1.7976931348623157e308;
+  else return 3.40282347e38f;
+}
+
+// Pick the FP64 or FP32 copy of a host-converted constant table.
+template <class Real>
+__device__ __forceinline__ const Real* pick(const double* d, const float* f) {
+  if constexpr (std::is_same<Real, double>::value) return d;
+  else return f;
+}
+
+template <class Real>
+__device__ __forceinline__ Weights<Real> weights_from(const Real* v) {
+  Weights<Real> w;
+  w.g0 = v[0]; w.g1 = v[1]; w.g2 = v[2];
+  w.d0 = v[3]; w.d1 = v[4]; w.d2 = v[5];
+  w.eps = v[6];
+  w.ig0 = v[7];
+  w.id0 = v[8];
+  return w;
+}
+
+// Maximum over the CTA (red: one slot per warp); the result is valid in
+// warp 0. Contains barriers: call from every thread.
+template <class T>
+__device__ __forceinline__ T block_max_t(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(0);
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
 // Quantities of one "+" reconstruction (Sec. 2.1) from f^+ and H = dx h^+ on
 // the stencil {i-1, i, i+1}: the three candidate values at x_{i+1/2}, the
 // smoothness indicators and the scaled derivative flux D = dx p_0'.

@@ -48,7 +48,9 @@ constexpr size_t kOffInstN = kOffStatus + 256;                          // int
 constexpr size_t kOffInstOff = kOffInstN + 256;                         // long long
 constexpr size_t kOffInstDx = kOffInstOff + 256;                        // double
 constexpr size_t kOffInstHx = kOffInstDx + 256;                         // double
-constexpr size_t kOffTileInst = kOffInstHx + 256;                       // int[kMaxTiles]
+constexpr size_t kOffInstGeo = kOffInstHx + 256;                       // double[3]
+constexpr size_t kOffInstGeof = kOffInstGeo + 256;                      // float[3]
+constexpr size_t kOffTileInst = kOffInstGeof + 256;                     // int[kMaxTiles]
 constexpr size_t kOffTileStart = kOffTileInst + align256(sizeof(int) * kMaxTiles);
 constexpr size_t kNoallocScratchBytes = kOffTileStart + align256(sizeof(int) * kMaxTiles);
 
@@ -77,6 +79,12 @@ __global__ void k_noalloc_setup(unsigned char* base, int ntiles, int n, double d
     *reinterpret_cast<long long*>(base + kOffInstOff) = 0;
     *reinterpret_cast<double*>(base + kOffInstDx) = dx;
     *reinterpret_cast<double*>(base + kOffInstHx) = hx;
+    double* geo = reinterpret_cast<double*>(base + kOffInstGeo);
+    float* geof = reinterpret_cast<float*>(base + kOffInstGeof);
+    geo[0] = dx;
+    geo[1] = 1.0 / dx;
+    geo[2] = 1.0 / (dx * dx);
+    for (int i = 0; i < 3; ++i) geof[i] = (float)geo[i];
   }
 }
 
@@ -139,6 +147,8 @@ extern "C" int hweno_step_1d_noalloc(int equation, int nx, double x0, double x1,
   a.inst_off = reinterpret_cast<const long long*>(base + kOffInstOff);
   a.inst_dx = reinterpret_cast<const double*>(base + kOffInstDx);
   a.inst_hx = reinterpret_cast<const double*>(base + kOffInstHx);
+  a.inst_geo = reinterpret_cast<const double*>(base + kOffInstGeo);
+  a.inst_geof = reinterpret_cast<const float*>(base + kOffInstGeof);
   a.status = reinterpret_cast<unsigned*>(base + kOffStatus);
   a.dt = reinterpret_cast<double*>(base + kOffDt);
   a.lands = reinterpret_cast<int*>(base + kOffLands);
@@ -153,6 +163,9 @@ extern "C" int hweno_step_1d_noalloc(int equation, int nx, double x0, double x1,
   sp.gas_gamma = gamma;
   sp.bc[0] = bc->xlo; sp.bc[1] = bc->xhi; sp.bc[2] = bc->ylo; sp.bc[3] = bc->yhi;
   for (int i = 0; i < 4; ++i) { sp.inflow[i] = bc->inflow[i]; sp.pre[i] = bc->pre[i]; }
+  const double tab[10] = {o.lin_w[0], o.lin_w[1], o.lin_w[2], o.lim_d[0], o.lim_d[1],
+                          o.lim_d[2], o.eps, 1.0 / o.lin_w[0], 1.0 / o.lim_d[0], gamma};
+  for (int i = 0; i < 10; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
   a.t = t;
   a.t_end = t_end;
   a.skip_done = 1;

@@ -26,6 +26,10 @@ struct SchemeParams {
   double inflow[4], pre[4];
   double dmr_x0, dmr_speed, dmr_angle;
   double dmr_tan, dmr_sin;  // tan and sin of dmr_angle, evaluated on the host
+  // constants in both precisions, converted once on the host:
+  // g0, g1, g2, d0, d1, d2, eps, 1/g0, 1/d0, gas gamma
+  double wd[10];
+  float wf[10];
 };
 
 // Arguments of one 1D launch (all instances of the batch).
@@ -49,6 +53,8 @@ struct Args1D {
   const long long* inst_off;  // first point of each instance
   const double* inst_dx;
   const double* inst_hx;      // dx or dx^{5/3} per dt_mode
+  const double* inst_geo;     // per instance dx, 1/dx, 1/dx^2 (FP64)
+  const float* inst_geof;     // the same in FP32
   // per-instance scalars (device)
   const double* t;
   double t_end;
@@ -89,6 +95,8 @@ struct Args2D {
   void* Wlim;
   int nx, ny;
   double dx, dy, hx, hy;  // mesh widths; h of the time-step rule
+  double geod[6];         // dx, 1/dx, 1/dx^2, dy, 1/dy, 1/dy^2
+  float geof[6];
   double x0, y0;
   const double* t;
   double t_end;

@@ -61,17 +61,6 @@ __device__ __forceinline__ Real wave_speed(const Real* u, Real gam) {
   }
 }
 
-template <class Real>
-__device__ __forceinline__ Weights<Real> make_weights(const SchemeParams& sp) {
-  Weights<Real> w;
-  w.g0 = Real(sp.lin_w[0]); w.g1 = Real(sp.lin_w[1]); w.g2 = Real(sp.lin_w[2]);
-  w.d0 = Real(sp.lim_d[0]); w.d1 = Real(sp.lim_d[1]); w.d2 = Real(sp.lim_d[2]);
-  w.eps = Real(sp.eps);
-  w.ig0 = Real(1.0 / sp.lin_w[0]);
-  w.id0 = Real(1.0 / sp.lim_d[0]);
-  return w;
-}
-
 // Time step of an instance from the wave speed of u^n (dt_mode), clipped to
 // land on t_end. Same expression order as the problem statement:
 // dt = cfl / (alpha / h).
@@ -89,47 +78,35 @@ __device__ __forceinline__ double time_step(const SchemeParams& sp, double alpha
   return lands ? rest : dt;
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  }
-  return v;
-}
-
 // Wave speed of the stage input, per instance (alpha of Sec. 2.1).
 template <int EQ, class Real>
-__global__ void __launch_bounds__(kThreads1D) k_alpha_1d(Args1D a) {
+__global__ void __launch_bounds__(kThreads1D) k_alpha_1d(const __grid_constant__ Args1D a) {
   constexpr int M = Dim1<EQ>::M;
-  __shared__ double red[kThreads1D / 32];
+  __shared__ Real red[kThreads1D / 32];
   const int b = blockIdx.x;
   const int k = a.tile_inst[b], s = a.tile_start[b], n = a.inst_n[k];
   if (a.skip_done && !(a.t[k] < a.t_end)) return;
   const int np = min(kTile1D, n - s);
   const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
-  const Real gam = Real(a.sp.gas_gamma);
-  double amax = 0.0;
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+  Real amax = Real(0);
   bool bad = false;
   for (int j = threadIdx.x; j < np; j += blockDim.x) {
     Real u[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + s + j];
-    const double sp = (double)wave_speed<EQ>(u, gam);
-    bad |= !(sp <= DBL_MAX);
+    const Real sp = wave_speed<EQ>(u, gam);
+    bad |= !(sp <= real_max<Real>());
     amax = fmax(amax, sp);
   }
   if (bad) atomicOr(a.status, STATUS_NONFINITE);
-  amax = block_max(amax, red);
+  amax = block_max_t(amax, red);
   if (threadIdx.x == 0)
-    atomicMax(&a.alpha_out[k], (unsigned long long)__double_as_longlong(amax));
+    atomicMax(&a.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
 }
 
 template <int EQ, class Real, int MODE>
-__global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
+__global__ void __launch_bounds__(kThreads1D) k_stage_1d(const __grid_constant__ Args1D a) {
   constexpr int M = Dim1<EQ>::M;
   constexpr int NP = kTile1D + 4;  // points with two ghosts per side
   constexpr int NF = kTile1D + 1;  // interfaces
@@ -138,28 +115,33 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
   __shared__ Real sFp[M][NP], sFm[M][NP], sHp[M][NP], sHm[M][NP];
   __shared__ Real sE[EUL ? 4 : 1][EUL ? NP : 1];  // sqrt(rho), u, H, c^2
   __shared__ Real sF[M][NF], sD[M][NF];
-  __shared__ double red[kThreads1D / 32];
+  __shared__ Real red[kThreads1D / 32];
+  __shared__ double s_dt;
 
   const int b = blockIdx.x;
   const int k = a.tile_inst[b], s = a.tile_start[b], n = a.inst_n[k];
   if (a.skip_done && !(a.t[k] < a.t_end)) return;
   const int np = min(kTile1D, n - s);
   const long long off = a.inst_off[k] * M;
-  const double dxd = a.inst_dx[k];
-  const Real dx = Real(dxd), idx = Real(1.0 / dxd), idx2 = Real(1.0 / (dxd * dxd));
+  const Real* geo = pick<Real>(a.inst_geo, a.inst_geof) + 3 * k;
+  const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
   const Real alpha = Real(a.alpha_in[k]);
-  const Real gam = Real(a.sp.gas_gamma), gm1 = gam - Real(1);
-  const Weights<Real> w = make_weights<Real>(a.sp);
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+  const Real gm1 = gam - Real(1);
+  const Weights<Real> w = weights_from(pick<Real>(a.sp.wd, a.sp.wf));
 
-  double dt = 0.0;
-  if constexpr (MODE == MODE_STAGE1) {
-    int lands;
-    dt = time_step(a.sp, a.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
-    if (s == 0 && threadIdx.x == 0) { a.dt[k] = dt; a.lands[k] = lands; }
-  } else if constexpr (MODE != MODE_RHS) {
-    dt = a.dt[k];
+  // time step: once per CTA (thread 0), read back after the barriers below
+  if (threadIdx.x == 0) {
+    double dt = 0.0;
+    if constexpr (MODE == MODE_STAGE1) {
+      int lands;
+      dt = time_step(a.sp, a.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
+      if (s == 0) { a.dt[k] = dt; a.lands[k] = lands; }
+    } else if constexpr (MODE != MODE_RHS) {
+      dt = a.dt[k];
+    }
+    s_dt = dt;
   }
-  const Real rdt = Real(dt);
 
   // 1-2: tile load with ghosts; point fluxes and splitting
   {
@@ -272,7 +254,8 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
   __syncthreads();
 
   // 4: points
-  double amax = 0.0;
+  const Real rdt = Real(s_dt);
+  Real amax = Real(0);
   bool bad = false;
   for (int j = threadIdx.x; j < np; j += blockDim.x) {
     const int g = j + 2;
@@ -343,17 +326,17 @@ __global__ void __launch_bounds__(kThreads1D) k_stage_1d(Args1D a) {
         static_cast<Real*>(a.Vout)[q] = vn[c];
       }
       if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
-        const double sp = (double)wave_speed<EQ>(un, gam);
-        bad |= !(sp <= DBL_MAX);
+        const Real sp = wave_speed<EQ>(un, gam);
+        bad |= !(sp <= real_max<Real>());
         amax = fmax(amax, sp);
       }
     }
   }
   if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
-    amax = block_max(amax, red);
+    amax = block_max_t(amax, red);
     if (threadIdx.x == 0)
-      atomicMax(&a.alpha_out[k], (unsigned long long)__double_as_longlong(amax));
+      atomicMax(&a.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
   }
 }
 

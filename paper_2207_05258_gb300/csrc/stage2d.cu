@@ -84,14 +84,14 @@ __device__ __forceinline__ void jvp2(const Real* U, const Prim2<Real>& q, const 
 }
 
 template <int EQ, class Real>
-__device__ __forceinline__ void speeds2(const Real* U, Real gam, double& sx, double& sy) {
+__device__ __forceinline__ void speeds2(const Real* U, Real gam, Real& sx, Real& sy) {
   if constexpr (EQ == HWENO_BURGERS) {
-    sx = sy = (double)fabs(U[0]);
+    sx = sy = fabs(U[0]);
   } else {
     const Prim2<Real> q = prim2(U, gam - Real(1));
     const Real c = sqrt(gam * q.p * q.ir);
-    sx = (double)(fabs(q.u) + c);
-    sy = (double)(fabs(q.v) + c);
+    sx = fabs(q.u) + c;
+    sy = fabs(q.v) + c;
   }
 }
 
@@ -133,17 +133,6 @@ struct Char2 {
   }
 };
 
-template <class Real>
-__device__ __forceinline__ Weights<Real> make_weights2(const SchemeParams& sp) {
-  Weights<Real> w;
-  w.g0 = Real(sp.lin_w[0]); w.g1 = Real(sp.lin_w[1]); w.g2 = Real(sp.lin_w[2]);
-  w.d0 = Real(sp.lim_d[0]); w.d1 = Real(sp.lim_d[1]); w.d2 = Real(sp.lim_d[2]);
-  w.eps = Real(sp.eps);
-  w.ig0 = Real(1.0 / sp.lin_w[0]);
-  w.id0 = Real(1.0 / sp.lim_d[0]);
-  return w;
-}
-
 __device__ __forceinline__ double time_step2(const Args2D& a, int& lands) {
   double dt;
   if (a.sp.dt_mode == 2) {
@@ -155,19 +144,6 @@ __device__ __forceinline__ double time_step2(const Args2D& a, int& lands) {
   const double rest = a.t_end - a.t[0];
   lands = dt >= rest;
   return lands ? rest : dt;
-}
-
-__device__ __forceinline__ double block_max2(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  }
-  return v;
 }
 
 // Ghost handling along one direction. kind: 0 copy, 1 mirror, 2 imposed
@@ -228,38 +204,40 @@ __device__ __forceinline__ float refl2(int c) {
 
 // ---------------------------------------------------------------------------
 template <int EQ, class Real>
-__global__ void __launch_bounds__(256) k_alpha_2d(Args2D a) {
+__global__ void __launch_bounds__(256) k_alpha_2d(const __grid_constant__ Args2D a) {
   constexpr int M = Dim2<EQ>::M;
-  __shared__ double red[8];
+  __shared__ Real red[8];
   if (a.skip_done && !(a.t[0] < a.t_end)) return;
   const long long N = (long long)a.nx * a.ny;
   const Real* U = static_cast<const Real*>(a.U);
-  const Real gam = Real(a.sp.gas_gamma);
-  double ax = 0.0, ay = 0.0;
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+  Real ax = Real(0), ay = Real(0);
   bool bad = false;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
        q += (long long)gridDim.x * blockDim.x) {
     Real u[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) u[c] = U[c * N + q];
-    double sx, sy;
+    Real sx, sy;
     speeds2<EQ>(u, gam, sx, sy);
-    bad |= !(sx <= DBL_MAX) || !(sy <= DBL_MAX);
+    bad |= !(sx <= real_max<Real>()) || !(sy <= real_max<Real>());
     ax = fmax(ax, sx);
     ay = fmax(ay, sy);
   }
   if (bad) atomicOr(a.status, STATUS_NONFINITE);
-  ax = block_max2(ax, red);
-  if (threadIdx.x == 0) atomicMax(&a.alpha_out[0], (unsigned long long)__double_as_longlong(ax));
-  ay = block_max2(ay, red);
-  if (threadIdx.x == 0) atomicMax(&a.alpha_out[1], (unsigned long long)__double_as_longlong(ay));
+  ax = block_max_t(ax, red);
+  if (threadIdx.x == 0)
+    atomicMax(&a.alpha_out[0], (unsigned long long)__double_as_longlong((double)ax));
+  ay = block_max_t(ay, red);
+  if (threadIdx.x == 0)
+    atomicMax(&a.alpha_out[1], (unsigned long long)__double_as_longlong((double)ay));
 }
 
 // ---------------------------------------------------------------------------
 // x-sweep
 // ---------------------------------------------------------------------------
 template <int EQ, class Real, int MODE>
-__global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(Args2D a) {
+__global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(const __grid_constant__ Args2D a) {
   constexpr int M = Dim2<EQ>::M;
   constexpr bool EUL = EQ == HWENO_EULER;
   constexpr int NP = kTileX2D + 4, NF = kTileX2D + 1;
@@ -274,10 +252,11 @@ __global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(Args2D a) {
   const int j = blockIdx.y, i0 = blockIdx.x * kTileX2D;
   const int np = min(kTileX2D, nx - i0);
   const long long row = (long long)j * nx;
-  const Real dx = Real(a.dx), idx = Real(1.0 / a.dx), idx2 = Real(1.0 / (a.dx * a.dx));
+  const Real* geo = pick<Real>(a.geod, a.geof);
+  const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
   const Real alpha = Real(a.alpha_in[0]);
-  const Real gam = Real(a.sp.gas_gamma), gm1 = gam - Real(1);
-  const Weights<Real> w = make_weights2<Real>(a.sp);
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9], gm1 = gam - Real(1);
+  const Weights<Real> w = weights_from(pick<Real>(a.sp.wd, a.sp.wf));
   if constexpr (MODE == MODE_STAGE1) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
       int lands;
@@ -444,7 +423,7 @@ struct YLayout {
 };
 
 template <int EQ, class Real, int MODE>
-__global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
+__global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(const __grid_constant__ Args2D a) {
   using Lay = YLayout<EQ, Real>;
   constexpr int M = Lay::M;
   constexpr bool EUL = Lay::EUL;
@@ -456,26 +435,33 @@ __global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
   Real* sEig = sm + (size_t)7 * M * P;  // 5 x P (Euler)
   Real* sI = sm + (size_t)Lay::NQ * P;  // interface arrays [3M][RF][C]
   auto IF = [&](int kind, int c) { return sI + (size_t)(kind * M + c) * Lay::RF * C; };
-  __shared__ double red[kThreads2D / 32];
+  __shared__ Real red[kThreads2D / 32];
+  __shared__ double s_dt, s_ts;
 
   if (a.skip_done && !(a.t[0] < a.t_end)) return;
   const int nx = a.nx, ny = a.ny;
   const long long N = (long long)nx * ny;
   const int i0 = blockIdx.x * C, j0 = blockIdx.y * kRowsY2D;
   const int ncol = min(C, nx - i0), nrow = min(kRowsY2D, ny - j0);
-  const Real dy = Real(a.dy), idy = Real(1.0 / a.dy), idy2 = Real(1.0 / (a.dy * a.dy));
+  const Real* geo = pick<Real>(a.geod, a.geof);
+  const Real dy = geo[3], idy = geo[4], idy2 = geo[5];
   const Real alpha = Real(a.alpha_in[1]);
-  const Real gam = Real(a.sp.gas_gamma), gm1 = gam - Real(1);
-  const Weights<Real> w = make_weights2<Real>(a.sp);
-  double dt = 0.0;
-  if constexpr (MODE == MODE_STAGE1) {
-    int lands;
-    dt = time_step2(a, lands);
-  } else if constexpr (MODE != MODE_RHS) {
-    dt = a.dt[0];
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9], gm1 = gam - Real(1);
+  const Weights<Real> w = weights_from(pick<Real>(a.sp.wd, a.sp.wf));
+  // time step and boundary time of the stage, once per CTA
+  if (threadIdx.x == 0) {
+    double dt = 0.0;
+    if constexpr (MODE == MODE_STAGE1) {
+      int lands;
+      dt = time_step2(a, lands);
+    } else if constexpr (MODE != MODE_RHS) {
+      dt = a.dt[0];
+    }
+    s_dt = dt;
+    s_ts = __dadd_rn(a.t[0], __dmul_rn(a.stage_c, dt));
   }
-  const Real rdt = Real(dt);
-  const double ts = __dadd_rn(a.t[0], __dmul_rn(a.stage_c, dt));
+  __syncthreads();
+  const double ts = s_ts;
 
   {
     const Real* U = static_cast<const Real*>(a.U);
@@ -589,7 +575,8 @@ __global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
   }
   __syncthreads();
 
-  double ax = 0.0, ay = 0.0;
+  const Real rdt = Real(s_dt);
+  Real ax = Real(0), ay = Real(0);
   bool bad = false;
   const Real* LX = static_cast<const Real*>(a.LX);
   const Real* VT = static_cast<const Real*>(a.VT);
@@ -670,9 +657,9 @@ __global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
         static_cast<Real*>(a.Wout)[qc] = wn;
       }
       if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
-        double sx, sy;
+        Real sx, sy;
         speeds2<EQ>(un, gam, sx, sy);
-        bad |= !(sx <= DBL_MAX) || !(sy <= DBL_MAX);
+        bad |= !(sx <= real_max<Real>()) || !(sy <= real_max<Real>());
         ax = fmax(ax, sx);
         ay = fmax(ay, sy);
       }
@@ -680,10 +667,12 @@ __global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(Args2D a) {
   }
   if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
-    ax = block_max2(ax, red);
-    if (threadIdx.x == 0) atomicMax(&a.alpha_out[0], (unsigned long long)__double_as_longlong(ax));
-    ay = block_max2(ay, red);
-    if (threadIdx.x == 0) atomicMax(&a.alpha_out[1], (unsigned long long)__double_as_longlong(ay));
+    ax = block_max_t(ax, red);
+    if (threadIdx.x == 0)
+      atomicMax(&a.alpha_out[0], (unsigned long long)__double_as_longlong((double)ax));
+    ay = block_max_t(ay, red);
+    if (threadIdx.x == 0)
+      atomicMax(&a.alpha_out[1], (unsigned long long)__double_as_longlong((double)ay));
   }
 }
 
