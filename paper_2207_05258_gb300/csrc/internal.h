@@ -67,6 +67,30 @@ struct Args1D {
   SchemeParams sp;
 };
 
+// Minimum resident CTAs per SM requested from the compiler for the stage
+// kernels, per precision (register budget = 64K / (threads x this)); chosen
+// by measurement.
+#ifndef HWENO_MINB_1D_F64
+#define HWENO_MINB_1D_F64 1
+#endif
+#ifndef HWENO_MINB_1D_F32
+#define HWENO_MINB_1D_F32 1
+#endif
+#ifndef HWENO_MINB_X_F64
+#define HWENO_MINB_X_F64 1
+#endif
+#ifndef HWENO_MINB_X_F32
+#define HWENO_MINB_X_F32 1
+#endif
+#ifndef HWENO_MINB_Y_F64
+#define HWENO_MINB_Y_F64 1
+#endif
+#ifndef HWENO_MINB_Y_F32
+#define HWENO_MINB_Y_F32 1
+#endif
+template <class Real, int F64, int F32>
+struct MinBlocks { static constexpr int value = sizeof(Real) == 8 ? F64 : F32; };
+
 // 2D tiles. x-sweep: one CTA per row segment of kTileX2D points (like 1D).
 // y-sweep: one CTA per block of kColsY2D columns x kRowsY2D rows, so that
 // (kRowsY2D + 1) x kColsY2D interfaces = kThreads2D.

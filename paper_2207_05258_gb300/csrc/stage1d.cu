@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kThreads1D) k_alpha_1d(const __grid_constant__
 }
 
 template <int EQ, class Real, int MODE>
-__global__ void __launch_bounds__(kThreads1D) k_stage_1d(const __grid_constant__ Args1D a) {
+__global__ void __launch_bounds__(kThreads1D, (MinBlocks<Real, HWENO_MINB_1D_F64, HWENO_MINB_1D_F32>::value)) k_stage_1d(const __grid_constant__ Args1D a) {
   constexpr int M = Dim1<EQ>::M;
   constexpr int NP = kTile1D + 4;  // points with two ghosts per side
   constexpr int NF = kTile1D + 1;  // interfaces

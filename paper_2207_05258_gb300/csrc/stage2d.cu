@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) k_alpha_2d(const __grid_constant__ Args2D
 // x-sweep
 // ---------------------------------------------------------------------------
 template <int EQ, class Real, int MODE>
-__global__ void __launch_bounds__(kThreads2D) k_xsweep_2d(const __grid_constant__ Args2D a) {
+__global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64, HWENO_MINB_X_F32>::value)) k_xsweep_2d(const __grid_constant__ Args2D a) {
   constexpr int M = Dim2<EQ>::M;
   constexpr bool EUL = EQ == HWENO_EULER;
   constexpr int NP = kTileX2D + 4, NF = kTileX2D + 1;
@@ -423,7 +423,7 @@ struct YLayout {
 };
 
 template <int EQ, class Real, int MODE>
-__global__ void __launch_bounds__(kThreads2D) k_ysweep_2d(const __grid_constant__ Args2D a) {
+__global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64, HWENO_MINB_Y_F32>::value)) k_ysweep_2d(const __grid_constant__ Args2D a) {
   using Lay = YLayout<EQ, Real>;
   constexpr int M = Lay::M;
   constexpr bool EUL = Lay::EUL;
