@@ -157,6 +157,22 @@ int hweno_rhs(hweno_ctx* ctx, const void* U, const void* V, const void* W, void*
 int hweno_step(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
                double* dt_used, void* stream);
 
+/* Advance until every instance has reached t_end or `max_steps` steps have
+ * been taken. The steps are recorded once into a CUDA graph of
+ * `steps_per_launch` SSP-RK3 steps, kept in the context for these arrays and
+ * t_end (re-recorded when they change), and the graph is replayed on
+ * `stream`; after each replay the host reads the number of active instances.
+ * Steps of finished instances are no-ops, so up to steps_per_launch - 1
+ * extra (empty) steps can run after the last instance lands. `stream` must
+ * not be NULL (graphs are recorded from a stream). max_steps = 0 only records
+ * the graph. On return (stream synchronised) *steps_taken (host, nullable)
+ * holds the steps launched and *point_updates (host, nullable) the number of
+ * grid points advanced through a full step, summed over instances and steps.
+ * Recording a graph creates driver objects but no device buffer. */
+int hweno_run(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
+              long long max_steps, int steps_per_launch, long long* steps_taken,
+              long long* point_updates, void* stream);
+
 /* As hweno_step with HOST arrays: copies U, V (, W) and t (host, [batch]) to
  * library-owned device buffers, takes `nsteps` steps, copies them back and
  * synchronises the stream. Pinned host memory makes the copies asynchronous. */

@@ -9,6 +9,7 @@
 //   stage 2: U1, V1      -> U2, V2;        alpha(U2) -> slot 2
 //   stage 3: U2, V2      -> U^{n+1}, V^{n+1} (in place; reads U^n, V~^n pointwise)
 //   finalize: t += dt (landing exactly on t_end), active count, status
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -57,6 +58,15 @@ struct hweno_ctx {
   void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
   double* d_ht = nullptr;
   int launches = 0;
+  int step_launches = 0;  // kernels per step of this context
+  // point-update counter of hweno_run (device) and its recorded graph
+  unsigned long long* d_pu = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  void* g_U = nullptr; void* g_V = nullptr; void* g_W = nullptr;
+  double* g_t = nullptr;
+  double g_tend = 0.0;
+  int g_k = 0;
+  bool capturing = false;
   // kernel timing (hweno_profile_start / hweno_profile_read)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
@@ -106,7 +116,9 @@ int dalloc(hweno_ctx* c, T** p, size_t bytes) {
 }
 
 void free_all(hweno_ctx* c) {
-  void* ptrs[] = {c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  void* ptrs[] = {c->d_pu, c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
                   c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
                   c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht};
@@ -166,10 +178,10 @@ Args1D base_args_1d(const hweno_ctx* c) {
 // Event bracket around one launch when profiling is on (kind 0 alpha, 1 stage,
 // 2 finalize).
 void prof_begin(hweno_ctx* c, cudaStream_t s) {
-  if (c->ev_used + 2 <= (int)c->ev.size()) cudaEventRecord(c->ev[c->ev_used], s);
+  if (!c->capturing && c->ev_used + 2 <= (int)c->ev.size()) cudaEventRecord(c->ev[c->ev_used], s);
 }
 void prof_end(hweno_ctx* c, cudaStream_t s, int kind) {
-  if (c->ev_used + 2 <= (int)c->ev.size()) {
+  if (!c->capturing && c->ev_used + 2 <= (int)c->ev.size()) {
     cudaEventRecord(c->ev[c->ev_used + 1], s);
     c->ev_kind[c->ev_used / 2] = kind;
     c->ev_used += 2;
@@ -230,10 +242,10 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
   prof_end(c, s, 1);
   prof_begin(c, s);
   if ((e = launch_finalize(c->batch, c->d_dt, c->d_lands, t, t_end, dt_used, slotd(c, 0),
-                           c->d_active, c->d_status, s)))
+                           c->d_active, c->d_status, c->d_inst_n, c->d_pu, s)))
     return cuda_fail(c, e, "finalize");
   prof_end(c, s, 2);
-  c->launches = 5;
+  c->launches = c->step_launches = 5;
   return HWENO_OK;
 }
 
@@ -304,10 +316,10 @@ int step_2d(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end, do
   prof_begin(c, s);
   if ((e = launch_finalize(1, c->d_dt, c->d_lands, t, t_end, dt_used,
                            reinterpret_cast<const double*>(c->d_alpha), c->d_active,
-                           c->d_status, s)))
+                           c->d_status, c->d_inst_n, c->d_pu, s)))
     return cuda_fail(c, e, "finalize");
   prof_end(c, s, 2);
-  c->launches = 8;
+  c->launches = c->step_launches = 8;
   return HWENO_OK;
 }
 
@@ -471,6 +483,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       (rc = dalloc(c, &c->d_lands, sizeof(int) * B)) ||
       (rc = dalloc(c, &c->d_active, sizeof(int))) ||
       (rc = dalloc(c, &c->d_status, sizeof(unsigned))) ||
+      (rc = dalloc(c, &c->d_pu, sizeof(unsigned long long))) ||
       (rc = dalloc(c, &c->d_U1, fb)) || (rc = dalloc(c, &c->d_V1, fb)) ||
       (rc = dalloc(c, &c->d_U2, fb)) || (rc = dalloc(c, &c->d_V2, fb)) ||
       (rc = dalloc(c, &c->d_Vt0, fb)) || (rc = dalloc(c, &c->d_hU, fb)) ||
@@ -498,7 +511,8 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       cudaMemcpy(c->d_inst_n, c->nx.data(), sizeof(int) * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_off, off.data(), sizeof(long long) * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_dx, c->inst_dx.data(), sizeof(double) * B, cudaMemcpyHostToDevice) ||
-      cudaMemset(c->d_status, 0, sizeof(unsigned));
+      cudaMemset(c->d_status, 0, sizeof(unsigned)) ||
+      cudaMemset(c->d_pu, 0, sizeof(unsigned long long));
   if (copy_failed) {
     free_all(c);
     delete c;
@@ -546,6 +560,61 @@ int hweno_step(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
   c->err.clear();
   if (c->dim == 2) return step_2d(c, U, V, W, t, t_end, dt_used, static_cast<cudaStream_t>(stream));
   return step_1d(c, U, V, t, t_end, dt_used, static_cast<cudaStream_t>(stream));
+}
+
+int hweno_run(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
+              long long max_steps, int k, long long* steps_taken, long long* point_updates,
+              void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!stream) return fail(c, HWENO_EINVAL, "hweno_run needs a non-NULL stream");
+  if (!U || !V || !t || k < 1 || max_steps < 0) return fail(c, HWENO_EINVAL, "bad argument");
+  if ((c->dim == 1) != (W == nullptr)) return fail(c, HWENO_EINVAL, "W must be given iff 2D");
+  if (!std::isfinite(t_end)) return fail(c, HWENO_EINVAL, "t_end not finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (!c->graph || c->g_U != U || c->g_V != V || c->g_W != W || c->g_t != t ||
+      c->g_tend != t_end || c->g_k != k) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)))
+      return cuda_fail(c, e, "cudaStreamBeginCapture");
+    c->capturing = true;
+    int rc = HWENO_OK;
+    for (int i = 0; i < k && rc == HWENO_OK; ++i) rc = hweno_step(c, U, V, W, t, t_end, nullptr, stream);
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rc != HWENO_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->g_U = U; c->g_V = V; c->g_W = W; c->g_t = t; c->g_tend = t_end; c->g_k = k;
+  }
+  if ((e = cudaMemsetAsync(c->d_pu, 0, sizeof(unsigned long long), s)))
+    return cuda_fail(c, e, "memset");
+  long long taken = 0;
+  while (taken < max_steps) {
+    if ((e = cudaGraphLaunch(c->graph, s))) return cuda_fail(c, e, "cudaGraphLaunch");
+    taken += k;
+    const int active = hweno_active_instances(c, stream);
+    if (active < 0) return active;
+    if (active == 0) break;
+  }
+  unsigned long long pu = 0;
+  if ((e = cudaMemcpyAsync(&pu, c->d_pu, sizeof pu, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(c, e, "read point updates");
+  if (steps_taken) *steps_taken = taken;
+  if (point_updates) *point_updates = (long long)pu;
+  c->launches = (int)std::min<long long>(2147483647LL, (long long)c->step_launches * taken);
+  return hweno_sync_status(c, stream);
 }
 
 int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,

@@ -69,24 +69,26 @@ struct Args1D {
 
 // Minimum resident CTAs per SM requested from the compiler for the stage
 // kernels, per precision (register budget = 64K / (threads x this)); chosen
-// by measurement.
+// by measurement: the FP64 kernels are FP64-pipe bound at any occupancy
+// (1..4 CTAs gave the same throughput), the FP32 ones gain from more warps
+// (1D: 8 CTAs, 64 registers, +12%; 2D: 5 CTAs).
 #ifndef HWENO_MINB_1D_F64
 #define HWENO_MINB_1D_F64 1
 #endif
 #ifndef HWENO_MINB_1D_F32
-#define HWENO_MINB_1D_F32 1
+#define HWENO_MINB_1D_F32 8
 #endif
 #ifndef HWENO_MINB_X_F64
 #define HWENO_MINB_X_F64 1
 #endif
 #ifndef HWENO_MINB_X_F32
-#define HWENO_MINB_X_F32 1
+#define HWENO_MINB_X_F32 5
 #endif
 #ifndef HWENO_MINB_Y_F64
 #define HWENO_MINB_Y_F64 1
 #endif
 #ifndef HWENO_MINB_Y_F32
-#define HWENO_MINB_Y_F32 1
+#define HWENO_MINB_Y_F32 5
 #endif
 template <class Real, int F64, int F32>
 struct MinBlocks { static constexpr int value = sizeof(Real) == 8 ? F64 : F32; };
@@ -142,8 +144,11 @@ cudaError_t launch_ysweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaS
 cudaError_t launch_alpha_1d(int eq, bool fp32, const Args1D& a, int ntiles, cudaStream_t s);
 cudaError_t launch_stage_1d(int eq, bool fp32, int mode, const Args1D& a, int ntiles,
                             cudaStream_t s);
+// Time update after stage 3; counts the instances still active and, when
+// pu is not null, adds inst_n[k] of every instance that took the step.
 cudaError_t launch_finalize(int batch, const double* dt, const int* lands, double* t,
                             double t_end, double* dt_used, const double* alpha,
-                            int* active_count, unsigned* status, cudaStream_t s);
+                            int* active_count, unsigned* status, const int* inst_n,
+                            unsigned long long* pu, cudaStream_t s);
 
 }  // namespace hweno

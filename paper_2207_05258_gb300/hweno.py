@@ -66,6 +66,9 @@ SIGNATURES = {
     "hweno_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
     "hweno_step_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                        _VP]),
+    "hweno_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_longlong,
+                                 ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_longlong), _VP]),
     "hweno_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, _VP,
                                           _VP]),
     "hweno_sync_status": (ctypes.c_int, [_VP, _VP]),
@@ -234,6 +237,15 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def run_graph(self, U, V, W=None, t=None, t_end=1.0, max_steps=1 << 40, steps_per_launch=32):
+        """hweno_run on torch's current stream (which must not be the legacy
+        default stream): returns (steps launched, point-updates)."""
+        steps, pu = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        self._check(lib.hweno_run(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t), float(t_end),
+                                  int(max_steps), int(steps_per_launch), ctypes.byref(steps),
+                                  ctypes.byref(pu), _stream()))
+        return steps.value, pu.value
 
     def run(self, U, V, W=None, t=None, t_end=1.0, max_steps=1 << 30, check_every=64):
         """Steps until every instance reaches t_end; returns the steps taken."""

@@ -1,0 +1,84 @@
+"""hweno_run: steps recorded once into a CUDA graph and replayed until every
+instance lands on t_end. The result must equal plain hweno_step calls bit for
+bit (same kernels, same arguments; steps of finished instances are no-ops),
+and the device point-update counter must equal sum_k N_k * steps_k with the
+per-instance step counts of the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2207_05258_gb300 import workloads as W
+from _util import oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hw():
+    from paper_2207_05258_gb300 import build
+    build.build()
+    from paper_2207_05258_gb300 import hweno
+    return hweno
+
+
+def _subset(w, pick):
+    Us, Vs = zip(*(w.instance(k) for k in pick))
+    return W.Workload("sub", "euler", 1, [w.nx[k] for k in pick], 1, w.x0, w.x1, w.y0, w.y1,
+                      w.t_end, w.bc, np.concatenate([u.ravel() for u in Us]),
+                      np.concatenate([v.ravel() for v in Vs]))
+
+
+@pytest.mark.parametrize("k", [1, 7, 32])
+def test_graph_run_matches_plain_steps(hw, k):
+    full = W.riemann_batch(count=40, seed=99)
+    w = _subset(full, [i for i in range(40) if full.nx[i] <= 400][:8])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = hw.Solver.from_workload(w)
+        U, V = torch.from_numpy(w.U.copy()).cuda(), torch.from_numpy(w.V.copy()).cuda()
+        t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+        steps, pu = s.run_graph(U, V, None, t, w.t_end, steps_per_launch=k)
+        s2 = hw.Solver.from_workload(w)
+        U2, V2 = torch.from_numpy(w.U.copy()).cuda(), torch.from_numpy(w.V.copy()).cuda()
+        t2 = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+        s2.run(U2, V2, None, t2, w.t_end, check_every=1)
+    torch.cuda.synchronize()
+    assert torch.equal(U, U2) and torch.equal(V, V2) and torch.equal(t, t2)
+    assert torch.all(t == w.t_end)
+    expect = 0
+    for i in range(w.batch):
+        Ui, Vi = w.instance(i)
+        _, _, _, _, n = O.run(oracle_problem(w, nx=w.nx[i]), Ui, Vi, None, 0.0, w.t_end)
+        expect += n * w.nx[i]
+    assert pu == expect
+    assert steps % k == 0 and steps >= max(1, pu // sum(w.nx))
+
+
+def test_graph_run_2d_and_record_only(hw):
+    w = W.double_mach(64, 16, t_end=0.01)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = hw.Solver.from_workload(w)
+        U = torch.from_numpy(w.U.copy()).cuda()
+        V, Wd = torch.zeros_like(U), torch.zeros_like(U)
+        t = torch.zeros(1, dtype=torch.float64, device="cuda")
+        steps, pu = s.run_graph(U, V, Wd, t, w.t_end, max_steps=0, steps_per_launch=4)
+        assert steps == 0 and pu == 0 and float(t.item()) == 0.0
+        steps, pu = s.run_graph(U, V, Wd, t, w.t_end, steps_per_launch=4)
+    torch.cuda.synchronize()
+    assert float(t.item()) == w.t_end
+    U2, V2, W2, tt, n = O.run(oracle_problem(w), w.U, w.V, w.W, 0.0, w.t_end)
+    assert pu == n * 64 * 16
+    assert np.max(np.abs(U.cpu().numpy().reshape(U2.shape) - U2)) <= 1e-10 * np.max(np.abs(U2))
+
+
+def test_graph_run_needs_a_stream(hw):
+    w = W.burgers1d_sine(64)
+    s = hw.Solver.from_workload(w)
+    U, V = torch.from_numpy(w.U.copy()).cuda(), torch.from_numpy(w.V.copy()).cuda()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    import ctypes
+    rc = hw.lib.hweno_run(s.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(V.data_ptr()), None,
+                          ctypes.c_void_p(t.data_ptr()), 1.0, 10, 4, None, None, None)
+    assert rc == hw.EINVAL
