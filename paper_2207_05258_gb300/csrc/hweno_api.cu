@@ -242,7 +242,7 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
   prof_end(c, s, 1);
   prof_begin(c, s);
   if ((e = launch_finalize(c->batch, c->d_dt, c->d_lands, t, t_end, dt_used, slotd(c, 0),
-                           c->d_active, c->d_status, c->d_inst_n, c->d_pu, s)))
+                           c->d_active, c->d_status, c->d_inst_n, 1, c->d_pu, s)))
     return cuda_fail(c, e, "finalize");
   prof_end(c, s, 2);
   c->launches = c->step_launches = 5;
@@ -316,7 +316,7 @@ int step_2d(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end, do
   prof_begin(c, s);
   if ((e = launch_finalize(1, c->d_dt, c->d_lands, t, t_end, dt_used,
                            reinterpret_cast<const double*>(c->d_alpha), c->d_active,
-                           c->d_status, c->d_inst_n, c->d_pu, s)))
+                           c->d_status, c->d_inst_n, c->ny, c->d_pu, s)))
     return cuda_fail(c, e, "finalize");
   prof_end(c, s, 2);
   c->launches = c->step_launches = 8;

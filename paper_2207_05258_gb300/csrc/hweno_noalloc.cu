@@ -191,8 +191,8 @@ extern "C" int hweno_step_1d_noalloc(int equation, int nx, double x0, double x1,
   a.alpha_in = reinterpret_cast<const double*>(alpha + 2); a.alpha_out = nullptr;
   if (launch_stage_1d(equation, fp32, MODE_STAGE3, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
   if (launch_finalize(1, a.dt, a.lands, t, t_end, dt_used, reinterpret_cast<const double*>(alpha),
-                      reinterpret_cast<int*>(base + kOffActive), a.status, nullptr, nullptr,
-                      s) != cudaSuccess)
+                      reinterpret_cast<int*>(base + kOffActive), a.status, nullptr, 1,
+                      nullptr, s) != cudaSuccess)
     return HWENO_ECUDA;
 
   unsigned st = 0;

@@ -145,10 +145,11 @@ cudaError_t launch_alpha_1d(int eq, bool fp32, const Args1D& a, int ntiles, cuda
 cudaError_t launch_stage_1d(int eq, bool fp32, int mode, const Args1D& a, int ntiles,
                             cudaStream_t s);
 // Time update after stage 3; counts the instances still active and, when
-// pu is not null, adds inst_n[k] of every instance that took the step.
+// pu is not null, adds inst_n[k] * rows (the instance's points; rows = ny in
+// 2D, 1 in 1D) of every instance that took the step.
 cudaError_t launch_finalize(int batch, const double* dt, const int* lands, double* t,
                             double t_end, double* dt_used, const double* alpha,
-                            int* active_count, unsigned* status, const int* inst_n,
+                            int* active_count, unsigned* status, const int* inst_n, int rows,
                             unsigned long long* pu, cudaStream_t s);
 
 }  // namespace hweno

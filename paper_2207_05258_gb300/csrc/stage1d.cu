@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kThreads1D, (MinBlocks<Real, HWENO_MINB_1D_F64
 
 __global__ void k_finalize(int batch, const double* dt, const int* lands, double* t, double t_end,
                            double* dt_used, const double* alpha, int* active, unsigned* status,
-                           const int* inst_n, unsigned long long* pu) {
+                           const int* inst_n, int rows, unsigned long long* pu) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= batch) return;
   double tk = t[k];
@@ -352,7 +352,7 @@ __global__ void k_finalize(int batch, const double* dt, const int* lands, double
     tk = lands[k] ? t_end : tk + d;
     t[k] = tk;
     if (!(alpha[k] <= DBL_MAX)) atomicOr(status, STATUS_NONFINITE);
-    if (pu) atomicAdd(pu, (unsigned long long)inst_n[k]);
+    if (pu) atomicAdd(pu, (unsigned long long)inst_n[k] * (unsigned long long)rows);
   }
   if (dt_used) dt_used[k] = d;
   if (tk < t_end) atomicAdd(active, 1);
@@ -395,10 +395,10 @@ cudaError_t launch_stage_1d(int eq, bool fp32, int mode, const Args1D& a, int nt
 
 cudaError_t launch_finalize(int batch, const double* dt, const int* lands, double* t,
                             double t_end, double* dt_used, const double* alpha, int* active,
-                            unsigned* status, const int* inst_n, unsigned long long* pu,
-                            cudaStream_t s) {
+                            unsigned* status, const int* inst_n, int rows,
+                            unsigned long long* pu, cudaStream_t s) {
   k_finalize<<<(batch + 127) / 128, 128, 0, s>>>(batch, dt, lands, t, t_end, dt_used, alpha,
-                                                  active, status, inst_n, pu);
+                                                  active, status, inst_n, rows, pu);
   return cudaGetLastError();
 }
 
