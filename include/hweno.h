@@ -179,6 +179,13 @@ int hweno_run(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end
 int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream);
 
+/* Conserved totals in FP64 (the discrete integrals conserved by the flux
+ * form of Eq. odeH / ode2H): totals[k * m + c] = sum_i U_c(x_i) dx (2D:
+ * times dy) for every instance k and component c, accumulated in FP64 in a
+ * fixed order (the same bits on every call), also for FP32 states. totals is
+ * a device array of batch * m doubles. */
+int hweno_totals(hweno_ctx* ctx, const void* U, double* totals, void* stream);
+
 /* Discrete adjoint of hweno_step (reverse of the three stages with the
  * wave speed, time step and weight branches frozen). Not built yet:
  * returns HWENO_ENOTSUP. */

@@ -61,6 +61,8 @@ struct hweno_ctx {
   int step_launches = 0;  // kernels per step of this context
   // point-update counter of hweno_run (device) and its recorded graph
   unsigned long long* d_pu = nullptr;
+  double* d_partial = nullptr;  // per-tile partial sums of hweno_totals
+  int ntiles_tot = 0;
   cudaGraphExec_t graph = nullptr;
   void* g_U = nullptr; void* g_V = nullptr; void* g_W = nullptr;
   double* g_t = nullptr;
@@ -118,7 +120,7 @@ int dalloc(hweno_ctx* c, T** p, size_t bytes) {
 void free_all(hweno_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
-  void* ptrs[] = {c->d_pu, c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
+  void* ptrs[] = {c->d_pu, c->d_partial, c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
                   c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
                   c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht};
@@ -466,6 +468,8 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
   c->npts = acc;
   c->elems = (size_t)c->m * (size_t)acc;
   c->ntiles = (int)tinst.size();
+  c->ntiles_tot = grid->dim == 1 ? c->ntiles
+                                 : ((c->nx[0] + kTileX2D - 1) / kTileX2D) * c->ny;
 
   int rc = HWENO_OK;
   const size_t fb = c->elems * c->esize;
@@ -484,6 +488,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       (rc = dalloc(c, &c->d_active, sizeof(int))) ||
       (rc = dalloc(c, &c->d_status, sizeof(unsigned))) ||
       (rc = dalloc(c, &c->d_pu, sizeof(unsigned long long))) ||
+      (rc = dalloc(c, &c->d_partial, sizeof(double) * 4 * (size_t)c->ntiles_tot)) ||
       (rc = dalloc(c, &c->d_U1, fb)) || (rc = dalloc(c, &c->d_V1, fb)) ||
       (rc = dalloc(c, &c->d_U2, fb)) || (rc = dalloc(c, &c->d_V2, fb)) ||
       (rc = dalloc(c, &c->d_Vt0, fb)) || (rc = dalloc(c, &c->d_hU, fb)) ||
@@ -642,6 +647,19 @@ int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t
       (e = cudaMemcpyAsync(t, c->d_ht, tb, cudaMemcpyDeviceToHost, s)))
     return cuda_fail(c, e, "copy out");
   return hweno_sync_status(c, stream);
+}
+
+int hweno_totals(hweno_ctx* c, const void* U, double* totals, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!U || !totals) return fail(c, HWENO_EINVAL, "null array");
+  const double cell = c->dim == 2 ? ((c->x1 - c->x0) / c->nx[0]) * ((c->y1 - c->y0) / c->ny) : 0.0;
+  const cudaError_t e = launch_totals(c->m, c->fp32, c->dim, U, c->ntiles_tot, c->d_tile_inst,
+                                      c->d_tile_start, c->d_inst_n, c->d_inst_off, c->batch,
+                                      c->nx[0], c->ny, cell, c->dim == 1 ? c->d_inst_dx : nullptr,
+                                      c->d_partial, totals, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "totals");
+  c->launches = 2;
+  return HWENO_OK;
 }
 
 int hweno_adjoint_step(hweno_ctx* c, const void*, const void*, const void*, double, void*, void*,

@@ -140,6 +140,15 @@ cudaError_t launch_alpha_2d(int eq, bool fp32, const Args2D& a, cudaStream_t s);
 cudaError_t launch_xsweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
 cudaError_t launch_ysweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
 
+// Conserved totals (totals.cu): per-tile FP64 partial sums, then a
+// fixed-order sum per instance. Tiles: the 1D tile table, or row segments of
+// kTileX2D points in 2D (instance 0).
+cudaError_t launch_totals(int m, bool fp32, int dim, const void* U, int ntiles,
+                          const int* tile_inst, const int* tile_start, const int* inst_n,
+                          const long long* inst_off, int batch, int nx, int ny, double cell,
+                          const double* inst_dx, double* partial, double* totals,
+                          cudaStream_t s);
+
 // Launchers (stage1d.cu). eq: 0 Burgers, 1 Euler; fp32: precision.
 cudaError_t launch_alpha_1d(int eq, bool fp32, const Args1D& a, int ntiles, cudaStream_t s);
 cudaError_t launch_stage_1d(int eq, bool fp32, int mode, const Args1D& a, int ntiles,

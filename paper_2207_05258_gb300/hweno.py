@@ -69,6 +69,7 @@ SIGNATURES = {
     "hweno_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_longlong,
                                  ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_longlong), _VP]),
+    "hweno_totals": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "hweno_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, _VP,
                                           _VP]),
     "hweno_sync_status": (ctypes.c_int, [_VP, _VP]),
@@ -202,6 +203,12 @@ class Solver:
         p = lambda x: None if x is None else ctypes.c_void_p(x.data_ptr())
         self._check(lib.hweno_step_host(self.h, p(U), p(V), p(W), p(t), float(t_end), nsteps,
                                         _stream()))
+
+    def totals(self, U):
+        """FP64 conserved totals, tensor [batch, m] (fixed summation order)."""
+        out = torch.empty(self.batch, self.m, dtype=torch.float64, device=U.device)
+        self._check(lib.hweno_totals(self.h, _ptr(U), _ptr(out), _stream()))
+        return out
 
     def active_instances(self) -> int:
         n = lib.hweno_active_instances(self.h, _stream())
