@@ -205,6 +205,7 @@ def run_ours(args, rank, world, dev_index):
             for _ in range(Wm):
                 s.step(U, V, Wd, t, w.t_end)
             s.sync_status()
+            tune = s.autotune(U, V, Wd, t, w.t_end)  # tile shape (1D); reads the state only
             s.run_graph(U, V, Wd, t, w.t_end, max_steps=0, steps_per_launch=K)  # record
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             if world > 1:
@@ -236,11 +237,13 @@ def run_ours(args, rank, world, dev_index):
                 prof = s.profile_read()
                 pu_ng = float(((hist > 0).double() * nx[None, :]).sum().item())
         s.close()
+        timed.tune = tune
         return ms, float(pu), prof, launches, ms_ng, pu_ng
 
     with ClockSampler(dev_index) as clk:
         ms, pu, prof, launches, ms_ng, pu_ng = timed(args.precision, args.steps, args.warmup, True)
     clocks = clk.summary()
+    tune = timed.tune
 
     if world > 1:
         ms, pu = reduce_over_ranks(ms, pu, "cuda")
@@ -283,6 +286,8 @@ def run_ours(args, rank, world, dev_index):
                              "set (state + stage buffers, %.0f MB) exceeds the 129 MB L2"
                              % (working_set_mb(w, args.precision))),
                       "timing": "K steps = one CUDA-graph replay (hweno_run), CUDA events",
+                      "tile_variant": tune[0] if w.dim == 1 else None,
+                      "autotune_stage1_ms": [round(x, 4) for x in tune[1]] if w.dim == 1 else None,
                       "parallelism": "replicas (one seeded batch per rank)"},
            "roofline": roof, "clocks": clocks, "gpu_launches": launches,
            "point_updates_timed": pu}

@@ -103,7 +103,7 @@ typedef struct hweno_grid {
 
 /* Scheme options. hweno_default_options fills the paper's values (Sec. 3):
  * lin_w = lim_d = {0.98, 0.01, 0.01}, eps = 1e-6, cfl = 0.6,
- * dt_mode = 0, limiter = 1, eig_avg = 0. */
+ * dt_mode = 0, limiter = 1, eig_avg = 0, and tile_variant = 0. */
 typedef struct hweno_options {
   double lin_w[3]; /* gamma_0..2 of the reconstruction: > 0, sum 1 (Sec. 2.1) */
   double lim_d[3]; /* d_0..2 of the limiter: > 0, sum 1 (Sec. 2.2) */
@@ -117,6 +117,8 @@ typedef struct hweno_options {
                       U_i of the sweep direction); 2: component-wise */
   int eig_avg;     /* eigenvectors at x_{i+1/2}: 0 Roe average of U_i, U_{i+1};
                       1 arithmetic mean */
+  int tile_variant; /* 1D tile shape 0..4 (see hweno_autotune; results do not
+                       depend on it); ignored in 2D */
 } hweno_options;
 
 typedef struct hweno_ctx hweno_ctx; /* opaque, library-owned */
@@ -178,6 +180,17 @@ int hweno_run(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end
  * synchronises the stream. Pinned host memory makes the copies asynchronous. */
 int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream);
+
+/* Tile-shape autotuner (1D): times the fused stage kernel of every tile
+ * variant (CTA sizes 64, 128, 256 threads, one or two points per thread) on
+ * the given state U, V at times t (device) with t_end, and keeps the fastest
+ * for the following calls of this context. Only library scratch is written
+ * (U, V, W, t are read). Synchronises `stream`. *chosen (host, nullable)
+ * receives the variant index (0 = the default 128 x 1); ms (host, nullable,
+ * 5 doubles) the best measured time of each variant in milliseconds. In 2D
+ * there is a single tile shape: *chosen = 0 and nothing is measured. */
+int hweno_autotune(hweno_ctx* ctx, const void* U, const void* V, const void* W, const double* t,
+                   double t_end, int* chosen, double* ms, void* stream);
 
 /* Conserved totals in FP64 (the discrete integrals conserved by the flux
  * form of Eq. odeH / ode2H): totals[k * m + c] = sum_i U_c(x_i) dx (2D:

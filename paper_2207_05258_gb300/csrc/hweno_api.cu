@@ -32,8 +32,11 @@ struct hweno_ctx {
   hweno_options opt{};
   long long npts = 0;
   size_t elems = 0, esize = 8;
-  // 1D batch tables
+  // 1D batch tables (for the current tile variant)
   int ntiles = 0;
+  int variant = 0;
+  int tile = kTile1D;
+  int tiles_cap = 0;  // capacity of the tile tables (smallest tile)
   int* d_tile_inst = nullptr;
   int* d_tile_start = nullptr;
   int* d_inst_n = nullptr;
@@ -100,6 +103,10 @@ int check_options(const hweno_options* o, std::string& why) {
   if (o->dt_mode == 2 && !(o->dt_fixed > 0)) { why = "dt_fixed must be > 0"; return HWENO_EINVAL; }
   if (o->limiter < 0 || o->limiter > 2) { why = "limiter must be 0, 1 or 2"; return HWENO_EINVAL; }
   if (o->eig_avg < 0 || o->eig_avg > 1) { why = "eig_avg must be 0 or 1"; return HWENO_EINVAL; }
+  if (o->tile_variant < 0 || o->tile_variant >= kNumVariants1D) {
+    why = "tile_variant out of range";
+    return HWENO_EINVAL;
+  }
   return HWENO_OK;
 }
 
@@ -150,6 +157,33 @@ SchemeParams scheme_params(const hweno_ctx* c) {
                           1.0 / c->opt.lim_d[0], c->gamma};
   for (int i = 0; i < 10; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
   return sp;
+}
+
+// Tile table of a 1D batch for tiles of `tile` points: (instance, first point)
+// per CTA, instances in order.
+void tile_table(const std::vector<int>& nx, int tile, std::vector<int>& tinst,
+                std::vector<int>& tstart) {
+  tinst.clear();
+  tstart.clear();
+  for (size_t k = 0; k < nx.size(); ++k)
+    for (int s = 0; s < nx[k]; s += tile) { tinst.push_back((int)k); tstart.push_back(s); }
+}
+
+// Upload the tile table of variant v (1D) and make it current.
+int use_variant(hweno_ctx* c, int v) {
+  std::vector<int> tinst, tstart;
+  tile_table(c->nx, tile_points(v), tinst, tstart);
+  if ((int)tinst.size() > c->tiles_cap) return fail(c, HWENO_EINVAL, "tile table capacity");
+  cudaError_t e;
+  if ((e = cudaMemcpy(c->d_tile_inst, tinst.data(), sizeof(int) * tinst.size(),
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(c->d_tile_start, tstart.data(), sizeof(int) * tstart.size(),
+                      cudaMemcpyHostToDevice)))
+    return cuda_fail(c, e, "upload tile table");
+  c->variant = v;
+  c->tile = tile_points(v);
+  c->ntiles = (int)tinst.size();
+  return HWENO_OK;
 }
 
 // Per-instance h of the time-step rule (dx, or dx^{5/3} for dt_mode 1).
@@ -218,13 +252,14 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
   a.U = U;
   a.alpha_out = slot(c, 0);
   prof_begin(c, s);
-  if ((e = launch_alpha_1d(c->eq, c->fp32, a, c->ntiles, s))) return cuda_fail(c, e, "alpha");
+  if ((e = launch_alpha_1d(c->eq, c->fp32, c->variant, a, c->ntiles, s)))
+    return cuda_fail(c, e, "alpha");
   prof_end(c, s, 0);
   // stage 1
   a.U = U; a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
   a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
   prof_begin(c, s);
-  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_STAGE1, a, c->ntiles, s)))
+  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE1, a, c->ntiles, s)))
     return cuda_fail(c, e, "stage 1");
   prof_end(c, s, 1);
   // stage 2
@@ -232,14 +267,14 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
   a.Vt0out = nullptr;
   a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
   prof_begin(c, s);
-  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_STAGE2, a, c->ntiles, s)))
+  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE2, a, c->ntiles, s)))
     return cuda_fail(c, e, "stage 2");
   prof_end(c, s, 1);
   // stage 3 (in place)
   a.U = c->d_U2; a.V = c->d_V2; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = U; a.Vout = V;
   a.alpha_in = slotd(c, 2); a.alpha_out = nullptr;
   prof_begin(c, s);
-  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_STAGE3, a, c->ntiles, s)))
+  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE3, a, c->ntiles, s)))
     return cuda_fail(c, e, "stage 3");
   prof_end(c, s, 1);
   prof_begin(c, s);
@@ -366,12 +401,13 @@ int rhs_1d(hweno_ctx* c, const void* U, const void* V, void* dU, void* dV, void*
   a.U = U;
   a.alpha_out = slot(c, 0);
   prof_begin(c, s);
-  if ((e = launch_alpha_1d(c->eq, c->fp32, a, c->ntiles, s))) return cuda_fail(c, e, "alpha");
+  if ((e = launch_alpha_1d(c->eq, c->fp32, c->variant, a, c->ntiles, s)))
+    return cuda_fail(c, e, "alpha");
   prof_end(c, s, 0);
   a.V = V; a.L1 = dU; a.L2 = dV; a.Vlim = Vlim;
   a.alpha_in = slotd(c, 0); a.alpha_out = nullptr;
   prof_begin(c, s);
-  if ((e = launch_stage_1d(c->eq, c->fp32, MODE_RHS, a, c->ntiles, s)))
+  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_RHS, a, c->ntiles, s)))
     return cuda_fail(c, e, "rhs");
   prof_end(c, s, 1);
   c->launches = 2;
@@ -448,7 +484,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
         (equation != HWENO_EULER || !(std::sin(bc->dmr_angle) > 0) || !(std::tan(bc->dmr_angle) > 0)))
       return bad("dmr");
   }
-  // sizes and (1D) tile tables
+  // sizes and (1D) tile tables: capacity for the smallest tile of any variant
   std::vector<int> tinst, tstart;
   std::vector<long long> off(c->batch);
   c->inst_dx.resize(c->batch);
@@ -457,25 +493,28 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
     off[k] = acc;
     acc += c->nx[k];
     c->inst_dx[k] = (c->x1 - c->x0) / c->nx[k];
-    if (grid->dim == 1)
-      for (int s = 0; s < c->nx[k]; s += kTile1D) { tinst.push_back(k); tstart.push_back(s); }
   }
-  if (grid->dim == 2) {
+  if (grid->dim == 1) {
+    tile_table(c->nx, kMinTile1D, tinst, tstart);
+    c->tiles_cap = (int)tinst.size();
+    tile_table(c->nx, kTile1D, tinst, tstart);
+  } else {
     acc = (long long)c->nx[0] * c->ny;
     tinst.push_back(0);
     tstart.push_back(0);
+    c->tiles_cap = 1;
   }
   c->npts = acc;
   c->elems = (size_t)c->m * (size_t)acc;
   c->ntiles = (int)tinst.size();
-  c->ntiles_tot = grid->dim == 1 ? c->ntiles
+  c->ntiles_tot = grid->dim == 1 ? c->tiles_cap
                                  : ((c->nx[0] + kTileX2D - 1) / kTileX2D) * c->ny;
 
   int rc = HWENO_OK;
   const size_t fb = c->elems * c->esize;
   const size_t B = (size_t)c->batch;
-  if ((rc = dalloc(c, &c->d_tile_inst, sizeof(int) * tinst.size())) ||
-      (rc = dalloc(c, &c->d_tile_start, sizeof(int) * tstart.size())) ||
+  if ((rc = dalloc(c, &c->d_tile_inst, sizeof(int) * c->tiles_cap)) ||
+      (rc = dalloc(c, &c->d_tile_start, sizeof(int) * c->tiles_cap)) ||
       (rc = dalloc(c, &c->d_inst_n, sizeof(int) * B)) ||
       (rc = dalloc(c, &c->d_inst_off, sizeof(long long) * B)) ||
       (rc = dalloc(c, &c->d_inst_dx, sizeof(double) * B)) ||
@@ -538,7 +577,9 @@ int hweno_set_options(hweno_ctx* c, const hweno_options* o) {
   if (check_options(o, why) != HWENO_OK) return fail(c, HWENO_EINVAL, why);
   const hweno_options old = c->opt;
   c->opt = *o;
-  const int rc = upload_hx(c);
+  int rc = upload_hx(c);
+  if (rc == HWENO_OK && c->dim == 1 && o->tile_variant != c->variant)
+    rc = use_variant(c, o->tile_variant);
   if (rc != HWENO_OK) c->opt = old;
   return rc;
 }
@@ -649,11 +690,70 @@ int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t
   return hweno_sync_status(c, stream);
 }
 
+int hweno_autotune(hweno_ctx* c, const void* U, const void* V, const void* W, const double* t,
+                   double t_end, int* chosen, double* ms, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!U || !V || !t) return fail(c, HWENO_EINVAL, "null array");
+  if (c->dim == 2) {  // one tile shape in 2D
+    if (chosen) *chosen = 0;
+    return HWENO_OK;
+  }
+  (void)W;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, HWENO_ECUDA, "event");
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(c, HWENO_ECUDA, "event"); }
+  int best = 0;
+  float best_ms = 1e30f;
+  int rc = HWENO_OK;
+  for (int v = 0; v < kNumVariants1D && rc == HWENO_OK; ++v) {
+    if ((rc = use_variant(c, v)) != HWENO_OK) break;
+    Args1D a = base_args_1d(c);
+    a.t = t; a.t_end = t_end; a.skip_done = 1; a.dt = c->d_dt; a.lands = c->d_lands;
+    a.U = U; a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
+    a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
+    Args1D pre = a;  // wave speed of U into slot 0, read by the stage-1 launches
+    pre.alpha_out = slot(c, 0);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)) ||
+        (e = launch_alpha_1d(c->eq, c->fp32, v, pre, c->ntiles, s))) {
+      rc = cuda_fail(c, e, "autotune");
+      break;
+    }
+    float tv = 1e30f;
+    for (int r = 0; r < 4; ++r) {  // first launch warms up, then the best of three
+      cudaEventRecord(e0, s);
+      if ((e = launch_stage_1d(c->eq, c->fp32, v, MODE_STAGE1, a, c->ntiles, s))) {
+        rc = cuda_fail(c, e, "autotune");
+        break;
+      }
+      cudaEventRecord(e1, s);
+      if ((e = cudaEventSynchronize(e1))) { rc = cuda_fail(c, e, "autotune"); break; }
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e0, e1);
+      if (r > 0) tv = std::min(tv, x);
+    }
+    if (ms) ms[v] = tv;
+    if (tv < best_ms) { best_ms = tv; best = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HWENO_OK) {
+    use_variant(c, 0);
+    return rc;
+  }
+  if ((rc = use_variant(c, best)) != HWENO_OK) return rc;
+  c->opt.tile_variant = best;
+  if (chosen) *chosen = best;
+  return hweno_sync_status(c, stream);
+}
+
 int hweno_totals(hweno_ctx* c, const void* U, double* totals, void* stream) {
   if (!c) return HWENO_EINVAL;
   if (!U || !totals) return fail(c, HWENO_EINVAL, "null array");
   const double cell = c->dim == 2 ? ((c->x1 - c->x0) / c->nx[0]) * ((c->y1 - c->y0) / c->ny) : 0.0;
-  const cudaError_t e = launch_totals(c->m, c->fp32, c->dim, U, c->ntiles_tot, c->d_tile_inst,
+  const int ntot = c->dim == 1 ? c->ntiles : c->ntiles_tot;
+  const cudaError_t e = launch_totals(c->m, c->fp32, c->dim, U, ntot, c->tile, c->d_tile_inst,
                                       c->d_tile_start, c->d_inst_n, c->d_inst_off, c->batch,
                                       c->nx[0], c->ny, cell, c->dim == 1 ? c->d_inst_dx : nullptr,
                                       c->d_partial, totals, static_cast<cudaStream_t>(stream));

@@ -95,7 +95,8 @@ bool weights_valid(const double* w) {
 bool options_valid(const hweno_options* o) {
   return weights_valid(o->lin_w) && weights_valid(o->lim_d) && o->eps > 0 && o->cfl > 0 &&
          o->dt_mode >= 0 && o->dt_mode <= 2 && (o->dt_mode != 2 || o->dt_fixed > 0) &&
-         o->limiter >= 0 && o->limiter <= 2 && o->eig_avg >= 0 && o->eig_avg <= 1;
+         o->limiter >= 0 && o->limiter <= 2 && o->eig_avg >= 0 && o->eig_avg <= 1 &&
+         o->tile_variant == 0;
 }
 
 bool bc_valid(int b) { return b >= HWENO_BC_PERIODIC && b <= HWENO_BC_INFLOW; }
@@ -180,16 +181,16 @@ extern "C" int hweno_step_1d_noalloc(int equation, int nx, double x0, double x1,
 
   a.U = U;
   a.alpha_out = alpha + 0;
-  if (launch_alpha_1d(equation, fp32, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
+  if (launch_alpha_1d(equation, fp32, 0, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
   a.U = U; a.V = V; a.Uout = U1; a.Vout = V1; a.Vt0out = Vt0;
   a.alpha_in = reinterpret_cast<const double*>(alpha + 0); a.alpha_out = alpha + 1;
-  if (launch_stage_1d(equation, fp32, MODE_STAGE1, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
+  if (launch_stage_1d(equation, fp32, 0, MODE_STAGE1, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
   a.U = U1; a.V = V1; a.U0 = U; a.Vt0 = Vt0; a.Uout = U2; a.Vout = V2; a.Vt0out = nullptr;
   a.alpha_in = reinterpret_cast<const double*>(alpha + 1); a.alpha_out = alpha + 2;
-  if (launch_stage_1d(equation, fp32, MODE_STAGE2, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
+  if (launch_stage_1d(equation, fp32, 0, MODE_STAGE2, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
   a.U = U2; a.V = V2; a.U0 = U; a.Vt0 = Vt0; a.Uout = U; a.Vout = V;
   a.alpha_in = reinterpret_cast<const double*>(alpha + 2); a.alpha_out = nullptr;
-  if (launch_stage_1d(equation, fp32, MODE_STAGE3, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
+  if (launch_stage_1d(equation, fp32, 0, MODE_STAGE3, a, ntiles, s) != cudaSuccess) return HWENO_ECUDA;
   if (launch_finalize(1, a.dt, a.lands, t, t_end, dt_used, reinterpret_cast<const double*>(alpha),
                       reinterpret_cast<int*>(base + kOffActive), a.status, nullptr, 1,
                       nullptr, s) != cudaSuccess)

@@ -12,11 +12,21 @@ enum : unsigned { STATUS_NONFINITE = 1u };
 
 enum Mode { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE2 = 2, MODE_STAGE3 = 3 };
 
-// 1D tiles: one CTA of kThreads1D threads handles up to kTile1D consecutive
-// points of one instance, so that each phase takes one pass: kTile1D + 4
-// loaded points, kTile1D + 1 interfaces and kTile1D updates all fit in 128.
+// 1D tiles: one CTA of `threads` threads handles up to threads * ppt - 4
+// consecutive points of one instance, so that each phase takes ppt passes:
+// the tile plus four ghosts, its interfaces and its updates all fit in
+// threads * ppt slots. Variant 0 (128 threads, one point each) is the
+// default; hweno_autotune measures the others. kThreads1D is the CTA size of
+// the wave-speed kernel.
+struct TileVariant {
+  int threads, ppt;
+};
+constexpr TileVariant kVariants1D[] = {{128, 1}, {64, 1}, {256, 1}, {128, 2}, {64, 2}};
+constexpr int kNumVariants1D = 5;
+constexpr int tile_points(int v) { return kVariants1D[v].threads * kVariants1D[v].ppt - 4; }
 constexpr int kThreads1D = 128;
-constexpr int kTile1D = kThreads1D - 4;
+constexpr int kTile1D = tile_points(0);
+constexpr int kMinTile1D = 60;  // smallest tile of any variant
 
 struct SchemeParams {
   double lin_w[3], lim_d[3], eps, cfl, dt_fixed;
@@ -143,16 +153,30 @@ cudaError_t launch_ysweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaS
 // Conserved totals (totals.cu): per-tile FP64 partial sums, then a
 // fixed-order sum per instance. Tiles: the 1D tile table, or row segments of
 // kTileX2D points in 2D (instance 0).
-cudaError_t launch_totals(int m, bool fp32, int dim, const void* U, int ntiles,
+cudaError_t launch_totals(int m, bool fp32, int dim, const void* U, int ntiles, int tile,
                           const int* tile_inst, const int* tile_start, const int* inst_n,
                           const long long* inst_off, int batch, int nx, int ny, double cell,
                           const double* inst_dx, double* partial, double* totals,
                           cudaStream_t s);
 
-// Launchers (stage1d.cu). eq: 0 Burgers, 1 Euler; fp32: precision.
-cudaError_t launch_alpha_1d(int eq, bool fp32, const Args1D& a, int ntiles, cudaStream_t s);
-cudaError_t launch_stage_1d(int eq, bool fp32, int mode, const Args1D& a, int ntiles,
-                            cudaStream_t s);
+// Launchers (stage1d.cu, stage1d_f32.cu). eq: 0 Burgers, 1 Euler; variant:
+// index into kVariants1D (the tile table must match its tile_points).
+cudaError_t launch_alpha_1d_f64(int eq, int variant, const Args1D& a, int ntiles, cudaStream_t s);
+cudaError_t launch_alpha_1d_f32(int eq, int variant, const Args1D& a, int ntiles, cudaStream_t s);
+cudaError_t launch_stage_1d_f64(int eq, int variant, int mode, const Args1D& a, int ntiles,
+                                cudaStream_t s);
+cudaError_t launch_stage_1d_f32(int eq, int variant, int mode, const Args1D& a, int ntiles,
+                                cudaStream_t s);
+inline cudaError_t launch_alpha_1d(int eq, bool fp32, int variant, const Args1D& a, int ntiles,
+                                   cudaStream_t s) {
+  return fp32 ? launch_alpha_1d_f32(eq, variant, a, ntiles, s)
+              : launch_alpha_1d_f64(eq, variant, a, ntiles, s);
+}
+inline cudaError_t launch_stage_1d(int eq, bool fp32, int variant, int mode, const Args1D& a,
+                                   int ntiles, cudaStream_t s) {
+  return fp32 ? launch_stage_1d_f32(eq, variant, mode, a, ntiles, s)
+              : launch_stage_1d_f64(eq, variant, mode, a, ntiles, s);
+}
 // Time update after stage 3; counts the instances still active and, when
 // pu is not null, adds inst_n[k] * rows (the instance's points; rows = ny in
 // 2D, 1 in 1D) of every instance that took the step.

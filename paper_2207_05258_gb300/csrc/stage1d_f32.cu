@@ -1,0 +1,18 @@
+// FP32 instantiations of the one-dimensional stage kernels (state and
+// reconstruction in single precision; wave speeds, time steps and times stay
+// FP64). Separate translation unit so that both precisions compile in
+// parallel.
+#include "stage1d_impl.cuh"
+
+namespace hweno {
+
+cudaError_t launch_alpha_1d_f32(int eq, int variant, const Args1D& a, int ntiles, cudaStream_t s) {
+  return alpha_prec<float>(eq, variant, a, ntiles, s);
+}
+
+cudaError_t launch_stage_1d_f32(int eq, int variant, int mode, const Args1D& a, int ntiles,
+                                cudaStream_t s) {
+  return stage_prec<float>(eq, variant, mode, a, ntiles, s);
+}
+
+}  // namespace hweno

@@ -1,0 +1,420 @@
+// Implementation of the one-dimensional L-HWENO stage kernels, shared by the
+// FP64 (stage1d.cu) and FP32 (stage1d_f32.cu) translation units; see
+// stage1d.cu for the structure of a stage.
+#pragma once
+
+#include <cfloat>
+
+#include "hweno.h"
+#include "hweno_math.cuh"
+#include "internal.h"
+
+namespace hweno {
+namespace {
+
+
+template <int EQ>
+struct Dim1 { static constexpr int M = EQ == HWENO_BURGERS ? 1 : 3; };
+
+// Source of point i (possibly a ghost) of an instance with n points.
+// kind: 0 copy, 1 mirror (reflective wall), 2 imposed state.
+__device__ __forceinline__ int map_1d(int i, int n, int bclo, int bchi, int& kind) {
+  kind = 0;
+  if (i >= 0 && i < n) return i;
+  const int b = i < 0 ? bclo : bchi;
+  if (b == HWENO_BC_PERIODIC) return i < 0 ? i + n : i - n;
+  if (b == HWENO_BC_OUTFLOW) return i < 0 ? 0 : n - 1;
+  if (b == HWENO_BC_REFLECTIVE) { kind = 1; return i < 0 ? -i - 1 : 2 * n - 1 - i; }
+  kind = 2;
+  return 0;
+}
+
+// Sign of component c of U under reflection (Burgers: u odd; Euler: momentum
+// odd). The normal derivative takes the opposite sign.
+template <int EQ>
+__device__ __forceinline__ float refl_sign(int c) {
+  return EQ == HWENO_BURGERS ? -1.f : (c == 1 ? -1.f : 1.f);
+}
+
+template <int EQ, class Real>
+__device__ __forceinline__ Real wave_speed(const Real* u, Real gam) {
+  if constexpr (EQ == HWENO_BURGERS) {
+    return fabs(u[0]);
+  } else {
+    const Real ir = Real(1) / u[0];
+    const Real vel = u[1] * ir;
+    const Real p = (gam - Real(1)) * (u[2] - Real(0.5) * u[1] * vel);
+    return fabs(vel) + sqrt(gam * p * ir);
+  }
+}
+
+// Time step of an instance from the wave speed of u^n (dt_mode), clipped to
+// land on t_end. Same expression order as the problem statement:
+// dt = cfl / (alpha / h).
+__device__ __forceinline__ double time_step(const SchemeParams& sp, double alpha, double h,
+                                            double t, double t_end, int& lands) {
+  double dt;
+  if (sp.dt_mode == 2) {
+    dt = sp.dt_fixed;
+  } else {
+    const double rate = alpha / h;
+    dt = rate > 0.0 ? sp.cfl / rate : __longlong_as_double(0x7ff0000000000000LL);
+  }
+  const double rest = t_end - t;
+  lands = dt >= rest;
+  return lands ? rest : dt;
+}
+
+// Wave speed of the stage input, per instance (alpha of Sec. 2.1).
+template <int EQ, class Real, int P>
+__global__ void __launch_bounds__(kThreads1D) k_alpha_1d(const __grid_constant__ Args1D a) {
+  constexpr int M = Dim1<EQ>::M;
+  __shared__ Real red[kThreads1D / 32];
+  const int b = blockIdx.x;
+  const int k = a.tile_inst[b], s = a.tile_start[b], n = a.inst_n[k];
+  if (a.skip_done && !(a.t[k] < a.t_end)) return;
+  const int np = min(P, n - s);
+  const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+  Real amax = Real(0);
+  bool bad = false;
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    Real u[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + s + j];
+    const Real sp = wave_speed<EQ>(u, gam);
+    bad |= !(sp <= real_max<Real>());
+    amax = fmax(amax, sp);
+  }
+  if (bad) atomicOr(a.status, STATUS_NONFINITE);
+  amax = block_max_t(amax, red);
+  if (threadIdx.x == 0)
+    atomicMax(&a.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
+}
+
+// Shared-memory layout of one tile of NT * PPT points (P = NT * PPT - 4
+// updated points, two ghosts per side, P + 1 interfaces).
+template <int EQ, class Real, int NT, int PPT>
+struct Layout1D {
+  static constexpr int M = Dim1<EQ>::M;
+  static constexpr bool EUL = EQ == HWENO_EULER;
+  static constexpr int P = NT * PPT - 4;
+  static constexpr int NP = P + 4;
+  static constexpr int NF = P + 1;
+  static constexpr int NE = EUL ? 4 : 0;  // sqrt(rho), u, H, c^2
+  static constexpr size_t bytes = sizeof(Real) * ((size_t)(6 * M + NE) * NP + 2 * M * NF);
+};
+
+// Resident CTAs requested per SM for a variant: the per-precision setting for
+// 128-thread CTAs, scaled to the variant's thread count.
+template <class Real, int NT>
+struct MinBlocks1D {
+  static constexpr int base = MinBlocks<Real, HWENO_MINB_1D_F64, HWENO_MINB_1D_F32>::value;
+  static constexpr int value = base * 128 / NT > 0 ? base * 128 / NT : 1;
+};
+
+template <int EQ, class Real, int MODE, int NT, int PPT>
+__global__ void __launch_bounds__(NT, (MinBlocks1D<Real, NT>::value))
+k_stage_1d(const __grid_constant__ Args1D a) {
+  using Lay = Layout1D<EQ, Real, NT, PPT>;
+  constexpr int M = Lay::M;
+  constexpr int NP = Lay::NP;
+  constexpr int NF = Lay::NF;
+  constexpr bool EUL = Lay::EUL;
+  extern __shared__ __align__(16) unsigned char smem1d[];
+  Real* base = reinterpret_cast<Real*>(smem1d);
+  Real(*sU)[NP] = reinterpret_cast<Real(*)[NP]>(base);
+  Real(*sV)[NP] = reinterpret_cast<Real(*)[NP]>(base + 1 * M * NP);
+  Real(*sFp)[NP] = reinterpret_cast<Real(*)[NP]>(base + 2 * M * NP);
+  Real(*sFm)[NP] = reinterpret_cast<Real(*)[NP]>(base + 3 * M * NP);
+  Real(*sHp)[NP] = reinterpret_cast<Real(*)[NP]>(base + 4 * M * NP);
+  Real(*sHm)[NP] = reinterpret_cast<Real(*)[NP]>(base + 5 * M * NP);
+  Real(*sE)[NP] = reinterpret_cast<Real(*)[NP]>(base + 6 * M * NP);
+  Real(*sF)[NF] = reinterpret_cast<Real(*)[NF]>(base + (6 * M + Lay::NE) * NP);
+  Real(*sD)[NF] = reinterpret_cast<Real(*)[NF]>(base + (6 * M + Lay::NE) * NP + M * NF);
+  __shared__ Real red[NT / 32];
+  __shared__ double s_dt;
+
+  const int b = blockIdx.x;
+  const int k = a.tile_inst[b], s = a.tile_start[b], n = a.inst_n[k];
+  if (a.skip_done && !(a.t[k] < a.t_end)) return;
+  const int np = min(Lay::P, n - s);
+  const long long off = a.inst_off[k] * M;
+  const Real* geo = pick<Real>(a.inst_geo, a.inst_geof) + 3 * k;
+  const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
+  const Real alpha = Real(a.alpha_in[k]);
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+  const Real gm1 = gam - Real(1);
+  const Weights<Real> w = weights_from(pick<Real>(a.sp.wd, a.sp.wf));
+
+  // time step: once per CTA (thread 0), read back after the barriers below
+  if (threadIdx.x == 0) {
+    double dt = 0.0;
+    if constexpr (MODE == MODE_STAGE1) {
+      int lands;
+      dt = time_step(a.sp, a.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
+      if (s == 0) { a.dt[k] = dt; a.lands[k] = lands; }
+    } else if constexpr (MODE != MODE_RHS) {
+      dt = a.dt[k];
+    }
+    s_dt = dt;
+  }
+
+  // 1-2: tile load with ghosts; point fluxes and splitting
+  {
+    const Real* U = static_cast<const Real*>(a.U) + off;
+    const Real* V = static_cast<const Real*>(a.V) + off;
+    const Real hdx = Real(0.5) * dx;
+    for (int g = threadIdx.x; g < np + 4; g += blockDim.x) {
+      int kind;
+      const int src = map_1d(s - 2 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
+      Real u[M], v[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        if (kind == 2) {
+          u[c] = Real(a.sp.inflow[c]);
+          v[c] = Real(0);
+        } else {
+          u[c] = U[(long long)c * n + src];
+          v[c] = V[(long long)c * n + src];
+          if (kind == 1) { const Real sg = Real(refl_sign<EQ>(c)); u[c] *= sg; v[c] *= -sg; }
+        }
+        sU[c][g] = u[c];
+        sV[c][g] = v[c];
+      }
+      Real F[M], H[M];
+      if constexpr (!EUL) {
+        F[0] = Real(0.5) * u[0] * u[0];
+        H[0] = u[0] * v[0];
+      } else {
+        // 1/rho and sqrt(rho) from one reciprocal square root
+        const Real rr = rsq(u[0]);
+        const Real ir = rr * rr;
+        const Real vel = u[1] * ir;
+        const Real p = gm1 * (u[2] - Real(0.5) * u[1] * vel);
+        const Real Ep = u[2] + p;
+        F[0] = u[1];
+        F[1] = u[1] * vel + p;
+        F[2] = Ep * vel;
+        const Real dvel = (v[1] - vel * v[0]) * ir;
+        const Real dp = gm1 * (v[2] - vel * v[1] + Real(0.5) * vel * vel * v[0]);
+        H[0] = v[1];
+        H[1] = v[1] * vel + u[1] * dvel + dp;
+        H[2] = (v[2] + dp) * vel + Ep * dvel;
+        sE[0][g] = u[0] * rr;
+        sE[1][g] = vel;
+        sE[2][g] = Ep * ir;
+        sE[3][g] = gam * p * ir;
+      }
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
+        sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
+        sHp[c][g] = hdx * (H[c] + alpha * v[c]);
+        sHm[c][g] = hdx * (H[c] - alpha * v[c]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // 3: interfaces x_{s+j-1/2}, j = 0..np; left point at shared index j + 1
+  for (int j = threadIdx.x; j <= np; j += blockDim.x) {
+    const int gl = j + 1;
+    if constexpr (!EUL) {
+      sF[0][j] = interface_flux(sFp[0][gl - 1], sFp[0][gl], sFp[0][gl + 1], sHp[0][gl - 1],
+                                sHp[0][gl], sHp[0][gl + 1], sFm[0][gl], sFm[0][gl + 1],
+                                sFm[0][gl + 2], sHm[0][gl], sHm[0][gl + 1], sHm[0][gl + 2], w);
+    } else {
+      Real uu, HH, cc;
+      if (a.sp.eig_avg == 0) {  // Roe average of U_i, U_{i+1}
+        const Real sl = sE[0][gl], sr = sE[0][gl + 1];
+        const Real is = Real(1) / (sl + sr);
+        uu = (sl * sE[1][gl] + sr * sE[1][gl + 1]) * is;
+        HH = (sl * sE[2][gl] + sr * sE[2][gl + 1]) * is;
+      } else {  // arithmetic mean state
+        const Real r = Real(0.5) * (sU[0][gl] + sU[0][gl + 1]);
+        const Real mo = Real(0.5) * (sU[1][gl] + sU[1][gl + 1]);
+        const Real E = Real(0.5) * (sU[2][gl] + sU[2][gl + 1]);
+        const Real ir = Real(1) / r;
+        uu = mo * ir;
+        HH = (E + gm1 * (E - Real(0.5) * mo * uu)) * ir;
+      }
+      Real ic;
+      sound_speed(gm1 * (HH - Real(0.5) * uu * uu), cc, ic);
+      Eigen<Real, 3> e;
+      euler_eigen<Real, 3>(0, uu, Real(0), HH, cc, ic, gm1, e);
+      Frac<Real> fr[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const Real l0 = e.L[q][0], l1 = e.L[q][1], l2 = e.L[q][2];
+        auto pj = [&](Real (*A)[NP], int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
+        fr[q] = interface_flux_frac(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1),
+                                    pj(sHp, gl - 1), pj(sHp, gl), pj(sHp, gl + 1),
+                                    pj(sFm, gl), pj(sFm, gl + 1), pj(sFm, gl + 2),
+                                    pj(sHm, gl), pj(sHm, gl + 1), pj(sHm, gl + 2), w);
+      }
+      Real f[3];
+      resolve2(fr[0], fr[1], f[0], f[1]);
+      f[2] = resolve1(fr[2]);
+      Real out[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[c] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sF[c][j] = out[c];
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+      sD[c][j] = derivative_flux(sFp[c][gl - 1], sFp[c][gl], sFp[c][gl + 1], sHp[c][gl - 1],
+                                 sHp[c][gl], sHp[c][gl + 1], sFm[c][gl], sFm[c][gl + 1],
+                                 sFm[c][gl + 2], sHm[c][gl], sHm[c][gl + 1], sHm[c][gl + 2]);
+  }
+  __syncthreads();
+
+  // 4: points
+  const Real rdt = Real(s_dt);
+  Real amax = Real(0);
+  bool bad = false;
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    const int g = j + 2;
+    Real l1[M], l2[M], vt[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      l1[c] = -(sF[c][j + 1] - sF[c][j]) * idx;
+      l2[c] = -(sD[c][j + 1] - sD[c][j]) * idx2;
+    }
+    if (a.sp.limiter == 0) {
+#pragma unroll
+      for (int c = 0; c < M; ++c) vt[c] = sV[c][g];
+    } else if (!EUL || a.sp.limiter == 2) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
+                                   dx * sV[c][g + 1], w) * idx;
+    } else if constexpr (EUL) {
+      Real cg, icg;
+      sound_speed(sE[3][g], cg, icg);
+      Eigen<Real, 3> e;
+      euler_eigen<Real, 3>(0, sE[1][g], Real(0), sE[2][g], cg, icg, gm1, e);
+      Frac<Real> zr[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const Real l0 = e.L[q][0], l1q = e.L[q][1], l2q = e.L[q][2];
+        auto pj = [&](Real (*A)[NP], int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
+        zr[q] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
+                                        dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
+      }
+      Real z[3];
+      resolve2(zr[0], zr[1], z[0], z[1]);
+      z[2] = resolve1(zr[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        vt[c] = (e.R[c][0] * z[0] + e.R[c][1] * z[1] + e.R[c][2] * z[2]) * idx;
+    }
+
+    const long long base = off + s + j;
+    if constexpr (MODE == MODE_RHS) {
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        static_cast<Real*>(a.L1)[base + (long long)c * n] = l1[c];
+        static_cast<Real*>(a.L2)[base + (long long)c * n] = l2[c];
+        if (a.Vlim) static_cast<Real*>(a.Vlim)[base + (long long)c * n] = vt[c];
+      }
+    } else {
+      Real un[M], vn[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        const long long q = base + (long long)c * n;
+        if constexpr (MODE == MODE_STAGE1) {
+          un[c] = sU[c][g] + rdt * l1[c];
+          vn[c] = vt[c] + rdt * l2[c];
+          static_cast<Real*>(a.Vt0out)[q] = vt[c];
+        } else if constexpr (MODE == MODE_STAGE2) {
+          const Real u0 = static_cast<const Real*>(a.U0)[q];
+          const Real v0 = static_cast<const Real*>(a.Vt0)[q];
+          un[c] = Real(0.75) * u0 + Real(0.25) * (sU[c][g] + rdt * l1[c]);
+          vn[c] = Real(0.75) * v0 + Real(0.25) * (vt[c] + rdt * l2[c]);
+        } else {
+          const Real u0 = static_cast<const Real*>(a.U0)[q];
+          const Real v0 = static_cast<const Real*>(a.Vt0)[q];
+          un[c] = Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * (sU[c][g] + rdt * l1[c]);
+          vn[c] = Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * (vt[c] + rdt * l2[c]);
+        }
+        static_cast<Real*>(a.Uout)[q] = un[c];
+        static_cast<Real*>(a.Vout)[q] = vn[c];
+      }
+      if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
+        const Real sp = wave_speed<EQ>(un, gam);
+        bad |= !(sp <= real_max<Real>());
+        amax = fmax(amax, sp);
+      }
+    }
+  }
+  if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
+    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    amax = block_max_t(amax, red);
+    if (threadIdx.x == 0)
+      atomicMax(&a.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
+  }
+}
+
+template <int EQ, class Real, int MODE, int NT, int PPT>
+cudaError_t stage_launch(const Args1D& a, int ntiles, cudaStream_t s) {
+  constexpr size_t bytes = Layout1D<EQ, Real, NT, PPT>::bytes;
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(k_stage_1d<EQ, Real, MODE, NT, PPT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_stage_1d<EQ, Real, MODE, NT, PPT><<<ntiles, NT, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int EQ, class Real, int NT, int PPT>
+cudaError_t stage_modes(int mode, const Args1D& a, int ntiles, cudaStream_t s) {
+  switch (mode) {
+    case MODE_RHS: return stage_launch<EQ, Real, MODE_RHS, NT, PPT>(a, ntiles, s);
+    case MODE_STAGE1: return stage_launch<EQ, Real, MODE_STAGE1, NT, PPT>(a, ntiles, s);
+    case MODE_STAGE2: return stage_launch<EQ, Real, MODE_STAGE2, NT, PPT>(a, ntiles, s);
+    default: return stage_launch<EQ, Real, MODE_STAGE3, NT, PPT>(a, ntiles, s);
+  }
+}
+
+// Variants of kVariants1D: (threads, points per thread).
+template <int EQ, class Real>
+cudaError_t stage_variants(int variant, int mode, const Args1D& a, int ntiles, cudaStream_t s) {
+  switch (variant) {
+    case 1: return stage_modes<EQ, Real, 64, 1>(mode, a, ntiles, s);
+    case 2: return stage_modes<EQ, Real, 256, 1>(mode, a, ntiles, s);
+    case 3: return stage_modes<EQ, Real, 128, 2>(mode, a, ntiles, s);
+    case 4: return stage_modes<EQ, Real, 64, 2>(mode, a, ntiles, s);
+    default: return stage_modes<EQ, Real, 128, 1>(mode, a, ntiles, s);
+  }
+}
+
+template <int EQ, class Real>
+cudaError_t alpha_variants(int variant, const Args1D& a, int ntiles, cudaStream_t s) {
+  switch (tile_points(variant)) {
+    case 60: k_alpha_1d<EQ, Real, 60><<<ntiles, kThreads1D, 0, s>>>(a); break;
+    case 252: k_alpha_1d<EQ, Real, 252><<<ntiles, kThreads1D, 0, s>>>(a); break;
+    default: k_alpha_1d<EQ, Real, 124><<<ntiles, kThreads1D, 0, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t stage_prec(int eq, int variant, int mode, const Args1D& a, int ntiles, cudaStream_t s) {
+  return eq == HWENO_BURGERS ? stage_variants<HWENO_BURGERS, Real>(variant, mode, a, ntiles, s)
+                             : stage_variants<HWENO_EULER, Real>(variant, mode, a, ntiles, s);
+}
+
+template <class Real>
+cudaError_t alpha_prec(int eq, int variant, const Args1D& a, int ntiles, cudaStream_t s) {
+  return eq == HWENO_BURGERS ? alpha_variants<HWENO_BURGERS, Real>(variant, a, ntiles, s)
+                             : alpha_variants<HWENO_EULER, Real>(variant, a, ntiles, s);
+}
+
+}  // namespace
+}  // namespace hweno

@@ -11,7 +11,8 @@ namespace {
 constexpr int kThreads = 128;
 
 template <class Real>
-__global__ void __launch_bounds__(kThreads) k_totals_partial(int m, int dim, const Real* U,
+__global__ void __launch_bounds__(kThreads) k_totals_partial(int m, int dim, int tile,
+                                                             const Real* U,
                                                              const int* tile_inst,
                                                              const int* tile_start,
                                                              const int* inst_n,
@@ -23,7 +24,7 @@ __global__ void __launch_bounds__(kThreads) k_totals_partial(int m, int dim, con
   int np;
   if (dim == 1) {
     const int k = tile_inst[b], s = tile_start[b], n = inst_n[k];
-    np = min(kTile1D, n - s);
+    np = min(tile, n - s);
     base = inst_off[k] * m + s;
     stride = n;
   } else {
@@ -78,17 +79,17 @@ __global__ void k_totals_final_2d(int m, int ntiles, const double* partial, doub
 
 }  // namespace
 
-cudaError_t launch_totals(int m, bool fp32, int dim, const void* U, int ntiles,
+cudaError_t launch_totals(int m, bool fp32, int dim, const void* U, int ntiles, int tile,
                           const int* tile_inst, const int* tile_start, const int* inst_n,
                           const long long* inst_off, int batch, int nx, int ny, double cell,
                           const double* inst_dx, double* partial, double* totals,
                           cudaStream_t s) {
   if (fp32)
-    k_totals_partial<float><<<ntiles, kThreads, 0, s>>>(m, dim, static_cast<const float*>(U),
+    k_totals_partial<float><<<ntiles, kThreads, 0, s>>>(m, dim, tile, static_cast<const float*>(U),
                                                         tile_inst, tile_start, inst_n, inst_off,
                                                         nx, ny, partial);
   else
-    k_totals_partial<double><<<ntiles, kThreads, 0, s>>>(m, dim, static_cast<const double*>(U),
+    k_totals_partial<double><<<ntiles, kThreads, 0, s>>>(m, dim, tile, static_cast<const double*>(U),
                                                          tile_inst, tile_start, inst_n,
                                                          inst_off, nx, ny, partial);
   cudaError_t e = cudaGetLastError();

@@ -50,7 +50,7 @@ class Options(ctypes.Structure):
     _fields_ = [("lin_w", ctypes.c_double * 3), ("lim_d", ctypes.c_double * 3),
                 ("eps", ctypes.c_double), ("cfl", ctypes.c_double), ("dt_mode", ctypes.c_int),
                 ("dt_fixed", ctypes.c_double), ("limiter", ctypes.c_int),
-                ("eig_avg", ctypes.c_int)]
+                ("eig_avg", ctypes.c_int), ("tile_variant", ctypes.c_int)]
 
 
 _VP = ctypes.c_void_p
@@ -70,6 +70,8 @@ SIGNATURES = {
                                  ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_longlong), _VP]),
     "hweno_totals": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "hweno_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_int), _DP, _VP]),
     "hweno_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, _VP,
                                           _VP]),
     "hweno_sync_status": (ctypes.c_int, [_VP, _VP]),
@@ -203,6 +205,15 @@ class Solver:
         p = lambda x: None if x is None else ctypes.c_void_p(x.data_ptr())
         self._check(lib.hweno_step_host(self.h, p(U), p(V), p(W), p(t), float(t_end), nsteps,
                                         _stream()))
+
+    def autotune(self, U, V, W=None, t=None, t_end=float("inf")):
+        """hweno_autotune: returns (chosen variant, per-variant ms)."""
+        t = torch.zeros(self.batch, dtype=torch.float64, device=U.device) if t is None else t
+        chosen = ctypes.c_int(0)
+        ms = (ctypes.c_double * 5)()
+        self._check(lib.hweno_autotune(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t), float(t_end),
+                                       ctypes.byref(chosen), ms, _stream()))
+        return chosen.value, list(ms)
 
     def totals(self, U):
         """FP64 conserved totals, tensor [batch, m] (fixed summation order)."""

@@ -241,3 +241,57 @@ def double_mach(nx: int = 1920, ny: int = 480, t_end: float = 0.2, gamma: float 
                     ("inflow", "outflow", "dmr_bottom", "dmr_top"),
                     U.ravel().copy(), Z.ravel().copy(), Z.ravel().copy(), gas_gamma=gamma,
                     inflow=post_c, pre=pre_c, dmr_x0=x0, dmr_speed=10.0, dmr_angle=ang)
+
+
+def _euler1d_piecewise(name, n, x0, x1, pieces, bc, t_end, gamma=1.4):
+    """1D Euler with piecewise-constant primitive data: pieces is a list of
+    (x_right_edge, (rho, u, p)); V = 0 (no derivative of a jump)."""
+    x = centers(x0, x1, n)
+    rho, u, p = np.empty(n), np.empty(n), np.empty(n)
+    left = x0
+    for edge, (r, uu, pp) in pieces:
+        sel = (x >= left) & (x < edge)
+        rho[sel], u[sel], p[sel] = r, uu, pp
+        left = edge
+    U = euler_conserved(rho, u, p, gamma)
+    return Workload(name, "euler", 1, [n], 1, x0, x1, 0.0, 1.0, t_end,
+                    (bc, bc, "periodic", "periodic"), U.ravel().copy(),
+                    np.zeros_like(U).ravel(), gas_gamma=gamma)
+
+
+def lax(n: int = 200, t_end: float = 0.16) -> Workload:
+    """Lax problem (Example 3.5): (0.445, 0.698, 3.528) | (0.5, 0, 0.571),
+    jump at x = 0 on [-0.5, 0.5], outflow."""
+    return _euler1d_piecewise("lax", n, -0.5, 0.5,
+                              [(0.0, (0.445, 0.698, 3.528)), (np.inf, (0.5, 0.0, 0.571))],
+                              "outflow", t_end)
+
+
+def shu_osher(n: int = 400, t_end: float = 1.8) -> Workload:
+    """Shu-Osher problem (Example 3.6) on [-5, 5], outflow: a Mach 3 shock at
+    x = -4 running into rho = 1 + 0.2 sin(5x). The smooth part carries its
+    exact derivative."""
+    x = centers(-5.0, 5.0, n)
+    post = x < -4.0
+    rho = np.where(post, 3.857143, 1.0 + 0.2 * np.sin(5.0 * x))
+    u = np.where(post, 2.629369, 0.0)
+    p = np.where(post, 10.333333, 1.0)
+    U = euler_conserved(rho, u, p, 1.4)
+    drho = np.where(post, 0.0, np.cos(5.0 * x))
+    V = np.stack([drho, np.zeros(n), np.zeros(n)])
+    return Workload("shu_osher", "euler", 1, [n], 1, -5.0, 5.0, 0.0, 1.0, t_end,
+                    ("outflow", "outflow", "periodic", "periodic"), U.ravel().copy(),
+                    V.ravel().copy())
+
+
+def blast_waves(n: int = 800, t_end: float = 0.038) -> Workload:
+    """Interaction of two blast waves (Example 3.7) on [0, 1], reflective
+    walls: p = 1000 | 0.01 | 100 split at x = 0.1 and 0.9, rho = 1, u = 0."""
+    return _euler1d_piecewise("blast_waves", n, 0.0, 1.0,
+                              [(0.1, (1.0, 0.0, 1000.0)), (0.9, (1.0, 0.0, 0.01)),
+                               (np.inf, (1.0, 0.0, 100.0))], "reflective", t_end)
+
+
+# Linear-weight sets of the study in Example 3.7 (reconstruction G, limiter D).
+WEIGHT_SETS = {"G1": (0.99, 0.005, 0.005), "G2": (1 / 3, 1 / 3, 1 / 3), "G3": (0.01, 0.495, 0.495),
+               "D1": (0.99, 0.005, 0.005), "D2": (1 / 3, 1 / 3, 1 / 3), "D3": (0.01, 0.495, 0.495)}

@@ -82,3 +82,31 @@ def test_graph_run_needs_a_stream(hw):
     rc = hw.lib.hweno_run(s.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(V.data_ptr()), None,
                           ctypes.c_void_p(t.data_ptr()), 1.0, 10, 4, None, None, None)
     assert rc == hw.EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_tile_variant_gives_the_same_bits(hw, precision):
+    """The tile shape only changes which CTA computes a point, not its
+    arithmetic: all variants agree bit for bit, and the autotuner picks one."""
+    full = W.riemann_batch(count=24, seed=17)
+    w = full
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    outs = []
+    for v in range(5):
+        s = hw.Solver.from_workload(w, precision=precision, tile_variant=v)
+        U, V = torch.from_numpy(w.U).to("cuda", dt), torch.from_numpy(w.V).to("cuda", dt)
+        t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            s.step(U, V, None, t, w.t_end)
+        s.sync_status()
+        outs.append((U.cpu(), V.cpu(), t.cpu(), s.totals(U).cpu()))
+        s.close()
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
+    s = hw.Solver.from_workload(w, precision=precision)
+    U, V = torch.from_numpy(w.U).to("cuda", dt), torch.from_numpy(w.V).to("cuda", dt)
+    chosen, ms = s.autotune(U, V, None, torch.zeros(w.batch, dtype=torch.float64, device="cuda"),
+                            w.t_end)
+    assert 0 <= chosen < 5 and all(m > 0 for m in ms)
+    assert ms[chosen] == min(ms)

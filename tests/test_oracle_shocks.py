@@ -103,3 +103,27 @@ def test_dmr_short_run_positive():
     assert np.all(np.isfinite(U)) and np.all(rho > 0) and np.all(p > 0)
     # far right, ahead of the shock, the gas is still at rest
     assert np.allclose(U[:, :, -8:], np.array(w.pre)[:, None, None], atol=1e-10)
+
+
+def test_lax_example_against_exact_solution():
+    """Example 3.5 (Lax problem) at T = 0.16: the L1 density error against the
+    exact Riemann solution falls with N."""
+    errs = []
+    for n in (100, 200, 400):
+        w = W.lax(n)
+        U, _, _, t, _ = O.run(oracle_problem(w), w.U, w.V, None, 0.0, w.t_end)
+        x = W.centers(-0.5, 0.5, n)
+        rho = exact.riemann_exact((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), G, x, w.t_end, x0=0.0)[0]
+        errs.append(float(np.mean(np.abs(U[0] - rho))))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-2, errs
+
+
+def test_blast_waves_stay_physical_and_conserve_mass():
+    """Example 3.7 with reflective walls: mass is conserved exactly by the
+    flux form with mirrored ghosts (zero mass flux through the walls)."""
+    w = W.blast_waves(200, t_end=0.01)
+    U, _, _, t, _ = O.run(oracle_problem(w), w.U, w.V, None, 0.0, w.t_end)
+    rho, m, E = U
+    p = (G - 1) * (E - 0.5 * m * m / rho)
+    assert np.all(rho > 0) and np.all(p > 0)
+    assert abs(rho.sum() - w.U.reshape(3, -1)[0].sum()) < 1e-12 * rho.sum()
