@@ -87,7 +87,8 @@ def test_graph_run_needs_a_stream(hw):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_tile_variant_gives_the_same_bits(hw, precision):
     """The tile shape only changes which CTA computes a point, not its
-    arithmetic: all variants agree bit for bit, and the autotuner picks one."""
+    arithmetic: all variants give the same state bits, and the autotuner picks
+    the fastest."""
     full = W.riemann_batch(count=24, seed=17)
     w = full
     dt = torch.float64 if precision == "fp64" else torch.float32
@@ -102,8 +103,10 @@ def test_every_tile_variant_gives_the_same_bits(hw, precision):
         outs.append((U.cpu(), V.cpu(), t.cpu(), s.totals(U).cpu()))
         s.close()
     for o in outs[1:]:
-        for a, b in zip(outs[0], o):
+        for a, b in zip(outs[0][:3], o[:3]):
             assert torch.equal(a, b)
+        # the totals' fixed summation order follows the tile size
+        assert torch.allclose(outs[0][3], o[3], rtol=1e-14, atol=0)
     s = hw.Solver.from_workload(w, precision=precision)
     U, V = torch.from_numpy(w.U).to("cuda", dt), torch.from_numpy(w.V).to("cuda", dt)
     chosen, ms = s.autotune(U, V, None, torch.zeros(w.batch, dtype=torch.float64, device="cuda"),
