@@ -58,10 +58,10 @@ ALGO_WORDS_PER_COMPONENT = {1: 17, 2: 26}
 # x 2.07 GHz.
 PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # DRAM bytes per point and launch of the fused stage kernel from an ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum over points; summary
-# in profiles/k_stage_1d_euler_fp64_riemann_batch.md). An entry is removed
-# whenever the kernel changes after its capture.
-MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 134.0}
+# capture of a stage-1 launch (dram__bytes_read.sum + dram__bytes_write.sum
+# over points; profiles/k_stage_1d_euler_fp{64,32}_riemann_batch.md). An entry
+# is removed whenever the kernel changes after its capture.
+MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 100.9, "fp32": 40.2}
 
 
 def parse():
