@@ -59,6 +59,7 @@ class Problem(ctypes.Structure):
         ("eps", ctypes.c_double), ("cfl", ctypes.c_double),
         ("dt_mode", ctypes.c_int), ("dt_fixed", ctypes.c_double),
         ("limiter", ctypes.c_int), ("eig_avg", ctypes.c_int),
+        ("alpha_fixed", ctypes.c_double),
     ]
 
 
@@ -87,6 +88,9 @@ def _load():
             L.or_step.argtypes = [_P, _D, _D, _D, _D, ctypes.c_double, _D]
             L.or_run.argtypes = [_P, _D, _D, _D, _D, ctypes.c_double, ctypes.c_long]
             L.or_run.restype = ctypes.c_long
+            L.or_run_tangent.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double,
+                                         ctypes.c_long]
+            L.or_run_tangent.restype = ctypes.c_long
             L.or_flops_per_point_step.argtypes = [_P, _D, _D, _D]
             L.or_flops_per_point_step.restype = ctypes.c_double
             _lib = L
@@ -112,7 +116,7 @@ def problem(eq, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gas_gamma=1.4,
             bc=(BC_PERIODIC,) * 4, inflow=(0, 0, 0, 0), pre=(0, 0, 0, 0),
             dmr_x0=1.0 / 6.0, dmr_speed=10.0, dmr_angle=np.pi / 3.0,
             lin_w=(0.98, 0.01, 0.01), lim_d=(0.98, 0.01, 0.01), eps=1e-6, cfl=0.6,
-            dt_mode=0, dt_fixed=0.0, limiter=1, eig_avg=0) -> Problem:
+            dt_mode=0, dt_fixed=0.0, limiter=1, eig_avg=0, alpha_fixed=0.0) -> Problem:
     p = Problem()
     p.eq, p.dim, p.nx, p.ny = eq, dim, nx, (ny if dim == 2 else 1)
     p.x0, p.x1, p.y0, p.y1 = x0, x1, y0, y1
@@ -125,6 +129,7 @@ def problem(eq, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gas_gamma=1.4,
     p.lim_d[:] = lim_d
     p.eps, p.cfl, p.dt_mode, p.dt_fixed = eps, cfl, dt_mode, dt_fixed
     p.limiter, p.eig_avg = limiter, eig_avg
+    p.alpha_fixed = alpha_fixed
     return p
 
 
@@ -222,6 +227,22 @@ def run(p, U, V, W=None, t=0.0, t_end=1.0, max_steps=1 << 40):
     tt = np.array([t], dtype=np.float64)
     k = _load().or_run(ctypes.byref(p), _ptr(U), _ptr(V), _ptr(W), _ptr(tt), t_end, max_steps)
     return U, V, W, float(tt[0]), int(k)
+
+
+def run_tangent(p, U, V, W, dU, dV, dW=None, t=0.0, t_end=1.0, max_steps=1 << 40):
+    """Forward-mode derivative of a run (dual numbers): returns
+    (U, V, W, dU, dV, dW, t, steps) with alpha frozen in every stage (its
+    state dependence is not differentiated) and the run's own time steps."""
+    shp = _shape(p)
+    U, V = _arr(U).reshape(shp).copy(), _arr(V).reshape(shp).copy()
+    dU, dV = _arr(dU).reshape(shp).copy(), _arr(dV).reshape(shp).copy()
+    two = p.dim == 2
+    W = _arr(W).reshape(shp).copy() if two else None
+    dW = _arr(dW).reshape(shp).copy() if two else None
+    tt = np.array([t], dtype=np.float64)
+    k = _load().or_run_tangent(ctypes.byref(p), _ptr(U), _ptr(V), _ptr(W), _ptr(dU), _ptr(dV),
+                               _ptr(dW), _ptr(tt), t_end, max_steps)
+    return U, V, W, dU, dV, dW, float(tt[0]), int(k)
 
 
 def flops_per_point_step(p, U, V, W=None) -> float:

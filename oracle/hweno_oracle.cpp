@@ -69,6 +69,38 @@ inline Flop fabs(Flop a) { return Flop(std::fabs(a.v)); }
 inline double val(Flop a) { return a.v; }
 inline double val(double a) { return a; }
 
+// Dual: a double with one tangent (forward-mode differentiation). Used to
+// differentiate a run with respect to its initial state; fabs takes the sign
+// of the value (the branch taken by the forward run).
+struct Dual {
+  double v, d;
+  Dual() : v(0.0), d(0.0) {}
+  Dual(double x) : v(x), d(0.0) {}  // NOLINT: implicit, so constants mix in
+  Dual(double x, double t) : v(x), d(t) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  const double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+inline Dual sqrt(Dual a) {
+  const double r = std::sqrt(a.v);
+  return Dual(r, a.d / (2.0 * r));
+}
+inline Dual fabs(Dual a) { return a.v < 0.0 ? Dual(-a.v, -a.d) : a; }
+inline double val(Dual a) { return a.v; }
+
+// The global Lax-Friedrichs coefficient is a constant of each stage when a
+// run is differentiated (its dependence on the state is frozen).
+inline void freeze(double&) {}
+inline void freeze(Flop&) {}
+inline void freeze(Dual& a) { a.d = 0.0; }
+
 using std::fabs;
 using std::sqrt;
 
@@ -105,6 +137,7 @@ struct or_problem {
   double dt_fixed;
   int limiter;      // 0 off, 1 characteristic, 2 component-wise
   int eig_avg;      // 0 Roe average, 1 arithmetic mean
+  double alpha_fixed;  // > 0: use this alpha in every stage and direction
 };
 }
 
@@ -627,6 +660,8 @@ void rhs_1d(const or_problem& P, const R* U, const R* V, double t, R* L1, R* L2,
     for (int c = 0; c < m; ++c) Ui[c] = U[c * n + i];
     alpha = rmax(alpha, wave_speed(P, 0, Ui));
   }
+  if (P.alpha_fixed > 0.0) alpha = P.alpha_fixed;
+  freeze(alpha);
   if (alpha_out) *alpha_out = alpha;
 
   // point fluxes f and h = f'(u) v on the ghosted line
@@ -678,6 +713,9 @@ void rhs_2d(const or_problem& P, const R* U, const R* V, const R* W, double t,
     ax = rmax(ax, wave_speed(P, 0, Uq));
     ay = rmax(ay, wave_speed(P, 1, Uq));
   }
+  if (P.alpha_fixed > 0.0) ax = ay = P.alpha_fixed;
+  freeze(ax);
+  freeze(ay);
   if (alpha_out) { alpha_out[0] = ax; alpha_out[1] = ay; }
 
   std::vector<R> A1(m * npt, R(0.0)), A2(m * npt, R(0.0)), A3(m * npt, R(0.0));
@@ -926,6 +964,34 @@ long or_run(const or_problem* P, double* U, double* V, double* W, double* t, dou
     double dt;
     step_generic(*P, U, V, W, t, t_end, &dt);
     ++k;
+  }
+  return k;
+}
+
+// Forward-mode derivative of a run: advances (U, V, W) and their tangents
+// (dU, dV, dW) until t_end or max_steps, with alpha frozen in every stage and
+// the time steps those of the run itself. Returns the steps taken.
+long or_run_tangent(const or_problem* P, double* U, double* V, double* W, double* dU,
+                    double* dV, double* dW, double* t, double t_end, long max_steps) {
+  const int m = ncomp(*P);
+  const size_t n = (size_t)m * P->nx * (P->dim == 2 ? P->ny : 1);
+  const bool two = P->dim == 2;
+  std::vector<Dual> u(n), v(n), w(two ? n : 0);
+  for (size_t q = 0; q < n; ++q) {
+    u[q] = Dual(U[q], dU[q]);
+    v[q] = Dual(V[q], dV[q]);
+    if (two) w[q] = Dual(W[q], dW[q]);
+  }
+  long k = 0;
+  while (*t < t_end && k < max_steps) {
+    double dt;
+    step_generic(*P, u.data(), v.data(), w.data(), t, t_end, &dt);
+    ++k;
+  }
+  for (size_t q = 0; q < n; ++q) {
+    U[q] = u[q].v; dU[q] = u[q].d;
+    V[q] = v[q].v; dV[q] = v[q].d;
+    if (two) { W[q] = w[q].v; dW[q] = w[q].d; }
   }
   return k;
 }
