@@ -199,11 +199,18 @@ int hweno_autotune(hweno_ctx* ctx, const void* U, const void* V, const void* W, 
  * a device array of batch * m doubles. */
 int hweno_totals(hweno_ctx* ctx, const void* U, double* totals, void* stream);
 
-/* Discrete adjoint of hweno_step (reverse of the three stages with the
- * wave speed, time step and weight branches frozen). Not built yet:
- * returns HWENO_ENOTSUP. */
+/* Discrete adjoint of one hweno_step (the fully discrete scheme of Sec. 2.2
+ * differentiated step by step): given the step's input state U, V (device)
+ * and the time step it took per instance dt (device, [batch], the dt_used of
+ * hweno_step; 0 = the instance did not step), replaces lamU, lamV (device,
+ * in: the gradient of a functional with respect to the step's output, out:
+ * with respect to its input). The wave speed of each stage and dt are frozen
+ * (constants of the step) and the |.| in the smoothness differences keeps the
+ * branch of the forward state; the nonlinear weights and the limiter are
+ * differentiated. Built for 1D Burgers in FP64 (others: HWENO_ENOTSUP);
+ * W, lamW must be NULL. Library scratch holds the replayed stages. */
 int hweno_adjoint_step(hweno_ctx* ctx, const void* U, const void* V, const void* W,
-                       double dt, void* lamU, void* lamV, void* lamW, void* stream);
+                       const double* dt, void* lamU, void* lamV, void* lamW, void* stream);
 
 /* Synchronise `stream`, read the device status word and return the latched
  * device error (HWENO_OK if none); clears the latch. */

@@ -1,0 +1,160 @@
+// Reverse-mode derivatives (vector-Jacobian products) of the scalar building
+// blocks of the L-HWENO stage (Zhang & Zhao, arXiv:2207.05258, Sec. 2.1-2.2),
+// written by hand from the forward formulas. They differentiate the functions
+// themselves (the per-weight form of the nonlinear weights), not the folded
+// arrangement used by the forward kernels; the |.| in tau keeps the sign of
+// its argument at the point of evaluation (the branch of the forward run).
+#pragma once
+
+#include "hweno_math.cuh"
+
+namespace hweno {
+
+namespace adj {
+constexpr double A1s = 19.0 / 192.0, A1h = 79.0 / 48.0, A1d = 27.0 / 64.0;
+constexpr double A3s = 11.0 / 24.0, A3h = 17.0 / 6.0;
+constexpr double K6 = 63.0 / 130.0, K7 = 8825.0 / 10934.0, K8 = 13.0 / 3.0, K9 = 781.0 / 20.0;
+constexpr double K10 = 1421461.0 / 2275.0, K11 = 21520059541.0 / 1377684.0;
+constexpr double C11 = 11.0 / 60.0, C19 = 19.0 / 30.0;
+}  // namespace adj
+
+__device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// One side of the nonlinear flux, f-hat^+ from (f, H = dx h) on {i-1, i, i+1}
+// (Sec. 2.1): returns the value and adds mu * d f-hat / d input to g[6]
+// (order fm, f0, fp, Hm, H0, Hp).
+__device__ __forceinline__ double side_vjp(double fm, double f0, double fp, double Hm, double H0,
+                                           double Hp, double mu, const Weights<double>& w,
+                                           double* g) {
+  using namespace adj;
+  const double sHp = Hm + Hp, dHp = Hm - Hp, lap = fm - 2.0 * f0 + fp, dif = fm - fp;
+  const double p0 = C11 * (fm + fp) + C19 * f0 + 0.05 * dHp + 0.5 * H0;
+  const double p1 = fm / 6.0 + 5.0 * f0 / 6.0 + 2.0 * H0 / 3.0;
+  const double p2 = 5.0 * f0 / 6.0 + fp / 6.0 + H0 / 3.0;
+  const double a1 = A1s * sHp + A1h * H0 + A1d * dif;
+  const double a2 = 0.375 * dHp + 1.25 * lap;
+  const double a3 = -A3s * sHp - A3h * H0 - 1.875 * dif;
+  const double a4 = -0.25 * dHp - 0.5 * lap;
+  const double a5 = 0.25 * sHp + H0 + 0.75 * dif;
+  const double e1 = a1 + 0.25 * a3 + 0.0625 * a5, e2 = a2 + K6 * a4, e3 = a3 + K7 * a5;
+  const double be0 = e1 * e1 + K8 * e2 * e2 + K9 * e3 * e3 + K10 * a4 * a4 + K11 * a5 * a5;
+  const double s1 = H0 - f0 + fm, s2 = H0 + f0 - fp;
+  const double be1 = H0 * H0 + K8 * s1 * s1, be2 = H0 * H0 + K8 * s2 * s2;
+  const double d1 = be0 - be1, d2 = be0 - be2;
+  const double t = fabs(d1) + fabs(d2), tau = 0.25 * t * t;
+  const double b0 = be0 + w.eps, b1 = be1 + w.eps, b2 = be2 + w.eps;
+  const double o0 = w.g0 * (1.0 + tau / b0), o1 = w.g1 * (1.0 + tau / b1),
+               o2 = w.g2 * (1.0 + tau / b2);
+  const double S = o0 + o1 + o2;
+  const double Q0 = (p0 - w.g1 * p1 - w.g2 * p2) * w.ig0;
+  const double fh = (o0 * Q0 + o1 * p1 + o2 * p2) / S;
+  // reverse
+  const double gN = mu / S, gS = -mu * fh / S;
+  const double go0 = gN * Q0 + gS, go1 = gN * p1 + gS, go2 = gN * p2 + gS;
+  const double gQ0 = gN * o0;
+  const double gp0 = gQ0 * w.ig0;
+  const double gp1 = gN * o1 - gQ0 * w.ig0 * w.g1;
+  const double gp2 = gN * o2 - gQ0 * w.ig0 * w.g2;
+  const double gtau = go0 * w.g0 / b0 + go1 * w.g1 / b1 + go2 * w.g2 / b2;
+  const double gb0 = -go0 * w.g0 * tau / (b0 * b0);
+  const double gb1 = -go1 * w.g1 * tau / (b1 * b1);
+  const double gb2 = -go2 * w.g2 * tau / (b2 * b2);
+  const double gt = 0.5 * t * gtau;
+  const double gd1 = gt * sgn(d1), gd2 = gt * sgn(d2);
+  const double gbe0 = gb0 + gd1 + gd2, gbe1 = gb1 - gd1, gbe2 = gb2 - gd2;
+  double gH0 = 2.0 * H0 * (gbe1 + gbe2);
+  const double gs1 = 2.0 * K8 * s1 * gbe1, gs2 = 2.0 * K8 * s2 * gbe2;
+  const double ge1 = 2.0 * e1 * gbe0, ge2 = 2.0 * K8 * e2 * gbe0, ge3 = 2.0 * K9 * e3 * gbe0;
+  double ga4 = 2.0 * K10 * a4 * gbe0, ga5 = 2.0 * K11 * a5 * gbe0;
+  const double ga1 = ge1, ga2 = ge2, ga3 = 0.25 * ge1 + ge3;
+  ga5 += 0.0625 * ge1 + K7 * ge3;
+  ga4 += K6 * ge2;
+  double gsHp = A1s * ga1 - A3s * ga3 + 0.25 * ga5;
+  double gdHp = 0.375 * ga2 - 0.25 * ga4 + 0.05 * gp0;
+  const double glap = 1.25 * ga2 - 0.5 * ga4;
+  const double gdif = A1d * ga1 - 1.875 * ga3 + 0.75 * ga5;
+  gH0 += A1h * ga1 - A3h * ga3 + ga5 + 0.5 * gp0 + 2.0 / 3.0 * gp1 + 1.0 / 3.0 * gp2 + gs1 + gs2;
+  g[0] += C11 * gp0 + gp1 / 6.0 + glap + gdif + gs1;
+  g[1] += C19 * gp0 + 5.0 / 6.0 * (gp1 + gp2) - 2.0 * glap - gs1 + gs2;
+  g[2] += C11 * gp0 + gp2 / 6.0 + glap - gdif - gs2;
+  g[3] += gsHp + gdHp;
+  g[4] += gH0;
+  g[5] += gsHp - gdHp;
+  return fh;
+}
+
+// Both sides of one field's flux at x_{i+1/2}: f-hat = f-hat^+ + f-hat^-;
+// gp (6: f^+ at i-1..i+1, H^+ at i-1..i+1) and gm (6: f^- at i..i+2, H^- at
+// i..i+2) receive mu times the partial derivatives. The "-" side is the
+// mirror image (reversed stencil, negated H).
+__device__ __forceinline__ void flux_vjp(const double* fp_, const double* Hp_, const double* fm_,
+                                         const double* Hm_, double mu, const Weights<double>& w,
+                                         double* gp, double* gm) {
+  side_vjp(fp_[0], fp_[1], fp_[2], Hp_[0], Hp_[1], Hp_[2], mu, w, gp);
+  double r[6] = {0, 0, 0, 0, 0, 0};
+  side_vjp(fm_[2], fm_[1], fm_[0], -Hm_[2], -Hm_[1], -Hm_[0], mu, w, r);
+  gm[0] += r[2]; gm[1] += r[1]; gm[2] += r[0];
+  gm[3] -= r[5]; gm[4] -= r[4]; gm[5] -= r[3];
+}
+
+// Linear derivative flux D = dx (h-hat^+ + h-hat^-) (Sec. 2.1, p_0'):
+// adds mu * dD/d input to gp, gm (same layout as flux_vjp).
+__device__ __forceinline__ void dflux_vjp(double mu, double* gp, double* gm) {
+  gp[0] += 0.25 * mu; gp[1] += -2.0 * mu; gp[2] += 1.75 * mu;
+  gp[3] += mu / 12.0; gp[4] += -mu / 6.0; gp[5] += -5.0 * mu / 12.0;
+  gm[0] += -1.75 * mu; gm[1] += 2.0 * mu; gm[2] += -0.25 * mu;
+  gm[3] += -5.0 * mu / 12.0; gm[4] += -mu / 6.0; gm[5] += mu / 12.0;
+}
+
+// HWENO limiter (Sec. 2.2) in scaled form, out = dx v-tilde from point values
+// um, u0, up and Vm = dx v_{i-1}, Vp = dx v_{i+1}: adds mu * d out / d input to
+// g[5] (order um, u0, up, Vm, Vp).
+__device__ __forceinline__ void limiter_vjp(double um, double u0, double up, double Vm, double Vp,
+                                            double mu, const Weights<double>& w, double* g) {
+  using namespace adj;
+  const double sV = Vm + Vp, dV = Vm - Vp, lap = um - 2.0 * u0 + up, dup = up - um;
+  const double q0 = 0.75 * dup - 0.25 * sV, q1 = u0 - um, q2 = up - u0;
+  const double a2 = 0.25 * dV + lap, a3 = 0.25 * sV - 0.25 * dup, a4 = -0.25 * dV - 0.5 * lap;
+  const double e1 = q0 + 0.25 * a3, e2 = a2 + K6 * a4;
+  const double be0 = e1 * e1 + K8 * e2 * e2 + K9 * a3 * a3 + K10 * a4 * a4;
+  const double be1 = q1 * q1, be2 = q2 * q2;
+  const double d1 = be0 - be1, d2 = be0 - be2;
+  const double t = fabs(d1) + fabs(d2), tau = 0.25 * t * t;
+  const double b0 = be0 + w.eps, b1 = be1 + w.eps, b2 = be2 + w.eps;
+  const double l0 = w.d0 * (1.0 + tau / b0), l1 = w.d1 * (1.0 + tau / b1),
+               l2 = w.d2 * (1.0 + tau / b2);
+  const double S = l0 + l1 + l2;
+  const double Q0 = (q0 - w.d1 * q1 - w.d2 * q2) * w.id0;
+  const double out = (l0 * Q0 + l1 * q1 + l2 * q2) / S;
+  const double gN = mu / S, gS = -mu * out / S;
+  const double gl0 = gN * Q0 + gS, gl1 = gN * q1 + gS, gl2 = gN * q2 + gS;
+  const double gQ0 = gN * l0;
+  double gq0 = gQ0 * w.id0;
+  double gq1 = gN * l1 - gQ0 * w.id0 * w.d1;
+  double gq2 = gN * l2 - gQ0 * w.id0 * w.d2;
+  const double gtau = gl0 * w.d0 / b0 + gl1 * w.d1 / b1 + gl2 * w.d2 / b2;
+  const double gt = 0.5 * t * gtau;
+  const double gd1 = gt * sgn(d1), gd2 = gt * sgn(d2);
+  const double gbe0 = -gl0 * w.d0 * tau / (b0 * b0) + gd1 + gd2;
+  const double gbe1 = -gl1 * w.d1 * tau / (b1 * b1) - gd1;
+  const double gbe2 = -gl2 * w.d2 * tau / (b2 * b2) - gd2;
+  gq1 += 2.0 * q1 * gbe1;
+  gq2 += 2.0 * q2 * gbe2;
+  const double ge1 = 2.0 * e1 * gbe0, ge2 = 2.0 * K8 * e2 * gbe0;
+  double ga3 = 2.0 * K9 * a3 * gbe0 + 0.25 * ge1;
+  double ga4 = 2.0 * K10 * a4 * gbe0 + K6 * ge2;
+  const double ga2 = ge2;
+  gq0 += ge1;
+  // a2, a3, a4, q0 -> (sV, dV, lap, dup)
+  const double gsV = -0.25 * gq0 + 0.25 * ga3;
+  const double gdV = 0.25 * ga2 - 0.25 * ga4;
+  const double glap = ga2 - 0.5 * ga4;
+  const double gdup = 0.75 * gq0 - 0.25 * ga3;
+  g[0] += glap - gdup - gq1;
+  g[1] += -2.0 * glap + gq1 - gq2;
+  g[2] += glap + gdup + gq2;
+  g[3] += gsV + gdV;
+  g[4] += gsV - gdV;
+}
+
+}  // namespace hweno

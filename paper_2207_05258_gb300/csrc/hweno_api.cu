@@ -37,6 +37,9 @@ struct hweno_ctx {
   int variant = 0;
   int tile = kTile1D;
   int tiles_cap = 0;  // capacity of the tile tables (smallest tile)
+  int* d_tile0_inst = nullptr;   // default-variant table kept for the adjoint
+  int* d_tile0_start = nullptr;
+  int ntiles0 = 0;
   int* d_tile_inst = nullptr;
   int* d_tile_start = nullptr;
   int* d_inst_n = nullptr;
@@ -57,6 +60,10 @@ struct hweno_ctx {
   void* d_U2 = nullptr; void* d_V2 = nullptr; void* d_W2 = nullptr;
   void* d_Vt0 = nullptr; void* d_Wt0 = nullptr;
   void* d_LX = nullptr; void* d_VT = nullptr;  // 2D: x-sweep results
+  // adjoint scratch (1D FP64): lambda of stages 2 and 1, base-term cotangents
+  double* d_aU2 = nullptr; double* d_aV2 = nullptr;
+  double* d_aU1 = nullptr; double* d_aV1 = nullptr;
+  double* d_acU = nullptr; double* d_acV = nullptr;
   // device copies for the host-buffer entry point
   void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
   double* d_ht = nullptr;
@@ -127,10 +134,11 @@ int dalloc(hweno_ctx* c, T** p, size_t bytes) {
 void free_all(hweno_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
-  void* ptrs[] = {c->d_pu, c->d_partial, c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
+  void* ptrs[] = {c->d_pu, c->d_partial, c->d_tile0_inst, c->d_tile0_start, c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
                   c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
-                  c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht};
+                  c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht,
+                  c->d_aU2, c->d_aV2, c->d_aU1, c->d_aV1, c->d_acU, c->d_acV};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -513,8 +521,11 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
   int rc = HWENO_OK;
   const size_t fb = c->elems * c->esize;
   const size_t B = (size_t)c->batch;
+  c->ntiles0 = (int)tinst.size();
   if ((rc = dalloc(c, &c->d_tile_inst, sizeof(int) * c->tiles_cap)) ||
       (rc = dalloc(c, &c->d_tile_start, sizeof(int) * c->tiles_cap)) ||
+      (rc = dalloc(c, &c->d_tile0_inst, sizeof(int) * c->ntiles0)) ||
+      (rc = dalloc(c, &c->d_tile0_start, sizeof(int) * c->ntiles0)) ||
       (rc = dalloc(c, &c->d_inst_n, sizeof(int) * B)) ||
       (rc = dalloc(c, &c->d_inst_off, sizeof(long long) * B)) ||
       (rc = dalloc(c, &c->d_inst_dx, sizeof(double) * B)) ||
@@ -535,7 +546,11 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       (c->dim == 2 &&
        ((rc = dalloc(c, &c->d_W1, fb)) || (rc = dalloc(c, &c->d_W2, fb)) ||
         (rc = dalloc(c, &c->d_Wt0, fb)) || (rc = dalloc(c, &c->d_LX, 3 * fb)) ||
-        (rc = dalloc(c, &c->d_VT, fb)) || (rc = dalloc(c, &c->d_hW, fb))))) {
+        (rc = dalloc(c, &c->d_VT, fb)) || (rc = dalloc(c, &c->d_hW, fb)))) ||
+      (c->dim == 1 && !c->fp32 &&
+       ((rc = dalloc(c, &c->d_aU2, fb)) || (rc = dalloc(c, &c->d_aV2, fb)) ||
+        (rc = dalloc(c, &c->d_aU1, fb)) || (rc = dalloc(c, &c->d_aV1, fb)) ||
+        (rc = dalloc(c, &c->d_acU, fb)) || (rc = dalloc(c, &c->d_acV, fb))))) {
     free_all(c);
     delete c;
     return rc;
@@ -551,6 +566,8 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       cudaMemcpy(c->d_inst_geo, geo.data(), sizeof(double) * 3 * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_geof, geof.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_tile_inst, tinst.data(), sizeof(int) * tinst.size(), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_tile0_inst, tinst.data(), sizeof(int) * tinst.size(), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_tile0_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_tile_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_n, c->nx.data(), sizeof(int) * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_off, off.data(), sizeof(long long) * B, cudaMemcpyHostToDevice) ||
@@ -762,10 +779,64 @@ int hweno_totals(hweno_ctx* c, const void* U, double* totals, void* stream) {
   return HWENO_OK;
 }
 
-int hweno_adjoint_step(hweno_ctx* c, const void*, const void*, const void*, double, void*, void*,
-                       void*, void*) {
+int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W,
+                       const double* dt, void* lamU, void* lamV, void* lamW, void* stream) {
   if (!c) return HWENO_EINVAL;
-  return fail(c, HWENO_ENOTSUP, "adjoint step not built");
+  if (c->dim != 1 || c->fp32 || c->eq != HWENO_BURGERS)
+    return fail(c, HWENO_ENOTSUP, "adjoint built for 1D Burgers in FP64");
+  if (!U || !V || !dt || !lamU || !lamV || W || lamW) return fail(c, HWENO_EINVAL, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  // 1. replay stages 1 and 2 of the forward step with its dt; alpha of each
+  //    stage input lands in slots 0, 1, 2 (frozen in the adjoint)
+  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)))
+    return cuda_fail(c, e, "memset");
+  Args1D a = base_args_1d(c);
+  a.t = c->d_ht;  // unused with skip_done = 0
+  a.t_end = 0.0;
+  a.skip_done = 0;
+  a.dt = c->d_dt;
+  a.lands = c->d_lands;
+  a.dt_in = dt;
+  a.U = U;
+  a.alpha_out = slot(c, 0);
+  if ((e = launch_alpha_1d(c->eq, false, c->variant, a, c->ntiles, s))) return cuda_fail(c, e, "alpha");
+  a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
+  a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
+  if ((e = launch_stage_1d(c->eq, false, c->variant, MODE_STAGE1, a, c->ntiles, s)))
+    return cuda_fail(c, e, "replay stage 1");
+  a.U = c->d_U1; a.V = c->d_V1; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = c->d_U2; a.Vout = c->d_V2;
+  a.Vt0out = nullptr; a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
+  if ((e = launch_stage_1d(c->eq, false, c->variant, MODE_STAGE2, a, c->ntiles, s)))
+    return cuda_fail(c, e, "replay stage 2");
+  // 2. reverse stages 3, 2, 1 (the adjoint kernel uses the default tiles)
+  AdjArgs1D g{};
+  g.tile_inst = c->d_tile0_inst; g.tile_start = c->d_tile0_start; g.inst_n = c->d_inst_n;
+  g.inst_off = c->d_inst_off; g.inst_geo = c->d_inst_geo; g.dt = dt;
+  g.sp = scheme_params(c);
+  double* lU = static_cast<double*>(lamU);
+  double* lV = static_cast<double*>(lamV);
+  // stage 3: lambda2 = (2/3) G'(x2)^T lambda^{n+1}
+  g.U = static_cast<const double*>(c->d_U2); g.V = static_cast<const double*>(c->d_V2);
+  g.alpha = slotd(c, 2); g.lamU = lU; g.lamV = lV; g.b = 2.0 / 3.0;
+  g.outU = c->d_aU2; g.outV = c->d_aV2;
+  if ((e = launch_adjoint_1d(c->eq, g, c->ntiles0, s))) return cuda_fail(c, e, "adjoint 3");
+  // stage 2: lambda1 = (1/4) G'(x1)^T lambda2; acc = lambda^{n+1}/3 + 3 lambda2/4
+  g.U = static_cast<const double*>(c->d_U1); g.V = static_cast<const double*>(c->d_V1);
+  g.alpha = slotd(c, 1); g.lamU = c->d_aU2; g.lamV = c->d_aV2; g.b = 0.25;
+  g.outU = c->d_aU1; g.outV = c->d_aV1;
+  g.lamNU = lU; g.lamNV = lV; g.accOutU = c->d_acU; g.accOutVt = c->d_acV;
+  g.cN = 1.0 / 3.0; g.c2 = 0.75;
+  if ((e = launch_adjoint_1d(c->eq, g, c->ntiles0, s))) return cuda_fail(c, e, "adjoint 2");
+  // stage 1: lambda^n = G'(x^n)^T lambda1 + base-term cotangents
+  g.U = static_cast<const double*>(U); g.V = static_cast<const double*>(V);
+  g.alpha = slotd(c, 0); g.lamU = c->d_aU1; g.lamV = c->d_aV1; g.b = 1.0;
+  g.accU = c->d_acU; g.accVt = c->d_acV; g.lamNU = nullptr; g.lamNV = nullptr;
+  g.accOutU = nullptr; g.accOutVt = nullptr;
+  g.outU = lU; g.outV = lV;
+  if ((e = launch_adjoint_1d(c->eq, g, c->ntiles0, s))) return cuda_fail(c, e, "adjoint 1");
+  c->launches = 6;
+  return HWENO_OK;
 }
 
 int hweno_sync_status(hweno_ctx* c, void* stream) {

@@ -72,6 +72,7 @@ struct Args1D {
   const double* alpha_in;     // wave speed of the stage input
   unsigned long long* alpha_out;  // max wave speed of the stage output (bits)
   double* dt;                 // per-instance time step (written in stage 1)
+  const double* dt_in;        // stage 1 takes dt from here when not null (replay)
   int* lands;                 // dt was clipped to t_end (stage 1)
   unsigned* status;
   SchemeParams sp;
@@ -149,6 +150,37 @@ struct Args2D {
 cudaError_t launch_alpha_2d(int eq, bool fp32, const Args2D& a, cudaStream_t s);
 cudaError_t launch_xsweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
 cudaError_t launch_ysweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
+
+// Adjoint of one stage of a 1D step (adjoint1d.cu), FP64. With x_k =
+// a_k B(x^n) + b G(x_{k-1}), G(x) = (U + dt L^1(x), v~(x) + dt L^2(x)), it
+// writes out = G'(x_{k-1})^T (b lam) [+ acc], i.e. the adjoint of the stage
+// input. Optionally (stage 2) also acc = cN lamN + c2 lam, the cotangent of
+// the base term (U^n, v~(x^n)).
+struct AdjArgs1D {
+  const double* U;       // stage input state x_{k-1}
+  const double* V;
+  const double* lamU;    // adjoint of the stage output
+  const double* lamV;
+  const double* accU;    // added to the U result (stage 1), nullable
+  const double* accVt;   // added to the cotangent of v~ (stage 1), nullable
+  const double* lamNU;   // lambda^{n+1} for acc (stage 2), nullable
+  const double* lamNV;
+  double* outU;
+  double* outV;
+  double* accOutU;       // acc (stage 2), nullable
+  double* accOutVt;
+  double b, cN, c2;
+  const int* tile_inst;
+  const int* tile_start;
+  const int* inst_n;
+  const long long* inst_off;
+  const double* inst_geo;
+  const double* alpha;   // frozen wave speed of the stage input, per instance
+  const double* dt;      // time step per instance (0: the instance did not step)
+  SchemeParams sp;
+};
+
+cudaError_t launch_adjoint_1d(int eq, const AdjArgs1D& a, int ntiles, cudaStream_t s);
 
 // Conserved totals (totals.cu): per-tile FP64 partial sums, then a
 // fixed-order sum per instance. Tiles: the 1D tile table, or row segments of

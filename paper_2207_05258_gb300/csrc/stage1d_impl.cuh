@@ -151,8 +151,9 @@ k_stage_1d(const __grid_constant__ Args1D a) {
   if (threadIdx.x == 0) {
     double dt = 0.0;
     if constexpr (MODE == MODE_STAGE1) {
-      int lands;
-      dt = time_step(a.sp, a.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
+      int lands = 0;
+      dt = a.dt_in ? a.dt_in[k]
+                   : time_step(a.sp, a.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
       if (s == 0) { a.dt[k] = dt; a.lands[k] = lands; }
     } else if constexpr (MODE != MODE_RHS) {
       dt = a.dt[k];

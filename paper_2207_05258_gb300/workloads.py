@@ -295,3 +295,27 @@ def blast_waves(n: int = 800, t_end: float = 0.038) -> Workload:
 # Linear-weight sets of the study in Example 3.7 (reconstruction G, limiter D).
 WEIGHT_SETS = {"G1": (0.99, 0.005, 0.005), "G2": (1 / 3, 1 / 3, 1 / 3), "G3": (0.01, 0.495, 0.495),
                "D1": (0.99, 0.005, 0.005), "D2": (1 / 3, 1 / 3, 1 / 3), "D3": (0.01, 0.495, 0.495)}
+
+
+def burgers_adjoint_batch(count: int = 256, n: int = 800, seed: int = 5, amplitude: float = 0.05,
+                          t_end: float = 0.5 / math.pi) -> Workload:
+    """Batch of 1D Burgers problems for gradient checks: u0 = 0.5 + sin(pi x)
+    plus a seeded smooth perturbation of up to 4 Fourier modes with total
+    amplitude <= `amplitude`, periodic on [0, 2], smooth up to t_end, with
+    the exact derivative as V."""
+    rng = SplitMix64(seed)
+    x = centers(0.0, 2.0, n)
+    Us, Vs = [], []
+    for _ in range(count):
+        u = 0.5 + np.sin(np.pi * x)
+        v = np.pi * np.cos(np.pi * x)
+        for mode in range(1, 5):
+            a = amplitude / 4.0 * rng.uniform(-1.0, 1.0)
+            ph = rng.uniform(0.0, 2.0 * math.pi)
+            u = u + a * np.sin(mode * np.pi * x + ph)
+            v = v + a * mode * np.pi * np.cos(mode * np.pi * x + ph)
+        Us.append(u)
+        Vs.append(v)
+    return Workload("burgers_adjoint_batch", "burgers", 1, [n] * count, 1, 0.0, 2.0, 0.0, 1.0,
+                    t_end, ("periodic",) * 4, np.concatenate(Us), np.concatenate(Vs),
+                    meta=dict(seed=seed))

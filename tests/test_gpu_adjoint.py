@@ -1,0 +1,124 @@
+"""The discrete adjoint (hweno_adjoint_step and the checkpointed autograd
+Function) against the oracle's forward-mode dual-number derivative: for a
+seeded direction d and adjoint seed lam, <adjoint(lam), d> must equal
+<lam, tangent(d)> with the same freezes (alpha per stage, dt of the run,
+|.| branches of the forward state). Also against central finite differences
+of the GPU forward (alpha not frozen there, so to a looser bound)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2207_05258_gb300 import workloads as W
+from _util import oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hw():
+    from paper_2207_05258_gb300 import build
+    build.build()
+    from paper_2207_05258_gb300 import hweno
+    return hweno
+
+
+def rough_batch(sizes, bc, seed):
+    rng = np.random.default_rng(seed)
+    Us, Vs = [], []
+    for n in sizes:
+        x = W.centers(0, 2, n)
+        Us.append(0.4 + np.sin(np.pi * x + rng.uniform(0, 6)) + 0.1 * rng.standard_normal(n))
+        Vs.append(np.pi * np.cos(np.pi * x) + rng.standard_normal(n))
+    return W.Workload("rb", "burgers", 1, list(sizes), 1, 0.0, 2.0, 0.0, 1.0, 1.0,
+                      (bc, bc, "periodic", "periodic"), np.concatenate(Us), np.concatenate(Vs),
+                      inflow=(0.6, 0, 0, 0))
+
+
+@pytest.mark.parametrize("bc", ["periodic", "outflow", "reflective", "inflow"])
+def test_one_step_dot_product_against_dual_oracle(hw, bc):
+    w = rough_batch([4, 31, 124, 125, 300], bc, 7)
+    s = hw.Solver.from_workload(w)
+    U, V = torch.from_numpy(w.U.copy()).cuda(), torch.from_numpy(w.V.copy()).cuda()
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+    U1, V1 = U.clone(), V.clone()
+    s.step(U1, V1, None, t, 1.0, dt)
+    rng = np.random.default_rng(11)
+    lamU = rng.standard_normal(w.U.size)
+    lamV = rng.standard_normal(w.V.size)
+    lU, lV = torch.from_numpy(lamU).cuda(), torch.from_numpy(lamV).cuda()
+    s.adjoint_step(U, V, None, dt, lU, lV)
+    s.sync_status()
+    gU, gV = lU.cpu().numpy(), lV.cpu().numpy()
+    off = 0
+    for k, n in enumerate(w.nx):
+        Uk, Vk = w.instance(k)
+        dU, dV = rng.standard_normal(Uk.shape), rng.standard_normal(Vk.shape)
+        out = O.run_tangent(oracle_problem(w, nx=n), Uk, Vk, None, dU, dV, None, 0.0, 1.0,
+                            max_steps=1)
+        lhs = float(np.dot(gU[off:off + n], dU.ravel()) + np.dot(gV[off:off + n], dV.ravel()))
+        rhs = float(np.dot(lamU[off:off + n], out[3].ravel()) +
+                    np.dot(lamV[off:off + n], out[4].ravel()))
+        scale = np.sqrt(np.sum(lamU[off:off + n] ** 2 + lamV[off:off + n] ** 2) *
+                        np.sum(out[3] ** 2 + out[4] ** 2)) + abs(rhs)
+        assert abs(lhs - rhs) <= 1e-12 * scale, (k, n, lhs, rhs)
+        off += n
+
+
+def test_gradient_of_final_time_functional(hw):
+    """J = sum_k sum_i u_k(T)^2 dx over a batch of smooth Burgers problems:
+    the checkpointed adjoint gradient against the dual-number oracle along
+    seeded directions, and against central differences of the GPU forward."""
+    from paper_2207_05258_gb300.adjoint import run_to_time
+    w = W.burgers_adjoint_batch(count=8, n=200)
+    s = hw.Solver.from_workload(w)
+    dx = 2.0 / 200
+    U0 = torch.from_numpy(w.U.copy()).cuda().requires_grad_(True)
+    V0 = torch.from_numpy(w.V.copy()).cuda().requires_grad_(True)
+    UT, VT = run_to_time(U0, V0, s, w.t_end, 7)
+    J = (UT * UT).sum() * dx
+    J.backward()
+    gU, gV = U0.grad.cpu().numpy(), V0.grad.cpu().numpy()
+    rng = np.random.default_rng(21)
+    for k in (0, 3, 7):
+        Uk, Vk = w.instance(k)
+        x = W.centers(0, 2, 200)
+        dU = (0.1 * np.sin(3 * np.pi * x + rng.uniform(0, 6))).reshape(1, -1)
+        dV = (0.3 * np.pi * np.cos(3 * np.pi * x)).reshape(1, -1)
+        out = O.run_tangent(oracle_problem(w, nx=200), Uk, Vk, None, dU, dV, None, 0.0, w.t_end)
+        dJ = float(np.sum(2.0 * out[0] * out[3]) * dx)
+        adj = float(np.dot(gU[k * 200:(k + 1) * 200], dU.ravel()) +
+                    np.dot(gV[k * 200:(k + 1) * 200], dV.ravel()))
+        assert abs(adj - dJ) <= 1e-10 * abs(dJ), (k, adj, dJ)
+        # central differences of the GPU forward (alpha recomputed there)
+        eps = 1e-6
+        Js = []
+        for sgn in (1.0, -1.0):
+            Ue, Ve = w.U.copy(), w.V.copy()
+            Ue[k * 200:(k + 1) * 200] += sgn * eps * dU.ravel()
+            Ve[k * 200:(k + 1) * 200] += sgn * eps * dV.ravel()
+            Ut, Vt = torch.from_numpy(Ue).cuda(), torch.from_numpy(Ve).cuda()
+            t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+            s.run(Ut, Vt, None, t, w.t_end)
+            Js.append(float((Ut[k * 200:(k + 1) * 200] ** 2).sum().item()) * dx)
+        fd = (Js[0] - Js[1]) / (2 * eps)
+        print("instance %d: adjoint %.12e dual %.12e fd %.12e" % (k, adj, dJ, fd))
+        assert abs(adj - fd) <= 1e-6 * abs(fd), (k, adj, fd)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(hw):
+    from paper_2207_05258_gb300.adjoint import run_to_time
+    w = W.burgers_adjoint_batch(count=3, n=128, t_end=0.05)
+    grads = []
+    for every in (1, 5, 1000):
+        s = hw.Solver.from_workload(w)
+        U0 = torch.from_numpy(w.U.copy()).cuda().requires_grad_(True)
+        V0 = torch.from_numpy(w.V.copy()).cuda().requires_grad_(True)
+        UT, VT = run_to_time(U0, V0, s, w.t_end, every)
+        ((UT * UT).sum() + (VT * VT).sum() * 1e-3).backward()
+        grads.append((U0.grad.clone(), V0.grad.clone()))
+    for g in grads[1:]:
+        assert torch.equal(g[0], grads[0][0]) and torch.equal(g[1], grads[0][1])
