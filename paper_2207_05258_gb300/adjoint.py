@@ -60,5 +60,8 @@ class RunToTime(torch.autograd.Function):
         return lamU, lamV, None, None, None, None, None
 
 
-def run_to_time(U0, V0, solver, t_end, checkpoint_every=20):
-    return RunToTime.apply(U0, V0, solver, t_end, checkpoint_every)
+def run_to_time(U0, V0, solver, t_end, checkpoint_every=20, max_steps=1 << 30, check_every=16):
+    """Differentiable run of a 1D Burgers FP64 `solver` from (U0, V0) at t = 0
+    to t_end; returns (U(T), V(T)). Memory: one state per checkpoint plus one
+    segment of states during the backward pass."""
+    return RunToTime.apply(U0, V0, solver, t_end, checkpoint_every, max_steps, check_every)
