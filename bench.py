@@ -73,7 +73,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--workload", default="riemann_batch",
-                    help="riemann_batch (default) | euler2d_smooth:N | double_mach:NXxNY")
+                    help="riemann_batch (default) | euler2d_smooth:N | double_mach:NXxNY | "
+                         "burgers_adjoint:COUNTxN (discrete adjoint of the step; own JSON line)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, fp32 and cpu_baseline legs")
     return ap.parse_args()
@@ -357,6 +358,88 @@ def cpu_baseline(w, budget_s=12.0, sample=128):
                       "%.1f s, single thread" % (sample, sum(w.nx[:sample]), el)}
 
 
+def run_adjoint(args, rank, world, dev_index):
+    """Discrete adjoint of the SSP-RK3 step (hweno_adjoint_step) on a batch of
+    1D Burgers problems (default 256 x N = 800, periodic, smooth seeded data):
+    (a) K adjoint steps timed one by one with CUDA events, each the reverse of
+    a recorded forward step (replay of stages 1-2, three reverse stage
+    kernels), L2 flushed between steps (the batch fits in L2); (b) one full
+    gradient of J = sum u(T)^2 dx through the checkpointed autograd Function
+    (checkpoint every 20 steps); (c) the forward step alone for the ratio."""
+    import torch
+    from paper_2207_05258_gb300 import hweno, workloads as W
+    from paper_2207_05258_gb300.adjoint import run_to_time
+
+    torch.cuda.set_device(dev_index)
+    size = args.workload.partition(":")[2] or "256x800"
+    count, n = (int(v) for v in size.split("x"))
+    w = W.burgers_adjoint_batch(count=count, n=n, seed=5 + rank)
+    s = hweno.Solver.from_workload(w)
+    dx = (w.x1 - w.x0) / n
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    with ClockSampler(dev_index) as clk, torch.cuda.stream(stream):
+        U = torch.from_numpy(w.U).cuda()
+        V = torch.from_numpy(w.V).cuda()
+        t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+        states, dts, fwd = [], [], []
+        for k in range(Wm + K):
+            states.append((U.clone(), V.clone()))
+            dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.step(U, V, None, t, w.t_end, dt)
+            e1.record()
+            dts.append(dt)
+            fwd.append((e0, e1))
+        lamU, lamV = 2.0 * U * dx, torch.zeros_like(V)
+        adj = []
+        for k in range(Wm + K - 1, -1, -1):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.adjoint_step(states[k][0], states[k][1], None, dts[k], lamU, lamV)
+            e1.record()
+            adj.append((e0, e1))
+        launches = s.launches_last_call
+        torch.cuda.synchronize()
+        s.sync_status()
+        adj_ms = sum(a.elapsed_time(b) for a, b in adj[Wm:])  # skip Wm warm-up steps
+        fwd_ms = sum(a.elapsed_time(b) for a, b in fwd[Wm:])
+        active = float(sum(float((d > 0).double().sum().item()) for d in dts[:K])) * n
+        # full gradient to T with checkpoints
+        U0 = torch.from_numpy(w.U).cuda().requires_grad_(True)
+        V0 = torch.from_numpy(w.V).cuda().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        UT, VT = run_to_time(U0, V0, s, w.t_end, 20)
+        J = (UT * UT).sum() * dx
+        J.backward()
+        torch.cuda.synchronize()
+        grad_s = time.perf_counter() - t0
+    steps_T = int(math.ceil(w.t_end / float(dts[0].min().item())))
+    if world > 1:
+        adj_ms, active = reduce_over_ranks(adj_ms, active, "cuda")
+    value = active / (adj_ms * 1e-3) / 1e6
+    return {"metric": "Mpoint-updates/s per adjoint RK step", "value": round(value, 3),
+            "unit": "Mpoint-updates/s", "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": round(adj_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "burgers_adjoint: %d x 1D Burgers N=%d, periodic [0,2], "
+                                   "u0 = 0.5 + sin(pi x) + seeded 4-mode perturbation, "
+                                   "T = 0.5/pi" % (count, n),
+                       "l2": "flushed between timed steps (256 MiB write; the batch fits in L2)",
+                       "timing": "CUDA events around each hweno_adjoint_step"},
+            "forward_ms_per_step": round(fwd_ms / K, 4),
+            "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
+            "full_gradient": {"seconds": round(grad_s, 4), "steps": steps_T,
+                              "checkpoint_every": 20,
+                              "note": "forward run + checkpointed backward, host-timed"},
+            "clocks": clk.summary(), "gpu_launches": launches * K}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the oracle
 # ---------------------------------------------------------------------------
@@ -419,7 +502,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    out, rank = run_ours(args, rank, world, local)
+    if args.workload.startswith("burgers_adjoint"):
+        out = run_adjoint(args, rank, world, local)
+    else:
+        out, rank = run_ours(args, rank, world, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -24,19 +24,6 @@ constexpr int NL = P + 6;      // loaded points s-3 .. s+P+2
 constexpr int NI = P + 3;      // interfaces j = s-2 .. s+P
 constexpr int NV = P + 2;      // limited derivatives j = s-1 .. s+P
 
-// Source of point p (maybe a ghost) and the signs of u and of its derivative:
-// kind 0 copy, 1 mirror, 2 imposed (no dependence on the state).
-__device__ __forceinline__ int ghost_src(int p, int n, int bclo, int bchi, int& kind) {
-  kind = 0;
-  if (p >= 0 && p < n) return p;
-  const int b = p < 0 ? bclo : bchi;
-  if (b == HWENO_BC_PERIODIC) return p < 0 ? p + n : p - n;
-  if (b == HWENO_BC_OUTFLOW) return p < 0 ? 0 : n - 1;
-  if (b == HWENO_BC_REFLECTIVE) { kind = 1; return p < 0 ? -p - 1 : 2 * n - 1 - p; }
-  kind = 2;
-  return 0;
-}
-
 __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constant__ AdjArgs1D a) {
   __shared__ double su[NL], sv[NL], sFp[NL], sFm[NL], sHp[NL], sHm[NL];
   __shared__ double mL1[P + 4], mL2[P + 4], mVt[NV];
@@ -118,10 +105,12 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
     }
   }
   // limited derivatives j = s-1+jl: points j-1, j, j+1 are loaded jl+1..jl+3
+  const bool limited = a.sp.limiter != 0;  // 0: v-tilde = v
   for (int jl = threadIdx.x; jl < np + 2; jl += blockDim.x) {
     double g[5] = {0, 0, 0, 0, 0};
-    limiter_vjp(su[jl + 1], su[jl + 2], su[jl + 3], dx * sv[jl + 1], dx * sv[jl + 3],
-                mVt[jl] * idx, w, g);
+    if (limited)
+      limiter_vjp(su[jl + 1], su[jl + 2], su[jl + 3], dx * sv[jl + 1], dx * sv[jl + 3],
+                  mVt[jl] * idx, w, g);
     lu[jl][0] = g[0]; lu[jl][1] = g[1]; lu[jl][2] = g[2];
     lv[jl][0] = dx * g[3]; lv[jl][1] = dx * g[4];
   }
@@ -136,6 +125,7 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
 #pragma unroll
     for (int d = 0; d < 3; ++d) ru += lu[ip + d][2 - d];
     rv += lv[ip][1] + lv[ip + 2][0];  // v_{i} enters v~_{i+1} (slot j-1) and v~_{i-1} (slot j+1)
+    if (!limited) rv += mVt[ip + 1];
     if (!periodic) {
       // ghosts at walls refer to owned points 0, 1 (left) and n-1, n-2 (right)
       auto add = [&](int jf, int kk, int p) {  // interface item jf, slot kk, point p
@@ -179,7 +169,7 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
 }  // namespace
 
 cudaError_t launch_adjoint_1d(int eq, const AdjArgs1D& a, int ntiles, cudaStream_t s) {
-  if (eq != HWENO_BURGERS) return cudaErrorNotSupported;
+  if (eq != HWENO_BURGERS) return launch_adjoint_1d_euler(a, ntiles, s);
   k_adjoint_burgers_1d<<<ntiles, 128, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -18,6 +18,20 @@ constexpr double K10 = 1421461.0 / 2275.0, K11 = 21520059541.0 / 1377684.0;
 constexpr double C11 = 11.0 / 60.0, C19 = 19.0 / 30.0;
 }  // namespace adj
 
+// Source of point p of an instance with n points (maybe a ghost): kind 0
+// copy, 1 mirror (reflective wall), 2 imposed state (no dependence on the
+// instance's values). Same mapping as the forward stage's loads.
+__device__ __forceinline__ int ghost_src(int p, int n, int bclo, int bchi, int& kind) {
+  kind = 0;
+  if (p >= 0 && p < n) return p;
+  const int b = p < 0 ? bclo : bchi;
+  if (b == HWENO_BC_PERIODIC) return p < 0 ? p + n : p - n;
+  if (b == HWENO_BC_OUTFLOW) return p < 0 ? 0 : n - 1;
+  if (b == HWENO_BC_REFLECTIVE) { kind = 1; return p < 0 ? -p - 1 : 2 * n - 1 - p; }
+  kind = 2;
+  return 0;
+}
+
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
 // One side of the nonlinear flux, f-hat^+ from (f, H = dx h) on {i-1, i, i+1}
@@ -43,22 +57,25 @@ __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, doub
   const double d1 = be0 - be1, d2 = be0 - be2;
   const double t = fabs(d1) + fabs(d2), tau = 0.25 * t * t;
   const double b0 = be0 + w.eps, b1 = be1 + w.eps, b2 = be2 + w.eps;
-  const double o0 = w.g0 * (1.0 + tau / b0), o1 = w.g1 * (1.0 + tau / b1),
-               o2 = w.g2 * (1.0 + tau / b2);
-  const double S = o0 + o1 + o2;
+  // 1/b0, 1/b1, 1/b2 from one division (b ~ beta + eps stays far from the
+  // FP64 range limits)
+  const double b12 = b1 * b2, inv = 1.0 / (b0 * b12);
+  const double ib0 = b12 * inv, ib1 = b0 * b2 * inv, ib2 = b0 * b1 * inv;
+  const double r0 = tau * ib0, r1 = tau * ib1, r2 = tau * ib2;
+  const double o0 = w.g0 * (1.0 + r0), o1 = w.g1 * (1.0 + r1), o2 = w.g2 * (1.0 + r2);
+  const double iS = 1.0 / (o0 + o1 + o2);
   const double Q0 = (p0 - w.g1 * p1 - w.g2 * p2) * w.ig0;
-  const double fh = (o0 * Q0 + o1 * p1 + o2 * p2) / S;
+  const double fh = (o0 * Q0 + o1 * p1 + o2 * p2) * iS;
   // reverse
-  const double gN = mu / S, gS = -mu * fh / S;
+  const double gN = mu * iS, gS = -gN * fh;
   const double go0 = gN * Q0 + gS, go1 = gN * p1 + gS, go2 = gN * p2 + gS;
   const double gQ0 = gN * o0;
   const double gp0 = gQ0 * w.ig0;
   const double gp1 = gN * o1 - gQ0 * w.ig0 * w.g1;
   const double gp2 = gN * o2 - gQ0 * w.ig0 * w.g2;
-  const double gtau = go0 * w.g0 / b0 + go1 * w.g1 / b1 + go2 * w.g2 / b2;
-  const double gb0 = -go0 * w.g0 * tau / (b0 * b0);
-  const double gb1 = -go1 * w.g1 * tau / (b1 * b1);
-  const double gb2 = -go2 * w.g2 * tau / (b2 * b2);
+  const double c0 = go0 * w.g0 * ib0, c1 = go1 * w.g1 * ib1, c2 = go2 * w.g2 * ib2;
+  const double gtau = c0 + c1 + c2;
+  const double gb0 = -c0 * r0, gb1 = -c1 * r1, gb2 = -c2 * r2;
   const double gt = 0.5 * t * gtau;
   const double gd1 = gt * sgn(d1), gd2 = gt * sgn(d2);
   const double gbe0 = gb0 + gd1 + gd2, gbe1 = gb1 - gd1, gbe2 = gb2 - gd2;
@@ -83,18 +100,19 @@ __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, doub
   return fh;
 }
 
-// Both sides of one field's flux at x_{i+1/2}: f-hat = f-hat^+ + f-hat^-;
-// gp (6: f^+ at i-1..i+1, H^+ at i-1..i+1) and gm (6: f^- at i..i+2, H^- at
-// i..i+2) receive mu times the partial derivatives. The "-" side is the
-// mirror image (reversed stencil, negated H).
-__device__ __forceinline__ void flux_vjp(const double* fp_, const double* Hp_, const double* fm_,
+// Both sides of one field's flux at x_{i+1/2}: returns f-hat = f-hat^+ +
+// f-hat^-; gp (6: f^+ at i-1..i+1, H^+ at i-1..i+1) and gm (6: f^- at i..i+2,
+// H^- at i..i+2) receive mu times the partial derivatives. The "-" side is
+// the mirror image (reversed stencil, negated H).
+__device__ __forceinline__ double flux_vjp(const double* fp_, const double* Hp_, const double* fm_,
                                          const double* Hm_, double mu, const Weights<double>& w,
                                          double* gp, double* gm) {
-  side_vjp(fp_[0], fp_[1], fp_[2], Hp_[0], Hp_[1], Hp_[2], mu, w, gp);
+  const double fp = side_vjp(fp_[0], fp_[1], fp_[2], Hp_[0], Hp_[1], Hp_[2], mu, w, gp);
   double r[6] = {0, 0, 0, 0, 0, 0};
-  side_vjp(fm_[2], fm_[1], fm_[0], -Hm_[2], -Hm_[1], -Hm_[0], mu, w, r);
+  const double fm = side_vjp(fm_[2], fm_[1], fm_[0], -Hm_[2], -Hm_[1], -Hm_[0], mu, w, r);
   gm[0] += r[2]; gm[1] += r[1]; gm[2] += r[0];
   gm[3] -= r[5]; gm[4] -= r[4]; gm[5] -= r[3];
+  return fp + fm;
 }
 
 // Linear derivative flux D = dx (h-hat^+ + h-hat^-) (Sec. 2.1, p_0'):
@@ -107,9 +125,9 @@ __device__ __forceinline__ void dflux_vjp(double mu, double* gp, double* gm) {
 }
 
 // HWENO limiter (Sec. 2.2) in scaled form, out = dx v-tilde from point values
-// um, u0, up and Vm = dx v_{i-1}, Vp = dx v_{i+1}: adds mu * d out / d input to
-// g[5] (order um, u0, up, Vm, Vp).
-__device__ __forceinline__ void limiter_vjp(double um, double u0, double up, double Vm, double Vp,
+// um, u0, up and Vm = dx v_{i-1}, Vp = dx v_{i+1}: returns out and adds
+// mu * d out / d input to g[5] (order um, u0, up, Vm, Vp).
+__device__ __forceinline__ double limiter_vjp(double um, double u0, double up, double Vm, double Vp,
                                             double mu, const Weights<double>& w, double* g) {
   using namespace adj;
   const double sV = Vm + Vp, dV = Vm - Vp, lap = um - 2.0 * u0 + up, dup = up - um;
@@ -121,23 +139,25 @@ __device__ __forceinline__ void limiter_vjp(double um, double u0, double up, dou
   const double d1 = be0 - be1, d2 = be0 - be2;
   const double t = fabs(d1) + fabs(d2), tau = 0.25 * t * t;
   const double b0 = be0 + w.eps, b1 = be1 + w.eps, b2 = be2 + w.eps;
-  const double l0 = w.d0 * (1.0 + tau / b0), l1 = w.d1 * (1.0 + tau / b1),
-               l2 = w.d2 * (1.0 + tau / b2);
-  const double S = l0 + l1 + l2;
+  const double b12 = b1 * b2, inv = 1.0 / (b0 * b12);
+  const double ib0 = b12 * inv, ib1 = b0 * b2 * inv, ib2 = b0 * b1 * inv;
+  const double r0 = tau * ib0, r1 = tau * ib1, r2 = tau * ib2;
+  const double l0 = w.d0 * (1.0 + r0), l1 = w.d1 * (1.0 + r1), l2 = w.d2 * (1.0 + r2);
+  const double iS = 1.0 / (l0 + l1 + l2);
   const double Q0 = (q0 - w.d1 * q1 - w.d2 * q2) * w.id0;
-  const double out = (l0 * Q0 + l1 * q1 + l2 * q2) / S;
-  const double gN = mu / S, gS = -mu * out / S;
+  const double out = (l0 * Q0 + l1 * q1 + l2 * q2) * iS;
+  const double gN = mu * iS, gS = -gN * out;
   const double gl0 = gN * Q0 + gS, gl1 = gN * q1 + gS, gl2 = gN * q2 + gS;
   const double gQ0 = gN * l0;
   double gq0 = gQ0 * w.id0;
   double gq1 = gN * l1 - gQ0 * w.id0 * w.d1;
   double gq2 = gN * l2 - gQ0 * w.id0 * w.d2;
-  const double gtau = gl0 * w.d0 / b0 + gl1 * w.d1 / b1 + gl2 * w.d2 / b2;
-  const double gt = 0.5 * t * gtau;
+  const double c0 = gl0 * w.d0 * ib0, c1 = gl1 * w.d1 * ib1, c2 = gl2 * w.d2 * ib2;
+  const double gt = 0.5 * t * (c0 + c1 + c2);
   const double gd1 = gt * sgn(d1), gd2 = gt * sgn(d2);
-  const double gbe0 = -gl0 * w.d0 * tau / (b0 * b0) + gd1 + gd2;
-  const double gbe1 = -gl1 * w.d1 * tau / (b1 * b1) - gd1;
-  const double gbe2 = -gl2 * w.d2 * tau / (b2 * b2) - gd2;
+  const double gbe0 = -c0 * r0 + gd1 + gd2;
+  const double gbe1 = -c1 * r1 - gd1;
+  const double gbe2 = -c2 * r2 - gd2;
   gq1 += 2.0 * q1 * gbe1;
   gq2 += 2.0 * q2 * gbe2;
   const double ge1 = 2.0 * e1 * gbe0, ge2 = 2.0 * K8 * e2 * gbe0;
@@ -155,6 +175,7 @@ __device__ __forceinline__ void limiter_vjp(double um, double u0, double up, dou
   g[2] += glap + gdup + gq2;
   g[3] += gsV + gdV;
   g[4] += gsV - gdV;
+  return out;
 }
 
 }  // namespace hweno

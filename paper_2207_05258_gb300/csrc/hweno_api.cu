@@ -782,8 +782,10 @@ int hweno_totals(hweno_ctx* c, const void* U, double* totals, void* stream) {
 int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W,
                        const double* dt, void* lamU, void* lamV, void* lamW, void* stream) {
   if (!c) return HWENO_EINVAL;
-  if (c->dim != 1 || c->fp32 || c->eq != HWENO_BURGERS)
-    return fail(c, HWENO_ENOTSUP, "adjoint built for 1D Burgers in FP64");
+  if (c->dim != 1 || c->fp32)
+    return fail(c, HWENO_ENOTSUP, "adjoint built for 1D problems in FP64");
+  if (c->eq == HWENO_EULER && c->opt.eig_avg != 0)
+    return fail(c, HWENO_ENOTSUP, "adjoint built for the Roe-averaged eigenvectors");
   if (!U || !V || !dt || !lamU || !lamV || W || lamW) return fail(c, HWENO_EINVAL, "bad argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;

@@ -181,6 +181,7 @@ struct AdjArgs1D {
 };
 
 cudaError_t launch_adjoint_1d(int eq, const AdjArgs1D& a, int ntiles, cudaStream_t s);
+cudaError_t launch_adjoint_1d_euler(const AdjArgs1D& a, int ntiles, cudaStream_t s);
 
 // Conserved totals (totals.cu): per-tile FP64 partial sums, then a
 // fixed-order sum per instance. Tiles: the 1D tile table, or row segments of

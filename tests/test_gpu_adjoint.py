@@ -128,3 +128,130 @@ def test_checkpoint_interval_does_not_change_the_gradient(hw):
         grads.append((U0.grad.clone(), V0.grad.clone()))
     for g in grads[1:]:
         assert torch.equal(g[0], grads[0][0]) and torch.equal(g[1], grads[0][1])
+
+
+def euler_rough_batch(sizes, bc, seed, riemann_every=0):
+    """Ragged batch of 1D Euler states on [0, 1]: smooth waves plus small
+    seeded noise (positive density and pressure) and noisy derivatives; every
+    `riemann_every`-th instance is a Riemann problem instead."""
+    rng = np.random.default_rng(seed)
+    Us, Vs = [], []
+    for k, n in enumerate(sizes):
+        x = W.centers(0, 1, n)
+        if riemann_every and k % riemann_every == riemann_every - 1:
+            lo = x < 0.5
+            rho, u, p = (np.where(lo, 1.0, 0.125), np.where(lo, 0.2, -0.1),
+                         np.where(lo, 1.0, 0.1))
+            V = np.zeros((3, n))
+        else:
+            ph = rng.uniform(0, 6.3, 3)
+            rho = 1 + 0.2 * np.sin(2 * np.pi * x + ph[0]) + 0.02 * rng.standard_normal(n)
+            u = 0.3 * np.sin(2 * np.pi * x + ph[1]) + 0.02 * rng.standard_normal(n)
+            p = 1 + 0.2 * np.cos(2 * np.pi * x + ph[2]) + 0.02 * rng.standard_normal(n)
+            V = 0.5 * rng.standard_normal((3, n))
+        Us.append(W.euler_conserved(rho, u, p, 1.4).ravel())
+        Vs.append(V.ravel())
+    return W.Workload("erb", "euler", 1, list(sizes), 1, 0.0, 1.0, 0.0, 1.0, 1.0,
+                      (bc, bc, "periodic", "periodic"), np.concatenate(Us), np.concatenate(Vs),
+                      inflow=(1.0, 0.2, 2.6, 0.0))
+
+
+def _dot_check(hw, w, seed, tol, **opts):
+    s = hw.Solver.from_workload(w, **opts)
+    U, V = torch.from_numpy(w.U.copy()).cuda(), torch.from_numpy(w.V.copy()).cuda()
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+    s.step(U.clone(), V.clone(), None, t, 1.0, dt)
+    rng = np.random.default_rng(seed)
+    lamU, lamV = rng.standard_normal(w.U.size), rng.standard_normal(w.V.size)
+    lU, lV = torch.from_numpy(lamU).cuda(), torch.from_numpy(lamV).cuda()
+    s.adjoint_step(U, V, None, dt, lU, lV)
+    s.sync_status()
+    gU, gV = lU.cpu().numpy(), lV.cpu().numpy()
+    m, off = w.m, 0
+    worst = 0.0
+    for k, n in enumerate(w.nx):
+        Uk, Vk = w.instance(k)
+        dU, dV = rng.standard_normal(Uk.shape), rng.standard_normal(Vk.shape)
+        out = O.run_tangent(oracle_problem(w, nx=n, **opts), Uk, Vk, None, dU, dV, None, 0.0,
+                            1.0, max_steps=1)
+        sl = slice(m * off, m * (off + n))
+        lhs = float(np.dot(gU[sl], dU.ravel()) + np.dot(gV[sl], dV.ravel()))
+        rhs = float(np.dot(lamU[sl], out[3].ravel()) + np.dot(lamV[sl], out[4].ravel()))
+        scale = np.sqrt(np.sum(lamU[sl] ** 2 + lamV[sl] ** 2) *
+                        np.sum(out[3] ** 2 + out[4] ** 2)) + abs(rhs)
+        worst = max(worst, abs(lhs - rhs) / scale)
+        assert abs(lhs - rhs) <= tol * scale, (k, n, lhs, rhs, scale)
+        off += n
+    return worst
+
+
+@pytest.mark.parametrize("bc", ["periodic", "outflow", "reflective", "inflow"])
+def test_euler_one_step_dot_product_against_dual_oracle(hw, bc):
+    w = euler_rough_batch([4, 31, 124, 125, 300], bc, 3, riemann_every=3)
+    worst = _dot_check(hw, w, 17, 1e-11)
+    print("euler %s: worst relative dot-product mismatch %.2e" % (bc, worst))
+
+
+@pytest.mark.parametrize("limiter", [0, 2])
+def test_euler_limiter_options(hw, limiter):
+    w = euler_rough_batch([50, 249], "outflow", 4, riemann_every=2)
+    _dot_check(hw, w, 19, 1e-11, limiter=limiter)
+
+
+def test_euler_gradient_through_checkpointed_run(hw):
+    """J = sum rho(T)^2 dx over smooth periodic Euler problems: adjoint
+    gradient against the dual-number oracle along seeded directions."""
+    from paper_2207_05258_gb300.adjoint import run_to_time
+    w = euler_rough_batch([96, 160], "periodic", 8)
+    w.t_end = 0.05
+    s = hw.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.copy()).cuda().requires_grad_(True)
+    V0 = torch.from_numpy(w.V.copy()).cuda().requires_grad_(True)
+    UT, VT = run_to_time(U0, V0, s, w.t_end, 4)
+    off, J = 0, 0.0
+    for n in w.nx:
+        J = J + (UT[3 * off:3 * off + n] ** 2).sum() / n
+        off += n
+    J.backward()
+    gU, gV = U0.grad.cpu().numpy(), V0.grad.cpu().numpy()
+    rng = np.random.default_rng(23)
+    off = 0
+    for k, n in enumerate(w.nx):
+        Uk, Vk = w.instance(k)
+        dU, dV = 0.01 * rng.standard_normal(Uk.shape), 0.1 * rng.standard_normal(Vk.shape)
+        out = O.run_tangent(oracle_problem(w, nx=n), Uk, Vk, None, dU, dV, None, 0.0, w.t_end)
+        dJ = float(np.sum(2.0 * out[0][0] * out[3][0]) / n)
+        sl = slice(3 * off, 3 * (off + n))
+        adj = float(np.dot(gU[sl], dU.ravel()) + np.dot(gV[sl], dV.ravel()))
+        scale = np.linalg.norm(np.concatenate([gU[sl], gV[sl]])) * np.linalg.norm(
+            np.concatenate([dU.ravel(), dV.ravel()]))
+        print("euler instance %d: adjoint %.12e dual %.12e" % (k, adj, dJ))
+        assert abs(adj - dJ) <= 1e-10 * scale, (k, adj, dJ, scale)
+        off += n
+
+
+def test_burgers_without_limiter(hw):
+    w = rough_batch([40, 130], "outflow", 9)
+    s = hw.Solver.from_workload(w, limiter=0)
+    U, V = torch.from_numpy(w.U.copy()).cuda(), torch.from_numpy(w.V.copy()).cuda()
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+    s.step(U.clone(), V.clone(), None, t, 1.0, dt)
+    rng = np.random.default_rng(5)
+    lamU, lamV = rng.standard_normal(w.U.size), rng.standard_normal(w.V.size)
+    lU, lV = torch.from_numpy(lamU).cuda(), torch.from_numpy(lamV).cuda()
+    s.adjoint_step(U, V, None, dt, lU, lV)
+    s.sync_status()
+    gU, gV = lU.cpu().numpy(), lV.cpu().numpy()
+    off = 0
+    for k, n in enumerate(w.nx):
+        Uk, Vk = w.instance(k)
+        dU, dV = rng.standard_normal(Uk.shape), rng.standard_normal(Vk.shape)
+        out = O.run_tangent(oracle_problem(w, nx=n, limiter=0), Uk, Vk, None, dU, dV, None,
+                            0.0, 1.0, max_steps=1)
+        lhs = float(np.dot(gU[off:off + n], dU.ravel()) + np.dot(gV[off:off + n], dV.ravel()))
+        rhs = float(np.dot(lamU[off:off + n], out[3].ravel()) +
+                    np.dot(lamV[off:off + n], out[4].ravel()))
+        assert abs(lhs - rhs) <= 1e-12 * (abs(rhs) + np.sqrt(n)), (k, lhs, rhs)
+        off += n
