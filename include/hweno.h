@@ -199,18 +199,26 @@ int hweno_autotune(hweno_ctx* ctx, const void* U, const void* V, const void* W, 
  * a device array of batch * m doubles. */
 int hweno_totals(hweno_ctx* ctx, const void* U, double* totals, void* stream);
 
-/* Discrete adjoint of one hweno_step (the fully discrete scheme of Sec. 2.2
- * differentiated step by step): given the step's input state U, V (device)
- * and the time step it took per instance dt (device, [batch], the dt_used of
- * hweno_step; 0 = the instance did not step), replaces lamU, lamV (device,
- * in: the gradient of a functional with respect to the step's output, out:
- * with respect to its input). The wave speed of each stage and dt are frozen
+/* Discrete adjoint of one hweno_step (the fully discrete scheme of Sec. 2.2,
+ * 1D Eq. odeH and 2D Eq. ode2H with the mixed fluxes of Eq. mixed,
+ * differentiated stage by stage): given the step's input state U, V (, W)
+ * (device), the time at the start of the step t (device, [batch]) and the
+ * time step it took dt (device, [batch], the dt_used of hweno_step; 0 = the
+ * instance did not step), replaces lamU, lamV (, lamW) (device, in: the
+ * gradient of a functional with respect to the step's output, out: with
+ * respect to its input). The wave speeds of each stage and dt are frozen
  * (constants of the step) and the |.| in the smoothness differences keeps the
- * branch of the forward state; the nonlinear weights and the limiter are
- * differentiated. Built for 1D Burgers in FP64 (others: HWENO_ENOTSUP);
- * W, lamW must be NULL. Library scratch holds the replayed stages. */
+ * branch of the forward state; the nonlinear weights, the characteristic
+ * eigenvectors (Roe average) and the limiter are differentiated. FP64 states
+ * only, Roe-averaged eigenvectors (eig_avg = 0), and in each direction both
+ * boundaries periodic or neither (else HWENO_ENOTSUP). 1D: W and lamW must be
+ * NULL and t is not read (may be NULL). 2D: W and lamW are required; t is
+ * read by the double-Mach top boundary and may be NULL otherwise. Library
+ * scratch holds the replayed stages (allocated on the first call: 12 fields
+ * of m x points doubles). */
 int hweno_adjoint_step(hweno_ctx* ctx, const void* U, const void* V, const void* W,
-                       const double* dt, void* lamU, void* lamV, void* lamW, void* stream);
+                       const double* t, const double* dt, void* lamU, void* lamV, void* lamW,
+                       void* stream);
 
 /* Synchronise `stream`, read the device status word and return the latched
  * device error (HWENO_OK if none); clears the latch. */

@@ -34,26 +34,6 @@ constexpr int NV = P + 2;   // limited derivatives j = s-1 .. s+P
 constexpr int NS = 12;      // per interface slot: gF[3], gH[3], gu[3], gv[3]
 constexpr int NLS = 15;     // per limiter item: gu at j-1, j, j+1 [3 each], gv at j-1, j+1
 
-// ---- forward-mode scalar (value, tangent) ----------------------------------
-struct Dd {
-  double v, d;
-  __device__ Dd() {}
-  __device__ Dd(double x) : v(x), d(0.0) {}  // NOLINT: constants mix in
-  __device__ Dd(double x, double t) : v(x), d(t) {}
-};
-__device__ __forceinline__ Dd operator+(Dd a, Dd b) { return Dd(a.v + b.v, a.d + b.d); }
-__device__ __forceinline__ Dd operator-(Dd a, Dd b) { return Dd(a.v - b.v, a.d - b.d); }
-__device__ __forceinline__ Dd operator-(Dd a) { return Dd(-a.v, -a.d); }
-__device__ __forceinline__ Dd operator*(Dd a, Dd b) { return Dd(a.v * b.v, a.d * b.v + a.v * b.d); }
-__device__ __forceinline__ Dd operator/(Dd a, Dd b) {
-  const double ib = 1.0 / b.v, q = a.v * ib;
-  return Dd(q, (a.d - q * b.d) * ib);
-}
-__device__ __forceinline__ Dd sqrt(Dd a) {
-  const double r = ::sqrt(a.v);
-  return Dd(r, 0.5 * a.d / r);
-}
-
 // Point flux F(u) and H = F'(u) v of the 1D Euler equations.
 template <class T>
 __device__ __forceinline__ void euler_fh(const T* u, const T* v, double gm1, T* F, T* H) {

@@ -60,10 +60,10 @@ struct hweno_ctx {
   void* d_U2 = nullptr; void* d_V2 = nullptr; void* d_W2 = nullptr;
   void* d_Vt0 = nullptr; void* d_Wt0 = nullptr;
   void* d_LX = nullptr; void* d_VT = nullptr;  // 2D: x-sweep results
-  // adjoint scratch (1D FP64): lambda of stages 2 and 1, base-term cotangents
-  double* d_aU2 = nullptr; double* d_aV2 = nullptr;
-  double* d_aU1 = nullptr; double* d_aV1 = nullptr;
-  double* d_acU = nullptr; double* d_acV = nullptr;
+  // adjoint scratch (FP64, allocated by the first hweno_adjoint_step): the
+  // adjoints of the stage-2 and stage-1 outputs, the base-term cotangents and
+  // (2D) the x-sweep part, each m x points doubles per field
+  double* d_adj = nullptr;
   // device copies for the host-buffer entry point
   void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
   double* d_ht = nullptr;
@@ -138,7 +138,7 @@ void free_all(hweno_ctx* c) {
                   c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
                   c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht,
-                  c->d_aU2, c->d_aV2, c->d_aU1, c->d_aV1, c->d_acU, c->d_acV};
+                  c->d_adj};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -546,11 +546,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       (c->dim == 2 &&
        ((rc = dalloc(c, &c->d_W1, fb)) || (rc = dalloc(c, &c->d_W2, fb)) ||
         (rc = dalloc(c, &c->d_Wt0, fb)) || (rc = dalloc(c, &c->d_LX, 3 * fb)) ||
-        (rc = dalloc(c, &c->d_VT, fb)) || (rc = dalloc(c, &c->d_hW, fb)))) ||
-      (c->dim == 1 && !c->fp32 &&
-       ((rc = dalloc(c, &c->d_aU2, fb)) || (rc = dalloc(c, &c->d_aV2, fb)) ||
-        (rc = dalloc(c, &c->d_aU1, fb)) || (rc = dalloc(c, &c->d_aV1, fb)) ||
-        (rc = dalloc(c, &c->d_acU, fb)) || (rc = dalloc(c, &c->d_acV, fb))))) {
+        (rc = dalloc(c, &c->d_VT, fb)) || (rc = dalloc(c, &c->d_hW, fb))))) {
     free_all(c);
     delete c;
     return rc;
@@ -779,15 +775,22 @@ int hweno_totals(hweno_ctx* c, const void* U, double* totals, void* stream) {
   return HWENO_OK;
 }
 
-int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W,
-                       const double* dt, void* lamU, void* lamV, void* lamW, void* stream) {
-  if (!c) return HWENO_EINVAL;
-  if (c->dim != 1 || c->fp32)
-    return fail(c, HWENO_ENOTSUP, "adjoint built for 1D problems in FP64");
-  if (c->eq == HWENO_EULER && c->opt.eig_avg != 0)
-    return fail(c, HWENO_ENOTSUP, "adjoint built for the Roe-averaged eigenvectors");
-  if (!U || !V || !dt || !lamU || !lamV || W || lamW) return fail(c, HWENO_EINVAL, "bad argument");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace {
+
+// Adjoint scratch fields: 0-2 lambda of the stage-2 output (U, V, W), 3-5 of
+// the stage-1 output, 6-8 base-term cotangents, 9-11 the 2D x-sweep part.
+int adjoint_scratch(hweno_ctx* c) {
+  if (c->d_adj) return HWENO_OK;
+  const size_t field = sizeof(double) * (size_t)c->m * (size_t)c->npts;
+  return dalloc(c, &c->d_adj, field * 12);
+}
+
+double* adj_field(hweno_ctx* c, int f) {
+  return c->d_adj + (size_t)f * (size_t)c->m * (size_t)c->npts;
+}
+
+int adjoint_1d(hweno_ctx* c, const void* U, const void* V, const double* dt, double* lU,
+               double* lV, cudaStream_t s) {
   cudaError_t e;
   // 1. replay stages 1 and 2 of the forward step with its dt; alpha of each
   //    stage input lands in slots 0, 1, 2 (frozen in the adjoint)
@@ -811,34 +814,138 @@ int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W
   a.Vt0out = nullptr; a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
   if ((e = launch_stage_1d(c->eq, false, c->variant, MODE_STAGE2, a, c->ntiles, s)))
     return cuda_fail(c, e, "replay stage 2");
-  // 2. reverse stages 3, 2, 1 (the adjoint kernel uses the default tiles)
+  // 2. reverse stages 3, 2, 1 (the adjoint kernels use the default tiles)
+  double *aU2 = adj_field(c, 0), *aV2 = adj_field(c, 1), *aU1 = adj_field(c, 3),
+         *aV1 = adj_field(c, 4), *acU = adj_field(c, 6), *acV = adj_field(c, 7);
   AdjArgs1D g{};
   g.tile_inst = c->d_tile0_inst; g.tile_start = c->d_tile0_start; g.inst_n = c->d_inst_n;
   g.inst_off = c->d_inst_off; g.inst_geo = c->d_inst_geo; g.dt = dt;
   g.sp = scheme_params(c);
-  double* lU = static_cast<double*>(lamU);
-  double* lV = static_cast<double*>(lamV);
   // stage 3: lambda2 = (2/3) G'(x2)^T lambda^{n+1}
   g.U = static_cast<const double*>(c->d_U2); g.V = static_cast<const double*>(c->d_V2);
   g.alpha = slotd(c, 2); g.lamU = lU; g.lamV = lV; g.b = 2.0 / 3.0;
-  g.outU = c->d_aU2; g.outV = c->d_aV2;
+  g.outU = aU2; g.outV = aV2;
   if ((e = launch_adjoint_1d(c->eq, g, c->ntiles0, s))) return cuda_fail(c, e, "adjoint 3");
   // stage 2: lambda1 = (1/4) G'(x1)^T lambda2; acc = lambda^{n+1}/3 + 3 lambda2/4
   g.U = static_cast<const double*>(c->d_U1); g.V = static_cast<const double*>(c->d_V1);
-  g.alpha = slotd(c, 1); g.lamU = c->d_aU2; g.lamV = c->d_aV2; g.b = 0.25;
-  g.outU = c->d_aU1; g.outV = c->d_aV1;
-  g.lamNU = lU; g.lamNV = lV; g.accOutU = c->d_acU; g.accOutVt = c->d_acV;
+  g.alpha = slotd(c, 1); g.lamU = aU2; g.lamV = aV2; g.b = 0.25;
+  g.outU = aU1; g.outV = aV1;
+  g.lamNU = lU; g.lamNV = lV; g.accOutU = acU; g.accOutVt = acV;
   g.cN = 1.0 / 3.0; g.c2 = 0.75;
   if ((e = launch_adjoint_1d(c->eq, g, c->ntiles0, s))) return cuda_fail(c, e, "adjoint 2");
   // stage 1: lambda^n = G'(x^n)^T lambda1 + base-term cotangents
   g.U = static_cast<const double*>(U); g.V = static_cast<const double*>(V);
-  g.alpha = slotd(c, 0); g.lamU = c->d_aU1; g.lamV = c->d_aV1; g.b = 1.0;
-  g.accU = c->d_acU; g.accVt = c->d_acV; g.lamNU = nullptr; g.lamNV = nullptr;
+  g.alpha = slotd(c, 0); g.lamU = aU1; g.lamV = aV1; g.b = 1.0;
+  g.accU = acU; g.accVt = acV; g.lamNU = nullptr; g.lamNV = nullptr;
   g.accOutU = nullptr; g.accOutVt = nullptr;
   g.outU = lU; g.outV = lV;
   if ((e = launch_adjoint_1d(c->eq, g, c->ntiles0, s))) return cuda_fail(c, e, "adjoint 1");
   c->launches = 6;
   return HWENO_OK;
+}
+
+int adjoint_2d(hweno_ctx* c, const void* U, const void* V, const void* W, const double* t,
+               const double* dt, double* lU, double* lV, double* lW, cudaStream_t s) {
+  cudaError_t e;
+  // 1. replay stages 1 and 2 with the recorded dt (alpha slots 0, 1, 2)
+  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 6, s)))
+    return cuda_fail(c, e, "memset");
+  Args2D a = base_args_2d(c);
+  a.t = t;
+  a.t_end = 0.0;
+  a.skip_done = 0;
+  a.dt_in = dt;
+  a.U = U;
+  a.alpha_out = c->d_alpha;
+  if ((e = launch_alpha_2d(c->eq, false, a, s))) return cuda_fail(c, e, "alpha");
+  struct Stage { const void *u, *v, *w; void *uo, *vo, *wo, *vt; double sc; };
+  const Stage st[2] = {{U, V, W, c->d_U1, c->d_V1, c->d_W1, c->d_Vt0, 0.0},
+                       {c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_VT, 1.0}};
+  for (int k = 0; k < 2; ++k) {
+    const int mode = MODE_STAGE1 + k;
+    a.U = st[k].u; a.V = st[k].v; a.W = st[k].w;
+    a.U0 = U; a.Vt0 = c->d_Vt0; a.Wt0 = c->d_Wt0;
+    a.Uout = st[k].uo; a.Vout = st[k].vo; a.Wout = st[k].wo;
+    a.Wt0out = k == 0 ? c->d_Wt0 : nullptr;
+    a.VT = st[k].vt;
+    a.stage_c = st[k].sc;
+    a.alpha_in = reinterpret_cast<const double*>(c->d_alpha + 2 * k);
+    a.alpha_out = c->d_alpha + 2 * (k + 1);
+    if ((e = launch_xsweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay x");
+    if ((e = launch_ysweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay y");
+  }
+  // 2. reverse stages 3, 2, 1: an x sweep into `part`, then a y sweep
+  AdjArgs2D g{};
+  g.nx = c->nx[0]; g.ny = c->ny; g.dx = a.dx; g.dy = a.dy;
+  for (int i = 0; i < 6; ++i) g.geod[i] = a.geod[i];
+  g.x0 = c->x0; g.y0 = c->y0; g.t = t; g.dt = dt; g.sp = a.sp;
+  g.part = adj_field(c, 9);
+  double* f[9];
+  for (int i = 0; i < 9; ++i) f[i] = adj_field(c, i);
+  struct Rev {
+    const void *u, *v, *w;
+    int slot;
+    double b, sc;
+    const double *lu, *lv, *lw;
+    double *ou, *ov, *ow;
+  };
+  const Rev rv[3] = {
+      {c->d_U2, c->d_V2, c->d_W2, 2, 2.0 / 3.0, 0.5, lU, lV, lW, f[0], f[1], f[2]},
+      {c->d_U1, c->d_V1, c->d_W1, 1, 0.25, 1.0, f[0], f[1], f[2], f[3], f[4], f[5]},
+      {U, V, W, 0, 1.0, 0.0, f[3], f[4], f[5], lU, lV, lW}};
+  for (int k = 0; k < 3; ++k) {
+    g.U = static_cast<const double*>(rv[k].u);
+    g.V = static_cast<const double*>(rv[k].v);
+    g.W = static_cast<const double*>(rv[k].w);
+    g.alpha = reinterpret_cast<const double*>(c->d_alpha + 2 * rv[k].slot);
+    g.b = rv[k].b;
+    g.stage_c = rv[k].sc;
+    g.lamU = rv[k].lu; g.lamV = rv[k].lv; g.lamW = rv[k].lw;
+    g.outU = rv[k].ou; g.outV = rv[k].ov; g.outW = rv[k].ow;
+    const bool st2 = k == 1, st1 = k == 2;
+    g.lamNU = st2 ? lU : nullptr; g.lamNV = st2 ? lV : nullptr; g.lamNW = st2 ? lW : nullptr;
+    g.accOutU = st2 ? f[6] : nullptr; g.accOutVt = st2 ? f[7] : nullptr;
+    g.accOutWt = st2 ? f[8] : nullptr;
+    g.cN = 1.0 / 3.0; g.c2 = 0.75;
+    g.accU = st1 ? f[6] : nullptr; g.accVt = st1 ? f[7] : nullptr; g.accWt = st1 ? f[8] : nullptr;
+    if ((e = launch_adjoint_2d(c->eq, 0, g, s))) return cuda_fail(c, e, "adjoint x");
+    if ((e = launch_adjoint_2d(c->eq, 1, g, s))) return cuda_fail(c, e, "adjoint y");
+  }
+  c->launches = 11;
+  return HWENO_OK;
+}
+
+}  // namespace
+
+int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W,
+                       const double* t, const double* dt, void* lamU, void* lamV, void* lamW,
+                       void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (c->fp32) return fail(c, HWENO_ENOTSUP, "adjoint built for FP64 states");
+  if (c->eq == HWENO_EULER && c->opt.eig_avg != 0)
+    return fail(c, HWENO_ENOTSUP, "adjoint built for the Roe-averaged eigenvectors");
+  const bool two = c->dim == 2;
+  if (!U || !V || !dt || !lamU || !lamV || (two != (W != nullptr)) || (two != (lamW != nullptr)))
+    return fail(c, HWENO_EINVAL, "bad argument");
+  const int bcs[4] = {c->bc.xlo, c->bc.xhi, c->bc.ylo, c->bc.yhi};
+  for (int d = 0; d < c->dim; ++d)
+    if ((bcs[2 * d] == HWENO_BC_PERIODIC) != (bcs[2 * d + 1] == HWENO_BC_PERIODIC))
+      return fail(c, HWENO_ENOTSUP, "adjoint needs both ends of a direction periodic or neither");
+  int rc;
+  if ((rc = adjoint_scratch(c)) != HWENO_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!two)
+    return adjoint_1d(c, U, V, dt, static_cast<double*>(lamU), static_cast<double*>(lamV), s);
+  const double* tt = t;
+  if (!tt) {  // no boundary time given: the boundaries must not depend on it
+    if (c->bc.yhi == HWENO_BC_DMR_TOP)
+      return fail(c, HWENO_EINVAL, "the double-Mach top boundary needs the step's time t");
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_ht, 0, sizeof(double), s))) return cuda_fail(c, e, "memset");
+    tt = c->d_ht;
+  }
+  return adjoint_2d(c, U, V, W, tt, dt, static_cast<double*>(lamU), static_cast<double*>(lamV),
+                    static_cast<double*>(lamW), s);
 }
 
 int hweno_sync_status(hweno_ctx* c, void* stream) {

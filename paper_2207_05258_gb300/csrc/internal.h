@@ -144,6 +144,7 @@ struct Args2D {
   double* dt;
   int* lands;
   unsigned* status;
+  const double* dt_in;  // replay (adjoint): time step given per step, else null
   SchemeParams sp;
 };
 
@@ -182,6 +183,46 @@ struct AdjArgs1D {
 
 cudaError_t launch_adjoint_1d(int eq, const AdjArgs1D& a, int ntiles, cudaStream_t s);
 cudaError_t launch_adjoint_1d_euler(const AdjArgs1D& a, int ntiles, cudaStream_t s);
+
+// Adjoint of one stage of a 2D step (adjoint2d.cu), FP64, as two sweeps over
+// lines (rows, then columns). With G(x) = (U + dt L^1, v~ + dt L^2, w~ + dt
+// L^3): the x sweep writes the cotangents that flow through the x-direction
+// terms (f-hat, h-hat, eta-hat, v~) to `part` [3m][ny][nx]; the y sweep adds
+// those of the y-direction terms (g-hat, theta-hat, xi-hat, w~), the stage's
+// direct term b lamU (+ accU) and `part`, and writes out (and, stage 2, acc).
+struct AdjArgs2D {
+  const double* U;  // stage input state
+  const double* V;
+  const double* W;
+  const double* lamU;  // adjoint of the stage output
+  const double* lamV;
+  const double* lamW;
+  const double* accU;   // stage 1: cotangents of the base term, nullable
+  const double* accVt;
+  const double* accWt;
+  const double* lamNU;  // stage 2: lambda^{n+1} for acc, nullable
+  const double* lamNV;
+  const double* lamNW;
+  double* part;         // x-sweep result [3m][ny][nx]
+  double* outU;
+  double* outV;
+  double* outW;
+  double* accOutU;      // stage 2: acc = cN lamN + c2 lam, nullable
+  double* accOutVt;
+  double* accOutWt;
+  double b, cN, c2;
+  int nx, ny;
+  double dx, dy;
+  double geod[6];       // dx, 1/dx, 1/dx^2, dy, 1/dy, 1/dy^2
+  double x0, y0;
+  const double* t;      // time at the start of the step (boundary time)
+  double stage_c;       // boundary time of the stage: t + stage_c * dt
+  const double* alpha;  // [2] frozen alpha_x, alpha_y of the stage input
+  const double* dt;     // [1] (0: the step did not happen)
+  SchemeParams sp;
+};
+
+cudaError_t launch_adjoint_2d(int eq, int dir, const AdjArgs2D& a, cudaStream_t s);
 
 // Conserved totals (totals.cu): per-tile FP64 partial sums, then a
 // fixed-order sum per instance. Tiles: the 1D tile table, or row segments of

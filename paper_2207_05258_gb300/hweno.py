@@ -72,7 +72,7 @@ SIGNATURES = {
     "hweno_totals": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "hweno_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_int), _DP, _VP]),
-    "hweno_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "hweno_adjoint_step": (ctypes.c_int, [_VP] * 10),
     "hweno_sync_status": (ctypes.c_int, [_VP, _VP]),
     "hweno_num_points": (ctypes.c_longlong, [_VP]),
     "hweno_active_instances": (ctypes.c_int, [_VP, _VP]),
@@ -220,10 +220,11 @@ class Solver:
         self._check(lib.hweno_totals(self.h, _ptr(U), _ptr(out), _stream()))
         return out
 
-    def adjoint_step(self, U, V, W, dt, lamU, lamV, lamW=None):
-        """hweno_adjoint_step: lamU, lamV (in: d J / d output of the step taken
-        from U, V with time steps dt) become d J / d input, in place."""
-        self._check(lib.hweno_adjoint_step(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(dt),
+    def adjoint_step(self, U, V, W, dt, lamU, lamV, lamW=None, t=None):
+        """hweno_adjoint_step: lamU, lamV (, lamW) (in: d J / d output of the
+        step taken from U, V (, W) at time t with time steps dt) become
+        d J / d input, in place."""
+        self._check(lib.hweno_adjoint_step(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t), _ptr(dt),
                                            _ptr(lamU), _ptr(lamV), _ptr(lamW), _stream()))
 
     def active_instances(self) -> int:

@@ -255,3 +255,113 @@ def test_burgers_without_limiter(hw):
                     np.dot(lamV[off:off + n], out[4].ravel()))
         assert abs(lhs - rhs) <= 1e-12 * (abs(rhs) + np.sqrt(n)), (k, lhs, rhs)
         off += n
+
+
+# ---------------------------------------------------------------------------
+# 2D
+# ---------------------------------------------------------------------------
+def rough_2d(eq, nx, ny, bcx, bcy, seed):
+    """2D state on [0,1]^2: smooth waves plus small seeded noise (Euler:
+    positive density and pressure) and noisy derivatives V, W."""
+    rng = np.random.default_rng(seed)
+    x = W.centers(0, 1, nx)[None, :]
+    y = W.centers(0, 1, ny)[:, None]
+    ph = rng.uniform(0, 6.3, 4)
+    noise = lambda: 0.02 * rng.standard_normal((ny, nx))
+    if eq == "euler":
+        rho = 1 + 0.2 * np.sin(2 * np.pi * (x + y) + ph[0]) + noise()
+        u = 0.3 * np.sin(2 * np.pi * x + ph[1]) + noise()
+        v = 0.2 * np.cos(2 * np.pi * y + ph[2]) + noise()
+        p = 1 + 0.2 * np.cos(2 * np.pi * (x - y) + ph[3]) + noise()
+        U = W.euler_conserved(rho, u, p, 1.4, v=v)
+        m = 4
+    else:
+        U = (0.3 + np.sin(2 * np.pi * (x + y) + ph[0]) + 5 * noise())[None]
+        m = 1
+    V = 0.5 * rng.standard_normal((m, ny, nx))
+    Wd = 0.5 * rng.standard_normal((m, ny, nx))
+    return W.Workload("r2", eq, 2, [nx], ny, 0.0, 1.0, 0.0, 1.0, 1.0, (bcx, bcx, bcy, bcy),
+                      U.ravel().copy(), V.ravel().copy(), Wd.ravel().copy(),
+                      inflow=(1.0, 0.2, 0.1, 2.6) if eq == "euler" else (0.6, 0, 0, 0))
+
+
+def _dot_check_2d(hw, w, seed, tol, pre_steps=0, **opts):
+    s = hw.Solver.from_workload(w, **opts)
+    U = torch.from_numpy(w.U.copy()).cuda()
+    V = torch.from_numpy(w.V.copy()).cuda()
+    Wd = torch.from_numpy(w.W.copy()).cuda()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(pre_steps):
+        s.step(U, V, Wd, t, 1.0)
+    t0 = t.clone()
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    s.step(U.clone(), V.clone(), Wd.clone(), t.clone(), 1.0, dt)
+    rng = np.random.default_rng(seed)
+    lam = [rng.standard_normal(w.U.size) for _ in range(3)]
+    lt = [torch.from_numpy(x).cuda() for x in lam]
+    s.adjoint_step(U, V, Wd, dt, lt[0], lt[1], lt[2], t=t0)
+    s.sync_status()
+    g = [x.cpu().numpy() for x in lt]
+    d = [rng.standard_normal(w.U.size) for _ in range(3)]
+    out = O.run_tangent(oracle_problem(w, **opts), U.cpu().numpy(), V.cpu().numpy(),
+                        Wd.cpu().numpy(), d[0], d[1], d[2], float(t0.item()), 1.0, max_steps=1)
+    lhs = sum(float(np.dot(g[i], d[i])) for i in range(3))
+    tan = [out[3].ravel(), out[4].ravel(), out[5].ravel()]
+    rhs = sum(float(np.dot(lam[i], tan[i])) for i in range(3))
+    scale = np.sqrt(sum(np.sum(x ** 2) for x in lam) * sum(np.sum(x ** 2) for x in tan)) + abs(rhs)
+    assert abs(lhs - rhs) <= tol * scale, (lhs, rhs, scale)
+    return abs(lhs - rhs) / scale
+
+
+@pytest.mark.parametrize("case", [
+    ("euler", 130, 128, "periodic", "periodic"),
+    ("euler", 40, 130, "reflective", "outflow"),
+    ("euler", 36, 28, "inflow", "reflective"),
+    ("burgers", 130, 20, "periodic", "periodic"),
+    ("burgers", 30, 40, "reflective", "outflow"),
+])
+def test_2d_one_step_dot_product_against_dual_oracle(hw, case):
+    eq, nx, ny, bcx, bcy = case
+    w = rough_2d(eq, nx, ny, bcx, bcy, 31)
+    r = _dot_check_2d(hw, w, 41, 1e-11)
+    print("2D %s %dx%d %s/%s: relative mismatch %.2e" % (eq, nx, ny, bcx, bcy, r))
+
+
+@pytest.mark.parametrize("limiter", [0, 2])
+def test_2d_euler_limiter_options(hw, limiter):
+    w = rough_2d("euler", 30, 26, "outflow", "periodic", 32)
+    _dot_check_2d(hw, w, 43, 1e-11, limiter=limiter)
+
+
+def test_2d_double_mach_boundaries_at_positive_time(hw):
+    """Double-Mach set-up (inflow left, outflow right, reflecting wall from
+    x = 1/6 on the bottom, exact moving shock on the top) a few steps in, so
+    that the top boundary's stage times matter."""
+    w = W.double_mach(64, 16)
+    r = _dot_check_2d(hw, w, 47, 1e-10, pre_steps=3)
+    print("double Mach 64x16: relative mismatch %.2e" % r)
+
+
+def test_2d_gradient_through_checkpointed_run(hw):
+    from paper_2207_05258_gb300.adjoint import run_to_time
+    w = rough_2d("euler", 24, 20, "periodic", "periodic", 33)
+    t_end = 0.02
+    s = hw.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.copy()).cuda().requires_grad_(True)
+    V0 = torch.from_numpy(w.V.copy()).cuda().requires_grad_(True)
+    W0 = torch.from_numpy(w.W.copy()).cuda().requires_grad_(True)
+    UT, VT, WT = run_to_time(U0, V0, s, t_end, 3, W0=W0)
+    n = 24 * 20
+    J = (UT[:n] ** 2).sum() / n + 1e-3 * (VT * WT).sum()
+    J.backward()
+    g = [x.grad.cpu().numpy() for x in (U0, V0, W0)]
+    rng = np.random.default_rng(51)
+    d = [0.01 * rng.standard_normal(w.U.size) for _ in range(3)]
+    out = O.run_tangent(oracle_problem(w), w.U, w.V, w.W, d[0], d[1], d[2], 0.0, t_end)
+    UTo, VTo, WTo = (x.ravel() for x in out[:3])
+    dU, dV, dW = (x.ravel() for x in out[3:6])
+    dJ = float(np.sum(2 * UTo[:n] * dU[:n]) / n + 1e-3 * np.sum(dV * WTo + VTo * dW))
+    adj = sum(float(np.dot(g[i], d[i])) for i in range(3))
+    scale = np.sqrt(sum(np.sum(x ** 2) for x in g) * sum(np.sum(x ** 2) for x in d))
+    print("2D gradient: adjoint %.12e dual %.12e" % (adj, dJ))
+    assert abs(adj - dJ) <= 1e-10 * scale, (adj, dJ, scale)
