@@ -74,7 +74,10 @@ def parse():
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--workload", default="riemann_batch",
                     help="riemann_batch (default) | euler2d_smooth:N | double_mach:NXxNY | "
-                         "burgers_adjoint:COUNTxN (discrete adjoint of the step; own JSON line)")
+                         "burgers_adjoint:COUNTxN | euler2d_adjoint:N (discrete adjoint of the "
+                         "step; own JSON line)")
+    ap.add_argument("--fd-directions", type=int, default=16,
+                    help="adjoint workloads: seeded directions checked by central differences")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, fp32 and cpu_baseline legs")
     return ap.parse_args()
@@ -359,85 +362,149 @@ def cpu_baseline(w, budget_s=12.0, sample=128):
 
 
 def run_adjoint(args, rank, world, dev_index):
-    """Discrete adjoint of the SSP-RK3 step (hweno_adjoint_step) on a batch of
-    1D Burgers problems (default 256 x N = 800, periodic, smooth seeded data):
-    (a) K adjoint steps timed one by one with CUDA events, each the reverse of
-    a recorded forward step (replay of stages 1-2, three reverse stage
-    kernels), L2 flushed between steps (the batch fits in L2); (b) one full
-    gradient of J = sum u(T)^2 dx through the checkpointed autograd Function
-    (checkpoint every 20 steps); (c) the forward step alone for the ratio."""
+    """Discrete adjoint of the SSP-RK3 step (hweno_adjoint_step).
+
+    Workloads: burgers_adjoint:COUNTxN (default 256 x 800: 1D Burgers,
+    periodic, u0 = 0.5 + sin(pi x) + a seeded 4-mode perturbation, T = 0.5/pi,
+    J = sum u(T)^2 dx) and euler2d_adjoint:N (default 512: 2D Euler periodic,
+    the density wave plus a seeded 4-mode perturbation, 400 fixed steps of
+    T/400, T = 0.25, J = sum rho(T)^2 dx dy). Measured: (a) K adjoint steps,
+    each the reverse of a recorded forward step (replay of stages 1-2 and the
+    reverse stage kernels), timed one by one with CUDA events, L2 flushed
+    between steps; the forward step alone for the ratio; (b) one full
+    gradient through the checkpointed autograd Function (checkpoint every 20
+    steps), host-timed; (c) --fd-directions seeded smooth directions d: the
+    adjoint's <grad J, d> against central differences of the GPU forward
+    (whose alpha is not frozen, so they agree to the alpha response)."""
     import torch
     from paper_2207_05258_gb300 import hweno, workloads as W
     from paper_2207_05258_gb300.adjoint import run_to_time
 
     torch.cuda.set_device(dev_index)
-    size = args.workload.partition(":")[2] or "256x800"
-    count, n = (int(v) for v in size.split("x"))
-    w = W.burgers_adjoint_batch(count=count, n=n, seed=5 + rank)
-    s = hweno.Solver.from_workload(w)
-    dx = (w.x1 - w.x0) / n
+    kind, _, size = args.workload.partition(":")
+    two = kind == "euler2d_adjoint"
+    if two:
+        n = int(size or 512)
+        w = W.euler2d_adjoint(n, seed=7 + rank)
+        s = hweno.Solver.from_workload(w, dt_mode=2, dt_fixed=w.meta["dt"])
+        t_end, max_steps = 1e30, w.meta["steps"]  # the fixed dt never lands
+        cell = ((w.x1 - w.x0) / n) ** 2
+        npts = n * n
+        desc = ("euler2d_adjoint: 2D Euler periodic [0,2]^2 %dx%d, rho = 1 + 0.2 sin(pi(x+y)) "
+                "+ seeded 4-mode perturbation (0.05), u = 0.7, v = 0.3, p = 1, %d steps of "
+                "dt = %.3g (T = %.3g)" % (n, n, max_steps, w.meta["dt"], w.t_end))
+        jfun = lambda UT: (UT[:npts] ** 2).sum() * cell
+    else:
+        count, n = (int(v) for v in (size or "256x800").split("x"))
+        w = W.burgers_adjoint_batch(count=count, n=n, seed=5 + rank)
+        s = hweno.Solver.from_workload(w)
+        t_end, max_steps = w.t_end, 1 << 30
+        cell = (w.x1 - w.x0) / n
+        npts = count * n
+        desc = ("burgers_adjoint: %d x 1D Burgers N=%d, periodic [0,2], u0 = 0.5 + sin(pi x) "
+                "+ seeded 4-mode perturbation, T = 0.5/pi" % (count, n))
+        jfun = lambda UT: (UT * UT).sum() * cell
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     K, Wm = args.steps, args.warmup
+    cuda = lambda a: torch.from_numpy(a).cuda() if a is not None else None
     stream = torch.cuda.Stream()
     with ClockSampler(dev_index) as clk, torch.cuda.stream(stream):
-        U = torch.from_numpy(w.U).cuda()
-        V = torch.from_numpy(w.V).cuda()
+        U, V, Wd = cuda(w.U), cuda(w.V), cuda(w.W)
         t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
         states, dts, fwd = [], [], []
         for k in range(Wm + K):
-            states.append((U.clone(), V.clone()))
+            states.append((U.clone(), V.clone(), Wd.clone() if two else None, t.clone()))
             dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            s.step(U, V, None, t, w.t_end, dt)
+            s.step(U, V, Wd, t, t_end, dt)
             e1.record()
             dts.append(dt)
             fwd.append((e0, e1))
-        lamU, lamV = 2.0 * U * dx, torch.zeros_like(V)
+        lam = [2.0 * U * cell, torch.zeros_like(V)] + ([torch.zeros_like(Wd)] if two else [])
+        if two:
+            lam[0][npts:] = 0.0
         adj = []
         for k in range(Wm + K - 1, -1, -1):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            s.adjoint_step(states[k][0], states[k][1], None, dts[k], lamU, lamV)
+            s.adjoint_step(states[k][0], states[k][1], states[k][2], dts[k], lam[0], lam[1],
+                           lam[2] if two else None, t=states[k][3])
             e1.record()
             adj.append((e0, e1))
         launches = s.launches_last_call
         torch.cuda.synchronize()
         s.sync_status()
-        adj_ms = sum(a.elapsed_time(b) for a, b in adj[Wm:])  # skip Wm warm-up steps
+        adj_ms = sum(a.elapsed_time(b) for a, b in adj[Wm:])  # skip the warm-up steps
         fwd_ms = sum(a.elapsed_time(b) for a, b in fwd[Wm:])
-        active = float(sum(float((d > 0).double().sum().item()) for d in dts[:K])) * n
-        # full gradient to T with checkpoints
-        U0 = torch.from_numpy(w.U).cuda().requires_grad_(True)
-        V0 = torch.from_numpy(w.V).cuda().requires_grad_(True)
+        if two:
+            active = float(K * npts)
+        else:
+            active = float(sum(float((d > 0).double().sum().item()) for d in dts[:K])) * n
+        del states
+        # (b) full gradient with checkpoints
+        U0, V0 = cuda(w.U).requires_grad_(True), cuda(w.V).requires_grad_(True)
+        W0 = cuda(w.W).requires_grad_(True) if two else None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        UT, VT = run_to_time(U0, V0, s, w.t_end, 20)
-        J = (UT * UT).sum() * dx
+        out = run_to_time(U0, V0, s, t_end, 20, max_steps=max_steps, W0=W0)
+        J = jfun(out[0])
         J.backward()
         torch.cuda.synchronize()
         grad_s = time.perf_counter() - t0
-    steps_T = int(math.ceil(w.t_end / float(dts[0].min().item())))
+        g = [U0.grad, V0.grad] + ([W0.grad] if two else [])
+        # (c) central differences along seeded smooth directions
+        fd = []
+        rng = W.SplitMix64(1234 + rank)
+        for _ in range(args.fd_directions):
+            if two:
+                comps = [W.fourier_2d(rng, n, n, 0.0, 2.0, 1e-2) for _ in range(4)]
+                d = [np.concatenate([c[i].ravel() for c in comps]) for i in range(3)]
+            else:
+                x = W.centers(0.0, 2.0, n)
+                du = np.concatenate([1e-2 * np.sin(np.pi * x * (1 + int(rng.uniform(0, 4))) +
+                                                   rng.uniform(0, 6.3)) for _ in range(count)])
+                d = [du, np.zeros_like(du)]
+            dg = [cuda(x) for x in d]
+            adj_dJ = float(sum((gi * di).sum().item() for gi, di in zip(g, dg)))
+            scale = math.sqrt(sum(float((gi * gi).sum().item()) for gi in g) *
+                              sum(float((di * di).sum().item()) for di in dg))
+            eps = 1e-6
+            Js = []
+            for sg in (1.0, -1.0):
+                Ue = cuda(w.U) + sg * eps * dg[0]
+                Ve = cuda(w.V) + sg * eps * dg[1]
+                We = cuda(w.W) + sg * eps * dg[2] if two else None
+                te = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+                s.run(Ue, Ve, We, te, t_end, max_steps=max_steps)
+                Js.append(float(jfun(Ue).item()))
+            fdv = (Js[0] - Js[1]) / (2 * eps)
+            fd.append({"adjoint": adj_dJ, "fd": fdv,
+                       "rel_to_cs_scale": abs(adj_dJ - fdv) / scale})
     if world > 1:
         adj_ms, active = reduce_over_ranks(adj_ms, active, "cuda")
     value = active / (adj_ms * 1e-3) / 1e6
-    return {"metric": "Mpoint-updates/s per adjoint RK step", "value": round(value, 3),
-            "unit": "Mpoint-updates/s", "n_gpus": world, "steps": K, "warmup": Wm,
-            "ms_per_step": round(adj_ms / K, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "burgers_adjoint: %d x 1D Burgers N=%d, periodic [0,2], "
-                                   "u0 = 0.5 + sin(pi x) + seeded 4-mode perturbation, "
-                                   "T = 0.5/pi" % (count, n),
-                       "l2": "flushed between timed steps (256 MiB write; the batch fits in L2)",
-                       "timing": "CUDA events around each hweno_adjoint_step"},
-            "forward_ms_per_step": round(fwd_ms / K, 4),
-            "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
-            "full_gradient": {"seconds": round(grad_s, 4), "steps": steps_T,
-                              "checkpoint_every": 20,
-                              "note": "forward run + checkpointed backward, host-timed"},
-            "clocks": clk.summary(), "gpu_launches": launches * K}
+    out = {"metric": "Mpoint-updates/s per adjoint RK step", "value": round(value, 3),
+           "unit": "Mpoint-updates/s", "n_gpus": world, "steps": K, "warmup": Wm,
+           "ms_per_step": round(adj_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": desc,
+                      "l2": "flushed between timed steps (256 MiB write)",
+                      "timing": "CUDA events around each hweno_adjoint_step"},
+           "forward_ms_per_step": round(fwd_ms / K, 4),
+           "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
+           "full_gradient": {"seconds": round(grad_s, 3), "checkpoint_every": 20,
+                             "note": "forward run + checkpointed backward, host-timed"},
+           "clocks": clk.summary(), "gpu_launches": launches * K}
+    if fd:
+        out["fd_check"] = {"directions": len(fd), "eps": 1e-6,
+                           "max_rel_to_cs_scale": max(f["rel_to_cs_scale"] for f in fd),
+                           "max_rel_to_dJ": max(abs(f["adjoint"] - f["fd"]) / abs(f["fd"])
+                                                for f in fd),
+                           "first": fd[0]}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -502,7 +569,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    if args.workload.startswith("burgers_adjoint"):
+    if args.workload.startswith(("burgers_adjoint", "euler2d_adjoint")):
         out = run_adjoint(args, rank, world, local)
     else:
         out, rank = run_ours(args, rank, world, local)

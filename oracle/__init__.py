@@ -26,7 +26,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-EQ_BURGERS, EQ_EULER = 0, 1
+EQ_BURGERS, EQ_EULER, EQ_BUCKLEY = 0, 1, 2
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECTIVE, BC_INFLOW, BC_DMR_BOTTOM, BC_DMR_TOP = range(6)
 
 
@@ -80,6 +80,8 @@ def _load():
             L.or_limiter.argtypes = [ctypes.c_double] * 6 + [_D, ctypes.c_double, _D]
             L.or_flux.argtypes = [_P, ctypes.c_int, _D, _D]
             L.or_jvp.argtypes = [_P, ctypes.c_int, _D, _D, _D]
+            L.or_bl_alpha01.argtypes = []
+            L.or_bl_alpha01.restype = ctypes.c_double
             L.or_wave_speed.argtypes = [_P, ctypes.c_int, _D]
             L.or_wave_speed.restype = ctypes.c_double
             L.or_eigen.argtypes = [_P, ctypes.c_int, _D, _D, _D, _D, _D]
@@ -252,3 +254,8 @@ def flops_per_point_step(p, U, V, W=None) -> float:
     U, V = _arr(U).reshape(shp), _arr(V).reshape(shp)
     W = _arr(W).reshape(shp) if p.dim == 2 else None
     return _load().or_flops_per_point_step(ctypes.byref(p), _ptr(U), _ptr(V), _ptr(W))
+
+
+def bl_alpha01():
+    """max |f'(u)| over u in [0, 1] of the Buckley-Leverett flux (reading R15)."""
+    return _load().or_bl_alpha01()

@@ -126,3 +126,66 @@ def normal_shock_post_state(mach, rho1, p1, gamma):
     p2 = p1 * (2.0 * g * M * M - (g - 1.0)) / (g + 1.0)
     u2 = M * c1 * (1.0 - rho1 / rho2)  # lab-frame speed of the shocked gas
     return rho2, p2, u2
+
+
+# ---------------------------------------------------------------------------
+# Buckley-Leverett (Example 3.4): f(u) = 4u^2 / (4u^2 + (1 - u)^2), on
+# [-1, 1] with u0 = 1 on [-1/2, 0], 0 elsewhere.
+#
+# Each jump is a Riemann problem whose entropy solution follows the convex
+# hull of f between the two states (Oleinik): for the fall 1 -> 0 at x = 0,
+# the upper concave envelope of f on [0, 1] is f on [u_a, 1] and the tangent
+# from (0, 0), touching f where f'(u) u = f(u); with D = 5u^2 - 2u + 1 that
+# is 2(1 - u) = D, i.e. u_a = 1/sqrt(5): a rarefaction (x/t = f'(u), u from 1
+# down to u_a) followed by a shock to 0 at speed f(u_a)/u_a. For the rise
+# 0 -> 1 at x = -1/2 the lower convex envelope is f on [0, u_b] and the
+# tangent to (1, 1), touching where f'(u)(1 - u) = 1 - f(u), i.e. 8u = D,
+# u_b = 1 - 2/sqrt(5): a rarefaction (x/t = f'(u), u from 0 up to u_b) then a
+# shock to 1 at speed f'(u_b). The two waves are independent while the left
+# shock has not reached the right fan's tail at x = 0 (f'(1) = 0), i.e. for
+# t < 1/2 / f'(u_b) ~ 0.472, which covers T = 0.4.
+# ---------------------------------------------------------------------------
+def bl_f(u):
+    return 4.0 * u * u / (4.0 * u * u + (1.0 - u) ** 2)
+
+
+def bl_df(u):
+    D = 4.0 * u * u + (1.0 - u) ** 2
+    return 8.0 * u * (1.0 - u) / (D * D)
+
+
+def _bl_invert(xi, lo, hi, iters=200):
+    """u in [lo, hi] with f'(u) = xi, f' monotone on [lo, hi] (bisection)."""
+    a, b = lo, hi
+    fa = bl_df(a) - xi
+    for _ in range(iters):
+        m = 0.5 * (a + b)
+        fm = bl_df(m) - xi
+        if (fm > 0) == (fa > 0):
+            a, fa = m, fm
+        else:
+            b = m
+    return 0.5 * (a + b)
+
+
+def buckley_leverett_exact(x, t):
+    """Entropy solution of Example 3.4 at time t < 0.47 on points x."""
+    x = np.asarray(x, dtype=np.float64)
+    u_a = 1.0 / np.sqrt(5.0)
+    u_b = 1.0 - 2.0 / np.sqrt(5.0)
+    s_a = bl_f(u_a) / u_a          # shock speed of the fall at x = 0
+    s_b = bl_df(u_b)               # shock speed of the rise at x = -1/2
+    assert t * s_b < 0.5, "the waves interact after t = 0.5 / f'(u_b)"
+    u = np.zeros_like(x)
+    for k, xk in enumerate(x):
+        if xk < -0.5:
+            u[k] = 0.0
+        elif xk < -0.5 + s_b * t:   # rise: fan u in [0, u_b], f' increasing there
+            u[k] = _bl_invert((xk + 0.5) / t, 0.0, u_b) if t > 0 else 0.0
+        elif xk < 0.0:
+            u[k] = 1.0
+        elif xk < s_a * t:          # fall: fan u in [u_a, 1], f' decreasing there
+            u[k] = _bl_invert(xk / t, u_a, 1.0)
+        else:
+            u[k] = 0.0
+    return u

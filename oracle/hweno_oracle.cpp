@@ -31,6 +31,9 @@
 //       same parity; imposed states carry zero derivatives.
 //   R10 double Mach reflection: Woodward-Colella setup, the incident shock
 //       passes (x_foot, 0) at 60 degrees to the x axis.
+//   R15 Buckley-Leverett (Example 3.4, non-convex f): alpha = max |f'(u)| over
+//       the admissible states u in [0, 1], and over any grid value outside
+//       [0, 1]; the maximum over [0, 1] is found by golden-section search.
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (no FMA
 // contraction, no fast-math).
@@ -110,7 +113,7 @@ template <class R> inline R rmax(R a, R b) { return (a < b) ? b : a; }
 // ---------------------------------------------------------------------------
 // Problem description (mirrored by a ctypes Structure in oracle/__init__.py).
 // ---------------------------------------------------------------------------
-enum { EQ_BURGERS = 0, EQ_EULER = 1 };
+enum { EQ_BURGERS = 0, EQ_EULER = 1, EQ_BUCKLEY = 2 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3,
        BC_DMR_BOTTOM = 4, BC_DMR_TOP = 5 };
 
@@ -118,7 +121,7 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3,
 
 extern "C" {
 struct or_problem {
-  int eq;           // EQ_BURGERS or EQ_EULER
+  int eq;           // EQ_BURGERS, EQ_EULER or EQ_BUCKLEY (1D)
   int dim;          // 1 or 2
   int nx, ny;       // points per direction (ny = 1 in 1D)
   double x0, x1, y0, y1;
@@ -144,7 +147,37 @@ struct or_problem {
 namespace {
 
 inline int ncomp(const or_problem& P) {
-  return P.eq == EQ_BURGERS ? 1 : (P.dim == 1 ? 3 : 4);
+  return P.eq == EQ_EULER ? (P.dim == 1 ? 3 : 4) : 1;
+}
+
+// Buckley-Leverett flux of Example 3.4, f(u) = 4u^2 / (4u^2 + (1 - u)^2), and
+// its derivative by the quotient rule: with D = 4u^2 + (1 - u)^2,
+// f' = (8u D - 4u^2 (8u - 2(1 - u))) / D^2 = 8u(1 - u) / D^2.
+template <class R>
+R bl_flux(R u) {
+  const R D = 4.0 * u * u + (1.0 - u) * (1.0 - u);
+  return 4.0 * u * u / D;
+}
+template <class R>
+R bl_dflux(R u) {
+  const R D = 4.0 * u * u + (1.0 - u) * (1.0 - u);
+  return 8.0 * u * (1.0 - u) / (D * D);
+}
+
+// max of |f'| over [0, 1] (reading R15): f' vanishes at both ends and has a
+// single interior maximum; golden-section search on the bracket.
+double bl_alpha01() {
+  static double cached = -1.0;
+  if (cached >= 0.0) return cached;
+  const double r = (std::sqrt(5.0) - 1.0) / 2.0;
+  double a = 0.0, b = 1.0;
+  for (int it = 0; it < 200 && b - a > 1e-15; ++it) {
+    const double c = b - r * (b - a), d = a + r * (b - a);
+    if (bl_dflux(c) > bl_dflux(d)) b = d;
+    else a = c;
+  }
+  cached = bl_dflux(0.5 * (a + b));
+  return cached;
 }
 
 // ---------------------------------------------------------------------------
@@ -278,6 +311,7 @@ Lim<R> hweno_limiter(R um, R u0, R up, R vm, R vp, double dx, const double d[3],
 template <class R>
 void flux(const or_problem& P, int dir, const R* U, R* F) {
   if (P.eq == EQ_BURGERS) { F[0] = 0.5 * U[0] * U[0]; return; }
+  if (P.eq == EQ_BUCKLEY) { F[0] = bl_flux(U[0]); return; }
   const double gm = P.gas_gamma - 1.0;
   if (P.dim == 1) {
     const R rho = U[0], m = U[1], E = U[2];
@@ -296,6 +330,7 @@ void flux(const or_problem& P, int dir, const R* U, R* F) {
 template <class R>
 void jvp(const or_problem& P, int dir, const R* U, const R* D, R* out) {
   if (P.eq == EQ_BURGERS) { out[0] = U[0] * D[0]; return; }
+  if (P.eq == EQ_BUCKLEY) { out[0] = bl_dflux(U[0]) * D[0]; return; }
   const double gm = P.gas_gamma - 1.0;
   if (P.dim == 1) {
     const R rho = U[0], m = U[1], E = U[2];
@@ -331,6 +366,7 @@ void jvp(const or_problem& P, int dir, const R* U, const R* D, R* out) {
 template <class R>
 R wave_speed(const or_problem& P, int dir, const R* U) {
   if (P.eq == EQ_BURGERS) return fabs(U[0]);
+  if (P.eq == EQ_BUCKLEY) return rmax(R(bl_alpha01()), fabs(bl_dflux(U[0])));  // R15
   const double gam = P.gas_gamma;
   if (P.dim == 1) {
     const R u = U[1] / U[0];
@@ -576,6 +612,7 @@ void limit_line(const or_problem& P, int dir, int n, double dx,
 // Sign of component c under reflection through a wall normal to `dir`.
 inline double refl_sign(const or_problem& P, int dir, int c) {
   if (P.eq == EQ_BURGERS) return -1.0;  // Burgers: (x, u) -> (-x, -u)
+  if (P.eq == EQ_BUCKLEY) return 1.0;   // a saturation: even
   return (c == 1 + dir) ? -1.0 : 1.0;   // normal momentum is odd
 }
 
@@ -927,6 +964,7 @@ void or_limiter(double um, double u0, double up, double vm, double vp, double dx
 }
 
 void or_flux(const or_problem* P, int dir, const double* U, double* F) { flux(*P, dir, U, F); }
+double or_bl_alpha01() { return bl_alpha01(); }
 void or_jvp(const or_problem* P, int dir, const double* U, const double* D, double* out) {
   jvp(*P, dir, U, D, out);
 }

@@ -54,7 +54,7 @@ class Workload:
     occupies m * nx[k] consecutive values starting at m * offsets[k].
     """
     name: str
-    equation: str                 # "burgers" or "euler"
+    equation: str                 # "burgers", "euler" or "buckley" (1D)
     dim: int
     nx: List[int]                 # points per instance (1D) or [nx] (2D)
     ny: int
@@ -78,7 +78,7 @@ class Workload:
 
     @property
     def m(self) -> int:
-        return 1 if self.equation == "burgers" else (3 if self.dim == 1 else 4)
+        return (3 if self.dim == 1 else 4) if self.equation == "euler" else 1
 
     @property
     def batch(self) -> int:
@@ -319,3 +319,59 @@ def burgers_adjoint_batch(count: int = 256, n: int = 800, seed: int = 5, amplitu
     return Workload("burgers_adjoint_batch", "burgers", 1, [n] * count, 1, 0.0, 2.0, 0.0, 1.0,
                     t_end, ("periodic",) * 4, np.concatenate(Us), np.concatenate(Vs),
                     meta=dict(seed=seed))
+
+
+def fourier_2d(rng: SplitMix64, n: int, ny: int, lo: float, hi: float, amplitude: float,
+               modes: int = 4):
+    """Seeded smooth periodic field on [lo, hi]^2 (a sum of `modes` Fourier
+    modes with wave numbers 1..2 in each direction, total amplitude <=
+    `amplitude`) and its exact x and y derivatives, on cell centres."""
+    L = hi - lo
+    x, y = centers(lo, hi, n), centers(lo, hi, ny)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    f = np.zeros_like(X)
+    fx = np.zeros_like(X)
+    fy = np.zeros_like(X)
+    for _ in range(modes):
+        a = amplitude / modes * rng.uniform(-1.0, 1.0)
+        kx = 2.0 * math.pi / L * int(rng.uniform(0.0, 3.0))
+        ky = 2.0 * math.pi / L * (1 + int(rng.uniform(0.0, 2.0)))
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        s = np.sin(kx * X + ky * Y + ph)
+        c = np.cos(kx * X + ky * Y + ph)
+        f += a * s
+        fx += a * kx * c
+        fy += a * ky * c
+    return f, fx, fy
+
+
+def euler2d_adjoint(n: int = 512, seed: int = 7, steps: int = 400, t_end: float = 0.25,
+                    gamma: float = 1.4) -> Workload:
+    """2D Euler gradient workload on [0, 2]^2, periodic: the density wave of
+    euler2d_smooth plus a seeded smooth perturbation of up to 4 Fourier modes
+    (amplitude 0.05) in rho, u = 0.7, v = 0.3, p = 1, exact U_x, U_y; a fixed
+    time step t_end / steps (CFL about 0.54 at n = 512)."""
+    rng = SplitMix64(seed)
+    x = centers(0.0, 2.0, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    f, fx, fy = fourier_2d(rng, n, n, 0.0, 2.0, 0.05)
+    u, v = 0.7, 0.3
+    rho = 1.0 + 0.2 * np.sin(np.pi * (X + Y)) + f
+    rx = 0.2 * np.pi * np.cos(np.pi * (X + Y)) + fx
+    ry = 0.2 * np.pi * np.cos(np.pi * (X + Y)) + fy
+    U = euler_conserved(rho, np.full_like(rho, u), np.ones_like(rho), gamma, v=np.full_like(rho, v))
+    Vx = np.stack([rx, rx * u, rx * v, 0.5 * rx * (u * u + v * v)])
+    Wy = np.stack([ry, ry * u, ry * v, 0.5 * ry * (u * u + v * v)])
+    return Workload("euler2d_adjoint", "euler", 2, [n], n, 0.0, 2.0, 0.0, 2.0, t_end,
+                    ("periodic",) * 4, U.ravel().copy(), Vx.ravel().copy(), Wy.ravel().copy(),
+                    gas_gamma=gamma, meta=dict(seed=seed, steps=steps, dt=t_end / steps))
+
+
+def buckley_leverett(n: int = 80, t_end: float = 0.4) -> Workload:
+    """Example 3.4: u_t + (4u^2 / (4u^2 + (1 - u)^2))_x = 0 on [-1, 1], u0 = 1
+    on [-1/2, 0] and 0 elsewhere, V = 0 (discontinuous data); outflow
+    boundaries (the paper states none; no wave reaches them before T)."""
+    x = centers(-1.0, 1.0, n)
+    U = np.where((x >= -0.5) & (x <= 0.0), 1.0, 0.0)
+    return Workload("buckley_leverett", "buckley", 1, [n], 1, -1.0, 1.0, 0.0, 1.0, t_end,
+                    ("outflow", "outflow", "periodic", "periodic"), U.copy(), np.zeros(n))

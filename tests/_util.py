@@ -16,7 +16,8 @@ def oracle_problem(w, nx=None, **kw):
     """Oracle problem record for workload `w` (instance size `nx` in a batch)."""
     args = dict(dt_mode=1 if w.dt_mode == "accuracy" else 0)
     args.update(kw)
-    return O.problem(O.EQ_BURGERS if w.equation == "burgers" else O.EQ_EULER, w.dim,
+    eq = dict(burgers=O.EQ_BURGERS, euler=O.EQ_EULER, buckley=O.EQ_BUCKLEY)[w.equation]
+    return O.problem(eq, w.dim,
                      nx if nx is not None else w.nx[0], w.ny, w.x0, w.x1, w.y0, w.y1,
                      w.gas_gamma, tuple(BC[b] for b in w.bc), w.inflow, w.pre, w.dmr_x0,
                      w.dmr_speed, w.dmr_angle, **args)
