@@ -54,9 +54,12 @@ extern "C" {
 #define HWENO_ENOTSUP (-6)    /* not implemented for this configuration */
 
 /* Equations (Sec. 3: Burgers, Eq. 1dbugers / 2dbugers; Euler, Eq. euler1 /
- * euler2 with E = p/(gamma-1) + rho |u|^2 / 2). */
+ * euler2 with E = p/(gamma-1) + rho |u|^2 / 2; Buckley-Leverett, Example 3.4,
+ * f(u) = 4u^2 / (4u^2 + (1-u)^2), 1D only, whose alpha is the maximum of
+ * |f'| over the admissible states [0, 1] and over grid values outside it). */
 #define HWENO_BURGERS 0
 #define HWENO_EULER 1
+#define HWENO_BUCKLEY 2
 
 /* Precision of state arrays and of the reconstruction arithmetic. Wave
  * speeds, time steps and times are always FP64. */
@@ -126,14 +129,16 @@ typedef struct hweno_ctx hweno_ctx; /* opaque, library-owned */
 /* Fill *opt with the paper's defaults (Sec. 3). */
 int hweno_default_options(hweno_options* opt);
 
-/* Create a solver for `equation` (HWENO_BURGERS / HWENO_EULER) on `grid`
- * with ratio of specific heats `gamma` (Euler; ignored for Burgers) and
+/* Create a solver for `equation` (HWENO_BURGERS / HWENO_EULER /
+ * HWENO_BUCKLEY) on `grid` with ratio of specific heats `gamma` (Euler;
+ * ignored otherwise) and
  * boundary conditions `bc` (the problem statement of Sec. 2.1 and Sec. 3).
  * Allocates all device scratch on the current device. On success *out holds
  * the context and HWENO_OK is returned; on failure *out is NULL and the code
  * says why: HWENO_EINVAL for an invalid grid, equation, gamma or boundary
  * set (nx, ny < 4; batch < 1; 2D with batch > 1; periodic on one side only;
- * DMR kinds outside y-low/y-high or with Burgers), HWENO_ENOMEM / HWENO_ECUDA
+ * DMR kinds outside y-low/y-high or with Burgers; Buckley-Leverett in 2D or
+ * with reflective walls), HWENO_ENOMEM / HWENO_ECUDA
  * for allocation or runtime failures. Options start at hweno_default_options. */
 int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double gamma,
                  const hweno_bc* bc);

@@ -143,6 +143,25 @@ void free_all(hweno_ctx* c) {
     if (p) cudaFree(p);
 }
 
+// Buckley-Leverett alpha over the admissible states (Example 3.4): with
+// D = 5u^2 - 2u + 1, f'(u) = 8u(1 - u)/D^2 vanishes at u = 0 and u = 1 and
+// peaks where its derivative, proportional to 10u^3 - 15u^2 + 1, vanishes in
+// (0, 1/2); the root is bracketed by the sign change and bisected.
+double buckley_alpha01() {
+  static const double value = [] {
+    double lo = 0.0, hi = 0.5;  // cubic: +1 at 0, -1.5 at 1/2
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (10.0 * mid * mid * mid - 15.0 * mid * mid + 1.0 > 0.0) lo = mid;
+      else hi = mid;
+    }
+    const double u = 0.5 * (lo + hi), D = 5.0 * u * u - 2.0 * u + 1.0;
+    return 8.0 * u * (1.0 - u) / (D * D);
+  }();
+  return value;
+}
+
 SchemeParams scheme_params(const hweno_ctx* c) {
   SchemeParams sp{};
   for (int i = 0; i < 3; ++i) { sp.lin_w[i] = c->opt.lin_w[i]; sp.lim_d[i] = c->opt.lim_d[i]; }
@@ -160,10 +179,11 @@ SchemeParams scheme_params(const hweno_ctx* c) {
   sp.dmr_angle = c->bc.dmr_angle;
   sp.dmr_tan = std::tan(c->bc.dmr_angle);
   sp.dmr_sin = std::sin(c->bc.dmr_angle);
-  const double tab[10] = {c->opt.lin_w[0], c->opt.lin_w[1], c->opt.lin_w[2], c->opt.lim_d[0],
+  const double tab[11] = {c->opt.lin_w[0], c->opt.lin_w[1], c->opt.lin_w[2], c->opt.lim_d[0],
                           c->opt.lim_d[1], c->opt.lim_d[2], c->opt.eps, 1.0 / c->opt.lin_w[0],
-                          1.0 / c->opt.lim_d[0], c->gamma};
-  for (int i = 0; i < 10; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
+                          1.0 / c->opt.lim_d[0], c->gamma,
+                          c->eq == HWENO_BUCKLEY ? buckley_alpha01() : 0.0};
+  for (int i = 0; i < 11; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
   return sp;
 }
 
@@ -452,7 +472,11 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
     (void)why;
     return HWENO_EINVAL;
   };
-  if (equation != HWENO_BURGERS && equation != HWENO_EULER) return bad("equation");
+  if (equation != HWENO_BURGERS && equation != HWENO_EULER && equation != HWENO_BUCKLEY)
+    return bad("equation");
+  if (equation == HWENO_BUCKLEY &&
+      (grid->dim != 1 || bc->xlo == HWENO_BC_REFLECTIVE || bc->xhi == HWENO_BC_REFLECTIVE))
+    return bad("Buckley-Leverett: 1D, no reflective walls");
   if (grid->dim != 1 && grid->dim != 2) return bad("dim");
   if (grid->precision != HWENO_FP64 && grid->precision != HWENO_FP32) return bad("precision");
   if (!(grid->x1 > grid->x0)) return bad("x range");
@@ -462,7 +486,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
   if (equation == HWENO_EULER && !(gamma > 1.0)) return bad("gamma");
   c->eq = equation;
   c->dim = grid->dim;
-  c->m = equation == HWENO_BURGERS ? 1 : (grid->dim == 1 ? 3 : 4);
+  c->m = equation == HWENO_EULER ? (grid->dim == 1 ? 3 : 4) : 1;
   c->batch = grid->batch;
   c->fp32 = grid->precision == HWENO_FP32;
   c->esize = c->fp32 ? 4 : 8;
@@ -922,6 +946,8 @@ int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W
                        void* stream) {
   if (!c) return HWENO_EINVAL;
   if (c->fp32) return fail(c, HWENO_ENOTSUP, "adjoint built for FP64 states");
+  if (c->eq == HWENO_BUCKLEY)
+    return fail(c, HWENO_ENOTSUP, "adjoint built for Burgers and Euler");
   if (c->eq == HWENO_EULER && c->opt.eig_avg != 0)
     return fail(c, HWENO_ENOTSUP, "adjoint built for the Roe-averaged eigenvectors");
   const bool two = c->dim == 2;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include "hweno.h"
 #include <stdint.h>
 
 namespace hweno {
@@ -37,9 +38,10 @@ struct SchemeParams {
   double dmr_x0, dmr_speed, dmr_angle;
   double dmr_tan, dmr_sin;  // tan and sin of dmr_angle, evaluated on the host
   // constants in both precisions, converted once on the host:
-  // g0, g1, g2, d0, d1, d2, eps, 1/g0, 1/d0, gas gamma
-  double wd[10];
-  float wf[10];
+  // g0, g1, g2, d0, d1, d2, eps, 1/g0, 1/d0, gas gamma, and (Buckley-Leverett)
+  // max |f'| over [0, 1]
+  double wd[11];
+  float wf[11];
 };
 
 // Arguments of one 1D launch (all instances of the batch).
@@ -241,13 +243,20 @@ cudaError_t launch_stage_1d_f64(int eq, int variant, int mode, const Args1D& a, 
                                 cudaStream_t s);
 cudaError_t launch_stage_1d_f32(int eq, int variant, int mode, const Args1D& a, int ntiles,
                                 cudaStream_t s);
+// Buckley-Leverett kernels, both precisions (stage1d_bl.cu).
+cudaError_t launch_alpha_1d_bl(bool fp32, int variant, const Args1D& a, int ntiles,
+                               cudaStream_t s);
+cudaError_t launch_stage_1d_bl(bool fp32, int variant, int mode, const Args1D& a, int ntiles,
+                               cudaStream_t s);
 inline cudaError_t launch_alpha_1d(int eq, bool fp32, int variant, const Args1D& a, int ntiles,
                                    cudaStream_t s) {
+  if (eq == HWENO_BUCKLEY) return launch_alpha_1d_bl(fp32, variant, a, ntiles, s);
   return fp32 ? launch_alpha_1d_f32(eq, variant, a, ntiles, s)
               : launch_alpha_1d_f64(eq, variant, a, ntiles, s);
 }
 inline cudaError_t launch_stage_1d(int eq, bool fp32, int variant, int mode, const Args1D& a,
                                    int ntiles, cudaStream_t s) {
+  if (eq == HWENO_BUCKLEY) return launch_stage_1d_bl(fp32, variant, mode, a, ntiles, s);
   return fp32 ? launch_stage_1d_f32(eq, variant, mode, a, ntiles, s)
               : launch_stage_1d_f64(eq, variant, mode, a, ntiles, s);
 }

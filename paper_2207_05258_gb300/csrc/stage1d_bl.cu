@@ -1,0 +1,21 @@
+// The 1D stage and wave-speed kernels (stage1d_impl.cuh) for the
+// Buckley-Leverett equation of Example 3.4 (Zhang & Zhao, arXiv:2207.05258,
+// Sec. 3), in FP64 and FP32, in a translation unit of their own so that the
+// three equations compile in parallel.
+#include "stage1d_impl.cuh"
+
+namespace hweno {
+
+cudaError_t launch_alpha_1d_bl(bool fp32, int variant, const Args1D& a, int ntiles,
+                               cudaStream_t s) {
+  return fp32 ? alpha_variants<HWENO_BUCKLEY, float>(variant, a, ntiles, s)
+              : alpha_variants<HWENO_BUCKLEY, double>(variant, a, ntiles, s);
+}
+
+cudaError_t launch_stage_1d_bl(bool fp32, int variant, int mode, const Args1D& a, int ntiles,
+                               cudaStream_t s) {
+  return fp32 ? stage_variants<HWENO_BUCKLEY, float>(variant, mode, a, ntiles, s)
+              : stage_variants<HWENO_BUCKLEY, double>(variant, mode, a, ntiles, s);
+}
+
+}  // namespace hweno

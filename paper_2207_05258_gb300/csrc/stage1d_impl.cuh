@@ -14,7 +14,7 @@ namespace {
 
 
 template <int EQ>
-struct Dim1 { static constexpr int M = EQ == HWENO_BURGERS ? 1 : 3; };
+struct Dim1 { static constexpr int M = EQ == HWENO_EULER ? 3 : 1; };
 
 // Source of point i (possibly a ghost) of an instance with n points.
 // kind: 0 copy, 1 mirror (reflective wall), 2 imposed state.
@@ -30,16 +30,33 @@ __device__ __forceinline__ int map_1d(int i, int n, int bclo, int bchi, int& kin
 }
 
 // Sign of component c of U under reflection (Burgers: u odd; Euler: momentum
-// odd). The normal derivative takes the opposite sign.
+// odd; a Buckley-Leverett saturation even, though the host rejects such
+// walls). The normal derivative takes the opposite sign.
 template <int EQ>
 __device__ __forceinline__ float refl_sign(int c) {
+  if (EQ == HWENO_BUCKLEY) return 1.f;
   return EQ == HWENO_BURGERS ? -1.f : (c == 1 ? -1.f : 1.f);
 }
 
+// Buckley-Leverett flux f = 4u^2/D and f' = 8u(1 - u)/D^2, D = 4u^2 + (1-u)^2.
+template <class Real>
+__device__ __forceinline__ void buckley_f(Real u, Real& f, Real& df) {
+  const Real w = Real(1) - u;
+  const Real iD = Real(1) / (Real(4) * u * u + w * w);
+  f = Real(4) * u * u * iD;
+  df = Real(8) * u * w * iD * iD;
+}
+
+// Per-point contribution to alpha; a01 = max |f'| over [0, 1] (Buckley-
+// Leverett only).
 template <int EQ, class Real>
-__device__ __forceinline__ Real wave_speed(const Real* u, Real gam) {
+__device__ __forceinline__ Real wave_speed(const Real* u, Real gam, Real a01) {
   if constexpr (EQ == HWENO_BURGERS) {
     return fabs(u[0]);
+  } else if constexpr (EQ == HWENO_BUCKLEY) {
+    Real f, df;
+    buckley_f(u[0], f, df);
+    return fmax(a01, fabs(df));
   } else {
     const Real ir = Real(1) / u[0];
     const Real vel = u[1] * ir;
@@ -76,13 +93,14 @@ __global__ void __launch_bounds__(kThreads1D) k_alpha_1d(const __grid_constant__
   const int np = min(P, n - s);
   const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
   const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+  const Real a01 = pick<Real>(a.sp.wd, a.sp.wf)[10];
   Real amax = Real(0);
   bool bad = false;
   for (int j = threadIdx.x; j < np; j += blockDim.x) {
     Real u[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + s + j];
-    const Real sp = wave_speed<EQ>(u, gam);
+    const Real sp = wave_speed<EQ>(u, gam, a01);
     bad |= !(sp <= real_max<Real>());
     amax = fmax(amax, sp);
   }
@@ -184,9 +202,13 @@ k_stage_1d(const __grid_constant__ Args1D a) {
         sV[c][g] = v[c];
       }
       Real F[M], H[M];
-      if constexpr (!EUL) {
+      if constexpr (EQ == HWENO_BURGERS) {
         F[0] = Real(0.5) * u[0] * u[0];
         H[0] = u[0] * v[0];
+      } else if constexpr (EQ == HWENO_BUCKLEY) {
+        Real df;
+        buckley_f(u[0], F[0], df);
+        H[0] = df * v[0];
       } else {
         // 1/rho and sqrt(rho) from one reciprocal square root
         const Real rr = rsq(u[0]);
@@ -344,7 +366,7 @@ k_stage_1d(const __grid_constant__ Args1D a) {
         static_cast<Real*>(a.Vout)[q] = vn[c];
       }
       if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
-        const Real sp = wave_speed<EQ>(un, gam);
+        const Real sp = wave_speed<EQ>(un, gam, pick<Real>(a.sp.wd, a.sp.wf)[10]);
         bad |= !(sp <= real_max<Real>());
         amax = fmax(amax, sp);
       }

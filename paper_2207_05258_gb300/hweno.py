@@ -18,7 +18,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libhweno.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-BURGERS, EULER = 0, 1
+BURGERS, EULER, BUCKLEY = 0, 1, 2
+EQUATIONS = dict(burgers=BURGERS, euler=EULER, buckley=BUCKLEY)
 FP64, FP32 = 0, 1
 BC = dict(periodic=0, outflow=1, reflective=2, inflow=3, dmr_bottom=4, dmr_top=5)
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
@@ -131,7 +132,7 @@ class Solver:
         nxs = [int(nx)] if isinstance(nx, int) else [int(n) for n in nx]
         self.equation, self.dim, self.nx, self.ny = equation, dim, nxs, (ny if dim == 2 else 1)
         self.batch = len(nxs) if dim == 1 else 1
-        self.m = 1 if equation == "burgers" else (3 if dim == 1 else 4)
+        self.m = (3 if dim == 1 else 4) if equation == "euler" else 1
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self._nx_arr = (ctypes.c_int * len(nxs))(*nxs)
         g = Grid(dim, nxs[0], self.ny, x0, x1, y0, y1, self.batch,
@@ -142,7 +143,7 @@ class Solver:
         b.pre[:] = list(pre) + [0.0] * (4 - len(pre))
         b.dmr_x0, b.dmr_speed, b.dmr_angle = dmr_x0, dmr_speed, dmr_angle
         h = ctypes.c_void_p()
-        rc = lib.hweno_create(ctypes.byref(h), BURGERS if equation == "burgers" else EULER,
+        rc = lib.hweno_create(ctypes.byref(h), EQUATIONS[equation],
                               ctypes.byref(g), gamma, ctypes.byref(b))
         if rc != OK:
             raise HwenoError(rc, "hweno_create failed")

@@ -54,7 +54,8 @@ def _create(hw, eq=0, dim=1, nx=16, ny=16, batch=1, nxs=None, prec=0, bc=(0, 0, 
 
 
 @pytest.mark.parametrize("kw", [
-    dict(nx=3), dict(nx=0), dict(batch=0), dict(batch=2, nxs=[16, 2]), dict(eq=2), dict(dim=3),
+    dict(nx=3), dict(nx=0), dict(batch=0), dict(batch=2, nxs=[16, 2]), dict(eq=3), dict(dim=3),
+    dict(eq=2, dim=2), dict(eq=2, bc=(2, 2, 0, 0)),
     dict(prec=5), dict(bc=(0, 1, 0, 0)), dict(bc=(4, 1, 0, 0)), dict(bc=(9, 9, 0, 0)),
     dict(eq=1, gamma=1.0), dict(dim=2, batch=2), dict(dim=2, ny=3), dict(dim=2, y1=0.0),
     dict(dim=2, bc=(1, 1, 5, 4)), dict(dim=2, eq=0, bc=(1, 1, 4, 5)),
