@@ -52,3 +52,14 @@ def test_reduce_over_two_gloo_ranks():
     assert [o[1] for o in out] == [11.0, 11.0]
     assert [o[2] for o in out] == [300.0, 300.0]
     assert out[0][3] != out[1][3]
+
+
+def test_cpu_baseline_all_cores_on_a_small_sample():
+    """The all-core oracle baseline (spawned processes) runs on CPU and
+    reports the processes it used."""
+    import bench
+    from paper_2207_05258_gb300 import workloads as W
+    w = W.riemann_batch(count=6, seed=3, sizes=(200, 400))
+    r = bench.cpu_baseline(w, budget_s=0.6, sample=6, processes=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle"
+    assert r["value"] > 0 and r["single_thread"] > 0
