@@ -61,7 +61,7 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # capture of a stage-1 launch (dram__bytes_read.sum + dram__bytes_write.sum
 # over points; profiles/k_stage_1d_euler_fp{64,32}_riemann_batch.md). An entry
 # is removed whenever the kernel changes after its capture.
-MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 100.9, "fp32": 40.2}
+MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 100.5, "fp32": None}
 
 
 def parse():
@@ -280,7 +280,7 @@ def run_ours(args, rank, world, dev_index):
     achieved = flop_stage * pts_per_stage / stage_time / 1e12
     peak = PEAK_TFLOPS[args.precision]
     traffic = (MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
-               if args.workload == "riemann_batch" else None)
+               if args.workload == "riemann_batch" else None)  # None: not yet re-captured
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
             "traffic": None if traffic is None else traffic * pts_per_stage,
