@@ -186,6 +186,24 @@ int hweno_run(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end
 int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream);
 
+/* Persistent run of a 1D batch: `steps` SSP-RK3 steps (Sec. 2.2) of every
+ * instance in ONE kernel launch (after a wave-speed launch for the first
+ * step). The CTAs stay resident and take work items (step, stage, tile) from
+ * a device counter in that order; a tile waits only for the previous stage
+ * of its own instance, so instances of different sizes and step counts flow
+ * through the stages without grid-wide barriers. Results agree with `steps`
+ * calls of hweno_step to rounding (the same stage code, compiled into another
+ * kernel, may fuse a*b + c*d differently); instances reaching t_end stop
+ * stepping. U, V, t (device) are updated in
+ * place. If point_updates (host) is not NULL the call synchronises `stream`
+ * and stores the point-updates of stepping instances there, then returns the
+ * latched device status; otherwise it returns after enqueueing. Waits are
+ * bounded (about two seconds); a wait that gives up latches HWENO_ETIMEOUT.
+ * 1D only (2D: HWENO_ENOTSUP). Library scratch: counters and alpha slots,
+ * allocated by the first call. */
+int hweno_run_persistent(hweno_ctx* ctx, void* U, void* V, double* t, double t_end, int steps,
+                         long long* point_updates, void* stream);
+
 /* Tile-shape autotuner (1D): times the fused stage kernel of every tile
  * variant (CTA sizes 64, 128, 256 threads, one or two points per thread) on
  * the given state U, V at times t (device) with t_end, and keeps the fastest

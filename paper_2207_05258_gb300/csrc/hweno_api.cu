@@ -64,6 +64,14 @@ struct hweno_ctx {
   // adjoints of the stage-2 and stage-1 outputs, the base-term cotangents and
   // (2D) the x-sweep part, each m x points doubles per field
   double* d_adj = nullptr;
+  // persistent run (allocated by the first hweno_run_persistent)
+  unsigned long long* d_next = nullptr;  // ticket counter, then done[batch], done3[batch]
+  unsigned* d_done = nullptr;
+  unsigned* d_done3 = nullptr;
+  unsigned long long* d_palpha = nullptr;  // 2 x 3 x batch alpha slots
+  int* d_inst_tiles = nullptr;
+  int persist_variant = -1;  // tile variant d_inst_tiles was built for
+  int persist_ctas = 0;
   // device copies for the host-buffer entry point
   void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
   double* d_ht = nullptr;
@@ -138,7 +146,7 @@ void free_all(hweno_ctx* c) {
                   c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
                   c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht,
-                  c->d_adj};
+                  c->d_adj, c->d_next, c->d_palpha, c->d_inst_tiles};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -700,6 +708,83 @@ int hweno_run(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
   return hweno_sync_status(c, stream);
 }
 
+int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end, int steps,
+                         long long* point_updates, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (c->dim != 1) return fail(c, HWENO_ENOTSUP, "persistent run built for 1D batches");
+  if (!U || !V || !t || steps < 1) return fail(c, HWENO_EINVAL, "bad argument");
+  if (!std::isfinite(t_end)) return fail(c, HWENO_EINVAL, "t_end not finite");
+  if ((long long)steps * 3LL * c->ntiles >= (1LL << 31))
+    return fail(c, HWENO_EINVAL, "too many steps for one launch");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  int rc;
+  const size_t B = c->batch;
+  if (!c->d_next) {
+    // counters: next (8 B), done, done3 (4 B per instance each), one allocation
+    if ((rc = dalloc(c, &c->d_next, sizeof(unsigned long long) + 2 * sizeof(unsigned) * B)) ||
+        (rc = dalloc(c, &c->d_palpha, sizeof(unsigned long long) * 6 * B)) ||
+        (rc = dalloc(c, &c->d_inst_tiles, sizeof(int) * B)))
+      return rc;
+    c->d_done = reinterpret_cast<unsigned*>(c->d_next + 1);
+    c->d_done3 = c->d_done + B;
+  }
+  if (c->persist_variant != c->variant) {
+    const int tp = tile_points(c->variant);
+    std::vector<int> nt(B);
+    for (size_t k = 0; k < B; ++k) nt[k] = (c->nx[k] + tp - 1) / tp;
+    if ((e = cudaMemcpy(c->d_inst_tiles, nt.data(), sizeof(int) * B, cudaMemcpyHostToDevice)))
+      return cuda_fail(c, e, "copy tile counts");
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+      return cuda_fail(c, e, "device attributes");
+    const int per_sm = run_1d_ctas_per_sm(c->eq, c->fp32, c->variant);
+    if (per_sm < 1) return fail(c, HWENO_ECUDA, "persistent kernel does not fit on an SM");
+    c->persist_ctas = sms * per_sm;
+    c->persist_variant = c->variant;
+  }
+  if ((e = cudaMemsetAsync(c->d_next, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned) * B, s)) ||
+      (e = cudaMemsetAsync(c->d_palpha, 0, sizeof(unsigned long long) * 6 * B, s)) ||
+      (e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)) ||
+      (e = cudaMemsetAsync(c->d_pu, 0, sizeof(unsigned long long), s)))
+    return cuda_fail(c, e, "memset");
+  Args1D a = base_args_1d(c);
+  a.t = t;
+  a.t_end = t_end;
+  a.skip_done = 1;
+  a.dt = c->d_dt;
+  a.lands = c->d_lands;
+  a.U = U;
+  a.V = V;
+  a.alpha_out = c->d_palpha;  // alpha(U^n) of the first step: slot [0][0]
+  prof_begin(c, s);
+  if ((e = launch_alpha_1d(c->eq, c->fp32, c->variant, a, c->ntiles, s)))
+    return cuda_fail(c, e, "alpha");
+  prof_end(c, s, 0);
+  a.alpha_out = nullptr;
+  PersistArgs p{};
+  p.next = c->d_next; p.done = c->d_done; p.done3 = c->d_done3;
+  p.inst_tiles = c->d_inst_tiles; p.alpha = c->d_palpha;
+  p.U1 = c->d_U1; p.V1 = c->d_V1; p.U2 = c->d_U2; p.V2 = c->d_V2; p.Vt0 = c->d_Vt0;
+  p.active = c->d_active; p.pu = c->d_pu;
+  p.steps = steps; p.ntiles = c->ntiles; p.batch = c->batch;
+  prof_begin(c, s);
+  if ((e = launch_run_1d(c->eq, c->fp32, c->variant, a, p, c->persist_ctas, s)))
+    return cuda_fail(c, e, "persistent run");
+  prof_end(c, s, 1);
+  c->launches = 2;
+  if (point_updates) {
+    unsigned long long pu = 0;
+    if ((e = cudaMemcpyAsync(&pu, c->d_pu, sizeof pu, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+      return cuda_fail(c, e, "read point updates");
+    *point_updates = (long long)pu;
+    return hweno_sync_status(c, stream);
+  }
+  return HWENO_OK;
+}
+
 int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream) {
   if (!c) return HWENO_EINVAL;
@@ -984,6 +1069,8 @@ int hweno_sync_status(hweno_ctx* c, void* stream) {
     return cuda_fail(c, e, "read status");
   if (st) {
     cudaMemset(c->d_status, 0, sizeof(unsigned));
+    if (st & STATUS_TIMEOUT)
+      return fail(c, HWENO_ETIMEOUT, "a persistent-run wait gave up (dependency not met in ~2 s)");
     if (st & STATUS_NONFINITE) return fail(c, HWENO_ENONFINITE, "non-finite wave speed");
   }
   return HWENO_OK;

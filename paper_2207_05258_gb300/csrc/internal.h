@@ -9,7 +9,7 @@
 namespace hweno {
 
 // Status-word bits written by kernels (read by hweno_sync_status).
-enum : unsigned { STATUS_NONFINITE = 1u };
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u };
 
 enum Mode { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE2 = 2, MODE_STAGE3 = 3 };
 
@@ -243,11 +243,52 @@ cudaError_t launch_stage_1d_f64(int eq, int variant, int mode, const Args1D& a, 
                                 cudaStream_t s);
 cudaError_t launch_stage_1d_f32(int eq, int variant, int mode, const Args1D& a, int ntiles,
                                 cudaStream_t s);
+// Persistent run of a 1D batch (stage1d_impl.cuh, k_run_1d): `steps` whole
+// SSP-RK3 steps in one launch. CTAs take tickets (step, stage, tile) in that
+// lexicographic order from `next`; a tile waits (bounded) until its instance
+// has completed every tile of the previous stage, counted in done[k]; the
+// last stage-3 tile of an instance does the time update and releases the
+// next step. alpha slots: [parity][stage][batch], zeroed by the host before
+// the launch, slot [0][0] holding alpha(U^n) of the first step.
+struct PersistArgs {
+  unsigned long long* next;   // ticket counter (zero at launch)
+  unsigned* done;             // per instance: completed tiles (zero at launch)
+  unsigned* done3;            // per instance: completed stage-3 tiles of the step
+  const int* inst_tiles;      // tiles per instance in the launch's tile table
+  unsigned long long* alpha;  // 2 x 3 x batch
+  void* U1; void* V1; void* U2; void* V2; void* Vt0;  // stage buffers
+  int* active;                // instances with t < t_end after the last step
+  unsigned long long* pu;     // point-updates of stepping instances (nullable)
+  int steps, ntiles, batch;
+};
+
+cudaError_t launch_run_1d_f64(int eq, int variant, const Args1D& a, const PersistArgs& p,
+                              int ctas, cudaStream_t s);
+cudaError_t launch_run_1d_f32(int eq, int variant, const Args1D& a, const PersistArgs& p,
+                              int ctas, cudaStream_t s);
+cudaError_t launch_run_1d_bl(bool fp32, int variant, const Args1D& a, const PersistArgs& p,
+                             int ctas, cudaStream_t s);
+// Resident CTAs of the persistent kernel per SM (occupancy), for the grid size.
+int run_1d_ctas_per_sm(int eq, bool fp32, int variant);
+int run_1d_ctas_per_sm_f64(int eq, int variant);
+int run_1d_ctas_per_sm_f32(int eq, int variant);
+int run_1d_ctas_per_sm_bl(bool fp32, int variant);
+
 // Buckley-Leverett kernels, both precisions (stage1d_bl.cu).
 cudaError_t launch_alpha_1d_bl(bool fp32, int variant, const Args1D& a, int ntiles,
                                cudaStream_t s);
 cudaError_t launch_stage_1d_bl(bool fp32, int variant, int mode, const Args1D& a, int ntiles,
                                cudaStream_t s);
+inline cudaError_t launch_run_1d(int eq, bool fp32, int variant, const Args1D& a,
+                                 const PersistArgs& p, int ctas, cudaStream_t s) {
+  if (eq == HWENO_BUCKLEY) return launch_run_1d_bl(fp32, variant, a, p, ctas, s);
+  return fp32 ? launch_run_1d_f32(eq, variant, a, p, ctas, s)
+              : launch_run_1d_f64(eq, variant, a, p, ctas, s);
+}
+inline int run_1d_ctas_per_sm(int eq, bool fp32, int variant) {
+  if (eq == HWENO_BUCKLEY) return run_1d_ctas_per_sm_bl(fp32, variant);
+  return fp32 ? run_1d_ctas_per_sm_f32(eq, variant) : run_1d_ctas_per_sm_f64(eq, variant);
+}
 inline cudaError_t launch_alpha_1d(int eq, bool fp32, int variant, const Args1D& a, int ntiles,
                                    cudaStream_t s) {
   if (eq == HWENO_BUCKLEY) return launch_alpha_1d_bl(fp32, variant, a, ntiles, s);

@@ -51,6 +51,13 @@ cudaError_t launch_stage_1d_f64(int eq, int variant, int mode, const Args1D& a, 
   return stage_prec<double>(eq, variant, mode, a, ntiles, s);
 }
 
+cudaError_t launch_run_1d_f64(int eq, int variant, const Args1D& a, const PersistArgs& p,
+                              int ctas, cudaStream_t s) {
+  return run_prec<double>(eq, variant, a, p, ctas, s);
+}
+
+int run_1d_ctas_per_sm_f64(int eq, int variant) { return occupancy_prec<double>(eq, variant); }
+
 cudaError_t launch_finalize(int batch, const double* dt, const int* lands, double* t,
                             double t_end, double* dt_used, const double* alpha, int* active,
                             unsigned* status, const int* inst_n, int rows,

@@ -18,4 +18,15 @@ cudaError_t launch_stage_1d_bl(bool fp32, int variant, int mode, const Args1D& a
               : stage_variants<HWENO_BUCKLEY, double>(variant, mode, a, ntiles, s);
 }
 
+cudaError_t launch_run_1d_bl(bool fp32, int variant, const Args1D& a, const PersistArgs& p,
+                             int ctas, cudaStream_t s) {
+  return fp32 ? run_variants<HWENO_BUCKLEY, float>(variant, a, p, ctas, s)
+              : run_variants<HWENO_BUCKLEY, double>(variant, a, p, ctas, s);
+}
+
+int run_1d_ctas_per_sm_bl(bool fp32, int variant) {
+  return fp32 ? occupancy_variants<HWENO_BUCKLEY, float>(variant)
+              : occupancy_variants<HWENO_BUCKLEY, double>(variant);
+}
+
 }  // namespace hweno

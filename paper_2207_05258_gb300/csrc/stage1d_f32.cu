@@ -15,4 +15,11 @@ cudaError_t launch_stage_1d_f32(int eq, int variant, int mode, const Args1D& a, 
   return stage_prec<float>(eq, variant, mode, a, ntiles, s);
 }
 
+cudaError_t launch_run_1d_f32(int eq, int variant, const Args1D& a, const PersistArgs& p,
+                              int ctas, cudaStream_t s) {
+  return run_prec<float>(eq, variant, a, p, ctas, s);
+}
+
+int run_1d_ctas_per_sm_f32(int eq, int variant) { return occupancy_prec<float>(eq, variant); }
+
 }  // namespace hweno

@@ -5,6 +5,8 @@
 
 #include <cfloat>
 
+#include <cuda/atomic>
+
 #include "hweno.h"
 #include "hweno_math.cuh"
 #include "internal.h"
@@ -131,9 +133,29 @@ struct MinBlocks1D {
   static constexpr int value = base * 128 / NT > 0 ? base * 128 / NT : 1;
 };
 
+// The arrays one stage reads and writes (the rest of Args1D is shared by
+// every stage of a step).
+struct StageIO {
+  const void* U;
+  const void* V;
+  const void* U0;
+  const void* Vt0;
+  void* Uout;
+  void* Vout;
+  void* Vt0out;
+  const double* alpha_in;
+  unsigned long long* alpha_out;
+};
+
+__device__ __forceinline__ StageIO io_of(const Args1D& a) {
+  return StageIO{a.U, a.V, a.U0, a.Vt0, a.Uout, a.Vout, a.Vt0out, a.alpha_in, a.alpha_out};
+}
+
+// One stage on the tile of instance k starting at point s (the whole CTA;
+// contains barriers, so every thread calls it with the same k, s).
 template <int EQ, class Real, int MODE, int NT, int PPT>
-__global__ void __launch_bounds__(NT, (MinBlocks1D<Real, NT>::value))
-k_stage_1d(const __grid_constant__ Args1D a) {
+__device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, const int k,
+                                           const int s) {
   using Lay = Layout1D<EQ, Real, NT, PPT>;
   constexpr int M = Lay::M;
   constexpr int NP = Lay::NP;
@@ -153,14 +175,13 @@ k_stage_1d(const __grid_constant__ Args1D a) {
   __shared__ Real red[NT / 32];
   __shared__ double s_dt;
 
-  const int b = blockIdx.x;
-  const int k = a.tile_inst[b], s = a.tile_start[b], n = a.inst_n[k];
+  const int n = a.inst_n[k];
   if (a.skip_done && !(a.t[k] < a.t_end)) return;
   const int np = min(Lay::P, n - s);
   const long long off = a.inst_off[k] * M;
   const Real* geo = pick<Real>(a.inst_geo, a.inst_geof) + 3 * k;
   const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
-  const Real alpha = Real(a.alpha_in[k]);
+  const Real alpha = Real(io.alpha_in[k]);
   const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
   const Real gm1 = gam - Real(1);
   const Weights<Real> w = weights_from(pick<Real>(a.sp.wd, a.sp.wf));
@@ -171,7 +192,7 @@ k_stage_1d(const __grid_constant__ Args1D a) {
     if constexpr (MODE == MODE_STAGE1) {
       int lands = 0;
       dt = a.dt_in ? a.dt_in[k]
-                   : time_step(a.sp, a.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
+                   : time_step(a.sp, io.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
       if (s == 0) { a.dt[k] = dt; a.lands[k] = lands; }
     } else if constexpr (MODE != MODE_RHS) {
       dt = a.dt[k];
@@ -181,8 +202,8 @@ k_stage_1d(const __grid_constant__ Args1D a) {
 
   // 1-2: tile load with ghosts; point fluxes and splitting
   {
-    const Real* U = static_cast<const Real*>(a.U) + off;
-    const Real* V = static_cast<const Real*>(a.V) + off;
+    const Real* U = static_cast<const Real*>(io.U) + off;
+    const Real* V = static_cast<const Real*>(io.V) + off;
     const Real hdx = Real(0.5) * dx;
     for (int g = threadIdx.x; g < np + 4; g += blockDim.x) {
       int kind;
@@ -295,6 +316,7 @@ k_stage_1d(const __grid_constant__ Args1D a) {
 
   // 4: points
   const Real rdt = Real(s_dt);
+  const bool want_alpha = MODE != MODE_RHS && io.alpha_out != nullptr;  // uniform
   Real amax = Real(0);
   bool bad = false;
   for (int j = threadIdx.x; j < np; j += blockDim.x) {
@@ -350,34 +372,43 @@ k_stage_1d(const __grid_constant__ Args1D a) {
         if constexpr (MODE == MODE_STAGE1) {
           un[c] = sU[c][g] + rdt * l1[c];
           vn[c] = vt[c] + rdt * l2[c];
-          static_cast<Real*>(a.Vt0out)[q] = vt[c];
+          static_cast<Real*>(io.Vt0out)[q] = vt[c];
         } else if constexpr (MODE == MODE_STAGE2) {
-          const Real u0 = static_cast<const Real*>(a.U0)[q];
-          const Real v0 = static_cast<const Real*>(a.Vt0)[q];
+          const Real u0 = static_cast<const Real*>(io.U0)[q];
+          const Real v0 = static_cast<const Real*>(io.Vt0)[q];
           un[c] = Real(0.75) * u0 + Real(0.25) * (sU[c][g] + rdt * l1[c]);
           vn[c] = Real(0.75) * v0 + Real(0.25) * (vt[c] + rdt * l2[c]);
         } else {
-          const Real u0 = static_cast<const Real*>(a.U0)[q];
-          const Real v0 = static_cast<const Real*>(a.Vt0)[q];
+          const Real u0 = static_cast<const Real*>(io.U0)[q];
+          const Real v0 = static_cast<const Real*>(io.Vt0)[q];
           un[c] = Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * (sU[c][g] + rdt * l1[c]);
           vn[c] = Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * (vt[c] + rdt * l2[c]);
         }
-        static_cast<Real*>(a.Uout)[q] = un[c];
-        static_cast<Real*>(a.Vout)[q] = vn[c];
+        static_cast<Real*>(io.Uout)[q] = un[c];
+        static_cast<Real*>(io.Vout)[q] = vn[c];
       }
-      if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
+      if (want_alpha) {
         const Real sp = wave_speed<EQ>(un, gam, pick<Real>(a.sp.wd, a.sp.wf)[10]);
         bad |= !(sp <= real_max<Real>());
         amax = fmax(amax, sp);
       }
     }
   }
-  if constexpr (MODE == MODE_STAGE1 || MODE == MODE_STAGE2) {
+  // the wave speed of the stage output (stages 1 and 2; stage 3 as well when
+  // the persistent run asks for the next step's alpha)
+  if (want_alpha) {
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
     amax = block_max_t(amax, red);
     if (threadIdx.x == 0)
-      atomicMax(&a.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
+      atomicMax(&io.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
   }
+}
+
+template <int EQ, class Real, int MODE, int NT, int PPT>
+__global__ void __launch_bounds__(NT, (MinBlocks1D<Real, NT>::value))
+k_stage_1d(const __grid_constant__ Args1D a) {
+  stage_tile<EQ, Real, MODE, NT, PPT>(a, io_of(a), a.tile_inst[blockIdx.x],
+                                      a.tile_start[blockIdx.x]);
 }
 
 template <int EQ, class Real, int MODE, int NT, int PPT>
@@ -437,6 +468,177 @@ template <class Real>
 cudaError_t alpha_prec(int eq, int variant, const Args1D& a, int ntiles, cudaStream_t s) {
   return eq == HWENO_BURGERS ? alpha_variants<HWENO_BURGERS, Real>(variant, a, ntiles, s)
                              : alpha_variants<HWENO_EULER, Real>(variant, a, ntiles, s);
+}
+
+
+// ---------------------------------------------------------------------------
+// Persistent run (PersistArgs): whole steps of a ragged batch in one launch.
+// ---------------------------------------------------------------------------
+
+// Bounded wait until *ctr >= target (acquire at device scope, so that the
+// loads after the CTA barrier see the other CTAs' stores). Gives up after
+// about two seconds, or as soon as another CTA has given up, and then sets
+// STATUS_TIMEOUT.
+__device__ __forceinline__ bool wait_count(unsigned* ctr, unsigned target, unsigned* status) {
+  cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(*ctr);
+  cuda::atomic_ref<unsigned, cuda::thread_scope_device> st(*status);
+  unsigned ns = 32;
+  for (int it = 0; it < (1 << 23); ++it) {
+    if (c.load(cuda::memory_order_acquire) >= target) return true;
+    if (st.load(cuda::memory_order_relaxed) & STATUS_TIMEOUT) return false;
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+  }
+  atomicOr(status, STATUS_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void release_add(unsigned* ctr, unsigned v) {
+  cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(*ctr);
+  c.fetch_add(v, cuda::memory_order_release);
+}
+
+// Tickets t = (step n, stage, tile b) in lexicographic order. A tile of
+// instance k in stage `stage` of step n needs all (3n + stage) * tiles(k)
+// earlier tiles of k to be complete; they hold smaller tickets, so the CTAs
+// that took them are resident: the waits always end. The last stage-3 tile of
+// k does the time update (as k_finalize), clears the alpha slots the step
+// after next accumulates into, and releases step n + 1 of k.
+template <int EQ, class Real, int NT, int PPT>
+__global__ void __launch_bounds__(NT, (MinBlocks1D<Real, NT>::value))
+k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p) {
+  __shared__ long long s_ticket;
+  __shared__ int s_stop;
+  const long long per_step = 3LL * p.ntiles;
+  const long long total = per_step * p.steps;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_ticket = (long long)atomicAdd(p.next, 1ULL);
+      cuda::atomic_ref<unsigned, cuda::thread_scope_device> st(*a.status);
+      s_stop = (st.load(cuda::memory_order_relaxed) & STATUS_TIMEOUT) != 0;
+    }
+    __syncthreads();  // also separates this tile's shared-memory use from the last one's
+    const long long tk = s_ticket;
+    if (tk >= total || s_stop) break;
+    const int n = (int)(tk / per_step);
+    const int r = (int)(tk - (long long)n * per_step);
+    const int stage = r / p.ntiles;
+    const int b = r - stage * p.ntiles;
+    const int k = a.tile_inst[b], s = a.tile_start[b];
+    const unsigned ntk = (unsigned)p.inst_tiles[k];
+    if (threadIdx.x == 0) wait_count(&p.done[k], (unsigned)(3 * n + stage) * ntk, a.status);
+    __syncthreads();
+    const int par = n & 1;
+    unsigned long long* slot0 = p.alpha + (size_t)(par * 3) * p.batch;  // this step's slots
+    StageIO io = io_of(a);
+    if (stage == 0) {
+      io.Uout = p.U1; io.Vout = p.V1; io.Vt0out = p.Vt0;
+      io.alpha_in = reinterpret_cast<const double*>(slot0);
+      io.alpha_out = slot0 + p.batch;
+      stage_tile<EQ, Real, MODE_STAGE1, NT, PPT>(a, io, k, s);
+    } else if (stage == 1) {
+      io.U = p.U1; io.V = p.V1; io.U0 = a.U; io.Vt0 = p.Vt0;
+      io.Uout = p.U2; io.Vout = p.V2; io.Vt0out = nullptr;
+      io.alpha_in = reinterpret_cast<const double*>(slot0 + p.batch);
+      io.alpha_out = slot0 + 2 * p.batch;
+      stage_tile<EQ, Real, MODE_STAGE2, NT, PPT>(a, io, k, s);
+    } else {
+      io.U = p.U2; io.V = p.V2; io.U0 = a.U; io.Vt0 = p.Vt0;
+      io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V); io.Vt0out = nullptr;
+      io.alpha_in = reinterpret_cast<const double*>(slot0 + 2 * p.batch);
+      io.alpha_out = p.alpha + (size_t)((par ^ 1) * 3) * p.batch;  // alpha(U^{n+1})
+      stage_tile<EQ, Real, MODE_STAGE3, NT, PPT>(a, io, k, s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (stage < 2) {
+        release_add(&p.done[k], 1u);
+      } else if (atomicAdd(&p.done3[k], 1u) + 1u == ntk) {
+        // time update of instance k (as k_finalize)
+        double tk_ = a.t[k];
+        if (tk_ < a.t_end) {
+          const double d = a.dt[k];
+          tk_ = a.lands[k] ? a.t_end : tk_ + d;
+          const_cast<double*>(a.t)[k] = tk_;
+          const double al = __longlong_as_double((long long)slot0[k]);
+          if (!(al <= DBL_MAX)) atomicOr(a.status, STATUS_NONFINITE);
+          if (p.pu) atomicAdd(p.pu, (unsigned long long)a.inst_n[k]);
+        }
+        if (n == p.steps - 1 && tk_ < a.t_end) atomicAdd(p.active, 1);
+        p.done3[k] = 0u;
+        slot0[k] = 0ull;                 // accumulated again by stage 3 of step n + 1
+        slot0[p.batch + k] = 0ull;       // and by stages 1, 2 of step n + 2
+        slot0[2 * p.batch + k] = 0ull;
+        __threadfence();
+        release_add(&p.done[k], ntk);
+      }
+    }
+  }
+}
+
+template <int EQ, class Real, int NT, int PPT>
+cudaError_t run_launch(const Args1D& a, const PersistArgs& p, int ctas, cudaStream_t s) {
+  constexpr size_t bytes = Layout1D<EQ, Real, NT, PPT>::bytes;
+  static bool configured = false;
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(k_run_1d<EQ, Real, NT, PPT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_run_1d<EQ, Real, NT, PPT><<<ctas, NT, bytes, s>>>(a, p);
+  return cudaGetLastError();
+}
+
+template <int EQ, class Real, int NT, int PPT>
+int run_occupancy() {
+  constexpr size_t bytes = Layout1D<EQ, Real, NT, PPT>::bytes;
+  if (cudaFuncSetAttribute(k_run_1d<EQ, Real, NT, PPT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_run_1d<EQ, Real, NT, PPT>, NT,
+                                                    bytes) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+template <int EQ, class Real>
+cudaError_t run_variants(int variant, const Args1D& a, const PersistArgs& p, int ctas,
+                         cudaStream_t s) {
+  switch (variant) {
+    case 1: return run_launch<EQ, Real, 64, 1>(a, p, ctas, s);
+    case 2: return run_launch<EQ, Real, 256, 1>(a, p, ctas, s);
+    case 3: return run_launch<EQ, Real, 128, 2>(a, p, ctas, s);
+    case 4: return run_launch<EQ, Real, 64, 2>(a, p, ctas, s);
+    default: return run_launch<EQ, Real, 128, 1>(a, p, ctas, s);
+  }
+}
+
+template <int EQ, class Real>
+int occupancy_variants(int variant) {
+  switch (variant) {
+    case 1: return run_occupancy<EQ, Real, 64, 1>();
+    case 2: return run_occupancy<EQ, Real, 256, 1>();
+    case 3: return run_occupancy<EQ, Real, 128, 2>();
+    case 4: return run_occupancy<EQ, Real, 64, 2>();
+    default: return run_occupancy<EQ, Real, 128, 1>();
+  }
+}
+
+template <class Real>
+cudaError_t run_prec(int eq, int variant, const Args1D& a, const PersistArgs& p, int ctas,
+                     cudaStream_t s) {
+  return eq == HWENO_BURGERS ? run_variants<HWENO_BURGERS, Real>(variant, a, p, ctas, s)
+                             : run_variants<HWENO_EULER, Real>(variant, a, p, ctas, s);
+}
+
+template <class Real>
+int occupancy_prec(int eq, int variant) {
+  return eq == HWENO_BURGERS ? occupancy_variants<HWENO_BURGERS, Real>(variant)
+                             : occupancy_variants<HWENO_EULER, Real>(variant);
 }
 
 }  // namespace

@@ -74,6 +74,8 @@ SIGNATURES = {
     "hweno_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_int), _DP, _VP]),
     "hweno_adjoint_step": (ctypes.c_int, [_VP] * 10),
+    "hweno_run_persistent": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                            _VP, _VP]),
     "hweno_sync_status": (ctypes.c_int, [_VP, _VP]),
     "hweno_num_points": (ctypes.c_longlong, [_VP]),
     "hweno_active_instances": (ctypes.c_int, [_VP, _VP]),
@@ -271,6 +273,15 @@ class Solver:
                                   int(max_steps), int(steps_per_launch), ctypes.byref(steps),
                                   ctypes.byref(pu), _stream()))
         return steps.value, pu.value
+
+    def run_persistent(self, U, V, t, t_end, steps, count=True):
+        """hweno_run_persistent: `steps` steps of a 1D batch in one persistent
+        launch; returns the point-updates (synchronising) when count is True."""
+        pu = ctypes.c_longlong(0)
+        self._check(lib.hweno_run_persistent(self.h, _ptr(U), _ptr(V), _ptr(t), float(t_end),
+                                             int(steps), ctypes.byref(pu) if count else None,
+                                             _stream()))
+        return pu.value if count else None
 
     def run(self, U, V, W=None, t=None, t_end=1.0, max_steps=1 << 30, check_every=64):
         """Steps until every instance reaches t_end; returns the steps taken."""
