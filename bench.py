@@ -62,6 +62,10 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # over points; profiles/k_stage_1d_euler_fp{64,32}_riemann_batch.md). An entry
 # is removed whenever the kernel changes after its capture.
 MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 100.5, "fp32": None}
+# DRAM bytes per point-step of the persistent kernel (all three stages), from
+# an ncu capture (profiles/k_run_1d_euler_fp64_riemann_batch.md); None until
+# taken for the kernel as it stands.
+MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.5, "fp32": None}
 
 
 def parse():
@@ -230,6 +234,20 @@ def run_ours(args, rank, world, dev_index):
                 dist.barrier()
             ms = e0.elapsed_time(e1)
             launches = s.launches_last_call
+            pers = None
+            if w.dim == 1:  # the same K steps as one persistent launch
+                p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.run_persistent(U, V, t, w.t_end, 1)  # first call: scratch, occupancy
+                if world > 1:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                s.profile_start(4)
+                p0.record()
+                ppu = s.run_persistent(U, V, t, w.t_end, K)  # synchronises after the kernel
+                p1.record()
+                torch.cuda.synchronize()
+                run_ms = s.profile_read()["stage"][0]  # the persistent kernel alone
+                pers = (p0.elapsed_time(p1), float(ppu), s.launches_last_call, run_ms)
             prof = ms_ng = pu_ng = None
             if profile:
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -248,12 +266,14 @@ def run_ours(args, rank, world, dev_index):
                 pu_ng = float(((hist > 0).double() * nx[None, :]).sum().item())
         s.close()
         timed.tune = tune
+        timed.pers = pers
         return ms, float(pu), prof, launches, ms_ng, pu_ng
 
     with ClockSampler(dev_index) as clk:
         ms, pu, prof, launches, ms_ng, pu_ng = timed(args.precision, args.steps, args.warmup, True)
     clocks = clk.summary()
     tune = timed.tune
+    pers = timed.pers
 
     # A working set that fits in L2 is timed step by step with an L2 flush
     # between steps (the plain pass); otherwise the graph replay is the
@@ -264,8 +284,20 @@ def run_ours(args, rank, world, dev_index):
     plain = {"value": round(pu_ng / (ms_ng * 1e-3) / 1e6, 3),
              "ms_per_step": round(ms_ng / args.steps, 4),
              "note": "same steps launched one by one, L2 flushed between steps"}
+    persistent = None
+    if pers is not None:
+        persistent = {"value": round(pers[1] / (pers[0] * 1e-3) / 1e6, 3),
+                      "ms_per_step": round(pers[0] / args.steps, 4),
+                      "note": "the next K steps as one persistent launch (hweno_run_persistent)"}
+    use_pers = (not small and pers is not None and pers[1] > 0 and
+                pers[1] / pers[0] > pu / ms)
+    timing_note = "K steps = one CUDA-graph replay (hweno_run), CUDA events"
     if small:
         ms, pu = ms_ng, pu_ng
+    elif use_pers:
+        ms, pu, launches = pers[0], pers[1], pers[2]
+        timing_note = ("K steps = one persistent launch (hweno_run_persistent) after one "
+                       "wave-speed launch, CUDA events")
     if world > 1:
         ms, pu = reduce_over_ranks(ms, pu, "cuda")
     value = pu / (ms * 1e-3) / 1e6
@@ -281,17 +313,26 @@ def run_ours(args, rank, world, dev_index):
     peak = PEAK_TFLOPS[args.precision]
     traffic = (MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
                if args.workload == "riemann_batch" else None)  # None: not yet re-captured
+    if use_pers:  # the headline kernel: K steps in one persistent launch
+        run_s = pers[3] * 1e-3
+        achieved = ALGO_FLOPS_PER_POINT_STEP[(w.equation, w.dim)] * pers[1] / run_s / 1e12
+        rtraffic = MEASURED_RUN_TRAFFIC_PER_POINT_STEP.get(args.precision)
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
-            "traffic": None if traffic is None else traffic * pts_per_stage,
-            "kernel": ("k_stage_1d<%s,%s>" % (w.equation, args.precision) if w.dim == 1 else
+            "traffic": (None if traffic is None else traffic * pts_per_stage) if not use_pers else
+                       (None if rtraffic is None else rtraffic * pers[1]),
+            "kernel": ("k_run_1d<%s,%s> (K = %d steps per launch)" % (w.equation, args.precision,
+                                                                     args.steps) if use_pers else
+                       "k_stage_1d<%s,%s>" % (w.equation, args.precision) if w.dim == 1 else
                        "k_xsweep_2d + k_ysweep_2d <%s,%s>" % (w.equation, args.precision)),
-            "kernel_share_of_step": round(stage_ms / sum(v[0] for v in prof.values()), 4),
+            "kernel_share_of_step": (round(pers[3] / pers[0], 4) if use_pers else
+                                     round(stage_ms / sum(v[0] for v in prof.values()), 4)),
             "flops_per_point_stage": round(flop_stage, 2),
             "peak_source": "nominal (recipe): FP64 1.25 TFLOP/s; FP32 = 152 SM x 128 x 2 x 2.07 GHz",
-            "hbm_achieved_gbs": round(ALGO_WORDS_PER_COMPONENT[w.dim] / 3.0 * w.m *
-                                      (8 if args.precision == "fp64" else 4) * pts_per_stage /
-                                      stage_time / 1e9, 1)}
+            "hbm_achieved_gbs": round(ALGO_WORDS_PER_COMPONENT[w.dim] * w.m *
+                                      (8 if args.precision == "fp64" else 4) *
+                                      (pers[1] / (pers[3] * 1e-3) if use_pers else
+                                       pts_per_stage / 3.0 / stage_time) / 1e9, 1)}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": "Mpoint-updates/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -300,6 +341,8 @@ def run_ours(args, rank, world, dev_index):
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
            ("graph" if small else "no_graph"): graph if small else plain,
+           **({"graph": graph, "persistent": persistent} if use_pers else
+              ({"persistent": persistent} if persistent else {})),
            "config": {"workload": describe(w),
                       "instances": w.batch, "points": w.points, "precision": args.precision,
                       "l2": ("flushed between timed steps (256 MiB write): the working set "
@@ -309,8 +352,7 @@ def run_ours(args, rank, world, dev_index):
                              "set (state + stage buffers, %.0f MB) exceeds the 129 MB L2"
                              % (working_set_mb(w, args.precision))),
                       "timing": ("each step bracketed by CUDA events, summed over K steps"
-                                 if small else
-                                 "K steps = one CUDA-graph replay (hweno_run), CUDA events"),
+                                 if small else timing_note),
                       "tile_variant": tune[0] if w.dim == 1 else None,
                       "autotune_stage1_ms": [round(x, 4) for x in tune[1]] if w.dim == 1 else None,
                       "parallelism": "replicas (one seeded batch per rank)"},
