@@ -46,6 +46,7 @@ METRIC = "Mpoint-updates/s per RK step"
 ALGO_FLOPS_PER_POINT_STEP = {
     ("euler", 1): 5068.4,
     ("burgers", 1): 1198.05,
+    ("buckley", 1): 1296.27,
     ("euler", 2): 15092.06,
     ("burgers", 2): 2484.84,
 }
@@ -77,7 +78,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--instances", type=int, default=2048)
     ap.add_argument("--workload", default="riemann_batch",
-                    help="riemann_batch (default) | burgers1d:N | euler2d_smooth:N | "
+                    help="riemann_batch (default) | burgers1d:N | buckley_batch:COUNT | "
+                         "euler2d_smooth:N | "
                          "double_mach:NXxNY | "
                          "burgers_adjoint:COUNTxN | euler2d_adjoint:N (discrete adjoint of the "
                          "step; own JSON line)")
@@ -165,6 +167,8 @@ def make_workload(name, rank, instances):
     kind, _, size = name.partition(":")
     if kind == "burgers1d":
         return W.burgers1d_sine(int(size or 400))
+    if kind == "buckley_batch":
+        return W.buckley_batch(count=int(size or instances), seed=rank_seed(rank) + 1)
     if kind == "euler2d_smooth":
         return W.euler2d_smooth(int(size or 2048), dt_mode="cfl")
     if kind == "double_mach":
@@ -174,6 +178,10 @@ def make_workload(name, rank, instances):
 
 
 def describe(w):
+    if w.name == "buckley_batch":
+        return ("buckley_batch: %d x Example 3.4 (Buckley-Leverett, u0 = 1 on [-1/2, 0]), "
+                "N in {200,400,800,1600,3200}, %d points, t_end 0.4, outflow"
+                % (w.batch, w.points))
     if w.name == "burgers1d_sine":
         return ("burgers1d: 1D Burgers periodic [0,2], N=%d, u0 = 0.5 + sin(pi x), "
                 "T = 1.5/pi" % w.nx[0])
@@ -550,9 +558,10 @@ def run_adjoint(args, rank, world, dev_index):
         fd = []
         rng = W.SplitMix64(1234 + rank)
         for _ in range(args.fd_directions):
-            if two:
-                comps = [W.fourier_2d(rng, n, n, 0.0, 2.0, 1e-2) for _ in range(4)]
-                d = [np.concatenate([c[i].ravel() for c in comps]) for i in range(3)]
+            if two:  # a perturbation of the initial density alone (and its derivatives)
+                f, fx, fy = W.fourier_2d(rng, n, n, 0.0, 2.0, 1e-2)
+                z = np.zeros(3 * npts)
+                d = [np.concatenate([g.ravel(), z]) for g in (f, fx, fy)]
             else:
                 x = W.centers(0.0, 2.0, n)
                 du = np.concatenate([1e-2 * np.sin(np.pi * x * (1 + int(rng.uniform(0, 4))) +

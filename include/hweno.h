@@ -106,7 +106,8 @@ typedef struct hweno_grid {
 
 /* Scheme options. hweno_default_options fills the paper's values (Sec. 3):
  * lin_w = lim_d = {0.98, 0.01, 0.01}, eps = 1e-6, cfl = 0.6,
- * dt_mode = 0, limiter = 1, eig_avg = 0, and tile_variant = 0. */
+ * dt_mode = 0, limiter = 1, eig_avg = 0, tile_variant = 0 and
+ * fused_small = 1. */
 typedef struct hweno_options {
   double lin_w[3]; /* gamma_0..2 of the reconstruction: > 0, sum 1 (Sec. 2.1) */
   double lim_d[3]; /* d_0..2 of the limiter: > 0, sum 1 (Sec. 2.2) */
@@ -122,7 +123,15 @@ typedef struct hweno_options {
                       1 arithmetic mean */
   int tile_variant; /* 1D tile shape 0..4 (see hweno_autotune; results do not
                        depend on it); ignored in 2D */
+  int fused_small;  /* 1D: 1 = when every instance has at most
+                       HWENO_FUSED_MAX_POINTS points, hweno_step runs the whole
+                       step (wave speed, three stages, time update) in one
+                       launch with one CTA per instance; 0 = always the tiled
+                       kernels. Results agree to rounding. */
 } hweno_options;
+
+/* Largest instance of the fused single-launch step (one 508-point tile). */
+#define HWENO_FUSED_MAX_POINTS 508
 
 typedef struct hweno_ctx hweno_ctx; /* opaque, library-owned */
 

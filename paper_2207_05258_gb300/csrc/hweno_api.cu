@@ -72,6 +72,7 @@ struct hweno_ctx {
   int* d_inst_tiles = nullptr;
   int persist_variant = -1;  // tile variant d_inst_tiles was built for
   int persist_ctas = 0;
+  int max_n = 0;  // largest instance (1D)
   // device copies for the host-buffer entry point
   void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
   double* d_ht = nullptr;
@@ -118,6 +119,7 @@ int check_options(const hweno_options* o, std::string& why) {
   if (o->dt_mode == 2 && !(o->dt_fixed > 0)) { why = "dt_fixed must be > 0"; return HWENO_EINVAL; }
   if (o->limiter < 0 || o->limiter > 2) { why = "limiter must be 0, 1 or 2"; return HWENO_EINVAL; }
   if (o->eig_avg < 0 || o->eig_avg > 1) { why = "eig_avg must be 0 or 1"; return HWENO_EINVAL; }
+  if (o->fused_small < 0 || o->fused_small > 1) { why = "fused_small must be 0 or 1"; return HWENO_EINVAL; }
   if (o->tile_variant < 0 || o->tile_variant >= kNumVariants1D) {
     why = "tile_variant out of range";
     return HWENO_EINVAL;
@@ -275,6 +277,26 @@ const double* slotd(hweno_ctx* c, int k) {
 int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_used,
             cudaStream_t s) {
   cudaError_t e;
+  if (c->opt.fused_small && c->max_n <= kFusedPoints) {  // one launch per step
+    if ((e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s))) return cuda_fail(c, e, "memset");
+    Args1D a = base_args_1d(c);
+    a.t = t;
+    a.t_end = t_end;
+    a.skip_done = 1;
+    a.dt = c->d_dt;
+    a.lands = c->d_lands;
+    a.U = U;
+    a.V = V;
+    FusedArgs f{};
+    f.U1 = c->d_U1; f.V1 = c->d_V1; f.U2 = c->d_U2; f.V2 = c->d_V2; f.Vt0 = c->d_Vt0;
+    f.alpha = c->d_alpha; f.dt_used = dt_used; f.active = c->d_active; f.pu = c->d_pu;
+    f.batch = c->batch;
+    prof_begin(c, s);
+    if ((e = launch_step_small_1d(c->eq, c->fp32, a, f, s))) return cuda_fail(c, e, "fused step");
+    prof_end(c, s, 1);
+    c->launches = c->step_launches = 1;
+    return HWENO_OK;
+  }
   if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)) ||
       (e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)))
     return cuda_fail(c, e, "memset");
@@ -465,6 +487,8 @@ int hweno_default_options(hweno_options* o) {
   o->dt_fixed = 0.0;
   o->limiter = 1;
   o->eig_avg = 0;
+  o->tile_variant = 0;
+  o->fused_small = 1;
   return HWENO_OK;
 }
 
@@ -507,6 +531,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
   for (int k = 0; k < c->batch; ++k) {
     c->nx[k] = grid->nx_per_instance ? grid->nx_per_instance[k] : grid->nx;
     if (c->nx[k] < 4) return bad("nx < 4");
+    c->max_n = std::max(c->max_n, c->nx[k]);
   }
   // boundary conditions
   const int sides[4] = {bc->xlo, bc->xhi, bc->ylo, bc->yhi};

@@ -262,6 +262,31 @@ struct PersistArgs {
   int steps, ntiles, batch;
 };
 
+// Fused step of small instances (stage1d_impl.cuh, k_step_small_1d): one CTA
+// per instance of at most kFusedPoints points runs the wave speed, the three
+// stages and the time update of one step. Stage buffers as in a plain step;
+// alpha slots [3][batch].
+constexpr int kFusedThreads = 128, kFusedPPT = 4;
+constexpr int kFusedPoints = kFusedThreads * kFusedPPT - 4;
+static_assert(kFusedPoints == HWENO_FUSED_MAX_POINTS, "fused tile");
+struct FusedArgs {
+  void* U1; void* V1; void* U2; void* V2; void* Vt0;
+  unsigned long long* alpha;  // 3 x batch
+  double* dt_used;            // nullable
+  int* active;
+  unsigned long long* pu;     // nullable
+  int batch;
+};
+cudaError_t launch_step_small_1d_f64(int eq, const Args1D& a, const FusedArgs& f, cudaStream_t s);
+cudaError_t launch_step_small_1d_f32(int eq, const Args1D& a, const FusedArgs& f, cudaStream_t s);
+cudaError_t launch_step_small_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f,
+                                    cudaStream_t s);
+inline cudaError_t launch_step_small_1d(int eq, bool fp32, const Args1D& a, const FusedArgs& f,
+                                        cudaStream_t s) {
+  if (eq == HWENO_BUCKLEY) return launch_step_small_1d_bl(fp32, a, f, s);
+  return fp32 ? launch_step_small_1d_f32(eq, a, f, s) : launch_step_small_1d_f64(eq, a, f, s);
+}
+
 cudaError_t launch_run_1d_f64(int eq, int variant, const Args1D& a, const PersistArgs& p,
                               int ctas, cudaStream_t s);
 cudaError_t launch_run_1d_f32(int eq, int variant, const Args1D& a, const PersistArgs& p,

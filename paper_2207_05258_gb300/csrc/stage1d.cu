@@ -58,6 +58,10 @@ cudaError_t launch_run_1d_f64(int eq, int variant, const Args1D& a, const Persis
 
 int run_1d_ctas_per_sm_f64(int eq, int variant) { return occupancy_prec<double>(eq, variant); }
 
+cudaError_t launch_step_small_1d_f64(int eq, const Args1D& a, const FusedArgs& f, cudaStream_t s) {
+  return step_small_prec<double>(eq, a, f, s);
+}
+
 cudaError_t launch_finalize(int batch, const double* dt, const int* lands, double* t,
                             double t_end, double* dt_used, const double* alpha, int* active,
                             unsigned* status, const int* inst_n, int rows,

@@ -24,6 +24,12 @@ cudaError_t launch_run_1d_bl(bool fp32, int variant, const Args1D& a, const Pers
               : run_variants<HWENO_BUCKLEY, double>(variant, a, p, ctas, s);
 }
 
+cudaError_t launch_step_small_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f,
+                                    cudaStream_t s) {
+  return fp32 ? step_small_launch<HWENO_BUCKLEY, float>(a, f, s)
+              : step_small_launch<HWENO_BUCKLEY, double>(a, f, s);
+}
+
 int run_1d_ctas_per_sm_bl(bool fp32, int variant) {
   return fp32 ? occupancy_variants<HWENO_BUCKLEY, float>(variant)
               : occupancy_variants<HWENO_BUCKLEY, double>(variant);

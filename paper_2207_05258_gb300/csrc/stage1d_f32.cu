@@ -22,4 +22,8 @@ cudaError_t launch_run_1d_f32(int eq, int variant, const Args1D& a, const Persis
 
 int run_1d_ctas_per_sm_f32(int eq, int variant) { return occupancy_prec<float>(eq, variant); }
 
+cudaError_t launch_step_small_1d_f32(int eq, const Args1D& a, const FusedArgs& f, cudaStream_t s) {
+  return step_small_prec<float>(eq, a, f, s);
+}
+
 }  // namespace hweno

@@ -641,5 +641,90 @@ int occupancy_prec(int eq, int variant) {
                              : occupancy_variants<HWENO_EULER, Real>(variant);
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused step of small instances (FusedArgs): one CTA per instance.
+// ---------------------------------------------------------------------------
+template <int EQ, class Real>
+__global__ void __launch_bounds__(kFusedThreads)
+k_step_small_1d(const __grid_constant__ Args1D a, const __grid_constant__ FusedArgs f) {
+  constexpr int M = Dim1<EQ>::M;
+  __shared__ Real red[kFusedThreads / 32];
+  const int k = blockIdx.x;
+  const int n = a.inst_n[k];
+  unsigned long long* s0 = f.alpha;
+  unsigned long long* s1 = f.alpha + f.batch;
+  unsigned long long* s2 = f.alpha + 2 * f.batch;
+  if (!(a.t[k] < a.t_end)) {  // finished: nothing moves (as k_finalize)
+    if (threadIdx.x == 0 && f.dt_used) f.dt_used[k] = 0.0;
+    return;
+  }
+  // alpha(U^n) over the instance; the stage slots start from zero
+  {
+    const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
+    const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+    const Real a01 = pick<Real>(a.sp.wd, a.sp.wf)[10];
+    Real amax = Real(0);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      Real u[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + j];
+      amax = fmax(amax, wave_speed<EQ>(u, gam, a01));
+    }
+    amax = block_max_t(amax, red);
+    if (threadIdx.x == 0) {
+      s0[k] = (unsigned long long)__double_as_longlong((double)amax);
+      s1[k] = 0ull;
+      s2[k] = 0ull;
+    }
+    __syncthreads();
+  }
+  StageIO io = io_of(a);
+  io.Uout = f.U1; io.Vout = f.V1; io.Vt0out = f.Vt0;
+  io.alpha_in = reinterpret_cast<const double*>(s0); io.alpha_out = s1;
+  stage_tile<EQ, Real, MODE_STAGE1, kFusedThreads, kFusedPPT>(a, io, k, 0);
+  __syncthreads();
+  io.U = f.U1; io.V = f.V1; io.U0 = a.U; io.Vt0 = f.Vt0; io.Uout = f.U2; io.Vout = f.V2;
+  io.Vt0out = nullptr;
+  io.alpha_in = reinterpret_cast<const double*>(s1); io.alpha_out = s2;
+  stage_tile<EQ, Real, MODE_STAGE2, kFusedThreads, kFusedPPT>(a, io, k, 0);
+  __syncthreads();
+  io.U = f.U2; io.V = f.V2; io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V);
+  io.alpha_in = reinterpret_cast<const double*>(s2); io.alpha_out = nullptr;
+  stage_tile<EQ, Real, MODE_STAGE3, kFusedThreads, kFusedPPT>(a, io, k, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) {  // time update (as k_finalize)
+    double tk = a.t[k];
+    const double d = a.dt[k];
+    tk = a.lands[k] ? a.t_end : tk + d;
+    const_cast<double*>(a.t)[k] = tk;
+    if (!(__longlong_as_double((long long)s0[k]) <= DBL_MAX)) atomicOr(a.status, STATUS_NONFINITE);
+    if (f.pu) atomicAdd(f.pu, (unsigned long long)n);
+    if (f.dt_used) f.dt_used[k] = d;
+    if (tk < a.t_end) atomicAdd(f.active, 1);
+  }
+}
+
+template <int EQ, class Real>
+cudaError_t step_small_launch(const Args1D& a, const FusedArgs& f, cudaStream_t s) {
+  constexpr size_t bytes = Layout1D<EQ, Real, kFusedThreads, kFusedPPT>::bytes;
+  static bool configured = false;
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(k_step_small_1d<EQ, Real>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_step_small_1d<EQ, Real><<<f.batch, kFusedThreads, bytes, s>>>(a, f);
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t step_small_prec(int eq, const Args1D& a, const FusedArgs& f, cudaStream_t s) {
+  return eq == HWENO_BURGERS ? step_small_launch<HWENO_BURGERS, Real>(a, f, s)
+                             : step_small_launch<HWENO_EULER, Real>(a, f, s);
+}
+
 }  // namespace
 }  // namespace hweno

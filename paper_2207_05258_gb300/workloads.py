@@ -375,3 +375,15 @@ def buckley_leverett(n: int = 80, t_end: float = 0.4) -> Workload:
     U = np.where((x >= -0.5) & (x <= 0.0), 1.0, 0.0)
     return Workload("buckley_leverett", "buckley", 1, [n], 1, -1.0, 1.0, 0.0, 1.0, t_end,
                     ("outflow", "outflow", "periodic", "periodic"), U.copy(), np.zeros(n))
+
+
+def buckley_batch(count: int = 2048, seed: int = 20220712, sizes=RIEMANN_SIZES,
+                  t_end: float = 0.4) -> Workload:
+    """Ragged batch of Example 3.4 problems (u0 = 1 on [-1/2, 0], else 0, on
+    [-1, 1], outflow): per instance N uniform over `sizes`."""
+    rng = SplitMix64(seed)
+    nx = [sizes[min(len(sizes) - 1, int(rng.uniform(0.0, len(sizes))))] for _ in range(count)]
+    Us = [buckley_leverett(n, t_end).U for n in nx]
+    return Workload("buckley_batch", "buckley", 1, nx, 1, -1.0, 1.0, 0.0, 1.0, t_end,
+                    ("outflow", "outflow", "periodic", "periodic"), np.concatenate(Us),
+                    np.zeros(sum(nx)))

@@ -19,6 +19,7 @@ from _util import oracle_problem
 @pytest.mark.parametrize("key,make", [
     (("euler", 1), lambda: W.euler1d_smooth(1000, dt_mode="cfl")),
     (("burgers", 1), lambda: W.burgers1d_sine(1000)),
+    (("buckley", 1), lambda: W.buckley_leverett(1000)),
     (("euler", 2), lambda: W.euler2d_smooth(64)),
     (("burgers", 2), lambda: W.burgers2d_sine(64)),
 ])

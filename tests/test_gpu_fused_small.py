@@ -1,0 +1,115 @@
+"""The fused small-instance step (one CTA per instance of at most
+HWENO_FUSED_MAX_POINTS points: wave speed, three stages and time update in
+one launch) against the tiled kernels (fused_small = 0) and the oracle. The
+stage code is shared; compiled into another kernel the compiler may fuse
+a*b + c*d differently, so the paths agree to rounding."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2207_05258_gb300 import workloads as W
+from _util import oracle_problem
+
+pytestmark = pytest.mark.gpu
+SIZES = [4, 5, 31, 123, 124, 125, 128, 248, 249, 400, 507, 508]
+
+
+@pytest.fixture(scope="module")
+def hw():
+    from paper_2207_05258_gb300 import build
+    build.build()
+    from paper_2207_05258_gb300 import hweno
+    return hweno
+
+
+def _batch(eq, sizes, seed):
+    rng = np.random.default_rng(seed)
+    Us, Vs = [], []
+    for k, n in enumerate(sizes):
+        x = W.centers(0, 1, n)
+        if eq == "euler":
+            lo = x < rng.uniform(0.3, 0.7)
+            rho = np.where(lo, 1.0, 0.125) + 0.1 * np.sin(2 * np.pi * x)
+            u = 0.1 * np.cos(2 * np.pi * x)
+            p = np.where(lo, 1.0, 0.1)
+            Us.append(W.euler_conserved(rho, u, p, 1.4).ravel())
+            Vs.append(np.zeros(3 * n))
+        elif eq == "burgers":
+            Us.append(0.3 + np.sin(2 * np.pi * x + rng.uniform(0, 6)))
+            Vs.append(2 * np.pi * np.cos(2 * np.pi * x))
+        else:
+            Us.append(np.clip(0.5 + 0.45 * np.sin(2 * np.pi * x + rng.uniform(0, 6)), 0, 1))
+            Vs.append(np.zeros(n))
+    bc = "outflow" if eq == "euler" else "periodic"
+    return W.Workload("fs", eq, 1, list(sizes), 1, 0.0, 1.0, 0.0, 1.0, 0.1,
+                      (bc, bc, "periodic", "periodic"), np.concatenate(Us), np.concatenate(Vs))
+
+
+def _steps(hw, w, K, t_end, precision="fp64", **opts):
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    s = hw.Solver.from_workload(w, precision=precision, **opts)
+    U = torch.from_numpy(w.U).to("cuda", dt)
+    V = torch.from_numpy(w.V).to("cuda", dt)
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    used = []
+    for _ in range(K):
+        d = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+        s.step(U, V, None, t, t_end, d)
+        used.append(d)
+    s.sync_status()
+    launches = s.launches_last_call
+    act = s.active_instances()
+    s.close()
+    return U, V, t, torch.stack(used), act, launches
+
+
+@pytest.mark.parametrize("eq", ["euler", "burgers", "buckley"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_matches_tiled(hw, eq, precision):
+    w = _batch(eq, SIZES, 3)
+    K, t_end = 8, 0.01
+    f = _steps(hw, w, K, t_end, precision)
+    g = _steps(hw, w, K, t_end, precision, fused_small=0)
+    assert f[5] == 1 and g[5] == 5          # one launch per step vs five
+    ru = 1e-13 * K if precision == "fp64" else 1e-5 * K
+    assert float((f[0] - g[0]).abs().max()) <= ru * float(g[0].abs().max())
+    assert float((f[2] - g[2]).abs().max()) <= (1e-14 if precision == "fp64" else 1e-6) * K * 0.01
+    assert torch.equal(f[3] > 0, g[3] > 0)  # the same instances step at the same steps
+    assert f[4] == g[4]
+
+
+def test_fused_against_the_oracle(hw):
+    w = _batch("euler", SIZES, 4)
+    U, V, t, used, act, _ = _steps(hw, w, 3, 1.0)
+    Ug = U.cpu().numpy()
+    off = 0
+    for k, n in enumerate(w.nx):
+        Uk, Vk = w.instance(k)
+        Uo, _, _, to, _ = O.run(oracle_problem(w, nx=n), Uk, Vk, None, 0.0, 1.0, max_steps=3)
+        g = Ug[3 * off:3 * (off + n)].reshape(3, n)
+        assert np.max(np.abs(g - Uo)) <= 1e-12 * np.max(np.abs(Uo)), (k, n)
+        assert abs(float(t[k]) - to) <= 1e-14 * to
+        off += n
+
+
+def test_larger_instances_use_the_tiled_kernels(hw):
+    w = _batch("burgers", [509, 40], 5)
+    *_, launches = _steps(hw, w, 1, 1.0)
+    assert launches == 5
+
+
+def test_config_1_to_final_time(hw):
+    """Example 3.1 / config 1 (Burgers N = 400, T = 1.5/pi, shock) through the
+    fused path against the oracle, shocked-run tolerance."""
+    import math
+    w = W.burgers1d_sine(400)
+    s = hw.Solver.from_workload(w)
+    U = torch.from_numpy(w.U).cuda()
+    V = torch.from_numpy(w.V).cuda()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.run(U, V, None, t, w.t_end)
+    Uo, Vo, _, to, _ = O.run(oracle_problem(w), w.U, w.V, None, 0.0, w.t_end)
+    assert float(t[0]) == to == w.t_end
+    assert np.max(np.abs(U.cpu().numpy() - Uo.ravel())) <= 1e-8 * np.max(np.abs(Uo))
+    assert s.launches_last_call >= 1
