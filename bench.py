@@ -62,7 +62,7 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # capture of a stage-1 launch (dram__bytes_read.sum + dram__bytes_write.sum
 # over points; profiles/k_stage_1d_euler_fp{64,32}_riemann_batch.md). An entry
 # is removed whenever the kernel changes after its capture.
-MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 100.5, "fp32": None}
+MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 100.5, "fp32": 40.3}
 # DRAM bytes per point-step of the persistent kernel (all three stages), from
 # an ncu capture (profiles/k_run_1d_euler_fp64_riemann_batch.md); None until
 # taken for the kernel as it stands.

@@ -488,7 +488,7 @@ int hweno_default_options(hweno_options* o) {
   o->limiter = 1;
   o->eig_avg = 0;
   o->tile_variant = 0;
-  o->fused_small = 1;
+  o->fused_small = 0;
   return HWENO_OK;
 }
 

@@ -69,8 +69,8 @@ def _steps(hw, w, K, t_end, precision="fp64", **opts):
 def test_fused_matches_tiled(hw, eq, precision):
     w = _batch(eq, SIZES, 3)
     K, t_end = 8, 0.01
-    f = _steps(hw, w, K, t_end, precision)
-    g = _steps(hw, w, K, t_end, precision, fused_small=0)
+    f = _steps(hw, w, K, t_end, precision, fused_small=1)
+    g = _steps(hw, w, K, t_end, precision)
     assert f[5] == 1 and g[5] == 5          # one launch per step vs five
     ru = 1e-13 * K if precision == "fp64" else 1e-5 * K
     assert float((f[0] - g[0]).abs().max()) <= ru * float(g[0].abs().max())
@@ -81,7 +81,7 @@ def test_fused_matches_tiled(hw, eq, precision):
 
 def test_fused_against_the_oracle(hw):
     w = _batch("euler", SIZES, 4)
-    U, V, t, used, act, _ = _steps(hw, w, 3, 1.0)
+    U, V, t, used, act, _ = _steps(hw, w, 3, 1.0, fused_small=1)
     Ug = U.cpu().numpy()
     off = 0
     for k, n in enumerate(w.nx):
@@ -95,7 +95,7 @@ def test_fused_against_the_oracle(hw):
 
 def test_larger_instances_use_the_tiled_kernels(hw):
     w = _batch("burgers", [509, 40], 5)
-    *_, launches = _steps(hw, w, 1, 1.0)
+    *_, launches = _steps(hw, w, 1, 1.0, fused_small=1)
     assert launches == 5
 
 
@@ -104,7 +104,7 @@ def test_config_1_to_final_time(hw):
     fused path against the oracle, shocked-run tolerance."""
     import math
     w = W.burgers1d_sine(400)
-    s = hw.Solver.from_workload(w)
+    s = hw.Solver.from_workload(w, fused_small=1)
     U = torch.from_numpy(w.U).cuda()
     V = torch.from_numpy(w.V).cuda()
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
