@@ -73,6 +73,12 @@ struct hweno_ctx {
   int persist_variant = -1;  // tile variant d_inst_tiles was built for
   int persist_ctas = 0;
   int max_n = 0;  // largest instance (1D)
+  // pipelined host-buffer steps (1D): streams, events and per-chunk counters
+  static constexpr int kChunks = 8;
+  cudaStream_t cs[kChunks] = {};
+  cudaEvent_t ce[kChunks] = {};
+  cudaEvent_t ce0 = nullptr;
+  int* d_chunk_active = nullptr;
   // device copies for the host-buffer entry point
   void* d_hU = nullptr; void* d_hV = nullptr; void* d_hW = nullptr;
   double* d_ht = nullptr;
@@ -148,9 +154,17 @@ void free_all(hweno_ctx* c) {
                   c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
                   c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht,
-                  c->d_adj, c->d_next, c->d_palpha, c->d_inst_tiles};
+                  c->d_adj, c->d_next, c->d_palpha, c->d_inst_tiles, c->d_chunk_active};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int i = 0; i < hweno_ctx::kChunks; ++i) {
+    if (c->cs[i]) cudaStreamDestroy(c->cs[i]);
+    if (c->ce[i]) cudaEventDestroy(c->ce[i]);
+    c->cs[i] = nullptr;
+    c->ce[i] = nullptr;
+  }
+  if (c->ce0) cudaEventDestroy(c->ce0);
+  c->ce0 = nullptr;
 }
 
 // Buckley-Leverett alpha over the admissible states (Example 3.4): with
@@ -272,6 +286,48 @@ void destroy_events(hweno_ctx* c) {
 unsigned long long* slot(hweno_ctx* c, int k) { return c->d_alpha + (size_t)k * c->batch; }
 const double* slotd(hweno_ctx* c, int k) {
   return reinterpret_cast<const double*>(c->d_alpha + (size_t)k * c->batch);
+}
+
+// One step of the instances [k0, k1) (tiles [t0, t1) of the current tile
+// table), counting the instances still active into *active. Instances
+// outside the range are not touched.
+int step_1d_range(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_used,
+                  cudaStream_t s, int k0, int k1, int t0, int t1, int* active) {
+  cudaError_t e;
+  const size_t nk = (size_t)(k1 - k0);
+  for (int j = 0; j < 3; ++j)
+    if ((e = cudaMemsetAsync(slot(c, j) + k0, 0, sizeof(unsigned long long) * nk, s)))
+      return cuda_fail(c, e, "memset");
+  Args1D a = base_args_1d(c);
+  a.tile_inst += t0;
+  a.tile_start += t0;
+  const int nt = t1 - t0;
+  a.t = t;
+  a.t_end = t_end;
+  a.skip_done = 1;
+  a.dt = c->d_dt;
+  a.lands = c->d_lands;
+  a.U = U;
+  a.alpha_out = slot(c, 0);
+  if ((e = launch_alpha_1d(c->eq, c->fp32, c->variant, a, nt, s))) return cuda_fail(c, e, "alpha");
+  a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
+  a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
+  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE1, a, nt, s)))
+    return cuda_fail(c, e, "stage 1");
+  a.U = c->d_U1; a.V = c->d_V1; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = c->d_U2; a.Vout = c->d_V2;
+  a.Vt0out = nullptr;
+  a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
+  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE2, a, nt, s)))
+    return cuda_fail(c, e, "stage 2");
+  a.U = c->d_U2; a.V = c->d_V2; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = U; a.Vout = V;
+  a.alpha_in = slotd(c, 2); a.alpha_out = nullptr;
+  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE3, a, nt, s)))
+    return cuda_fail(c, e, "stage 3");
+  if ((e = launch_finalize((int)nk, c->d_dt + k0, c->d_lands + k0, t + k0, t_end,
+                           dt_used ? dt_used + k0 : nullptr, slotd(c, 0) + k0, active,
+                           c->d_status, c->d_inst_n + k0, 1, c->d_pu, s)))
+    return cuda_fail(c, e, "finalize");
+  return HWENO_OK;
 }
 
 int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_used,
@@ -810,6 +866,83 @@ int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end
   return HWENO_OK;
 }
 
+namespace {
+
+// hweno_step_host for 1D: the batch is cut into up to kChunks ranges of
+// whole instances with about equal points; each range is copied in, stepped
+// and copied out on its own stream, so that copies of one range overlap the
+// kernels of the others. Ordered after the work on `s` and before what
+// follows on it.
+int step_host_1d_pipelined(hweno_ctx* c, void* U, void* V, double* t, double t_end, int nsteps,
+                           cudaStream_t s) {
+  cudaError_t e;
+  const int C = std::min(hweno_ctx::kChunks, c->batch);
+  if (!c->ce0) {
+    if ((e = cudaEventCreateWithFlags(&c->ce0, cudaEventDisableTiming)))
+      return cuda_fail(c, e, "event");
+    for (int i = 0; i < hweno_ctx::kChunks; ++i)
+      if ((e = cudaStreamCreateWithFlags(&c->cs[i], cudaStreamNonBlocking)) ||
+          (e = cudaEventCreateWithFlags(&c->ce[i], cudaEventDisableTiming)))
+        return cuda_fail(c, e, "stream");
+    int rc;
+    if ((rc = dalloc(c, &c->d_chunk_active, sizeof(int) * hweno_ctx::kChunks))) return rc;
+  }
+  // ranges of instances and of tiles
+  const int tp = tile_points(c->variant);
+  std::vector<long long> first_tile(c->batch + 1, 0), first_pt(c->batch + 1, 0);
+  for (int k = 0; k < c->batch; ++k) {
+    first_tile[k + 1] = first_tile[k] + (c->nx[k] + tp - 1) / tp;
+    first_pt[k + 1] = first_pt[k] + c->nx[k];
+  }
+  std::vector<int> cut(C + 1, 0);
+  cut[C] = c->batch;
+  for (int i = 1, k = 0; i < C; ++i) {
+    const long long goal = first_pt[c->batch] * i / C;
+    while (k < c->batch && first_pt[k] < goal) ++k;
+    cut[i] = std::max(k, cut[i - 1]);
+  }
+  if ((e = cudaEventRecord(c->ce0, s))) return cuda_fail(c, e, "event record");
+  const size_t es = (size_t)c->m * c->esize;
+  char* dU = static_cast<char*>(c->d_hU);
+  char* dV = static_cast<char*>(c->d_hV);
+  char* hU = static_cast<char*>(U);
+  char* hV = static_cast<char*>(V);
+  for (int i = 0; i < C; ++i) {
+    const int k0 = cut[i], k1 = cut[i + 1];
+    cudaStream_t cs = c->cs[i];
+    if ((e = cudaStreamWaitEvent(cs, c->ce0, 0))) return cuda_fail(c, e, "wait");
+    if (k1 > k0) {
+      const size_t o = es * (size_t)first_pt[k0], b = es * (size_t)(first_pt[k1] - first_pt[k0]);
+      const size_t tb = sizeof(double) * (k1 - k0);
+      if ((e = cudaMemcpyAsync(dU + o, hU + o, b, cudaMemcpyHostToDevice, cs)) ||
+          (e = cudaMemcpyAsync(dV + o, hV + o, b, cudaMemcpyHostToDevice, cs)) ||
+          (e = cudaMemcpyAsync(c->d_ht + k0, t + k0, tb, cudaMemcpyHostToDevice, cs)) ||
+          (e = cudaMemsetAsync(c->d_chunk_active + i, 0, sizeof(int), cs)))
+        return cuda_fail(c, e, "copy in");
+      for (int j = 0; j < nsteps; ++j) {
+        const int rc = step_1d_range(c, c->d_hU, c->d_hV, c->d_ht, t_end, nullptr, cs, k0, k1,
+                                     (int)first_tile[k0], (int)first_tile[k1],
+                                     c->d_chunk_active + i);
+        if (rc != HWENO_OK) return rc;
+      }
+      if ((e = cudaMemcpyAsync(hU + o, dU + o, b, cudaMemcpyDeviceToHost, cs)) ||
+          (e = cudaMemcpyAsync(hV + o, dV + o, b, cudaMemcpyDeviceToHost, cs)) ||
+          (e = cudaMemcpyAsync(t + k0, c->d_ht + k0, tb, cudaMemcpyDeviceToHost, cs)))
+        return cuda_fail(c, e, "copy out");
+    }
+    if ((e = cudaEventRecord(c->ce[i], cs)) || (e = cudaStreamWaitEvent(s, c->ce[i], 0)))
+      return cuda_fail(c, e, "event");
+  }
+  // instances still active, counted after all ranges (their finalize counters
+  // are per range and per step)
+  if ((e = launch_count_active(c->batch, c->d_ht, t_end, c->d_active, s)))
+    return cuda_fail(c, e, "count");
+  c->launches = 5 * nsteps * C + 1;
+  return HWENO_OK;
+}
+
+}  // namespace
+
 int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream) {
   if (!c) return HWENO_EINVAL;
@@ -817,6 +950,11 @@ int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t
   if (c->dim == 1 && W) return fail(c, HWENO_EINVAL, "W given in 1D");
   if (c->dim == 2 && !W) return fail(c, HWENO_EINVAL, "W required in 2D");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c->dim == 1 && !c->opt.fused_small && c->batch > 1) {
+    const int rc = step_host_1d_pipelined(c, U, V, t, t_end, nsteps, s);
+    if (rc != HWENO_OK) return rc;
+    return hweno_sync_status(c, stream);
+  }
   const size_t fb = c->elems * c->esize, tb = sizeof(double) * c->batch;
   cudaError_t e;
   if ((e = cudaMemcpyAsync(c->d_hU, U, fb, cudaMemcpyHostToDevice, s)) ||

@@ -329,6 +329,9 @@ inline cudaError_t launch_stage_1d(int eq, bool fp32, int variant, int mode, con
 // Time update after stage 3; counts the instances still active and, when
 // pu is not null, adds inst_n[k] * rows (the instance's points; rows = ny in
 // 2D, 1 in 1D) of every instance that took the step.
+// Number of instances with t < t_end (one CTA; written, not added).
+cudaError_t launch_count_active(int batch, const double* t, double t_end, int* active,
+                                cudaStream_t s);
 cudaError_t launch_finalize(int batch, const double* dt, const int* lands, double* t,
                             double t_end, double* dt_used, const double* alpha,
                             int* active_count, unsigned* status, const int* inst_n, int rows,

@@ -40,7 +40,24 @@ __global__ void k_finalize(int batch, const double* dt, const int* lands, double
   if (tk < t_end) atomicAdd(active, 1);
 }
 
+__global__ void k_count_active(int batch, const double* t, double t_end, int* active) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int k = threadIdx.x; k < batch; k += blockDim.x) mine += t[k] < t_end;
+  atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) *active = cnt;
+}
+
 }  // namespace
+
+cudaError_t launch_count_active(int batch, const double* t, double t_end, int* active,
+                                cudaStream_t s) {
+  k_count_active<<<1, 256, 0, s>>>(batch, t, t_end, active);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_alpha_1d_f64(int eq, int variant, const Args1D& a, int ntiles, cudaStream_t s) {
   return alpha_prec<double>(eq, variant, a, ntiles, s);

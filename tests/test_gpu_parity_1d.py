@@ -294,6 +294,30 @@ def test_host_entry_point_matches_device_path(hw):
     s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pipelined_host_steps_match_device_steps(hw, precision):
+    """hweno_step_host cuts a batch into chunks of instances, each copied,
+    stepped and copied back on its own stream: the result is bit for bit the
+    device path's, instances finishing during the steps included."""
+    w = W.riemann_batch(count=300, seed=77, sizes=(4, 31, 124, 125, 200, 400, 1600))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    s = hw.Solver.from_workload(w, precision=precision, tile_variant=3)
+    Ud, Vd = dev(w.U, dt), dev(w.V, dt)
+    td = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    for _ in range(6):
+        s.step(Ud, Vd, None, td, 0.004)
+    s.sync_status()
+    act_dev = s.active_instances()
+    U = torch.from_numpy(w.U).to(dt).pin_memory()
+    V = torch.from_numpy(w.V).to(dt).pin_memory()
+    t = torch.zeros(w.batch, dtype=torch.float64).pin_memory()
+    s.step_host(U, V, None, t, 0.004, nsteps=4)
+    s.step_host(U, V, None, t, 0.004, nsteps=2)
+    assert torch.equal(U, Ud.cpu()) and torch.equal(V, Vd.cpu()) and torch.equal(t, td.cpu())
+    assert s.active_instances() == act_dev and 0 < act_dev < w.batch
+    s.close()
+
+
 def test_fp32_error_against_fp64_oracle(hw, record_property):
     """FP32 state and reconstruction: error against the FP64 oracle, stated
     (relative L-inf of U; first measured 2.4e-5 on this case). The bound is
