@@ -24,10 +24,11 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy stream); all
  *    work is enqueued on it and the calls return without synchronising,
  *    except hweno_sync_status and hweno_step_host.
- *  - The library allocates all of its scratch (stage buffers, the stored
+ *  - The library allocates the scratch of a step (stage buffers, the stored
  *    limited derivative, per-instance wave speeds and time steps, a status
- *    word) in hweno_create and frees it in hweno_destroy; no other call
- *    allocates device memory.
+ *    word) in hweno_create and frees everything in hweno_destroy. Only
+ *    hweno_adjoint_step, hweno_run_persistent and the pipelined
+ *    hweno_step_host allocate more, once, on their first call.
  *  - Every call returns an int status: HWENO_OK (0) or a negative code; a
  *    readable message is kept in the context (hweno_last_error). Errors the
  *    device detects (a non-finite wave speed) are latched into the context's
@@ -195,7 +196,13 @@ int hweno_run(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end
 
 /* As hweno_step with HOST arrays: copies U, V (, W) and t (host, [batch]) to
  * library-owned device buffers, takes `nsteps` steps, copies them back and
- * synchronises the stream. Pinned host memory makes the copies asynchronous. */
+ * synchronises the stream. Pinned host memory makes the copies asynchronous.
+ * A 1D batch (fused_small = 0) is cut into up to eight ranges of whole
+ * instances with about equal points, each copied in, stepped and copied out
+ * on a library stream of its own, so that the copies of one range overlap
+ * the kernels of the others; the results are those of hweno_step bit for bit
+ * and hweno_active_instances counts after the call. The first such call
+ * creates the streams and events. */
 int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream);
 
