@@ -224,6 +224,15 @@ int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double
 int hweno_run_persistent(hweno_ctx* ctx, void* U, void* V, double* t, double t_end, int steps,
                          long long* point_updates, void* stream);
 
+/* Test hook for failure detection (no counterpart in the paper). kind = 1:
+ * the next hweno_run_persistent expects one tile too many for instance 0, so
+ * the waits for that instance cannot be satisfied; they give up after about
+ * two seconds, every CTA then stops, and the call returns HWENO_ETIMEOUT
+ * (latched status). The context stays usable: the following calls rebuild
+ * the tile counts. kind = 0 clears a pending injection. Nothing faults or
+ * hangs the device. */
+int hweno_test_inject(hweno_ctx* ctx, int kind);
+
 /* Tile-shape autotuner (1D): times the fused stage kernel of every tile
  * variant (CTA sizes 64, 128, 256 threads, one or two points per thread) on
  * the given state U, V at times t (device) with t_end, and keeps the fastest

@@ -73,6 +73,7 @@ struct hweno_ctx {
   int persist_variant = -1;  // tile variant d_inst_tiles was built for
   int persist_ctas = 0;
   int max_n = 0;  // largest instance (1D)
+  int inject = 0;  // hweno_test_inject: 1 = the next persistent run waits in vain
   // pipelined host-buffer steps (1D): streams, events and per-chunk counters
   static constexpr int kChunks = 8;
   cudaStream_t cs[kChunks] = {};
@@ -810,10 +811,11 @@ int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end
     c->d_done = reinterpret_cast<unsigned*>(c->d_next + 1);
     c->d_done3 = c->d_done + B;
   }
-  if (c->persist_variant != c->variant) {
+  if (c->persist_variant != c->variant || c->inject == 1) {
     const int tp = tile_points(c->variant);
     std::vector<int> nt(B);
     for (size_t k = 0; k < B; ++k) nt[k] = (c->nx[k] + tp - 1) / tp;
+    if (c->inject == 1) nt[0] += 1;  // instance 0 then waits for a tile that does not exist
     if ((e = cudaMemcpy(c->d_inst_tiles, nt.data(), sizeof(int) * B, cudaMemcpyHostToDevice)))
       return cuda_fail(c, e, "copy tile counts");
     int dev = 0, sms = 0;
@@ -823,7 +825,8 @@ int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end
     const int per_sm = run_1d_ctas_per_sm(c->eq, c->fp32, c->variant);
     if (per_sm < 1) return fail(c, HWENO_ECUDA, "persistent kernel does not fit on an SM");
     c->persist_ctas = sms * per_sm;
-    c->persist_variant = c->variant;
+    c->persist_variant = c->inject == 1 ? -1 : c->variant;  // a corrupted table is rebuilt next time
+    c->inject = 0;
   }
   if ((e = cudaMemsetAsync(c->d_next, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned) * B, s)) ||
       (e = cudaMemsetAsync(c->d_palpha, 0, sizeof(unsigned long long) * 6 * B, s)) ||
@@ -942,6 +945,13 @@ int step_host_1d_pipelined(hweno_ctx* c, void* U, void* V, double* t, double t_e
 }
 
 }  // namespace
+
+int hweno_test_inject(hweno_ctx* c, int kind) {
+  if (!c) return HWENO_EINVAL;
+  if (kind != 0 && kind != 1) return fail(c, HWENO_EINVAL, "unknown injection");
+  c->inject = kind;
+  return HWENO_OK;
+}
 
 int hweno_step_host(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream) {

@@ -75,6 +75,7 @@ SIGNATURES = {
     "hweno_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_int), _DP, _VP]),
     "hweno_adjoint_step": (ctypes.c_int, [_VP] * 10),
+    "hweno_test_inject": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hweno_run_persistent": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                             _VP, _VP]),
     "hweno_sync_status": (ctypes.c_int, [_VP, _VP]),
@@ -274,6 +275,10 @@ class Solver:
                                   int(max_steps), int(steps_per_launch), ctypes.byref(steps),
                                   ctypes.byref(pu), _stream()))
         return steps.value, pu.value
+
+    def test_inject(self, kind: int):
+        """hweno_test_inject (failure-detection tests)."""
+        self._check(lib.hweno_test_inject(self.h, int(kind)))
 
     def run_persistent(self, U, V, t, t_end, steps, count=True):
         """hweno_run_persistent: `steps` steps of a 1D batch in one persistent

@@ -125,3 +125,29 @@ def test_against_the_oracle(hw):
         assert np.max(np.abs(g - Uo)) <= 1e-12 * np.max(np.abs(Uo)), k
         assert abs(tg[k] - to) <= 1e-14 * to
         off += n
+
+
+def test_a_wait_that_cannot_end_times_out_and_the_context_survives(hw):
+    """Failure detection without a fault: the injected tile count makes
+    instance 0's waits unsatisfiable; the bounded waits give up (about two
+    seconds), the call reports ETIMEOUT, and afterwards plain and persistent
+    steps of the same context work and agree with a fresh context."""
+    import time
+    w = _batch("euler", 12)
+    s = hw.Solver.from_workload(w)
+    U = torch.from_numpy(w.U).cuda()
+    V = torch.from_numpy(w.V).cuda()
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    s.test_inject(1)
+    t0 = time.perf_counter()
+    with pytest.raises(hw.HwenoError) as err:
+        s.run_persistent(U.clone(), V.clone(), t.clone(), 1.0, 2)
+    assert err.value.code == hw.ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    # the context is usable again
+    U1, V1, t1 = U.clone(), V.clone(), t.clone()
+    s.run_persistent(U1, V1, t1, 1.0, 2)
+    r = hw.Solver.from_workload(w)
+    U2, V2, t2 = U.clone(), V.clone(), t.clone()
+    r.run_persistent(U2, V2, t2, 1.0, 2)
+    assert torch.equal(U1, U2) and torch.equal(t1, t2)
