@@ -59,7 +59,7 @@ class Problem(ctypes.Structure):
         ("eps", ctypes.c_double), ("cfl", ctypes.c_double),
         ("dt_mode", ctypes.c_int), ("dt_fixed", ctypes.c_double),
         ("limiter", ctypes.c_int), ("eig_avg", ctypes.c_int),
-        ("alpha_fixed", ctypes.c_double),
+        ("alpha_fixed", ctypes.c_double), ("freeze_weights", ctypes.c_int),
     ]
 
 
@@ -78,6 +78,11 @@ def _load():
             L.or_hweno_face.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, _D,
                                         ctypes.c_double, _D]
             L.or_limiter.argtypes = [ctypes.c_double] * 6 + [_D, ctypes.c_double, _D]
+            L.or_hweno_face_tangent.argtypes = [ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
+                                                _D, ctypes.c_double, ctypes.c_int, _D]
+            L.or_limiter_tangent.argtypes = [ctypes.c_double] * 5 + [_D, ctypes.c_double, _D,
+                                                                      ctypes.c_double, ctypes.c_int]
+            L.or_limiter_tangent.restype = ctypes.c_double
             L.or_flux.argtypes = [_P, ctypes.c_int, _D, _D]
             L.or_jvp.argtypes = [_P, ctypes.c_int, _D, _D, _D]
             L.or_bl_alpha01.argtypes = []
@@ -118,7 +123,8 @@ def problem(eq, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gas_gamma=1.4,
             bc=(BC_PERIODIC,) * 4, inflow=(0, 0, 0, 0), pre=(0, 0, 0, 0),
             dmr_x0=1.0 / 6.0, dmr_speed=10.0, dmr_angle=np.pi / 3.0,
             lin_w=(0.98, 0.01, 0.01), lim_d=(0.98, 0.01, 0.01), eps=1e-6, cfl=0.6,
-            dt_mode=0, dt_fixed=0.0, limiter=1, eig_avg=0, alpha_fixed=0.0) -> Problem:
+            dt_mode=0, dt_fixed=0.0, limiter=1, eig_avg=0, alpha_fixed=0.0,
+            freeze_weights=0) -> Problem:
     p = Problem()
     p.eq, p.dim, p.nx, p.ny = eq, dim, nx, (ny if dim == 2 else 1)
     p.x0, p.x1, p.y0, p.y1 = x0, x1, y0, y1
@@ -132,6 +138,7 @@ def problem(eq, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gas_gamma=1.4,
     p.eps, p.cfl, p.dt_mode, p.dt_fixed = eps, cfl, dt_mode, dt_fixed
     p.limiter, p.eig_avg = limiter, eig_avg
     p.alpha_fixed = alpha_fixed
+    p.freeze_weights = int(freeze_weights)
     return p
 
 
@@ -259,3 +266,20 @@ def flops_per_point_step(p, U, V, W=None) -> float:
 def bl_alpha01():
     """max |f'(u)| over u in [0, 1] of the Buckley-Leverett flux (reading R15)."""
     return _load().or_bl_alpha01()
+
+
+def hweno_face_tangent(side, f, h, df, dh, dx, lin_w=(0.98, 0.01, 0.01), eps=1e-6, frozen=False):
+    """(d f-hat, d h-hat) of one face along (df, dh) (forward mode), with the
+    nonlinear weights frozen or differentiated."""
+    out = np.zeros(2)
+    _load().or_hweno_face_tangent(side, _ptr(_arr(f, 3)), _ptr(_arr(h, 3)), _ptr(_arr(df, 3)),
+                                  _ptr(_arr(dh, 3)), dx, _ptr(_arr(lin_w, 3)), eps, int(frozen),
+                                  _ptr(out))
+    return out
+
+
+def limiter_tangent(um, u0, up, vm, vp, direction, dx, lim_d=(0.98, 0.01, 0.01), eps=1e-6,
+                    frozen=False):
+    """d v-tilde of the limiter along `direction` (5 values)."""
+    return _load().or_limiter_tangent(um, u0, up, vm, vp, _ptr(_arr(direction, 5)), dx,
+                                      _ptr(_arr(lim_d, 3)), eps, int(frozen))

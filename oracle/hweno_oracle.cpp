@@ -141,6 +141,7 @@ struct or_problem {
   int limiter;      // 0 off, 1 characteristic, 2 component-wise
   int eig_avg;      // 0 Roe average, 1 arithmetic mean
   double alpha_fixed;  // > 0: use this alpha in every stage and direction
+  int freeze_weights;  // tangent runs: nonlinear weights held constant
 };
 }
 
@@ -200,9 +201,11 @@ R p0_prime(const R f[3], const R h[3], double dx) {
   return (f[0] - 8.0 * f[1] + 7.0 * f[2]) / (4.0 * dx) + (h[0] - 2.0 * h[1] - 5.0 * h[2]) / 12.0;
 }
 
+// freeze_w: the nonlinear weights enter as constants (their tangent is
+// dropped), for the frozen-weights derivative of the scheme.
 template <class R>
 Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
-                   double eps) {
+                   double eps, bool freeze_w = false) {
   Face<R> o;
   const R fm = f[0], f0 = f[1], fp = f[2];
   const R hm = h[0], h0 = h[1], hp = h[2];
@@ -239,6 +242,8 @@ Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
   for (int l = 0; l < 3; ++l) wbar[l] = g[l] * (1.0 + o.tau / (o.beta[l] + eps));
   const R wsum = wbar[0] + wbar[1] + wbar[2];
   for (int l = 0; l < 3; ++l) o.omega[l] = wbar[l] / wsum;
+  if (freeze_w)
+    for (int l = 0; l < 3; ++l) freeze(o.omega[l]);
 
   // Final combination and the linear derivative flux.
   o.fhat = o.omega[0] * (o.p[0] / g[0] - (g[1] / g[0]) * o.p[1] - (g[2] / g[0]) * o.p[2]) +
@@ -254,10 +259,10 @@ Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
 // derivative flux reflects back with a sign change.
 template <class R>
 Face<R> hweno_minus(const R f[3], const R h[3], double dx, const double g[3],
-                    double eps) {
+                    double eps, bool freeze_w = false) {
   const R fr[3] = {f[2], f[1], f[0]};
   const R hr[3] = {-h[2], -h[1], -h[0]};
-  Face<R> o = hweno_plus(fr, hr, dx, g, eps);
+  Face<R> o = hweno_plus(fr, hr, dx, g, eps, freeze_w);
   o.hhat = -o.hhat;
   o.dp0 = -o.dp0;
   return o;
@@ -276,7 +281,7 @@ struct Lim {
 
 template <class R>
 Lim<R> hweno_limiter(R um, R u0, R up, R vm, R vp, double dx, const double d[3],
-                     double eps) {
+                     double eps, bool freeze_w = false) {
   Lim<R> o;
   o.dq[0] = (3.0 / (4.0 * dx)) * (up - um) - (1.0 / 4.0) * (vm + vp);
   o.dq[1] = (u0 - um) / dx;
@@ -296,6 +301,8 @@ Lim<R> hweno_limiter(R um, R u0, R up, R vm, R vp, double dx, const double d[3],
   for (int l = 0; l < 3; ++l) lbar[l] = d[l] * (1.0 + o.tau / (o.beta[l] + eps));
   const R lsum = lbar[0] + lbar[1] + lbar[2];
   for (int l = 0; l < 3; ++l) o.lambda[l] = lbar[l] / lsum;
+  if (freeze_w)
+    for (int l = 0; l < 3; ++l) freeze(o.lambda[l]);
 
   o.vt = o.lambda[0] * (o.dq[0] / d[0] - (d[1] / d[0]) * o.dq[1] - (d[2] / d[0]) * o.dq[2]) +
          o.lambda[1] * o.dq[1] + o.lambda[2] * o.dq[2];
@@ -512,8 +519,8 @@ void sweep_line(const or_problem& P, int dir, int n, double dx, R alpha,
       const R h3p[3] = {hp[0][gi - 1], hp[0][gi], hp[0][gi + 1]};
       const R f3m[3] = {fmn[0][gi], fmn[0][gi + 1], fmn[0][gi + 2]};
       const R h3m[3] = {hmn[0][gi], hmn[0][gi + 1], hmn[0][gi + 2]};
-      const Face<R> a = hweno_plus(f3p, h3p, dx, gw, P.eps);
-      const Face<R> b = hweno_minus(f3m, h3m, dx, gw, P.eps);
+      const Face<R> a = hweno_plus(f3p, h3p, dx, gw, P.eps, P.freeze_weights != 0);
+      const Face<R> b = hweno_minus(f3m, h3m, dx, gw, P.eps, P.freeze_weights != 0);
       fh[0] = a.fhat + b.fhat;
       hh[0] = a.hhat + b.hhat;
     } else {
@@ -541,8 +548,8 @@ void sweep_line(const or_problem& P, int dir, int n, double dx, R alpha,
         const R h3p[3] = {whp[0][s], whp[1][s], whp[2][s]};
         const R f3m[3] = {wfm[0][s], wfm[1][s], wfm[2][s]};
         const R h3m[3] = {whm[0][s], whm[1][s], whm[2][s]};
-        const Face<R> a = hweno_plus(f3p, h3p, dx, gw, P.eps);
-        const Face<R> b = hweno_minus(f3m, h3m, dx, gw, P.eps);
+        const Face<R> a = hweno_plus(f3p, h3p, dx, gw, P.eps, P.freeze_weights != 0);
+        const Face<R> b = hweno_minus(f3m, h3m, dx, gw, P.eps, P.freeze_weights != 0);
         fchar[s] = a.fhat + b.fhat;
       }
       matvec(m, Rm, fchar, fh);
@@ -583,7 +590,7 @@ void limit_line(const or_problem& P, int dir, int n, double dx,
     if (m == 1 || P.limiter == 2) {
       for (int c = 0; c < m; ++c)
         Dt[c][i] = hweno_limiter(Ug[c][g - 1], Ug[c][g], Ug[c][g + 1], Dg[c][g - 1],
-                                 Dg[c][g + 1], dx, P.lim_d, P.eps).vt;
+                                 Dg[c][g + 1], dx, P.lim_d, P.eps, P.freeze_weights != 0).vt;
       continue;
     }
     R U0[4];
@@ -600,7 +607,8 @@ void limit_line(const or_problem& P, int dir, int n, double dx,
     matvec(m, Lm, xm, wm); matvec(m, Lm, x0, w0); matvec(m, Lm, xp, wp);
     matvec(m, Lm, dm, zm); matvec(m, Lm, dp, zp);
     for (int s = 0; s < m; ++s)
-      zt[s] = hweno_limiter(wm[s], w0[s], wp[s], zm[s], zp[s], dx, P.lim_d, P.eps).vt;
+      zt[s] = hweno_limiter(wm[s], w0[s], wp[s], zm[s], zp[s], dx, P.lim_d, P.eps,
+                            P.freeze_weights != 0).vt;
     matvec(m, Rm, zt, out);
     for (int c = 0; c < m; ++c) Dt[c][i] = out[c];
   }
@@ -952,6 +960,28 @@ void or_hweno_face(int side, const double* f, const double* h, double dx,
   const double v[13] = {o.fhat, o.hhat, o.p[0], o.p[1], o.p[2], o.dp0, o.beta[0],
                         o.beta[1], o.beta[2], o.tau, o.omega[0], o.omega[1], o.omega[2]};
   std::memcpy(out, v, sizeof v);
+}
+
+// Tangent of one face (Dual): out = (d fhat, d hhat) along (df, dh), with
+// the nonlinear weights frozen or not.
+void or_hweno_face_tangent(int side, const double* f, const double* h, const double* df,
+                           const double* dh, double dx, const double* g, double eps, int frozen,
+                           double* out) {
+  Dual fd[3], hd[3];
+  for (int k = 0; k < 3; ++k) { fd[k] = Dual(f[k], df[k]); hd[k] = Dual(h[k], dh[k]); }
+  const Face<Dual> o = side == 0 ? hweno_plus(fd, hd, dx, g, eps, frozen != 0)
+                                 : hweno_minus(fd, hd, dx, g, eps, frozen != 0);
+  out[0] = o.fhat.d;
+  out[1] = o.hhat.d;
+}
+
+// Tangent of the limiter (Dual): d vt along (dum, du0, dup, dvm, dvp).
+double or_limiter_tangent(double um, double u0, double up, double vm, double vp,
+                          const double* dir, double dx, const double* d, double eps,
+                          int frozen) {
+  const Lim<Dual> o = hweno_limiter(Dual(um, dir[0]), Dual(u0, dir[1]), Dual(up, dir[2]),
+                                    Dual(vm, dir[3]), Dual(vp, dir[4]), dx, d, eps, frozen != 0);
+  return o.vt.d;
 }
 
 // out: vt, dq0..2, beta0..2, tau, lambda0..2 (11 values)

@@ -57,3 +57,66 @@ def test_tangent_is_linear_in_the_seed():
     tc = O.run_tangent(P, U, V, None, 2 * a[0] - b[0], 2 * a[1] - b[1], None, 0.0, 0.2)
     assert np.allclose(tc[3], 2 * ta[3] - tb[3], rtol=1e-12, atol=1e-12)
     assert np.allclose(tc[4], 2 * ta[4] - tb[4], rtol=1e-12, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Frozen-weights derivative (the option of the adjoint that holds the
+# nonlinear weights at their forward values)
+# ---------------------------------------------------------------------------
+def _face_closed_form(side, f, h, df, dh, dx, g, eps):
+    """d f-hat with the weights held: sum_l omega_l d(candidate_l), the
+    candidates being linear in the data (their values come from or_hweno_face
+    at the perturbation itself, since p_l(d) = d p_l)."""
+    o = O.hweno_face(side, f, h, dx, g, eps)
+    z = O.hweno_face(side, df, dh, dx, g, eps)  # p_0, p_1, p_2 of the direction
+    w = (o["omega0"], o["omega1"], o["omega2"])
+    p = (z["p0"], z["p1"], z["p2"])
+    return w[0] * (p[0] / g[0] - g[1] / g[0] * p[1] - g[2] / g[0] * p[2]) + w[1] * p[1] + w[2] * p[2]
+
+
+def test_face_tangent_frozen_weights_is_the_weighted_candidate_derivative():
+    rng = np.random.default_rng(3)
+    g = (0.98, 0.01, 0.01)
+    for side in (0, 1):
+        for _ in range(20):
+            f, h = rng.standard_normal(3), rng.standard_normal(3)
+            df, dh = rng.standard_normal(3), rng.standard_normal(3)
+            dx = rng.uniform(0.01, 0.5)
+            got = O.hweno_face_tangent(side, f, h, df, dh, dx, g, 1e-6, frozen=True)[0]
+            want = _face_closed_form(side, f, h, df, dh, dx, g, 1e-6)
+            assert abs(got - want) <= 1e-12 * (1 + abs(want)), (side, got, want)
+
+
+def test_face_tangent_unfrozen_against_central_differences():
+    rng = np.random.default_rng(4)
+    g = (0.98, 0.01, 0.01)
+    for side in (0, 1):
+        for _ in range(10):
+            f, h = rng.standard_normal(3), rng.standard_normal(3)
+            df, dh = rng.standard_normal(3), rng.standard_normal(3)
+            got = O.hweno_face_tangent(side, f, h, df, dh, 0.1, g, 1e-6)[0]
+            e = 1e-6
+            fd = (O.hweno_face(side, f + e * df, h + e * dh, 0.1, g, 1e-6)["fhat"] -
+                  O.hweno_face(side, f - e * df, h - e * dh, 0.1, g, 1e-6)["fhat"]) / (2 * e)
+            assert abs(got - fd) <= 1e-6 * (1 + abs(fd)), (got, fd)
+
+
+def test_limiter_tangent_frozen_and_unfrozen():
+    rng = np.random.default_rng(5)
+    d = (0.98, 0.01, 0.01)
+    for _ in range(20):
+        x = rng.standard_normal(5)
+        dirn = rng.standard_normal(5)
+        dx = 0.1
+        o = O.limiter(*x, dx, d, 1e-6)
+        z = O.limiter(*dirn, dx, d, 1e-6)  # dq_l of the direction (linear)
+        lam, dq = (o["lambda0"], o["lambda1"], o["lambda2"]), (z["dq0"], z["dq1"], z["dq2"])
+        want = lam[0] * (dq[0] / d[0] - d[1] / d[0] * dq[1] - d[2] / d[0] * dq[2]) + \
+            lam[1] * dq[1] + lam[2] * dq[2]
+        got = O.limiter_tangent(*x, dirn, dx, d, 1e-6, frozen=True)
+        assert abs(got - want) <= 1e-12 * (1 + abs(want))
+        e = 1e-6
+        fd = (O.limiter(*(x + e * dirn), dx, d, 1e-6)["vt"] -
+              O.limiter(*(x - e * dirn), dx, d, 1e-6)["vt"]) / (2 * e)
+        got_full = O.limiter_tangent(*x, dirn, dx, d, 1e-6)
+        assert abs(got_full - fd) <= 1e-6 * (1 + abs(fd))
