@@ -107,8 +107,8 @@ typedef struct hweno_grid {
 
 /* Scheme options. hweno_default_options fills the paper's values (Sec. 3):
  * lin_w = lim_d = {0.98, 0.01, 0.01}, eps = 1e-6, cfl = 0.6,
- * dt_mode = 0, limiter = 1, eig_avg = 0, tile_variant = 0 and
- * fused_small = 0. */
+ * dt_mode = 0, limiter = 1, eig_avg = 0, tile_variant = 0, fused_small = 0
+ * and adj_frozen_weights = 0. */
 typedef struct hweno_options {
   double lin_w[3]; /* gamma_0..2 of the reconstruction: > 0, sum 1 (Sec. 2.1) */
   double lim_d[3]; /* d_0..2 of the limiter: > 0, sum 1 (Sec. 2.2) */
@@ -133,6 +133,10 @@ typedef struct hweno_options {
                        instances the tiled kernels are faster (Burgers N = 400:
                        133 vs 81 us per step); the fused step pays off in FP32
                        or for batches of many small instances. */
+  int adj_frozen_weights; /* hweno_adjoint_step: 0 = differentiate the
+                       nonlinear weights of the reconstruction and the
+                       limiter; 1 = hold them at their forward values (the
+                       adjoint of the scheme linearised with frozen weights) */
 } hweno_options;
 
 /* Largest instance of the fused single-launch step (one 508-point tile). */

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
     const double mf = (mL1[jf + 1] - mL1[jf]) * idx;    // d J / d f-hat_{j+1/2}
     const double mD = (mL2[jf + 1] - mL2[jf]) * idx2;   // d J / d (dx h-hat_{j+1/2})
     double gp[6] = {0, 0, 0, 0, 0, 0}, gm[6] = {0, 0, 0, 0, 0, 0};
-    flux_vjp(&sFp[jf], &sHp[jf], &sFm[jf + 1], &sHm[jf + 1], mf, w, gp, gm);
+    flux_vjp(&sFp[jf], &sHp[jf], &sFm[jf + 1], &sHm[jf + 1], mf, w, gp, gm,
+             a.sp.adj_frozen != 0);
     dflux_vjp(mD, gp, gm);
     // chain to (u, v) of the four stencil points
 #pragma unroll
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
     double g[5] = {0, 0, 0, 0, 0};
     if (limited)
       limiter_vjp(su[jl + 1], su[jl + 2], su[jl + 3], dx * sv[jl + 1], dx * sv[jl + 3],
-                  mVt[jl] * idx, w, g);
+                  mVt[jl] * idx, w, g, a.sp.adj_frozen != 0);
     lu[jl][0] = g[0]; lu[jl][1] = g[1]; lu[jl][2] = g[2];
     lv[jl][0] = dx * g[3]; lv[jl][1] = dx * g[4];
   }

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NT, 2) k_adjoint_euler_1d(const __grid_constan
         pHm[kk] = e.L[q][0] * sHm[0][jf + 1 + kk] + e.L[q][1] * sHm[1][jf + 1 + kk] + e.L[q][2] * sHm[2][jf + 1 + kk];
       }
       double gp[6] = {0, 0, 0, 0, 0, 0}, gm[6] = {0, 0, 0, 0, 0, 0};
-      const double fq = flux_vjp(pFp, pHp, pFm, pHm, gq, w, gp, gm);
+      const double fq = flux_vjp(pFp, pHp, pFm, pHm, gq, w, gp, gm, a.sp.adj_frozen != 0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         gR[c][q] = mf[c] * fq;
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(NT, 2) k_adjoint_euler_1d(const __grid_constan
       for (int c = 0; c < 3; ++c) {
         double g5[5] = {0, 0, 0, 0, 0};
         limiter_vjp(su[c][jl + 1], su[c][jl + 2], su[c][jl + 3], dx * sv[c][jl + 1],
-                    dx * sv[c][jl + 3], mVt[c][jl] * idx, w, g5);
+                    dx * sv[c][jl + 3], mVt[c][jl] * idx, w, g5, a.sp.adj_frozen != 0);
         gu[0][c] = g5[0]; gu[1][c] = g5[1]; gu[2][c] = g5[2];
         gv[0][c] = dx * g5[3]; gv[1][c] = dx * g5[4];
       }
@@ -325,7 +325,8 @@ __global__ void __launch_bounds__(NT, 2) k_adjoint_euler_1d(const __grid_constan
         };
         double g5[5] = {0, 0, 0, 0, 0};
         const double z = limiter_vjp(pj(su, jl + 1), pj(su, jl + 2), pj(su, jl + 3),
-                                     dx * pj(sv, jl + 1), dx * pj(sv, jl + 3), gz, w, g5);
+                                     dx * pj(sv, jl + 1), dx * pj(sv, jl + 3), gz, w, g5,
+                                     a.sp.adj_frozen != 0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           gR[c][q] = mVt[c][jl] * idx * z;

@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
     }
     if constexpr (!EUL) {
       double gp[6] = {0, 0, 0, 0, 0, 0}, gm[6] = {0, 0, 0, 0, 0, 0};
-      flux_vjp(&sFp[0][jf], &sHp[0][jf], &sFm[0][jf + 1], &sHm[0][jf + 1], mf[0], w, gp, gm);
+      flux_vjp(&sFp[0][jf], &sHp[0][jf], &sFm[0][jf + 1], &sHm[0][jf + 1], mf[0], w, gp, gm,
+               a.sp.adj_frozen != 0);
 #pragma unroll
       for (int kk = 0; kk < 3; ++kk) {
         acc(kk, 0, gp[kk]); acc(kk, 2, gp[3 + kk]);
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
           }
         }
         double gp[6] = {0, 0, 0, 0, 0, 0}, gm[6] = {0, 0, 0, 0, 0, 0};
-        const double fq = flux_vjp(pFp, pHp, pFm, pHm, gq, w, gp, gm);
+        const double fq = flux_vjp(pFp, pHp, pFm, pHm, gq, w, gp, gm, a.sp.adj_frozen != 0);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           gLR[(16 + c * 4 + q) * NT] = mf[c] * fq;  // gR[c][q]
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
       for (int c = 0; c < M; ++c) {
         double g5[5] = {0, 0, 0, 0, 0};
         limiter_vjp(su[c][jl + 1], su[c][jl + 2], su[c][jl + 3], h * sN[c][jl + 1],
-                    h * sN[c][jl + 3], ml[c][jl] * ih, w, g5);
+                    h * sN[c][jl + 3], ml[c][jl] * ih, w, g5, a.sp.adj_frozen != 0);
         sLm[c][jl] = g5[0]; sLm[M + c][jl] = g5[1]; sLm[2 * M + c][jl] = g5[2];
         sLm[3 * M + c][jl] = h * g5[3]; sLm[4 * M + c][jl] = h * g5[4];
       }
@@ -415,7 +416,8 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
             x[4] += e.L[q][c] * sN[c][jl + 3];
           }
           double g5[5] = {0, 0, 0, 0, 0};
-          const double z = limiter_vjp(x[0], x[1], x[2], h * x[3], h * x[4], gz, w, g5);
+          const double z = limiter_vjp(x[0], x[1], x[2], h * x[3], h * x[4], gz, w, g5,
+                                       a.sp.adj_frozen != 0);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             gLR[(16 + c * 4 + q) * NT] = ml[c][jl] * ih * z;

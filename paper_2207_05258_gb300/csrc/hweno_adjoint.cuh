@@ -4,6 +4,8 @@
 // themselves (the per-weight form of the nonlinear weights), not the folded
 // arrangement used by the forward kernels; the |.| in tau keeps the sign of
 // its argument at the point of evaluation (the branch of the forward run).
+// With `frozen` the nonlinear weights count as constants: only the
+// candidates' (linear) dependence on the data is propagated.
 #pragma once
 
 #include "hweno_math.cuh"
@@ -60,7 +62,7 @@ __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.
 // (order fm, f0, fp, Hm, H0, Hp).
 __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, double Hm, double H0,
                                            double Hp, double mu, const Weights<double>& w,
-                                           double* g) {
+                                           double* g, bool frozen = false) {
   using namespace adj;
   const double sHp = Hm + Hp, dHp = Hm - Hp, lap = fm - 2.0 * f0 + fp, dif = fm - fp;
   const double p0 = C11 * (fm + fp) + C19 * f0 + 0.05 * dHp + 0.5 * H0;
@@ -94,7 +96,8 @@ __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, doub
   const double gp0 = gQ0 * w.ig0;
   const double gp1 = gN * o1 - gQ0 * w.ig0 * w.g1;
   const double gp2 = gN * o2 - gQ0 * w.ig0 * w.g2;
-  const double c0 = go0 * w.g0 * ib0, c1 = go1 * w.g1 * ib1, c2 = go2 * w.g2 * ib2;
+  const double fz = frozen ? 0.0 : 1.0;  // weights held: no tau / beta terms
+  const double c0 = fz * go0 * w.g0 * ib0, c1 = fz * go1 * w.g1 * ib1, c2 = fz * go2 * w.g2 * ib2;
   const double gtau = c0 + c1 + c2;
   const double gb0 = -c0 * r0, gb1 = -c1 * r1, gb2 = -c2 * r2;
   const double gt = 0.5 * t * gtau;
@@ -127,10 +130,11 @@ __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, doub
 // the mirror image (reversed stencil, negated H).
 __device__ __forceinline__ double flux_vjp(const double* fp_, const double* Hp_, const double* fm_,
                                          const double* Hm_, double mu, const Weights<double>& w,
-                                         double* gp, double* gm) {
-  const double fp = side_vjp(fp_[0], fp_[1], fp_[2], Hp_[0], Hp_[1], Hp_[2], mu, w, gp);
+                                         double* gp, double* gm, bool frozen = false) {
+  const double fp = side_vjp(fp_[0], fp_[1], fp_[2], Hp_[0], Hp_[1], Hp_[2], mu, w, gp, frozen);
   double r[6] = {0, 0, 0, 0, 0, 0};
-  const double fm = side_vjp(fm_[2], fm_[1], fm_[0], -Hm_[2], -Hm_[1], -Hm_[0], mu, w, r);
+  const double fm =
+      side_vjp(fm_[2], fm_[1], fm_[0], -Hm_[2], -Hm_[1], -Hm_[0], mu, w, r, frozen);
   gm[0] += r[2]; gm[1] += r[1]; gm[2] += r[0];
   gm[3] -= r[5]; gm[4] -= r[4]; gm[5] -= r[3];
   return fp + fm;
@@ -149,7 +153,8 @@ __device__ __forceinline__ void dflux_vjp(double mu, double* gp, double* gm) {
 // um, u0, up and Vm = dx v_{i-1}, Vp = dx v_{i+1}: returns out and adds
 // mu * d out / d input to g[5] (order um, u0, up, Vm, Vp).
 __device__ __forceinline__ double limiter_vjp(double um, double u0, double up, double Vm, double Vp,
-                                            double mu, const Weights<double>& w, double* g) {
+                                            double mu, const Weights<double>& w, double* g,
+                                            bool frozen = false) {
   using namespace adj;
   const double sV = Vm + Vp, dV = Vm - Vp, lap = um - 2.0 * u0 + up, dup = up - um;
   const double q0 = 0.75 * dup - 0.25 * sV, q1 = u0 - um, q2 = up - u0;
@@ -173,7 +178,8 @@ __device__ __forceinline__ double limiter_vjp(double um, double u0, double up, d
   double gq0 = gQ0 * w.id0;
   double gq1 = gN * l1 - gQ0 * w.id0 * w.d1;
   double gq2 = gN * l2 - gQ0 * w.id0 * w.d2;
-  const double c0 = gl0 * w.d0 * ib0, c1 = gl1 * w.d1 * ib1, c2 = gl2 * w.d2 * ib2;
+  const double fz = frozen ? 0.0 : 1.0;
+  const double c0 = fz * gl0 * w.d0 * ib0, c1 = fz * gl1 * w.d1 * ib1, c2 = fz * gl2 * w.d2 * ib2;
   const double gt = 0.5 * t * (c0 + c1 + c2);
   const double gd1 = gt * sgn(d1), gd2 = gt * sgn(d2);
   const double gbe0 = -c0 * r0 + gd1 + gd2;

@@ -127,6 +127,10 @@ int check_options(const hweno_options* o, std::string& why) {
   if (o->limiter < 0 || o->limiter > 2) { why = "limiter must be 0, 1 or 2"; return HWENO_EINVAL; }
   if (o->eig_avg < 0 || o->eig_avg > 1) { why = "eig_avg must be 0 or 1"; return HWENO_EINVAL; }
   if (o->fused_small < 0 || o->fused_small > 1) { why = "fused_small must be 0 or 1"; return HWENO_EINVAL; }
+  if (o->adj_frozen_weights < 0 || o->adj_frozen_weights > 1) {
+    why = "adj_frozen_weights must be 0 or 1";
+    return HWENO_EINVAL;
+  }
   if (o->tile_variant < 0 || o->tile_variant >= kNumVariants1D) {
     why = "tile_variant out of range";
     return HWENO_EINVAL;
@@ -196,6 +200,7 @@ SchemeParams scheme_params(const hweno_ctx* c) {
   sp.dt_mode = c->opt.dt_mode;
   sp.limiter = c->opt.limiter;
   sp.eig_avg = c->opt.eig_avg;
+  sp.adj_frozen = c->opt.adj_frozen_weights;
   sp.gas_gamma = c->gamma;
   sp.bc[0] = c->bc.xlo; sp.bc[1] = c->bc.xhi; sp.bc[2] = c->bc.ylo; sp.bc[3] = c->bc.yhi;
   for (int i = 0; i < 4; ++i) { sp.inflow[i] = c->bc.inflow[i]; sp.pre[i] = c->bc.pre[i]; }

@@ -32,6 +32,7 @@ constexpr int kMinTile1D = 60;  // smallest tile of any variant
 struct SchemeParams {
   double lin_w[3], lim_d[3], eps, cfl, dt_fixed;
   int dt_mode, limiter, eig_avg;
+  int adj_frozen;  // adjoint: nonlinear weights held at their forward values
   double gas_gamma;
   int bc[4];
   double inflow[4], pre[4];

@@ -303,7 +303,10 @@ def _dot_check_2d(hw, w, seed, tol, pre_steps=0, **opts):
     s.sync_status()
     g = [x.cpu().numpy() for x in lt]
     d = [rng.standard_normal(w.U.size) for _ in range(3)]
-    out = O.run_tangent(oracle_problem(w, **opts), U.cpu().numpy(), V.cpu().numpy(),
+    oopts = dict(opts)
+    if "adj_frozen_weights" in oopts:  # the oracle's name for the same reading
+        oopts["freeze_weights"] = oopts.pop("adj_frozen_weights")
+    out = O.run_tangent(oracle_problem(w, **oopts), U.cpu().numpy(), V.cpu().numpy(),
                         Wd.cpu().numpy(), d[0], d[1], d[2], float(t0.item()), 1.0, max_steps=1)
     lhs = sum(float(np.dot(g[i], d[i])) for i in range(3))
     tan = [out[3].ravel(), out[4].ravel(), out[5].ravel()]
@@ -365,3 +368,47 @@ def test_2d_gradient_through_checkpointed_run(hw):
     scale = np.sqrt(sum(np.sum(x ** 2) for x in g) * sum(np.sum(x ** 2) for x in d))
     print("2D gradient: adjoint %.12e dual %.12e" % (adj, dJ))
     assert abs(adj - dJ) <= 1e-10 * scale, (adj, dJ, scale)
+
+
+# ---------------------------------------------------------------------------
+# frozen-weights mode (adj_frozen_weights = 1) against the oracle's tangent
+# with the weights held (freeze_weights = 1)
+# ---------------------------------------------------------------------------
+def test_frozen_weights_1d_burgers_and_euler(hw):
+    for w in (rough_batch([31, 124, 300], "outflow", 61),
+              euler_rough_batch([31, 125, 300], "reflective", 62, riemann_every=2)):
+        s = hw.Solver.from_workload(w, adj_frozen_weights=1)
+        U, V = torch.from_numpy(w.U.copy()).cuda(), torch.from_numpy(w.V.copy()).cuda()
+        t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+        dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+        s.step(U.clone(), V.clone(), None, t, 1.0, dt)
+        rng = np.random.default_rng(63)
+        lamU, lamV = rng.standard_normal(w.U.size), rng.standard_normal(w.V.size)
+        lU, lV = torch.from_numpy(lamU).cuda(), torch.from_numpy(lamV).cuda()
+        s.adjoint_step(U, V, None, dt, lU, lV)
+        s.sync_status()
+        gU, gV = lU.cpu().numpy(), lV.cpu().numpy()
+        m, off = w.m, 0
+        for k, n in enumerate(w.nx):
+            Uk, Vk = w.instance(k)
+            dU, dV = rng.standard_normal(Uk.shape), rng.standard_normal(Vk.shape)
+            out = O.run_tangent(oracle_problem(w, nx=n, freeze_weights=1), Uk, Vk, None, dU, dV,
+                                None, 0.0, 1.0, max_steps=1)
+            full = O.run_tangent(oracle_problem(w, nx=n), Uk, Vk, None, dU, dV, None, 0.0, 1.0,
+                                 max_steps=1)
+            sl = slice(m * off, m * (off + n))
+            lhs = float(np.dot(gU[sl], dU.ravel()) + np.dot(gV[sl], dV.ravel()))
+            rhs = float(np.dot(lamU[sl], out[3].ravel()) + np.dot(lamV[sl], out[4].ravel()))
+            rfull = float(np.dot(lamU[sl], full[3].ravel()) + np.dot(lamV[sl], full[4].ravel()))
+            scale = np.sqrt(np.sum(lamU[sl] ** 2 + lamV[sl] ** 2) *
+                            np.sum(out[3] ** 2 + out[4] ** 2)) + abs(rhs)
+            assert abs(lhs - rhs) <= 1e-11 * scale, (w.equation, k, lhs, rhs)
+            if w.equation == "euler" and k == 1:  # a Riemann instance: freezing matters
+                assert abs(rfull - rhs) > 1e-6 * scale
+            off += n
+
+
+def test_frozen_weights_2d_euler(hw):
+    w = rough_2d("euler", 40, 30, "periodic", "outflow", 64)
+    r = _dot_check_2d(hw, w, 65, 1e-11, adj_frozen_weights=1)
+    print("2D frozen weights: relative mismatch %.2e" % r)
