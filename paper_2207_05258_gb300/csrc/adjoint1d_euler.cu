@@ -436,13 +436,8 @@ constexpr size_t kSmemEuler =
 }  // namespace
 
 cudaError_t launch_adjoint_1d_euler(const AdjArgs1D& a, int ntiles, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_adjoint_euler_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemEuler);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static unsigned configured = 0;  // devices whose limit is raised
+  if (const cudaError_t e = ensure_smem_limit(k_adjoint_euler_1d, kSmemEuler, configured)) return e;
   k_adjoint_euler_1d<<<ntiles, NT, kSmemEuler, s>>>(a);
   return cudaGetLastError();
 }

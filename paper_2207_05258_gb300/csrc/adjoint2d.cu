@@ -534,13 +534,8 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
 template <int EQ, int DIR>
 cudaError_t sweep_launch(const AdjArgs2D& a, cudaStream_t s) {
   constexpr size_t bytes = AdjLayout2D<EQ>::bytes;
-  static bool configured = false;
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_adjoint_sweep_2d<EQ, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static unsigned configured = 0;  // devices whose limit is raised
+  if (const cudaError_t e = ensure_smem_limit(k_adjoint_sweep_2d<EQ, DIR>, bytes, configured)) return e;
   const int n = DIR == 0 ? a.nx : a.ny, lines = DIR == 0 ? a.ny : a.nx;
   const dim3 grid((n + P - 1) / P, lines);
   k_adjoint_sweep_2d<EQ, DIR><<<grid, NT, bytes, s>>>(a);

@@ -8,6 +8,21 @@
 
 namespace hweno {
 
+// Raise kernel f's dynamic shared-memory limit to `bytes` once per device
+// (the attribute belongs to the function on the current device); `done`
+// holds one bit per device already configured.
+template <class K>
+inline cudaError_t ensure_smem_limit(K* f, size_t bytes, unsigned& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned bit = dev < 32 ? (1u << dev) : 0u;
+  if (bit && (done & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
 // Status-word bits written by kernels (read by hweno_sync_status).
 enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u };
 

@@ -414,14 +414,8 @@ k_stage_1d(const __grid_constant__ Args1D a) {
 template <int EQ, class Real, int MODE, int NT, int PPT>
 cudaError_t stage_launch(const Args1D& a, int ntiles, cudaStream_t s) {
   constexpr size_t bytes = Layout1D<EQ, Real, NT, PPT>::bytes;
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(k_stage_1d<EQ, Real, MODE, NT, PPT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static unsigned configured = 0;  // devices whose limit is raised
+  if (const cudaError_t e = ensure_smem_limit(k_stage_1d<EQ, Real, MODE, NT, PPT>, bytes, configured)) return e;
   k_stage_1d<EQ, Real, MODE, NT, PPT><<<ntiles, NT, bytes, s>>>(a);
   return cudaGetLastError();
 }
@@ -580,14 +574,8 @@ k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p
 template <int EQ, class Real, int NT, int PPT>
 cudaError_t run_launch(const Args1D& a, const PersistArgs& p, int ctas, cudaStream_t s) {
   constexpr size_t bytes = Layout1D<EQ, Real, NT, PPT>::bytes;
-  static bool configured = false;
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(k_run_1d<EQ, Real, NT, PPT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static unsigned configured = 0;  // devices whose limit is raised
+  if (const cudaError_t e = ensure_smem_limit(k_run_1d<EQ, Real, NT, PPT>, bytes, configured)) return e;
   k_run_1d<EQ, Real, NT, PPT><<<ctas, NT, bytes, s>>>(a, p);
   return cudaGetLastError();
 }
@@ -708,14 +696,8 @@ k_step_small_1d(const __grid_constant__ Args1D a, const __grid_constant__ FusedA
 template <int EQ, class Real>
 cudaError_t step_small_launch(const Args1D& a, const FusedArgs& f, cudaStream_t s) {
   constexpr size_t bytes = Layout1D<EQ, Real, kFusedThreads, kFusedPPT>::bytes;
-  static bool configured = false;
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(k_step_small_1d<EQ, Real>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static unsigned configured = 0;  // devices whose limit is raised
+  if (const cudaError_t e = ensure_smem_limit(k_step_small_1d<EQ, Real>, bytes, configured)) return e;
   k_step_small_1d<EQ, Real><<<f.batch, kFusedThreads, bytes, s>>>(a, f);
   return cudaGetLastError();
 }

@@ -572,14 +572,8 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
 template <int EQ, class Real, int MODE>
 cudaError_t ysweep_launch(const Args2D& a, cudaStream_t s) {
   constexpr size_t bytes = YLayout<EQ, Real>::bytes;
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(k_ysweep_2d<EQ, Real, MODE>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static unsigned configured = 0;  // devices whose limit is raised
+  if (const cudaError_t e = ensure_smem_limit(k_ysweep_2d<EQ, Real, MODE>, bytes, configured)) return e;
   const dim3 grid((a.nx + kColsY2D - 1) / kColsY2D, (a.ny + kRowsY2D - 1) / kRowsY2D);
   k_ysweep_2d<EQ, Real, MODE><<<grid, kThreads2D, bytes, s>>>(a);
   return cudaGetLastError();
