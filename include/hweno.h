@@ -122,8 +122,9 @@ typedef struct hweno_options {
                       U_i of the sweep direction); 2: component-wise */
   int eig_avg;     /* eigenvectors at x_{i+1/2}: 0 Roe average of U_i, U_{i+1};
                       1 arithmetic mean */
-  int tile_variant; /* 1D tile shape 0..4 (see hweno_autotune; results do not
-                       depend on it); ignored in 2D */
+  int tile_variant; /* 1D tile shape 0 .. HWENO_TILE_VARIANTS - 1 (see
+                       hweno_autotune; results do not depend on it); ignored
+                       in 2D */
   int fused_small;  /* 1D: 1 = when every instance has at most
                        HWENO_FUSED_MAX_POINTS points, hweno_step runs the whole
                        step (wave speed, three stages, time update) in one
@@ -138,6 +139,9 @@ typedef struct hweno_options {
                        limiter; 1 = hold them at their forward values (the
                        adjoint of the scheme linearised with frozen weights) */
 } hweno_options;
+
+/* Number of 1D tile shapes (hweno_options.tile_variant, hweno_autotune). */
+#define HWENO_TILE_VARIANTS 5
 
 /* Largest instance of the fused single-launch step (one 508-point tile). */
 #define HWENO_FUSED_MAX_POINTS 508
@@ -242,8 +246,10 @@ int hweno_test_inject(hweno_ctx* ctx, int kind);
  * the given state U, V at times t (device) with t_end, and keeps the fastest
  * for the following calls of this context. Only library scratch is written
  * (U, V, W, t are read). Synchronises `stream`. *chosen (host, nullable)
- * receives the variant index (0 = the default 128 x 1); ms (host, nullable,
- * 5 doubles) the best measured time of each variant in milliseconds. In 2D
+ * receives the variant index (0 = the default 128 x 1; variants 1..4 are
+ * 64 x 1, 256 x 1, 128 x 2 and 64 x 2, threads x points per thread);
+ * ms (host, nullable, HWENO_TILE_VARIANTS doubles) the best measured time of
+ * each variant in milliseconds. In 2D
  * there is a single tile shape: *chosen = 0 and nothing is measured. */
 int hweno_autotune(hweno_ctx* ctx, const void* U, const void* V, const void* W, const double* t,
                    double t_end, int* chosen, double* ms, void* stream);

@@ -38,7 +38,8 @@ struct TileVariant {
   int threads, ppt;
 };
 constexpr TileVariant kVariants1D[] = {{128, 1}, {64, 1}, {256, 1}, {128, 2}, {64, 2}};
-constexpr int kNumVariants1D = 5;
+constexpr int kNumVariants1D = HWENO_TILE_VARIANTS;
+static_assert(sizeof(kVariants1D) / sizeof(kVariants1D[0]) == kNumVariants1D, "variant table");
 constexpr int tile_points(int v) { return kVariants1D[v].threads * kVariants1D[v].ppt - 4; }
 constexpr int kThreads1D = 128;
 constexpr int kTile1D = tile_points(0);

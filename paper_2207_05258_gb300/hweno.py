@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5
 BURGERS, EULER, BUCKLEY = 0, 1, 2
 EQUATIONS = dict(burgers=BURGERS, euler=EULER, buckley=BUCKLEY)
 FP64, FP32 = 0, 1
+TILE_VARIANTS = 5  # HWENO_TILE_VARIANTS: 1D tile shapes
 BC = dict(periodic=0, outflow=1, reflective=2, inflow=3, dmr_bottom=4, dmr_top=5)
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
           ETIMEOUT: "ETIMEOUT", ENOTSUP: "ENOTSUP"}
@@ -214,7 +215,7 @@ class Solver:
         """hweno_autotune: returns (chosen variant, per-variant ms)."""
         t = torch.zeros(self.batch, dtype=torch.float64, device=U.device) if t is None else t
         chosen = ctypes.c_int(0)
-        ms = (ctypes.c_double * 5)()
+        ms = (ctypes.c_double * TILE_VARIANTS)()
         self._check(lib.hweno_autotune(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t), float(t_end),
                                        ctypes.byref(chosen), ms, _stream()))
         return chosen.value, list(ms)

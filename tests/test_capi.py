@@ -34,6 +34,17 @@ def test_library_exports_every_declared_function(hw):
     assert set(hw.SIGNATURES) == set(names)
 
 
+def test_binding_constants_match_the_header(hw):
+    text = open(os.path.join(ROOT, "include", "hweno.h")).read()
+    defines = dict(l.split()[1:3] for l in text.splitlines()
+                   if l.startswith("#define HWENO_") and len(l.split()) >= 3)
+    value = lambda name: int(defines["HWENO_" + name].strip("()"))
+    assert value("TILE_VARIANTS") == hw.TILE_VARIANTS
+    for name in ("OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ENOTSUP",
+                 "BURGERS", "EULER", "BUCKLEY"):
+        assert value(name) == getattr(hw, name), name
+
+
 def test_default_options_are_the_papers(hw):
     o = hw.default_options()
     assert list(o.lin_w) == [0.98, 0.01, 0.01] and list(o.lim_d) == [0.98, 0.01, 0.01]

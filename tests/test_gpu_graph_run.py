@@ -93,7 +93,7 @@ def test_every_tile_variant_gives_the_same_bits(hw, precision):
     w = full
     dt = torch.float64 if precision == "fp64" else torch.float32
     outs = []
-    for v in range(5):
+    for v in range(hw.TILE_VARIANTS):
         s = hw.Solver.from_workload(w, precision=precision, tile_variant=v)
         U, V = torch.from_numpy(w.U).to("cuda", dt), torch.from_numpy(w.V).to("cuda", dt)
         t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
@@ -111,5 +111,5 @@ def test_every_tile_variant_gives_the_same_bits(hw, precision):
     U, V = torch.from_numpy(w.U).to("cuda", dt), torch.from_numpy(w.V).to("cuda", dt)
     chosen, ms = s.autotune(U, V, None, torch.zeros(w.batch, dtype=torch.float64, device="cuda"),
                             w.t_end)
-    assert 0 <= chosen < 5 and all(m > 0 for m in ms)
+    assert 0 <= chosen < hw.TILE_VARIANTS and all(m > 0 for m in ms)
     assert ms[chosen] == min(ms)

@@ -78,7 +78,7 @@ def _compare(hw, w, precision, variant, K, t_end):
     return act2
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", range(5))
 def test_euler_fp64_every_variant(hw, variant):
     w = _batch("euler", 7)
     _compare(hw, w, "fp64", variant, 6, 1.0)
