@@ -51,23 +51,38 @@ __device__ __forceinline__ void euler_fh(const T* u, const T* v, double gm1, T* 
   H[2] = (v[2] + dp) * vel + Ep * dvel;
 }
 
-// gu += d(gF.F + gH.H)/du, gv += d(gH.H)/dv at (u, v).
+// gu += d(gF.F + gH.H)/du, gv += d(gH.H)/dv at (u, v): one reverse pass
+// through euler_fh.
 __device__ __forceinline__ void point_vjp(const double* u, const double* v, const double* gF,
                                           const double* gH, double gm1, double* gu, double* gv) {
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    Dd uu[3], vv[3], F[3], H[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      uu[c] = Dd(u[c], k == c ? 1.0 : 0.0);
-      vv[c] = Dd(v[c], k == 3 + c ? 1.0 : 0.0);
-    }
-    euler_fh(uu, vv, gm1, F, H);
-    const double s = gF[0] * F[0].d + gF[1] * F[1].d + gF[2] * F[2].d + gH[0] * H[0].d +
-                     gH[1] * H[1].d + gH[2] * H[2].d;
-    if (k < 3) gu[k] += s;
-    else gv[k - 3] += s;
-  }
+  const double ir = 1.0 / u[0], vel = u[1] * ir;
+  const double p = gm1 * (u[2] - 0.5 * u[1] * vel), Ep = u[2] + p;
+  const double dvel = (v[1] - vel * v[0]) * ir;
+  const double dp = gm1 * (v[2] - vel * v[1] + 0.5 * vel * vel * v[0]);
+  // F = (u1, u1 vel + p, Ep vel); H = (v1, v1 vel + u1 dvel + dp, (v2 + dp) vel + Ep dvel)
+  double a_vel = gF[1] * u[1] + gF[2] * Ep + gH[1] * v[1] + gH[2] * (v[2] + dp);
+  double a_p = gF[1];
+  double a_Ep = gF[2] * vel + gH[2] * dvel;
+  const double a_dvel = gH[1] * u[1] + gH[2] * Ep;
+  const double a_dp = gH[1] + gH[2] * vel;
+  double a_u0 = 0.0, a_u1 = gF[0] + gF[1] * vel + gH[1] * dvel, a_u2 = 0.0;
+  // dvel = (v1 - vel v0) / rho, dp = gm1 (v2 - vel v1 + vel^2 v0 / 2)
+  a_vel += -a_dvel * v[0] * ir + a_dp * gm1 * (vel * v[0] - v[1]);
+  double a_ir = a_dvel * (v[1] - vel * v[0]);
+  gv[0] += 0.5 * gm1 * a_dp * vel * vel - a_dvel * vel * ir;
+  gv[1] += gH[0] + gH[1] * vel + a_dvel * ir - gm1 * a_dp * vel;
+  gv[2] += gH[2] * vel + gm1 * a_dp;
+  // Ep = u2 + p, p = gm1 (u2 - u1 vel / 2), vel = u1 / rho
+  a_p += a_Ep;
+  a_u2 += a_Ep + gm1 * a_p;
+  a_u1 -= 0.5 * gm1 * a_p * vel;
+  a_vel -= 0.5 * gm1 * a_p * u[1];
+  a_u1 += a_vel * ir;
+  a_ir += a_vel * u[1];
+  a_u0 -= a_ir * ir * ir;
+  gu[0] += a_u0;
+  gu[1] += a_u1;
+  gu[2] += a_u2;
 }
 
 // Eigenvectors at velocity u and enthalpy H: returns them in e and the
@@ -78,23 +93,34 @@ __device__ __forceinline__ void eigen_at(double u, double H, double gm1, Eigen<d
   euler_eigen<double, 3>(0, u, 0.0, H, c, ic, gm1, e);
 }
 
+// One reverse pass through the formulas of euler_eigen (M = 3: q = u^2/2,
+// b1 = (gamma-1)/c^2, b2 = b1 q, c^2 = (gamma-1)(H - q)).
 __device__ __forceinline__ void eigen_vjp(double u, double H, double gm1, const double (*gL)[3],
                                           const double (*gR)[3], double& gu, double& gH) {
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const Dd uu(u, k == 0 ? 1.0 : 0.0), HH(H, k == 1 ? 1.0 : 0.0);
-    const Dd c = sqrt(Dd(gm1) * (HH - 0.5 * uu * uu));
-    const Dd ic = Dd(1.0) / c;
-    Eigen<Dd, 3> e;
-    euler_eigen<Dd, 3>(0, uu, Dd(0.0), HH, c, ic, Dd(gm1), e);
-    double s = 0.0;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) s += gL[r][q] * e.L[r][q].d + gR[r][q] * e.R[r][q].d;
-    if (k == 0) gu = s;
-    else gH = s;
-  }
+  const double q = 0.5 * u * u;
+  const double c = ::sqrt(gm1 * (H - q)), ic = 1.0 / c;
+  const double b1 = gm1 * ic * ic;
+  const double sL1 = gL[0][1] + gL[2][1];
+  const double a_b2 = 0.5 * (gL[0][0] + gL[2][0]) - gL[1][0];
+  const double a_uc = 0.5 * (gL[0][0] - gL[2][0]);
+  double a_b1 = -0.5 * u * sL1 + 0.5 * (gL[0][2] + gL[2][2]) + u * gL[1][1] - gL[1][2];
+  double a_ic = 0.5 * (gL[2][1] - gL[0][1]);
+  double a_u = b1 * (gL[1][1] - 0.5 * sL1) + gR[1][0] + gR[1][1] + gR[1][2] +
+               c * (gR[2][2] - gR[2][0]);
+  double a_c = gR[1][2] - gR[1][0] + u * (gR[2][2] - gR[2][0]);
+  double a_H = gR[2][0] + gR[2][2];
+  double a_q = gR[2][1];
+  // b2 = b1 q, uc = u ic, b1 = gm1 ic^2, ic = 1/c, c = sqrt(gm1 (H - q))
+  a_b1 += q * a_b2;
+  a_q += b1 * a_b2;
+  a_u += ic * a_uc;
+  a_ic += u * a_uc + 2.0 * gm1 * ic * a_b1;
+  a_c -= ic * ic * a_ic;
+  const double a_in = 0.5 * gm1 * ic * a_c;  // d c / d (H - q) = gm1 / (2 c)
+  a_H += a_in;
+  a_q -= a_in;
+  gu = a_u + u * a_q;
+  gH = a_H;
 }
 
 // Velocity and total enthalpy of a conserved state, H = gamma E / rho -

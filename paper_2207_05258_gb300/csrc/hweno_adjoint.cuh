@@ -140,6 +140,27 @@ __device__ __forceinline__ double flux_vjp(const double* fp_, const double* Hp_,
   return fp + fm;
 }
 
+// One side of flux_vjp: sd = 0 the "+" side from (f0, f1, f2, H0, H1, H2) =
+// f^+, H^+ at i-1..i+1; sd = 1 the "-" side from f^-, H^- at i..i+2 (its
+// mirror image). Returns the side's value and adds mu times its partial
+// derivatives to g (f then H, in stencil order).
+__device__ __forceinline__ double side_half(int sd, double f0, double f1, double f2, double H0,
+                                          double H1, double H2, double mu,
+                                          const Weights<double>& w, double* g,
+                                          bool frozen = false) {
+  double r[6] = {0, 0, 0, 0, 0, 0};
+  const double v = side_vjp(sd ? f2 : f0, f1, sd ? f0 : f2, sd ? -H2 : H0, sd ? -H1 : H1,
+                            sd ? -H0 : H2, mu, w, r, frozen);
+  if (sd) {
+    g[0] += r[2]; g[1] += r[1]; g[2] += r[0];
+    g[3] -= r[5]; g[4] -= r[4]; g[5] -= r[3];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[k] += r[k];
+  }
+  return v;
+}
+
 // Linear derivative flux D = dx (h-hat^+ + h-hat^-) (Sec. 2.1, p_0'):
 // adds mu * dD/d input to gp, gm (same layout as flux_vjp).
 __device__ __forceinline__ void dflux_vjp(double mu, double* gp, double* gm) {
