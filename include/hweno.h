@@ -133,12 +133,22 @@ typedef struct hweno_options {
                        1/152 of the GPU's FP64 pipe, so for a few FP64
                        instances the tiled kernels are faster (Burgers N = 400:
                        133 vs 81 us per step); the fused step pays off in FP32
-                       or for batches of many small instances. */
+                       or for batches of many small instances.
+                       2 = when every instance has at most
+                       HWENO_CLUSTER_MAX_POINTS points, one launch per step
+                       on thread-block clusters: one cluster per instance,
+                       one 124-point tile per CTA, each CTA on an SM of its
+                       own (it reserves 116 KB of shared memory), the stages
+                       separated by cluster barriers. Meant for a few small
+                       instances, where the latency of a step matters. */
   int adj_frozen_weights; /* hweno_adjoint_step: 0 = differentiate the
                        nonlinear weights of the reconstruction and the
                        limiter; 1 = hold them at their forward values (the
                        adjoint of the scheme linearised with frozen weights) */
 } hweno_options;
+
+/* Largest instance of the cluster step (fused_small = 2): 8 tiles of 124. */
+#define HWENO_CLUSTER_MAX_POINTS 992
 
 /* Number of 1D tile shapes (hweno_options.tile_variant, hweno_autotune). */
 #define HWENO_TILE_VARIANTS 5

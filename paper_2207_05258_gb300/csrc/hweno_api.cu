@@ -126,7 +126,7 @@ int check_options(const hweno_options* o, std::string& why) {
   if (o->dt_mode == 2 && !(o->dt_fixed > 0)) { why = "dt_fixed must be > 0"; return HWENO_EINVAL; }
   if (o->limiter < 0 || o->limiter > 2) { why = "limiter must be 0, 1 or 2"; return HWENO_EINVAL; }
   if (o->eig_avg < 0 || o->eig_avg > 1) { why = "eig_avg must be 0 or 1"; return HWENO_EINVAL; }
-  if (o->fused_small < 0 || o->fused_small > 1) { why = "fused_small must be 0 or 1"; return HWENO_EINVAL; }
+  if (o->fused_small < 0 || o->fused_small > 2) { why = "fused_small must be 0, 1 or 2"; return HWENO_EINVAL; }
   if (o->adj_frozen_weights < 0 || o->adj_frozen_weights > 1) {
     why = "adj_frozen_weights must be 0 or 1";
     return HWENO_EINVAL;
@@ -339,7 +339,8 @@ int step_1d_range(hweno_ctx* c, void* U, void* V, double* t, double t_end, doubl
 int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_used,
             cudaStream_t s) {
   cudaError_t e;
-  if (c->opt.fused_small && c->max_n <= kFusedPoints) {  // one launch per step
+  const bool cluster = c->opt.fused_small == 2 && c->max_n <= kClusterMax * kTile1D;
+  if ((c->opt.fused_small == 1 && c->max_n <= kFusedPoints) || cluster) {  // one launch per step
     if ((e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s))) return cuda_fail(c, e, "memset");
     Args1D a = base_args_1d(c);
     a.t = t;
@@ -354,7 +355,13 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
     f.alpha = c->d_alpha; f.dt_used = dt_used; f.active = c->d_active; f.pu = c->d_pu;
     f.batch = c->batch;
     prof_begin(c, s);
-    if ((e = launch_step_small_1d(c->eq, c->fp32, a, f, s))) return cuda_fail(c, e, "fused step");
+    if (cluster) {
+      const int C = (int)((c->max_n + kTile1D - 1) / kTile1D);
+      if ((e = launch_step_cluster_1d(c->eq, c->fp32, a, f, C, s)))
+        return cuda_fail(c, e, "cluster step");
+    } else if ((e = launch_step_small_1d(c->eq, c->fp32, a, f, s))) {
+      return cuda_fail(c, e, "fused step");
+    }
     prof_end(c, s, 1);
     c->launches = c->step_launches = 1;
     return HWENO_OK;

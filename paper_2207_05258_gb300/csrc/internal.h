@@ -304,6 +304,25 @@ inline cudaError_t launch_step_small_1d(int eq, bool fp32, const Args1D& a, cons
   return fp32 ? launch_step_small_1d_f32(eq, a, f, s) : launch_step_small_1d_f64(eq, a, f, s);
 }
 
+// Fused step on thread-block clusters (stage1d_impl.cuh, k_step_cluster_1d):
+// one cluster of C <= kClusterMax CTAs per instance, one kTile1D-point tile
+// per CTA, each CTA alone on its SM (kClusterSmem of shared memory).
+constexpr int kClusterMax = 8;
+constexpr size_t kClusterSmem = 116 * 1024;
+static_assert(kClusterMax * kTile1D == HWENO_CLUSTER_MAX_POINTS, "cluster step size");
+cudaError_t launch_step_cluster_1d_f64(int eq, const Args1D& a, const FusedArgs& f, int C,
+                                       cudaStream_t s);
+cudaError_t launch_step_cluster_1d_f32(int eq, const Args1D& a, const FusedArgs& f, int C,
+                                       cudaStream_t s);
+cudaError_t launch_step_cluster_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f, int C,
+                                      cudaStream_t s);
+inline cudaError_t launch_step_cluster_1d(int eq, bool fp32, const Args1D& a, const FusedArgs& f,
+                                          int C, cudaStream_t s) {
+  if (eq == HWENO_BUCKLEY) return launch_step_cluster_1d_bl(fp32, a, f, C, s);
+  return fp32 ? launch_step_cluster_1d_f32(eq, a, f, C, s)
+              : launch_step_cluster_1d_f64(eq, a, f, C, s);
+}
+
 cudaError_t launch_run_1d_f64(int eq, int variant, const Args1D& a, const PersistArgs& p,
                               int ctas, cudaStream_t s);
 cudaError_t launch_run_1d_f32(int eq, int variant, const Args1D& a, const PersistArgs& p,

@@ -30,6 +30,12 @@ cudaError_t launch_step_small_1d_bl(bool fp32, const Args1D& a, const FusedArgs&
               : step_small_launch<HWENO_BUCKLEY, double>(a, f, s);
 }
 
+cudaError_t launch_step_cluster_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f, int C,
+                                      cudaStream_t s) {
+  return fp32 ? step_cluster_launch<HWENO_BUCKLEY, float>(a, f, C, s)
+              : step_cluster_launch<HWENO_BUCKLEY, double>(a, f, C, s);
+}
+
 int run_1d_ctas_per_sm_bl(bool fp32, int variant) {
   return fp32 ? occupancy_variants<HWENO_BUCKLEY, float>(variant)
               : occupancy_variants<HWENO_BUCKLEY, double>(variant);

@@ -5,6 +5,7 @@
 
 #include <cfloat>
 
+#include <cooperative_groups.h>
 #include <cuda/atomic>
 
 #include "hweno.h"
@@ -700,6 +701,120 @@ cudaError_t step_small_launch(const Args1D& a, const FusedArgs& f, cudaStream_t 
   if (const cudaError_t e = ensure_smem_limit(k_step_small_1d<EQ, Real>, bytes, configured)) return e;
   k_step_small_1d<EQ, Real><<<f.batch, kFusedThreads, bytes, s>>>(a, f);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fused step of small instances on thread-block clusters (fused_small = 2):
+// one cluster of C CTAs per instance, CTA r of the cluster holding the
+// kTile1D-point tile that starts at r * kTile1D, each CTA alone on its SM
+// (its shared-memory request leaves no room for a second one). The wave
+// speed of U^n is reduced through distributed shared memory; the stages are
+// separated by cluster barriers, whose release / acquire order makes each
+// stage's global writes (state, alpha slots) visible to the next. Every CTA
+// passes the same five barriers whatever its share of the instance.
+// ---------------------------------------------------------------------------
+template <int EQ, class Real>
+__global__ void __launch_bounds__(kThreads1D)
+k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ FusedArgs f) {
+  namespace cg = cooperative_groups;
+  constexpr int M = Dim1<EQ>::M;
+  constexpr int P = kTile1D;
+  __shared__ Real red[kThreads1D / 32];
+  __shared__ double part;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int k = blockIdx.x / C;
+  const int n = a.inst_n[k];
+  const int s = rank * P;
+  const bool live = a.t[k] < a.t_end;  // read before anything below writes t
+  const bool has = live && s < n;
+  unsigned long long* s0 = f.alpha;
+  unsigned long long* s1 = f.alpha + f.batch;
+  unsigned long long* s2 = f.alpha + 2 * f.batch;
+  {  // alpha(U^n) of this tile's points
+    Real amax = Real(0);
+    if (has) {
+      const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
+      const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+      const Real a01 = pick<Real>(a.sp.wd, a.sp.wf)[10];
+      const int e = min(s + P, n);
+      for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
+        Real u[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + j];
+        amax = fmax(amax, wave_speed<EQ>(u, gam, a01));
+      }
+    }
+    amax = block_max_t(amax, red);
+    if (threadIdx.x == 0) part = (double)amax;
+  }
+  cl.sync();
+  if (live && rank == 0 && threadIdx.x == 0) {  // the instance's alpha; stage slots from zero
+    double m = 0.0;
+    for (int r = 0; r < C; ++r) m = fmax(m, *cl.map_shared_rank(&part, r));
+    s0[k] = (unsigned long long)__double_as_longlong(m);
+    s1[k] = 0ull;
+    s2[k] = 0ull;
+  }
+  cl.sync();
+  StageIO io = io_of(a);
+  io.Uout = f.U1; io.Vout = f.V1; io.Vt0out = f.Vt0;
+  io.alpha_in = reinterpret_cast<const double*>(s0); io.alpha_out = s1;
+  if (has) stage_tile<EQ, Real, MODE_STAGE1, kThreads1D, 1>(a, io, k, s);
+  cl.sync();
+  io.U = f.U1; io.V = f.V1; io.U0 = a.U; io.Vt0 = f.Vt0; io.Uout = f.U2; io.Vout = f.V2;
+  io.Vt0out = nullptr;
+  io.alpha_in = reinterpret_cast<const double*>(s1); io.alpha_out = s2;
+  if (has) stage_tile<EQ, Real, MODE_STAGE2, kThreads1D, 1>(a, io, k, s);
+  cl.sync();
+  io.U = f.U2; io.V = f.V2; io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V);
+  io.alpha_in = reinterpret_cast<const double*>(s2); io.alpha_out = nullptr;
+  if (has) stage_tile<EQ, Real, MODE_STAGE3, kThreads1D, 1>(a, io, k, s);
+  cl.sync();  // every CTA is past its reads of t[k]
+  if (rank == 0 && threadIdx.x == 0) {
+    if (!live) {  // finished: nothing moves (as k_finalize)
+      if (f.dt_used) f.dt_used[k] = 0.0;
+    } else {  // time update (as k_finalize); tile 0 wrote dt and lands
+      double tk = a.t[k];
+      const double d = a.dt[k];
+      tk = a.lands[k] ? a.t_end : tk + d;
+      const_cast<double*>(a.t)[k] = tk;
+      if (!(__longlong_as_double((long long)s0[k]) <= DBL_MAX)) atomicOr(a.status, STATUS_NONFINITE);
+      if (f.pu) atomicAdd(f.pu, (unsigned long long)n);
+      if (f.dt_used) f.dt_used[k] = d;
+      if (tk < a.t_end) atomicAdd(f.active, 1);
+    }
+  }
+}
+
+template <int EQ, class Real>
+cudaError_t step_cluster_launch(const Args1D& a, const FusedArgs& f, int C, cudaStream_t s) {
+  constexpr size_t tile = Layout1D<EQ, Real, kThreads1D, 1>::bytes;
+  constexpr size_t bytes = tile > kClusterSmem ? tile : kClusterSmem;
+  static unsigned configured = 0;  // devices whose limit is raised
+  if (const cudaError_t e = ensure_smem_limit(k_step_cluster_1d<EQ, Real>, bytes, configured))
+    return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(f.batch * C));
+  cfg.blockDim = dim3(kThreads1D);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_step_cluster_1d<EQ, Real>, a, f);
+}
+
+template <class Real>
+cudaError_t step_cluster_prec(int eq, const Args1D& a, const FusedArgs& f, int C,
+                              cudaStream_t s) {
+  return eq == HWENO_BURGERS ? step_cluster_launch<HWENO_BURGERS, Real>(a, f, C, s)
+                             : step_cluster_launch<HWENO_EULER, Real>(a, f, C, s);
 }
 
 template <class Real>

@@ -22,6 +22,7 @@ BURGERS, EULER, BUCKLEY = 0, 1, 2
 EQUATIONS = dict(burgers=BURGERS, euler=EULER, buckley=BUCKLEY)
 FP64, FP32 = 0, 1
 TILE_VARIANTS = 5  # HWENO_TILE_VARIANTS: 1D tile shapes
+CLUSTER_MAX_POINTS = 992  # HWENO_CLUSTER_MAX_POINTS: fused_small = 2
 BC = dict(periodic=0, outflow=1, reflective=2, inflow=3, dmr_bottom=4, dmr_top=5)
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
           ETIMEOUT: "ETIMEOUT", ENOTSUP: "ENOTSUP"}

@@ -1,6 +1,8 @@
-"""The fused small-instance step (one CTA per instance of at most
-HWENO_FUSED_MAX_POINTS points: wave speed, three stages and time update in
-one launch) against the tiled kernels (fused_small = 0) and the oracle. The
+"""The fused small-instance steps against the tiled kernels (fused_small =
+0) and the oracle: fused_small = 1, one CTA per instance of at most
+HWENO_FUSED_MAX_POINTS points, and fused_small = 2, one thread-block cluster
+per instance of at most HWENO_CLUSTER_MAX_POINTS points (one tile per CTA);
+both run the wave speed, three stages and time update in one launch. The
 stage code is shared; compiled into another kernel the compiler may fuse
 a*b + c*d differently, so the paths agree to rounding."""
 import numpy as np
@@ -13,6 +15,9 @@ from _util import oracle_problem
 
 pytestmark = pytest.mark.gpu
 SIZES = [4, 5, 31, 123, 124, 125, 128, 248, 249, 400, 507, 508]
+# the cluster step: up to eight 124-point tiles; ragged tile counts per batch
+SIZES_CLUSTER = SIZES + [620, 871, 991, 992]
+MODES = {1: SIZES, 2: SIZES_CLUSTER}
 
 
 @pytest.fixture(scope="module")
@@ -64,12 +69,13 @@ def _steps(hw, w, K, t_end, precision="fp64", **opts):
     return U, V, t, torch.stack(used), act, launches
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("eq", ["euler", "burgers", "buckley"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_fused_matches_tiled(hw, eq, precision):
-    w = _batch(eq, SIZES, 3)
+def test_fused_matches_tiled(hw, eq, precision, mode):
+    w = _batch(eq, MODES[mode], 3)
     K, t_end = 8, 0.01
-    f = _steps(hw, w, K, t_end, precision, fused_small=1)
+    f = _steps(hw, w, K, t_end, precision, fused_small=mode)
     g = _steps(hw, w, K, t_end, precision)
     assert f[5] == 1 and g[5] == 5          # one launch per step vs five
     ru = 1e-13 * K if precision == "fp64" else 1e-5 * K
@@ -79,9 +85,10 @@ def test_fused_matches_tiled(hw, eq, precision):
     assert f[4] == g[4]
 
 
-def test_fused_against_the_oracle(hw):
-    w = _batch("euler", SIZES, 4)
-    U, V, t, used, act, _ = _steps(hw, w, 3, 1.0, fused_small=1)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fused_against_the_oracle(hw, mode):
+    w = _batch("euler", MODES[mode], 4)
+    U, V, t, used, act, _ = _steps(hw, w, 3, 1.0, fused_small=mode)
     Ug = U.cpu().numpy()
     off = 0
     for k, n in enumerate(w.nx):
@@ -93,18 +100,46 @@ def test_fused_against_the_oracle(hw):
         off += n
 
 
-def test_larger_instances_use_the_tiled_kernels(hw):
-    w = _batch("burgers", [509, 40], 5)
-    *_, launches = _steps(hw, w, 1, 1.0, fused_small=1)
+@pytest.mark.parametrize("mode,n", [(1, 509), (2, 993)])
+def test_larger_instances_use_the_tiled_kernels(hw, mode, n):
+    w = _batch("burgers", [n, 40], 5)
+    *_, launches = _steps(hw, w, 1, 1.0, fused_small=mode)
     assert launches == 5
 
 
-def test_config_1_to_final_time(hw):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_finished_instances_do_not_move(hw, mode):
+    """Instances whose time has reached t_end keep their state, report
+    dt_used = 0 and are not counted active; the others step as in the tiled
+    path."""
+    w = _batch("euler", [40, 400, 700 if mode == 2 else 300], 6)
+    s = hw.Solver.from_workload(w, fused_small=mode)
+    g = hw.Solver.from_workload(w)
+    t_end = 0.05
+    res = []
+    for solver in (s, g):
+        U = torch.from_numpy(w.U).cuda()
+        V = torch.from_numpy(w.V).cuda()
+        t = torch.tensor([0.0, t_end, 0.0], dtype=torch.float64, device="cuda")
+        d = torch.empty(3, dtype=torch.float64, device="cuda")
+        solver.step(U, V, None, t, t_end, d)
+        solver.sync_status()
+        res.append((U.cpu(), t.cpu(), d.cpu(), solver.active_instances()))
+    (Uf, tf, df, af), (Ug, tg, dg, ag) = res
+    off = 3 * 40
+    n1 = 3 * 400
+    assert torch.equal(Uf[off:off + n1], torch.from_numpy(w.U)[off:off + n1])
+    assert float(df[1]) == 0.0 and float(tf[1]) == t_end
+    assert float((Uf - Ug).abs().max()) <= 1e-13 * float(Ug.abs().max())
+    assert torch.allclose(tf, tg, rtol=1e-14, atol=0) and af == ag == 2
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_config_1_to_final_time(hw, mode):
     """Example 3.1 / config 1 (Burgers N = 400, T = 1.5/pi, shock) through the
-    fused path against the oracle, shocked-run tolerance."""
-    import math
+    fused paths against the oracle, shocked-run tolerance."""
     w = W.burgers1d_sine(400)
-    s = hw.Solver.from_workload(w, fused_small=1)
+    s = hw.Solver.from_workload(w, fused_small=mode)
     U = torch.from_numpy(w.U).cuda()
     V = torch.from_numpy(w.V).cuda()
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
