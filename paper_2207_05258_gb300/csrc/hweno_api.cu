@@ -356,8 +356,7 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
     f.batch = c->batch;
     prof_begin(c, s);
     if (cluster) {
-      const int C = (int)((c->max_n + kTile1D - 1) / kTile1D);
-      if ((e = launch_step_cluster_1d(c->eq, c->fp32, a, f, C, s)))
+      if ((e = launch_step_cluster_1d(c->eq, c->fp32, a, f, (int)c->max_n, s)))
         return cuda_fail(c, e, "cluster step");
     } else if ((e = launch_step_small_1d(c->eq, c->fp32, a, f, s))) {
       return cuda_fail(c, e, "fused step");

@@ -305,22 +305,25 @@ inline cudaError_t launch_step_small_1d(int eq, bool fp32, const Args1D& a, cons
 }
 
 // Fused step on thread-block clusters (stage1d_impl.cuh, k_step_cluster_1d):
-// one cluster of C <= kClusterMax CTAs per instance, one kTile1D-point tile
-// per CTA, each CTA alone on its SM (kClusterSmem of shared memory).
+// one cluster per instance of at most kClusterMax * kTile1D points, one tile
+// per CTA, each CTA alone on its SM (kClusterSmem of shared memory); max_n is
+// the largest instance of the batch.
 constexpr int kClusterMax = 8;
 constexpr size_t kClusterSmem = 116 * 1024;
+// Latency form of the cluster step: 28-point tiles, up to 16 CTAs per cluster
+constexpr int kSplitTile = 28, kSplitMax = 16;
 static_assert(kClusterMax * kTile1D == HWENO_CLUSTER_MAX_POINTS, "cluster step size");
-cudaError_t launch_step_cluster_1d_f64(int eq, const Args1D& a, const FusedArgs& f, int C,
+cudaError_t launch_step_cluster_1d_f64(int eq, const Args1D& a, const FusedArgs& f, int max_n,
                                        cudaStream_t s);
-cudaError_t launch_step_cluster_1d_f32(int eq, const Args1D& a, const FusedArgs& f, int C,
+cudaError_t launch_step_cluster_1d_f32(int eq, const Args1D& a, const FusedArgs& f, int max_n,
                                        cudaStream_t s);
-cudaError_t launch_step_cluster_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f, int C,
+cudaError_t launch_step_cluster_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f, int max_n,
                                       cudaStream_t s);
 inline cudaError_t launch_step_cluster_1d(int eq, bool fp32, const Args1D& a, const FusedArgs& f,
-                                          int C, cudaStream_t s) {
-  if (eq == HWENO_BUCKLEY) return launch_step_cluster_1d_bl(fp32, a, f, C, s);
-  return fp32 ? launch_step_cluster_1d_f32(eq, a, f, C, s)
-              : launch_step_cluster_1d_f64(eq, a, f, C, s);
+                                          int max_n, cudaStream_t s) {
+  if (eq == HWENO_BUCKLEY) return launch_step_cluster_1d_bl(fp32, a, f, max_n, s);
+  return fp32 ? launch_step_cluster_1d_f32(eq, a, f, max_n, s)
+              : launch_step_cluster_1d_f64(eq, a, f, max_n, s);
 }
 
 cudaError_t launch_run_1d_f64(int eq, int variant, const Args1D& a, const PersistArgs& p,

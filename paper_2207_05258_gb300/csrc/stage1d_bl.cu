@@ -30,10 +30,10 @@ cudaError_t launch_step_small_1d_bl(bool fp32, const Args1D& a, const FusedArgs&
               : step_small_launch<HWENO_BUCKLEY, double>(a, f, s);
 }
 
-cudaError_t launch_step_cluster_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f, int C,
+cudaError_t launch_step_cluster_1d_bl(bool fp32, const Args1D& a, const FusedArgs& f, int max_n,
                                       cudaStream_t s) {
-  return fp32 ? step_cluster_launch<HWENO_BUCKLEY, float>(a, f, C, s)
-              : step_cluster_launch<HWENO_BUCKLEY, double>(a, f, C, s);
+  return fp32 ? step_cluster_launch<HWENO_BUCKLEY, float>(a, f, max_n, s)
+              : step_cluster_launch<HWENO_BUCKLEY, double>(a, f, max_n, s);
 }
 
 int run_1d_ctas_per_sm_bl(bool fp32, int variant) {

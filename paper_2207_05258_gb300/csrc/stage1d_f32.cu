@@ -26,9 +26,9 @@ cudaError_t launch_step_small_1d_f32(int eq, const Args1D& a, const FusedArgs& f
   return step_small_prec<float>(eq, a, f, s);
 }
 
-cudaError_t launch_step_cluster_1d_f32(int eq, const Args1D& a, const FusedArgs& f, int C,
+cudaError_t launch_step_cluster_1d_f32(int eq, const Args1D& a, const FusedArgs& f, int max_n,
                                        cudaStream_t s) {
-  return step_cluster_prec<float>(eq, a, f, C, s);
+  return step_cluster_prec<float>(eq, a, f, max_n, s);
 }
 
 }  // namespace hweno

@@ -704,6 +704,327 @@ cudaError_t step_small_launch(const Args1D& a, const FusedArgs& f, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------------
+// Latency form of one stage for the cluster step: a kSplitTile-point tile
+// (32 loaded points, one per lane) on four warps, which sit on the SM's four
+// sub-partitions. The FP64 cost of a warp instruction does not depend on
+// how many lanes are active, so a stage's time is set by the longest
+// instruction stream of one warp; here the work of a point is divided over
+// the warps instead of the points: warp 0 the "+" reconstructions of the
+// interfaces, warp 1 the "-" ones, warp 2 the limiter, warp 3 the derivative
+// fluxes; warp 0 then combines the sides and updates the points.
+// ---------------------------------------------------------------------------
+template <int EQ, class Real>
+struct SplitLayout {
+  static constexpr int M = Dim1<EQ>::M;
+  static constexpr int P = kSplitTile;
+  static constexpr int NP = P + 4;  // loaded points s-2 .. s+P+1
+  static constexpr int NF = P + 1;  // interfaces
+  static constexpr int NE = EQ == HWENO_EULER ? 4 : 0;
+  // sU, sV, sFp, sFm, sHp, sHm [M][NP]; sE [NE][NP]; side numerators and
+  // denominators [2][M][NF] each; sD, sF [M][NF]; sVt [M][P]
+  static constexpr size_t bytes =
+      sizeof(Real) * ((size_t)(6 * M + NE) * NP + (size_t)6 * M * NF + (size_t)M * P);
+};
+static_assert(kSplitTile + 4 == 32, "one loaded point per lane");
+
+// One side of an interface flux as a deferred quotient: sd = 0 the "+"
+// reconstruction from f^+, H^+ at i-1, i, i+1; sd = 1 the "-" one from
+// f^-, H^- at i, i+1, i+2 (the mirror image: reversed, H negated).
+template <class Real>
+__device__ __forceinline__ Frac<Real> side_frac(int sd, Real f0, Real f1, Real f2, Real H0,
+                                               Real H1, Real H2, const Weights<Real>& w) {
+  const Cand<Real> c = candidates(sd ? f2 : f0, f1, sd ? f0 : f2, sd ? -H2 : H0, sd ? -H1 : H1,
+                                  sd ? -H0 : H2, w.eps);
+  if constexpr (std::is_same<Real, double>::value) {
+    Real n, d;
+    combine_nd(c, w, n, d);
+    return Frac<Real>{n, d};
+  } else {
+    return Frac<Real>{combine_direct(c, w), Real(1)};
+  }
+}
+
+// The two sides of one field summed as in interface_flux_frac.
+template <class Real>
+__device__ __forceinline__ Frac<Real> sides_sum(Real na, Real da, Real nb, Real db) {
+  if constexpr (std::is_same<Real, double>::value) return Frac<Real>{na * db + nb * da, da * db};
+  else return Frac<Real>{na + nb, Real(1)};
+}
+
+template <int EQ, class Real, int MODE>
+__device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO& io, const int k,
+                                                 const int s) {
+  using Lay = SplitLayout<EQ, Real>;
+  constexpr int M = Lay::M;
+  constexpr int NP = Lay::NP;
+  constexpr int NF = Lay::NF;
+  constexpr int P = Lay::P;
+  constexpr bool EUL = EQ == HWENO_EULER;
+  extern __shared__ __align__(16) unsigned char smem1d[];
+  Real* base = reinterpret_cast<Real*>(smem1d);
+  Real(*sU)[NP] = reinterpret_cast<Real(*)[NP]>(base);
+  Real(*sV)[NP] = sU + M;
+  Real(*sFp)[NP] = sV + M;
+  Real(*sFm)[NP] = sFp + M;
+  Real(*sHp)[NP] = sFm + M;
+  Real(*sHm)[NP] = sHp + M;
+  Real(*sE)[NP] = sHm + M;
+  Real(*sSn)[M][NF] = reinterpret_cast<Real(*)[M][NF]>(base + (6 * M + Lay::NE) * NP);  // [2]
+  Real(*sSd)[M][NF] = sSn + 2;                                                        // [2]
+  Real(*sD)[NF] = reinterpret_cast<Real(*)[NF]>(sSd + 2);
+  Real(*sF)[NF] = sD + M;
+  Real(*sVt)[P] = reinterpret_cast<Real(*)[P]>(sF + M);
+  __shared__ double s_dt;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.inst_n[k];
+  if (a.skip_done && !(a.t[k] < a.t_end)) return;
+  const int np = min(P, n - s);
+  const long long off = a.inst_off[k] * M;
+  const Real* geo = pick<Real>(a.inst_geo, a.inst_geof) + 3 * k;
+  const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
+  const Real alpha = Real(io.alpha_in[k]);
+  const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+  const Real gm1 = gam - Real(1);
+  const Weights<Real> w = weights_from(pick<Real>(a.sp.wd, a.sp.wf));
+
+  if (threadIdx.x == 0) {  // time step (as stage_tile)
+    double dt = 0.0;
+    if constexpr (MODE == MODE_STAGE1) {
+      int lands = 0;
+      dt = a.dt_in ? a.dt_in[k]
+                   : time_step(a.sp, io.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
+      if (s == 0) { a.dt[k] = dt; a.lands[k] = lands; }
+    } else {
+      dt = a.dt[k];
+    }
+    s_dt = dt;
+  }
+
+  // A (warp 0): the tile with ghosts, point fluxes and splitting; lane g is
+  // point s - 2 + g
+  if (warp == 0 && lane < np + 4) {
+    const Real* U = static_cast<const Real*>(io.U) + off;
+    const Real* V = static_cast<const Real*>(io.V) + off;
+    const Real hdx = Real(0.5) * dx;
+    const int g = lane;
+    int kind;
+    const int src = map_1d(s - 2 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
+    Real u[M], v[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      if (kind == 2) {
+        u[c] = Real(a.sp.inflow[c]);
+        v[c] = Real(0);
+      } else {
+        u[c] = U[(long long)c * n + src];
+        v[c] = V[(long long)c * n + src];
+        if (kind == 1) { const Real sg = Real(refl_sign<EQ>(c)); u[c] *= sg; v[c] *= -sg; }
+      }
+      sU[c][g] = u[c];
+      sV[c][g] = v[c];
+    }
+    Real F[M], H[M];
+    if constexpr (EQ == HWENO_BURGERS) {
+      F[0] = Real(0.5) * u[0] * u[0];
+      H[0] = u[0] * v[0];
+    } else if constexpr (EQ == HWENO_BUCKLEY) {
+      Real df;
+      buckley_f(u[0], F[0], df);
+      H[0] = df * v[0];
+    } else {
+      const Real rr = rsq(u[0]);
+      const Real ir = rr * rr;
+      const Real vel = u[1] * ir;
+      const Real p = gm1 * (u[2] - Real(0.5) * u[1] * vel);
+      const Real Ep = u[2] + p;
+      F[0] = u[1];
+      F[1] = u[1] * vel + p;
+      F[2] = Ep * vel;
+      const Real dvel = (v[1] - vel * v[0]) * ir;
+      const Real dp = gm1 * (v[2] - vel * v[1] + Real(0.5) * vel * vel * v[0]);
+      H[0] = v[1];
+      H[1] = v[1] * vel + u[1] * dvel + dp;
+      H[2] = (v[2] + dp) * vel + Ep * dvel;
+      sE[0][g] = u[0] * rr;
+      sE[1][g] = vel;
+      sE[2][g] = Ep * ir;
+      sE[3][g] = gam * p * ir;
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
+      sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
+      sHp[c][g] = hdx * (H[c] + alpha * v[c]);
+      sHm[c][g] = hdx * (H[c] - alpha * v[c]);
+    }
+  }
+  __syncthreads();
+
+  // B: warps 0 / 1 the "+" / "-" side of interface x_{s+j-1/2}, j = lane
+  // (left point at loaded index j + 1); warp 2 the limited derivative of
+  // point j = lane; warp 3 the derivative flux of interface j = lane
+  Eigen<Real, 3> e{};  // Euler: eigenvectors at the interface (warps 0, 1)
+  if (warp < 2) {
+    const int sd = warp, j = lane, gl = j + 1, b = gl - 1 + sd;  // first stencil point
+    if (j <= np) {
+      Real(*SF)[NP] = sd ? sFm : sFp;
+      Real(*SH)[NP] = sd ? sHm : sHp;
+      if constexpr (!EUL) {
+        const Frac<Real> fr = side_frac(sd, SF[0][b], SF[0][b + 1], SF[0][b + 2], SH[0][b],
+                                        SH[0][b + 1], SH[0][b + 2], w);
+        sSn[sd][0][j] = fr.n;
+        sSd[sd][0][j] = fr.d;
+      } else {
+        Real uu, HH, cc;
+        if (a.sp.eig_avg == 0) {  // Roe average of U_i, U_{i+1}
+          const Real sl = sE[0][gl], sr = sE[0][gl + 1];
+          const Real is = Real(1) / (sl + sr);
+          uu = (sl * sE[1][gl] + sr * sE[1][gl + 1]) * is;
+          HH = (sl * sE[2][gl] + sr * sE[2][gl + 1]) * is;
+        } else {  // arithmetic mean state
+          const Real r = Real(0.5) * (sU[0][gl] + sU[0][gl + 1]);
+          const Real mo = Real(0.5) * (sU[1][gl] + sU[1][gl + 1]);
+          const Real E = Real(0.5) * (sU[2][gl] + sU[2][gl + 1]);
+          const Real ir = Real(1) / r;
+          uu = mo * ir;
+          HH = (E + gm1 * (E - Real(0.5) * mo * uu)) * ir;
+        }
+        Real ic;
+        sound_speed(gm1 * (HH - Real(0.5) * uu * uu), cc, ic);
+        euler_eigen<Real, 3>(0, uu, Real(0), HH, cc, ic, gm1, e);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const Real l0 = e.L[q][0], l1 = e.L[q][1], l2 = e.L[q][2];
+          auto pj = [&](Real (*A)[NP], int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
+          const Frac<Real> fr = side_frac(sd, pj(SF, b), pj(SF, b + 1), pj(SF, b + 2), pj(SH, b),
+                                          pj(SH, b + 1), pj(SH, b + 2), w);
+          sSn[sd][q][j] = fr.n;
+          sSd[sd][q][j] = fr.d;
+        }
+      }
+    }
+  } else if (warp == 2) {
+    const int j = lane, g = j + 2;
+    if (j < np) {
+      Real vt[M];
+      if (a.sp.limiter == 0) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) vt[c] = sV[c][g];
+      } else if (!EUL || a.sp.limiter == 2) {
+#pragma unroll
+        for (int c = 0; c < M; ++c)
+          vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
+                                     dx * sV[c][g + 1], w) * idx;
+      } else if constexpr (EUL) {
+        Real cg, icg;
+        sound_speed(sE[3][g], cg, icg);
+        Eigen<Real, 3> el;
+        euler_eigen<Real, 3>(0, sE[1][g], Real(0), sE[2][g], cg, icg, gm1, el);
+        Frac<Real> zr[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const Real l0 = el.L[q][0], l1q = el.L[q][1], l2q = el.L[q][2];
+          auto pj = [&](Real (*A)[NP], int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
+          zr[q] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
+                                          dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
+        }
+        Real z[3];
+        resolve2(zr[0], zr[1], z[0], z[1]);
+        z[2] = resolve1(zr[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          vt[c] = (el.R[c][0] * z[0] + el.R[c][1] * z[1] + el.R[c][2] * z[2]) * idx;
+      }
+#pragma unroll
+      for (int c = 0; c < M; ++c) sVt[c][j] = vt[c];
+    }
+  } else {
+    const int j = lane, gl = j + 1;
+    if (j <= np)
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        sD[c][j] = derivative_flux(sFp[c][gl - 1], sFp[c][gl], sFp[c][gl + 1], sHp[c][gl - 1],
+                                   sHp[c][gl], sHp[c][gl + 1], sFm[c][gl], sFm[c][gl + 1],
+                                   sFm[c][gl + 2], sHm[c][gl], sHm[c][gl + 1], sHm[c][gl + 2]);
+  }
+  __syncthreads();
+
+  // C (warp 0): interface fluxes from the two sides, then the points
+  if (warp != 0) return;
+  {
+    const int j = lane;
+    if (j <= np) {
+      if constexpr (!EUL) {
+        sF[0][j] = resolve1(sides_sum(sSn[0][0][j], sSd[0][0][j], sSn[1][0][j], sSd[1][0][j]));
+      } else {
+        Frac<Real> fr[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          fr[q] = sides_sum(sSn[0][q][j], sSd[0][q][j], sSn[1][q][j], sSd[1][q][j]);
+        Real f[3];
+        resolve2(fr[0], fr[1], f[0], f[1]);
+        f[2] = resolve1(fr[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sF[c][j] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
+      }
+    }
+  }
+  __syncwarp();
+  const Real rdt = Real(s_dt);
+  const bool want_alpha = io.alpha_out != nullptr;  // uniform
+  Real amax = Real(0);
+  bool bad = false;
+  const int j = lane;
+  if (j < np) {
+    const int g = j + 2;
+    Real l1[M], l2[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      l1[c] = -(sF[c][j + 1] - sF[c][j]) * idx;
+      l2[c] = -(sD[c][j + 1] - sD[c][j]) * idx2;
+    }
+    const long long base_q = off + s + j;
+    Real un[M], vn[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      const long long q = base_q + (long long)c * n;
+      const Real vt = sVt[c][j];
+      if constexpr (MODE == MODE_STAGE1) {
+        un[c] = sU[c][g] + rdt * l1[c];
+        vn[c] = vt + rdt * l2[c];
+        static_cast<Real*>(io.Vt0out)[q] = vt;
+      } else if constexpr (MODE == MODE_STAGE2) {
+        const Real u0 = static_cast<const Real*>(io.U0)[q];
+        const Real v0 = static_cast<const Real*>(io.Vt0)[q];
+        un[c] = Real(0.75) * u0 + Real(0.25) * (sU[c][g] + rdt * l1[c]);
+        vn[c] = Real(0.75) * v0 + Real(0.25) * (vt + rdt * l2[c]);
+      } else {
+        const Real u0 = static_cast<const Real*>(io.U0)[q];
+        const Real v0 = static_cast<const Real*>(io.Vt0)[q];
+        un[c] = Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * (sU[c][g] + rdt * l1[c]);
+        vn[c] = Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * (vt + rdt * l2[c]);
+      }
+      static_cast<Real*>(io.Uout)[q] = un[c];
+      static_cast<Real*>(io.Vout)[q] = vn[c];
+    }
+    if (want_alpha) {
+      const Real sp = wave_speed<EQ>(un, gam, pick<Real>(a.sp.wd, a.sp.wf)[10]);
+      bad = !(sp <= real_max<Real>());
+      amax = sp;
+    }
+  }
+  if (want_alpha) {
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      if (bad) atomicOr(a.status, STATUS_NONFINITE);
+      atomicMax(&io.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fused step of small instances on thread-block clusters (fused_small = 2):
 // one cluster of C CTAs per instance, CTA r of the cluster holding the
 // kTile1D-point tile that starts at r * kTile1D, each CTA alone on its SM
@@ -713,12 +1034,18 @@ cudaError_t step_small_launch(const Args1D& a, const FusedArgs& f, cudaStream_t 
 // stage's global writes (state, alpha slots) visible to the next. Every CTA
 // passes the same five barriers whatever its share of the instance.
 // ---------------------------------------------------------------------------
-template <int EQ, class Real>
+template <int EQ, class Real, int MODE, bool SPLIT>
+__device__ __forceinline__ void cluster_stage(const Args1D& a, const StageIO& io, int k, int s) {
+  if constexpr (SPLIT) stage_tile_split<EQ, Real, MODE>(a, io, k, s);
+  else stage_tile<EQ, Real, MODE, kThreads1D, 1>(a, io, k, s);
+}
+
+template <int EQ, class Real, bool SPLIT>
 __global__ void __launch_bounds__(kThreads1D)
 k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ FusedArgs f) {
   namespace cg = cooperative_groups;
   constexpr int M = Dim1<EQ>::M;
-  constexpr int P = kTile1D;
+  constexpr int P = SPLIT ? kSplitTile : kTile1D;
   __shared__ Real red[kThreads1D / 32];
   __shared__ double part;
   cg::cluster_group cl = cg::this_cluster();
@@ -761,16 +1088,16 @@ k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ Fuse
   StageIO io = io_of(a);
   io.Uout = f.U1; io.Vout = f.V1; io.Vt0out = f.Vt0;
   io.alpha_in = reinterpret_cast<const double*>(s0); io.alpha_out = s1;
-  if (has) stage_tile<EQ, Real, MODE_STAGE1, kThreads1D, 1>(a, io, k, s);
+  if (has) cluster_stage<EQ, Real, MODE_STAGE1, SPLIT>(a, io, k, s);
   cl.sync();
   io.U = f.U1; io.V = f.V1; io.U0 = a.U; io.Vt0 = f.Vt0; io.Uout = f.U2; io.Vout = f.V2;
   io.Vt0out = nullptr;
   io.alpha_in = reinterpret_cast<const double*>(s1); io.alpha_out = s2;
-  if (has) stage_tile<EQ, Real, MODE_STAGE2, kThreads1D, 1>(a, io, k, s);
+  if (has) cluster_stage<EQ, Real, MODE_STAGE2, SPLIT>(a, io, k, s);
   cl.sync();
   io.U = f.U2; io.V = f.V2; io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V);
   io.alpha_in = reinterpret_cast<const double*>(s2); io.alpha_out = nullptr;
-  if (has) stage_tile<EQ, Real, MODE_STAGE3, kThreads1D, 1>(a, io, k, s);
+  if (has) cluster_stage<EQ, Real, MODE_STAGE3, SPLIT>(a, io, k, s);
   cl.sync();  // every CTA is past its reads of t[k]
   if (rank == 0 && threadIdx.x == 0) {
     if (!live) {  // finished: nothing moves (as k_finalize)
@@ -788,13 +1115,26 @@ k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ Fuse
   }
 }
 
-template <int EQ, class Real>
-cudaError_t step_cluster_launch(const Args1D& a, const FusedArgs& f, int C, cudaStream_t s) {
-  constexpr size_t tile = Layout1D<EQ, Real, kThreads1D, 1>::bytes;
+// Launch on clusters of C CTAs; returns cudaErrorNotSupported (nothing
+// launched) when the device cannot hold such a cluster.
+template <int EQ, class Real, bool SPLIT>
+cudaError_t step_cluster_try(const Args1D& a, const FusedArgs& f, int C, cudaStream_t s) {
+  constexpr size_t tile =
+      SPLIT ? SplitLayout<EQ, Real>::bytes : Layout1D<EQ, Real, kThreads1D, 1>::bytes;
   constexpr size_t bytes = tile > kClusterSmem ? tile : kClusterSmem;
+  auto kern = k_step_cluster_1d<EQ, Real, SPLIT>;
   static unsigned configured = 0;  // devices whose limit is raised
-  if (const cudaError_t e = ensure_smem_limit(k_step_cluster_1d<EQ, Real>, bytes, configured))
-    return e;
+  if (const cudaError_t e = ensure_smem_limit(kern, bytes, configured)) return e;
+  static unsigned nonportable = 0;  // devices allowed clusters above 8
+  int dev = 0;
+  if (const cudaError_t e = cudaGetDevice(&dev)) return e;
+  const unsigned bit = dev < 32 ? 1u << dev : 0u;
+  if (C > 8 && !(nonportable & bit)) {
+    if (const cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
+      return e;
+    nonportable |= bit;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(f.batch * C));
   cfg.blockDim = dim3(kThreads1D);
@@ -807,14 +1147,38 @@ cudaError_t step_cluster_launch(const Args1D& a, const FusedArgs& f, int C, cuda
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_step_cluster_1d<EQ, Real>, a, f);
+  // whether a cluster of this size fits, once per device and size
+  static signed char fits[32][kSplitMax + 1] = {};  // 0 unknown, 1 yes, -1 no
+  signed char& ok = fits[dev < 32 ? dev : 0][C];
+  if (ok == 0) {
+    int clusters = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) { cudaGetLastError(); clusters = 0; }
+    ok = clusters > 0 ? 1 : -1;
+  }
+  if (ok < 0) return cudaErrorNotSupported;
+  return cudaLaunchKernelEx(&cfg, kern, a, f);
+}
+
+// The cluster step: for instances of at most kSplitMax * kSplitTile points
+// the latency form (28-point tiles, the work of a point over four warps) when
+// the device holds such clusters, else 124-point tiles.
+template <int EQ, class Real>
+cudaError_t step_cluster_launch(const Args1D& a, const FusedArgs& f, int max_n, cudaStream_t s) {
+  const int Cs = (max_n + kSplitTile - 1) / kSplitTile;
+  if (Cs <= kSplitMax) {
+    const cudaError_t e = step_cluster_try<EQ, Real, true>(a, f, Cs, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  const int C = (max_n + kTile1D - 1) / kTile1D;
+  return step_cluster_try<EQ, Real, false>(a, f, C, s);
 }
 
 template <class Real>
-cudaError_t step_cluster_prec(int eq, const Args1D& a, const FusedArgs& f, int C,
+cudaError_t step_cluster_prec(int eq, const Args1D& a, const FusedArgs& f, int max_n,
                               cudaStream_t s) {
-  return eq == HWENO_BURGERS ? step_cluster_launch<HWENO_BURGERS, Real>(a, f, C, s)
-                             : step_cluster_launch<HWENO_EULER, Real>(a, f, C, s);
+  return eq == HWENO_BURGERS ? step_cluster_launch<HWENO_BURGERS, Real>(a, f, max_n, s)
+                             : step_cluster_launch<HWENO_EULER, Real>(a, f, max_n, s);
 }
 
 template <class Real>

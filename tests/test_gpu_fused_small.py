@@ -17,7 +17,11 @@ pytestmark = pytest.mark.gpu
 SIZES = [4, 5, 31, 123, 124, 125, 128, 248, 249, 400, 507, 508]
 # the cluster step: up to eight 124-point tiles; ragged tile counts per batch
 SIZES_CLUSTER = SIZES + [620, 871, 991, 992]
-MODES = {1: SIZES, 2: SIZES_CLUSTER}
+# instances of at most 448 points: the cluster step's latency form (28-point
+# tiles, up to 16 per cluster, the work of a point over four warps)
+SIZES_SPLIT = [4, 5, 27, 28, 29, 31, 56, 57, 124, 125, 248, 400, 447, 448]
+MODES = {1: SIZES, 2: SIZES_CLUSTER, 3: SIZES_SPLIT}
+FUSED = {1: 1, 2: 2, 3: 2}  # option value of each case
 
 
 @pytest.fixture(scope="module")
@@ -69,13 +73,13 @@ def _steps(hw, w, K, t_end, precision="fp64", **opts):
     return U, V, t, torch.stack(used), act, launches
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("eq", ["euler", "burgers", "buckley"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_matches_tiled(hw, eq, precision, mode):
     w = _batch(eq, MODES[mode], 3)
     K, t_end = 8, 0.01
-    f = _steps(hw, w, K, t_end, precision, fused_small=mode)
+    f = _steps(hw, w, K, t_end, precision, fused_small=FUSED[mode])
     g = _steps(hw, w, K, t_end, precision)
     assert f[5] == 1 and g[5] == 5          # one launch per step vs five
     ru = 1e-13 * K if precision == "fp64" else 1e-5 * K
@@ -85,16 +89,18 @@ def test_fused_matches_tiled(hw, eq, precision, mode):
     assert f[4] == g[4]
 
 
-@pytest.mark.parametrize("mode", [1, 2])
-def test_fused_against_the_oracle(hw, mode):
-    w = _batch("euler", MODES[mode], 4)
-    U, V, t, used, act, _ = _steps(hw, w, 3, 1.0, fused_small=mode)
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("eq", ["euler", "burgers"])
+def test_fused_against_the_oracle(hw, mode, eq):
+    w = _batch(eq, MODES[mode], 4)
+    m = 3 if eq == "euler" else 1
+    U, V, t, used, act, _ = _steps(hw, w, 3, 1.0, fused_small=FUSED[mode])
     Ug = U.cpu().numpy()
     off = 0
     for k, n in enumerate(w.nx):
         Uk, Vk = w.instance(k)
         Uo, _, _, to, _ = O.run(oracle_problem(w, nx=n), Uk, Vk, None, 0.0, 1.0, max_steps=3)
-        g = Ug[3 * off:3 * (off + n)].reshape(3, n)
+        g = Ug[m * off:m * (off + n)].reshape(m, n)
         assert np.max(np.abs(g - Uo)) <= 1e-12 * np.max(np.abs(Uo)), (k, n)
         assert abs(float(t[k]) - to) <= 1e-14 * to
         off += n
@@ -107,13 +113,13 @@ def test_larger_instances_use_the_tiled_kernels(hw, mode, n):
     assert launches == 5
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_finished_instances_do_not_move(hw, mode):
     """Instances whose time has reached t_end keep their state, report
     dt_used = 0 and are not counted active; the others step as in the tiled
     path."""
     w = _batch("euler", [40, 400, 700 if mode == 2 else 300], 6)
-    s = hw.Solver.from_workload(w, fused_small=mode)
+    s = hw.Solver.from_workload(w, fused_small=FUSED[mode])
     g = hw.Solver.from_workload(w)
     t_end = 0.05
     res = []
@@ -135,7 +141,7 @@ def test_finished_instances_do_not_move(hw, mode):
 
 
 @pytest.mark.parametrize("mode", [1, 2])
-def test_config_1_to_final_time(hw, mode):
+def test_config_1_to_final_time(hw, mode):  # N = 400: mode 2 takes the latency form
     """Example 3.1 / config 1 (Burgers N = 400, T = 1.5/pi, shock) through the
     fused paths against the oracle, shocked-run tolerance."""
     w = W.burgers1d_sine(400)
