@@ -137,10 +137,14 @@ typedef struct hweno_options {
                        2 = when every instance has at most
                        HWENO_CLUSTER_MAX_POINTS points, one launch per step
                        on thread-block clusters: one cluster per instance,
-                       one 124-point tile per CTA, each CTA on an SM of its
-                       own (it reserves 116 KB of shared memory), the stages
-                       separated by cluster barriers. Meant for a few small
-                       instances, where the latency of a step matters. */
+                       one tile per CTA, each CTA on an SM of its own (it
+                       reserves 116 KB of shared memory), the stages
+                       separated by cluster barriers. Up to 448 points the
+                       tiles have 28 points and the work of a point is
+                       divided over the CTA's four warps (up to 16 CTAs per
+                       cluster, where the device allows it); otherwise 124
+                       points (up to 8). Meant for a few small instances,
+                       where the latency of a step matters. */
   int adj_frozen_weights; /* hweno_adjoint_step: 0 = differentiate the
                        nonlinear weights of the reconstruction and the
                        limiter; 1 = hold them at their forward values (the
