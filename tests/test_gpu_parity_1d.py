@@ -338,3 +338,13 @@ def test_fp32_error_against_fp64_oracle(hw, record_property):
         l1 = np.mean(np.abs(GU[k][0] - o[0][k][0])) / np.mean(np.abs(o[0][k][0]))
         print("fp32 Riemann instance %d (N=%d) T=0.05: rel L1(rho) = %.3e" % (k, w.nx[k], l1))
         assert l1 < 1e-4, (k, l1)
+
+
+@pytest.mark.parametrize("opts", [dict(fused_small=3), dict(fused_small=-1), dict(tile_variant=5),
+                                  dict(adj_frozen_weights=2), dict(limiter=3), dict(dt_mode=3),
+                                  dict(eig_avg=2), dict(cfl=0.0), dict(eps=-1.0)])
+def test_invalid_options_are_rejected(hw, opts):
+    w = euler_batch([64], 43, "riemann")
+    with pytest.raises(hw.HwenoError) as e:
+        hw.Solver.from_workload(w, **opts)
+    assert e.value.code == hw.EINVAL
