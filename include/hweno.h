@@ -143,8 +143,9 @@ typedef struct hweno_options {
                        tiles have 28 points and the work of a point is
                        divided over the CTA's four warps (up to 16 CTAs per
                        cluster, where the device allows it); otherwise 124
-                       points (up to 8). Meant for a few small instances,
-                       where the latency of a step matters. */
+                       points (up to 8); a device that cannot hold the
+                       cluster gets the tiled kernels. Meant for a few small
+                       instances, where the latency of a step matters. */
   int adj_frozen_weights; /* hweno_adjoint_step: 0 = differentiate the
                        nonlinear weights of the reconstruction and the
                        limiter; 1 = hold them at their forward values (the

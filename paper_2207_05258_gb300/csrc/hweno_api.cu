@@ -355,15 +355,19 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
     f.alpha = c->d_alpha; f.dt_used = dt_used; f.active = c->d_active; f.pu = c->d_pu;
     f.batch = c->batch;
     prof_begin(c, s);
+    bool launched = true;
     if (cluster) {
-      if ((e = launch_step_cluster_1d(c->eq, c->fp32, a, f, (int)c->max_n, s)))
-        return cuda_fail(c, e, "cluster step");
+      e = launch_step_cluster_1d(c->eq, c->fp32, a, f, (int)c->max_n, s);
+      if (e == cudaErrorNotSupported) launched = false;  // no such cluster here: tiled kernels
+      else if (e) return cuda_fail(c, e, "cluster step");
     } else if ((e = launch_step_small_1d(c->eq, c->fp32, a, f, s))) {
       return cuda_fail(c, e, "fused step");
     }
-    prof_end(c, s, 1);
-    c->launches = c->step_launches = 1;
-    return HWENO_OK;
+    if (launched) {
+      prof_end(c, s, 1);
+      c->launches = c->step_launches = 1;
+      return HWENO_OK;
+    }
   }
   if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)) ||
       (e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)))
