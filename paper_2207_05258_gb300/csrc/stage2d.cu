@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <cfloat>
 
+#include <cuda_pipeline.h>
+
 #include "hweno.h"
 #include "flux2d.cuh"
 #include "hweno_math.cuh"
@@ -312,7 +314,12 @@ struct YLayout {
   // per-point arrays: U, W, G+, G-, T+, T-, xi (M each), eigen data (5, Euler)
   static constexpr int NQ = 7 * M + (EUL ? 5 : 0);
   static constexpr int NI = 3 * M;                                  // g-hat, theta-hat, xi-hat
-  static constexpr size_t bytes = sizeof(Real) * ((size_t)NQ * P + (size_t)NI * RF * C) + 64;
+  // FP32: the epilogue's global inputs (x parts of L, v~, U^n, v~^n, w~^n),
+  // fetched asynchronously at the start, one row of kRowsY2D x C per field
+  static constexpr int NPRE = std::is_same<Real, float>::value ? 7 * M : 0;
+  static constexpr int PE = kRowsY2D * C;
+  static constexpr size_t bytes =
+      sizeof(Real) * ((size_t)NQ * P + (size_t)NI * RF * C + (size_t)NPRE * PE) + 64;
 };
 
 template <int EQ, class Real, int MODE>
@@ -336,6 +343,34 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
   const long long N = (long long)nx * ny;
   const int i0 = blockIdx.x * C, j0 = blockIdx.y * kRowsY2D;
   const int ncol = min(C, nx - i0), nrow = min(kRowsY2D, ny - j0);
+  static_assert(kRowsY2D * C <= kThreads2D, "one epilogue point per thread");
+  // FP32: start the copies of this thread's epilogue inputs now, so that
+  // their latency hides behind the loads and the interface phase
+  Real* sPre = sI + (size_t)Lay::NI * Lay::RF * C;  // [NPRE][PE]
+  if constexpr (Lay::NPRE > 0) {
+    const int k = threadIdx.x, r = k / C, col = k % C;
+    if (k < Lay::PE && col < ncol && r < nrow) {
+      const long long q = (long long)(j0 + r) * nx + i0 + col;
+      const Real* LX = static_cast<const Real*>(a.LX);
+      const Real* VT = static_cast<const Real*>(a.VT);
+      auto cp = [&](int f, const Real* src) {
+        __pipeline_memcpy_async(&sPre[f * Lay::PE + k], src, sizeof(Real));
+      };
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        cp(c, LX + c * N + q);
+        cp(M + c, LX + (M + c) * N + q);
+        cp(2 * M + c, LX + (2 * M + c) * N + q);
+        cp(3 * M + c, VT + c * N + q);
+        if constexpr (MODE == MODE_STAGE2 || MODE == MODE_STAGE3) {
+          cp(4 * M + c, static_cast<const Real*>(a.U0) + c * N + q);
+          cp(5 * M + c, static_cast<const Real*>(a.Vt0) + c * N + q);
+          cp(6 * M + c, static_cast<const Real*>(a.Wt0) + c * N + q);
+        }
+      }
+    }
+    __pipeline_commit();
+  }
   const Real* geo = pick<Real>(a.geod, a.geof);
   const Real dy = geo[3], idy = geo[4], idy2 = geo[5];
   const Real alpha = Real(a.alpha_in[1]);
@@ -364,9 +399,10 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
       const int r = k / C, col = k % C;
       if (col >= ncol || r >= nrow + 4) continue;
-      const int i = i0 + col;
-      const double xc = __dadd_rn(a.x0, __dmul_rn((double)i + 0.5, a.dx));
-      const Src s = map_y(j0 - 2 + r, ny, xc, a.y0, a.dy, ts, a.sp);
+      const int i = i0 + col, jj = j0 - 2 + r;
+      // cell-centre x, needed only by the double-Mach maps of ghost rows
+      const double xc = jj < 0 || jj >= ny ? __dadd_rn(a.x0, __dmul_rn((double)i + 0.5, a.dx)) : 0.0;
+      const Src s = map_y(jj, ny, xc, a.y0, a.dy, ts, a.sp);
       Real u[M], v[M], ww[M];
 #pragma unroll
       for (int c = 0; c < M; ++c) {
@@ -473,20 +509,26 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
   bool bad = false;
   const Real* LX = static_cast<const Real*>(a.LX);
   const Real* VT = static_cast<const Real*>(a.VT);
+  if constexpr (Lay::NPRE > 0) __pipeline_wait_prior(0);  // this thread's copies
   for (int k = threadIdx.x; k < kRowsY2D * C; k += blockDim.x) {
     const int r = k / C, col = k % C;
     if (col >= ncol || r >= nrow) continue;
     const int g = r + 2;
     const int kc = g * C + col;
     const long long q = (long long)(j0 + r) * nx + i0 + col;
+    // an epilogue input: prefetched (FP32) or read here
+    auto in = [&](int f, const Real* src) -> Real {
+      if constexpr (Lay::NPRE > 0) return sPre[f * Lay::PE + k];
+      else return *src;
+    };
     Real l1[M], l2[M], l3[M], vt[M], wt[M], u[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
       const int ka = r * C + col, kb = (r + 1) * C + col;
-      l1[c] = LX[c * N + q] - (IF(0, c)[kb] - IF(0, c)[ka]) * idy;
-      l2[c] = LX[(M + c) * N + q] - (IF(2, c)[kb] - IF(2, c)[ka]) * idy;
-      l3[c] = LX[(2 * M + c) * N + q] - (IF(1, c)[kb] - IF(1, c)[ka]) * idy2;
-      vt[c] = VT[c * N + q];
+      l1[c] = in(c, LX + c * N + q) - (IF(0, c)[kb] - IF(0, c)[ka]) * idy;
+      l2[c] = in(M + c, LX + (M + c) * N + q) - (IF(2, c)[kb] - IF(2, c)[ka]) * idy;
+      l3[c] = in(2 * M + c, LX + (2 * M + c) * N + q) - (IF(1, c)[kb] - IF(1, c)[ka]) * idy2;
+      vt[c] = in(3 * M + c, VT + c * N + q);
       u[c] = PT(0, c)[kc];
     }
     if (a.sp.limiter == 0) {
@@ -536,9 +578,9 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
           wn = wt[c] + rdt * l3[c];
           static_cast<Real*>(a.Wt0out)[qc] = wt[c];
         } else {
-          const Real u0 = static_cast<const Real*>(a.U0)[qc];
-          const Real v0 = static_cast<const Real*>(a.Vt0)[qc];
-          const Real w0 = static_cast<const Real*>(a.Wt0)[qc];
+          const Real u0 = in(4 * M + c, static_cast<const Real*>(a.U0) + qc);
+          const Real v0 = in(5 * M + c, static_cast<const Real*>(a.Vt0) + qc);
+          const Real w0 = in(6 * M + c, static_cast<const Real*>(a.Wt0) + qc);
           const Real c0 = MODE == MODE_STAGE2 ? Real(0.75) : Real(1.0 / 3.0);
           const Real c1 = MODE == MODE_STAGE2 ? Real(0.25) : Real(2.0 / 3.0);
           un[c] = c0 * u0 + c1 * (u[c] + rdt * l1[c]);
