@@ -297,11 +297,21 @@ def run_ours(args, rank, world, dev_index):
                 clus = (sum(a.elapsed_time(b) for a, b in evc),
                         float(((histc > 0).double() * nx[None, :]).sum().item()),
                         sc.launches_last_call * K, kern[0])
+                # and the next K steps as one cluster launch (hweno_run_persistent)
+                q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                q0.record()
+                cpu = sc.run_persistent(U, V, t, w.t_end, K)
+                q1.record()
+                torch.cuda.synchronize()
+                timed.clus_run = (q0.elapsed_time(q1), float(cpu))
                 sc.close()
         s.close()
         timed.tune = tune
         timed.pers = pers
         timed.clus = clus
+        if clus is None:
+            timed.clus_run = None
         return ms, float(pu), prof, launches, ms_ng, pu_ng
 
     with ClockSampler(dev_index) as clk:
@@ -334,6 +344,13 @@ def run_ours(args, rank, world, dev_index):
                    "ms_per_step": round(clus[0] / args.steps, 4),
                    "note": "each step one launch on thread-block clusters (fused_small = 2), "
                            "L2 flushed between steps"}
+    cluster_run = None
+    if getattr(timed, "clus_run", None) and timed.clus_run[1] > 0:
+        cr = timed.clus_run
+        cluster_run = {"value": round(cr[1] / (cr[0] * 1e-3) / 1e6, 3),
+                       "ms_per_step": round(cr[0] / args.steps, 4),
+                       "note": "the next K steps as one launch on thread-block clusters "
+                               "(hweno_run_persistent with fused_small = 2), no flush inside"}
     use_clus = (small and clus is not None and clus[1] > 0 and
                 clus[1] / clus[0] > pu_ng / ms_ng)
     if small:
@@ -395,6 +412,7 @@ def run_ours(args, rank, world, dev_index):
            **({"graph": graph, "persistent": persistent} if use_pers else
               ({"persistent": persistent} if persistent else {})),
            **({"cluster": cluster} if cluster and not use_clus else {}),
+           **({"cluster_run": cluster_run} if cluster_run else {}),
            **({"plain": plain} if use_clus else {}),
            "config": {"workload": describe(w),
                       "instances": w.batch, "points": w.points, "precision": args.precision,

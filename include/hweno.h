@@ -243,7 +243,10 @@ int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double
  * latched device status; otherwise it returns after enqueueing. Waits are
  * bounded (about two seconds); a wait that gives up latches HWENO_ETIMEOUT.
  * 1D only (2D: HWENO_ENOTSUP). Library scratch: counters and alpha slots,
- * allocated by the first call. */
+ * allocated by the first call. With fused_small = 2 and instances within
+ * HWENO_CLUSTER_MAX_POINTS, the steps run instead as one launch of the
+ * cluster step (one cluster per instance, cluster barriers between stages and
+ * steps); it gives the bits of `steps` calls of hweno_step with that option. */
 int hweno_run_persistent(hweno_ctx* ctx, void* U, void* V, double* t, double t_end, int steps,
                          long long* point_updates, void* stream);
 

@@ -816,6 +816,40 @@ int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   int rc;
+  if (c->opt.fused_small == 2 && c->max_n <= kClusterMax * kTile1D) {
+    // small instances: the K steps as one launch of the cluster step
+    if ((e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)) ||
+        (e = cudaMemsetAsync(c->d_pu, 0, sizeof(unsigned long long), s)))
+      return cuda_fail(c, e, "memset");
+    Args1D a = base_args_1d(c);
+    a.t = t;
+    a.t_end = t_end;
+    a.skip_done = 1;
+    a.dt = c->d_dt;
+    a.lands = c->d_lands;
+    a.U = U;
+    a.V = V;
+    FusedArgs f{};
+    f.U1 = c->d_U1; f.V1 = c->d_V1; f.U2 = c->d_U2; f.V2 = c->d_V2; f.Vt0 = c->d_Vt0;
+    f.alpha = c->d_alpha; f.dt_used = nullptr; f.active = c->d_active; f.pu = c->d_pu;
+    f.batch = c->batch;
+    f.steps = steps;
+    prof_begin(c, s);
+    e = launch_step_cluster_1d(c->eq, c->fp32, a, f, (int)c->max_n, s);
+    if (e == cudaSuccess) {
+      prof_end(c, s, 1);
+      c->launches = 1;
+      if (!point_updates) return HWENO_OK;
+      unsigned long long pu = 0;
+      if ((e = cudaMemcpyAsync(&pu, c->d_pu, sizeof pu, cudaMemcpyDeviceToHost, s)) ||
+          (e = cudaStreamSynchronize(s)))
+        return cuda_fail(c, e, "read point updates");
+      *point_updates = (long long)pu;
+      return hweno_sync_status(c, stream);
+    }
+    if (e != cudaErrorNotSupported) return cuda_fail(c, e, "cluster run");
+    // no such cluster here: the tiled persistent kernel below
+  }
   const size_t B = c->batch;
   if (!c->d_next) {
     // counters: next (8 B), done, done3 (4 B per instance each), one allocation

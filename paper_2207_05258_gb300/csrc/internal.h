@@ -293,6 +293,7 @@ struct FusedArgs {
   int* active;
   unsigned long long* pu;     // nullable
   int batch;
+  int steps = 1;              // cluster step: steps per launch
 };
 cudaError_t launch_step_small_1d_f64(int eq, const Args1D& a, const FusedArgs& f, cudaStream_t s);
 cudaError_t launch_step_small_1d_f32(int eq, const Args1D& a, const FusedArgs& f, cudaStream_t s);

@@ -1031,8 +1031,10 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
 // (its shared-memory request leaves no room for a second one). The wave
 // speed of U^n is reduced through distributed shared memory; the stages are
 // separated by cluster barriers, whose release / acquire order makes each
-// stage's global writes (state, alpha slots) visible to the next. Every CTA
-// passes the same five barriers whatever its share of the instance.
+// stage's global writes (state, alpha slots) visible to the next. f.steps
+// steps run in one launch (one from hweno_step, K from the persistent run).
+// Every CTA passes the same six barriers per step whatever its share of the
+// instance.
 // ---------------------------------------------------------------------------
 template <int EQ, class Real, int MODE, bool SPLIT>
 __device__ __forceinline__ void cluster_stage(const Args1D& a, const StageIO& io, int k, int s) {
@@ -1054,64 +1056,67 @@ k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ Fuse
   const int k = blockIdx.x / C;
   const int n = a.inst_n[k];
   const int s = rank * P;
-  const bool live = a.t[k] < a.t_end;  // read before anything below writes t
-  const bool has = live && s < n;
   unsigned long long* s0 = f.alpha;
   unsigned long long* s1 = f.alpha + f.batch;
   unsigned long long* s2 = f.alpha + 2 * f.batch;
-  {  // alpha(U^n) of this tile's points
-    Real amax = Real(0);
-    if (has) {
-      const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
-      const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
-      const Real a01 = pick<Real>(a.sp.wd, a.sp.wf)[10];
-      const int e = min(s + P, n);
-      for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
-        Real u[M];
+  for (int step = 0; step < f.steps; ++step) {
+    const bool live = a.t[k] < a.t_end;  // t[k] is written only after the fifth barrier
+    const bool has = live && s < n;
+    {  // alpha(U^n) of this tile's points
+      Real amax = Real(0);
+      if (has) {
+        const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
+        const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+        const Real a01 = pick<Real>(a.sp.wd, a.sp.wf)[10];
+        const int e = min(s + P, n);
+        for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
+          Real u[M];
 #pragma unroll
-        for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + j];
-        amax = fmax(amax, wave_speed<EQ>(u, gam, a01));
+          for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + j];
+          amax = fmax(amax, wave_speed<EQ>(u, gam, a01));
+        }
+      }
+      amax = block_max_t(amax, red);
+      if (threadIdx.x == 0) part = (double)amax;
+    }
+    cl.sync();
+    if (live && rank == 0 && threadIdx.x == 0) {  // the instance's alpha; stage slots from zero
+      double m = 0.0;
+      for (int r = 0; r < C; ++r) m = fmax(m, *cl.map_shared_rank(&part, r));
+      s0[k] = (unsigned long long)__double_as_longlong(m);
+      s1[k] = 0ull;
+      s2[k] = 0ull;
+    }
+    cl.sync();
+    StageIO io = io_of(a);
+    io.Uout = f.U1; io.Vout = f.V1; io.Vt0out = f.Vt0;
+    io.alpha_in = reinterpret_cast<const double*>(s0); io.alpha_out = s1;
+    if (has) cluster_stage<EQ, Real, MODE_STAGE1, SPLIT>(a, io, k, s);
+    cl.sync();
+    io.U = f.U1; io.V = f.V1; io.U0 = a.U; io.Vt0 = f.Vt0; io.Uout = f.U2; io.Vout = f.V2;
+    io.Vt0out = nullptr;
+    io.alpha_in = reinterpret_cast<const double*>(s1); io.alpha_out = s2;
+    if (has) cluster_stage<EQ, Real, MODE_STAGE2, SPLIT>(a, io, k, s);
+    cl.sync();
+    io.U = f.U2; io.V = f.V2; io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V);
+    io.alpha_in = reinterpret_cast<const double*>(s2); io.alpha_out = nullptr;
+    if (has) cluster_stage<EQ, Real, MODE_STAGE3, SPLIT>(a, io, k, s);
+    cl.sync();  // every CTA is past its reads of t[k]
+    if (rank == 0 && threadIdx.x == 0) {
+      if (!live) {  // finished: nothing moves (as k_finalize)
+        if (f.dt_used) f.dt_used[k] = 0.0;
+      } else {  // time update (as k_finalize); tile 0 wrote dt and lands
+        double tk = a.t[k];
+        const double d = a.dt[k];
+        tk = a.lands[k] ? a.t_end : tk + d;
+        const_cast<double*>(a.t)[k] = tk;
+        if (!(__longlong_as_double((long long)s0[k]) <= DBL_MAX)) atomicOr(a.status, STATUS_NONFINITE);
+        if (f.pu) atomicAdd(f.pu, (unsigned long long)n);
+        if (f.dt_used) f.dt_used[k] = d;
+        if (step == f.steps - 1 && tk < a.t_end) atomicAdd(f.active, 1);
       }
     }
-    amax = block_max_t(amax, red);
-    if (threadIdx.x == 0) part = (double)amax;
-  }
-  cl.sync();
-  if (live && rank == 0 && threadIdx.x == 0) {  // the instance's alpha; stage slots from zero
-    double m = 0.0;
-    for (int r = 0; r < C; ++r) m = fmax(m, *cl.map_shared_rank(&part, r));
-    s0[k] = (unsigned long long)__double_as_longlong(m);
-    s1[k] = 0ull;
-    s2[k] = 0ull;
-  }
-  cl.sync();
-  StageIO io = io_of(a);
-  io.Uout = f.U1; io.Vout = f.V1; io.Vt0out = f.Vt0;
-  io.alpha_in = reinterpret_cast<const double*>(s0); io.alpha_out = s1;
-  if (has) cluster_stage<EQ, Real, MODE_STAGE1, SPLIT>(a, io, k, s);
-  cl.sync();
-  io.U = f.U1; io.V = f.V1; io.U0 = a.U; io.Vt0 = f.Vt0; io.Uout = f.U2; io.Vout = f.V2;
-  io.Vt0out = nullptr;
-  io.alpha_in = reinterpret_cast<const double*>(s1); io.alpha_out = s2;
-  if (has) cluster_stage<EQ, Real, MODE_STAGE2, SPLIT>(a, io, k, s);
-  cl.sync();
-  io.U = f.U2; io.V = f.V2; io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V);
-  io.alpha_in = reinterpret_cast<const double*>(s2); io.alpha_out = nullptr;
-  if (has) cluster_stage<EQ, Real, MODE_STAGE3, SPLIT>(a, io, k, s);
-  cl.sync();  // every CTA is past its reads of t[k]
-  if (rank == 0 && threadIdx.x == 0) {
-    if (!live) {  // finished: nothing moves (as k_finalize)
-      if (f.dt_used) f.dt_used[k] = 0.0;
-    } else {  // time update (as k_finalize); tile 0 wrote dt and lands
-      double tk = a.t[k];
-      const double d = a.dt[k];
-      tk = a.lands[k] ? a.t_end : tk + d;
-      const_cast<double*>(a.t)[k] = tk;
-      if (!(__longlong_as_double((long long)s0[k]) <= DBL_MAX)) atomicOr(a.status, STATUS_NONFINITE);
-      if (f.pu) atomicAdd(f.pu, (unsigned long long)n);
-      if (f.dt_used) f.dt_used[k] = d;
-      if (tk < a.t_end) atomicAdd(f.active, 1);
-    }
+    cl.sync();  // the new t[k] before the next step reads it
   }
 }
 

@@ -154,3 +154,33 @@ def test_config_1_to_final_time(hw, mode):  # N = 400: mode 2 takes the latency 
     assert float(t[0]) == to == w.t_end
     assert np.max(np.abs(U.cpu().numpy() - Uo.ravel())) <= 1e-8 * np.max(np.abs(Uo))
     assert s.launches_last_call >= 1
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_cluster_persistent_run_matches_the_steps(hw, mode):
+    """hweno_run_persistent with fused_small = 2: the K steps as one launch of
+    the cluster step give the bits of K single-step calls; instances that
+    reach t_end on the way stop; the point-updates count the stepping ones."""
+    w = _batch("euler", MODES[mode], 7)
+    K, t_end = 6, 0.02
+    a = hw.Solver.from_workload(w, fused_small=2)
+    b = hw.Solver.from_workload(w, fused_small=2)
+    U1, V1 = torch.from_numpy(w.U).cuda(), torch.from_numpy(w.V).cuda()
+    U2, V2 = U1.clone(), V1.clone()
+    t1 = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    t2 = t1.clone()
+    nx = torch.tensor(w.nx, dtype=torch.float64, device="cuda")
+    pu_steps = 0.0
+    for _ in range(K):
+        d = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+        a.step(U1, V1, None, t1, t_end, d)
+        pu_steps += float(((d > 0).double() * nx).sum())
+    a.sync_status()
+    pu = b.run_persistent(U2, V2, t2, t_end, K)
+    assert b.launches_last_call == 1
+    assert torch.equal(U1, U2) and torch.equal(V1, V2) and torch.equal(t1, t2)
+    assert pu == pu_steps
+    assert b.active_instances() == a.active_instances()
+    assert 0 < a.active_instances() < w.batch  # some finished on the way
+    a.close()
+    b.close()
