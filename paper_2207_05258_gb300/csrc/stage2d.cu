@@ -144,7 +144,18 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
   if (a.skip_done && !(a.t[0] < a.t_end)) return;
   const int nx = a.nx;
   const long long N = (long long)nx * a.ny;
-  const int j = blockIdx.y, i0 = blockIdx.x * kTileX2D;
+  // block -> (row segment, row): the full segments of every row first, the
+  // ragged last segments (shorter work) at the end of the dispatch order
+  int tile = blockIdx.x, j = blockIdx.y;
+  {
+    const int T = gridDim.x, F = T - 1;
+    if (F > 0 && nx % kTileX2D != 0) {
+      const long long b = (long long)blockIdx.y * T + blockIdx.x, full = (long long)a.ny * F;
+      if (b < full) { tile = (int)(b % F); j = (int)(b / F); }
+      else { tile = F; j = (int)(b - full); }
+    }
+  }
+  const int i0 = tile * kTileX2D;
   const int np = min(kTileX2D, nx - i0);
   const long long row = (long long)j * nx;
   const Real* geo = pick<Real>(a.geod, a.geof);
