@@ -439,6 +439,14 @@ def run_ours(args, rank, world, dev_index):
             out["fp32"] = {"value": round(pu32 / (ms32 * 1e-3) / 1e6, 3),
                            "ms_per_step": round(ms32 / args.steps, 4),
                            "stage_kernel_ms": round(prof32["stage"][0] / prof32["stage"][1], 4)}
+            p32 = timed.pers
+            if p32 is not None and p32[1] > 0:  # the same K steps as one persistent launch
+                out["fp32"]["persistent"] = {"value": round(p32[1] / (p32[0] * 1e-3) / 1e6, 3),
+                                             "ms_per_step": round(p32[0] / args.steps, 4)}
+            c32 = timed.clus_run
+            if c32 is not None and c32[1] > 0:  # small instances: K steps in one cluster launch
+                out["fp32"]["cluster_run"] = {"value": round(c32[1] / (c32[0] * 1e-3) / 1e6, 3),
+                                              "ms_per_step": round(c32[0] / args.steps, 4)}
         out["e2e"] = run_e2e(args, w, hweno, torch)
         if rank == 0 and w.dim == 1:
             out["cpu_baseline"] = cpu_baseline(w, budget_s=16.0)
