@@ -9,10 +9,10 @@
 // the cotangent of the characteristic flux is R^T mu; the sides are reversed
 // by hand (side_vjp); the projections give the cotangents of the split point
 // fluxes and of L, R; L, R are pulled back to the Roe state (u-bar, H-bar) by
-// forward-mode differentiation of the eigenvector formulas, and the Roe
-// average to the two states by hand. The split point fluxes F^{+-}, H^{+-}
-// are pulled back to (u, v) once per point by forward-mode differentiation of
-// the flux F(u) and of H = F'(u) v.
+// one reverse pass through the eigenvector formulas, and the Roe average to
+// the two states by hand. The split point fluxes F^{+-}, H^{+-} are pulled
+// back to (u, v) once per point by a reverse pass through the flux F(u) and
+// H = F'(u) v.
 //
 // Tiling as the Burgers adjoint: one CTA per tile of P points, items
 // (interfaces j = s-2 .. s+P, limited derivatives j = s-1 .. s+P) store their

@@ -18,9 +18,9 @@
 // bounds these kernels): interface items j = s-2 .. s+P and limiter items
 // j = s-1 .. s+P store per-stencil-slot cotangents field-major in shared
 // memory; every loaded point gathers its slots in a fixed order and pulls the
-// point-flux cotangents back to (U, N, T) by forward-mode differentiation of
-// the flux and Jacobian-vector products; owned points add their ghost images
-// at walls. The characteristic pieces follow the 1D Euler adjoint with the
+// point-flux cotangents back to (U, N, T) by a reverse pass through the flux
+// and Jacobian-vector products; owned points add their ghost images at walls.
+// Two threads (in different warps) share each item. The characteristic pieces follow the 1D Euler adjoint with the
 // 4x4 eigen-system of A_d at the Roe average (u, v, H). No atomics.
 #include "flux2d.cuh"
 #include "hweno.h"
@@ -233,7 +233,18 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
   const int nx = a.nx, ny = a.ny;
   const long long Ntot = (long long)nx * ny;
   const int n = DIR == 0 ? nx : ny;
-  const int line = blockIdx.y, s = blockIdx.x * P;
+  // block -> (tile, line): the full tiles of every line first, the ragged
+  // last tiles (shorter work) at the end of the dispatch order
+  int tile = blockIdx.x, line = blockIdx.y;
+  {
+    const int T = gridDim.x, F = T - 1;
+    if (F > 0 && n % P != 0) {
+      const long long b = (long long)blockIdx.y * T + blockIdx.x, full = (long long)gridDim.y * F;
+      if (b < full) { tile = (int)(b % F); line = (int)(b / F); }
+      else { tile = F; line = (int)(b - full); }
+    }
+  }
+  const int s = tile * P;
   const int np = min(P, n - s);
   auto at = [&](int p) -> long long {
     return DIR == 0 ? (long long)line * nx + p : (long long)p * nx + line;

@@ -1,7 +1,7 @@
 // Point fluxes, flux Jacobian-vector products and boundary mappings of the
 // 2D equations (Zhang & Zhao, arXiv:2207.05258, Eq. EQ3 and Sec. 3), shared by
 // the 2D stage kernels and their adjoint. The arithmetic is templated on the
-// scalar so that the adjoint can differentiate it in forward mode.
+// scalar (FP64 and FP32 paths).
 #pragma once
 
 #include "hweno.h"

@@ -20,27 +20,6 @@ constexpr double K10 = 1421461.0 / 2275.0, K11 = 21520059541.0 / 1377684.0;
 constexpr double C11 = 11.0 / 60.0, C19 = 19.0 / 30.0;
 }  // namespace adj
 
-// Forward-mode scalar (value, tangent), for differentiating the small
-// nonlinear pieces (eigenvectors, point fluxes) inside the reverse kernels.
-struct Dd {
-  double v, d;
-  __device__ Dd() {}
-  __device__ Dd(double x) : v(x), d(0.0) {}  // NOLINT: constants mix in
-  __device__ Dd(double x, double t) : v(x), d(t) {}
-};
-__device__ __forceinline__ Dd operator+(Dd a, Dd b) { return Dd(a.v + b.v, a.d + b.d); }
-__device__ __forceinline__ Dd operator-(Dd a, Dd b) { return Dd(a.v - b.v, a.d - b.d); }
-__device__ __forceinline__ Dd operator-(Dd a) { return Dd(-a.v, -a.d); }
-__device__ __forceinline__ Dd operator*(Dd a, Dd b) { return Dd(a.v * b.v, a.d * b.v + a.v * b.d); }
-__device__ __forceinline__ Dd operator/(Dd a, Dd b) {
-  const double ib = 1.0 / b.v, q = a.v * ib;
-  return Dd(q, (a.d - q * b.d) * ib);
-}
-__device__ __forceinline__ Dd sqrt(Dd a) {
-  const double r = ::sqrt(a.v);
-  return Dd(r, 0.5 * a.d / r);
-}
-
 // Source of point p of an instance with n points (maybe a ghost): kind 0
 // copy, 1 mirror (reflective wall), 2 imposed state (no dependence on the
 // instance's values). Same mapping as the forward stage's loads.

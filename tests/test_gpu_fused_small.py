@@ -184,3 +184,24 @@ def test_cluster_persistent_run_matches_the_steps(hw, mode):
     assert 0 < a.active_instances() < w.batch  # some finished on the way
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("eq,bc", [("euler", ("reflective", "inflow")),
+                                   ("euler", ("inflow", "reflective")),
+                                   ("burgers", ("reflective", "outflow")),
+                                   ("buckley", ("inflow", "outflow"))])
+def test_fused_boundaries_match_tiled(hw, mode, eq, bc):
+    """Walls (mirrored ghosts) and imposed inflow states in the fused loads,
+    against the tiled kernels."""
+    import dataclasses
+    w = _batch(eq, MODES[mode], 8)
+    inflow = (1.0, 0.2, 2.6, 0.0) if eq == "euler" else (0.4, 0.0, 0.0, 0.0)
+    w = dataclasses.replace(w, bc=(bc[0], bc[1], "periodic", "periodic"), inflow=inflow)
+    K, t_end = 6, 0.01
+    f = _steps(hw, w, K, t_end, "fp64", fused_small=FUSED[mode])
+    g = _steps(hw, w, K, t_end, "fp64")
+    assert f[5] == 1 and g[5] == 5
+    assert float((f[0] - g[0]).abs().max()) <= 1e-13 * K * float(g[0].abs().max())
+    assert float((f[1] - g[1]).abs().max()) <= 1e-12 * K * float(g[1].abs().max() + 1.0)
+    assert torch.allclose(f[2], g[2], rtol=1e-14, atol=0)
