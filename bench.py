@@ -316,6 +316,8 @@ def run_ours(args, rank, world, dev_index):
 
     with ClockSampler(dev_index) as clk:
         ms, pu, prof, launches, ms_ng, pu_ng = timed(args.precision, args.steps, args.warmup, True)
+    # the FP64 rate a DFMA-only loop reaches here (context for the FP64 roofline)
+    fp64_loop = hweno.measure_fp64_peak() if args.precision == "fp64" else None
     clocks = clk.summary()
     tune = timed.tune
     pers = timed.pers
@@ -384,6 +386,9 @@ def run_ours(args, rank, world, dev_index):
         rtraffic = MEASURED_RUN_TRAFFIC_PER_POINT_STEP.get(args.precision)
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
+            **({"dfma_loop_tflops": round(fp64_loop, 4),
+                "frac_of_dfma_loop": round(achieved / fp64_loop, 4)}
+               if args.precision == "fp64" and fp64_loop else {}),
             "traffic": (None if traffic is None else traffic * pts_per_stage) if not use_pers else
                        (None if rtraffic is None else rtraffic * pers[1]),
             "kernel": ("k_run_1d<%s,%s> (K = %d steps per launch)" % (w.equation, args.precision,

@@ -325,6 +325,14 @@ int hweno_launches_last_call(const hweno_ctx* ctx);
 int hweno_profile_start(hweno_ctx* ctx, int capacity);
 int hweno_profile_read(hweno_ctx* ctx, double* ms, int* n, void* stream);
 
+/* Measured FP64 ceiling (no counterpart in the paper; a measurement aid):
+ * times a loop of independent DFMA chains with eight warps per SM, no memory
+ * traffic, and stores the rate in *tflops (host) as FP64 TFLOP/s (2 flops per
+ * DFMA) on the current device at its current clocks. Allocates and frees a
+ * small output buffer; synchronises `stream`. HWENO_EINVAL for a null
+ * pointer, HWENO_ENOMEM / HWENO_ECUDA on CUDA failures. */
+int hweno_measure_fp64_peak(double* tflops, void* stream);
+
 /* Allocation-free step (this entry point has no counterpart in the paper; it
  * serves callers that cannot allocate device memory: code inside a host
  * framework that owns all device allocations through its own pool, code that

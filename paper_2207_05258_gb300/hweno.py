@@ -90,6 +90,7 @@ SIGNATURES = {
                                              ctypes.c_double, ctypes.c_double, ctypes.POINTER(Bc),
                                              ctypes.POINTER(Options), _VP, _VP, _VP,
                                              ctypes.c_double, _VP, _VP]),
+    "hweno_measure_fp64_peak": (ctypes.c_int, [_DP, _VP]),
     "hweno_last_error": (ctypes.c_char_p, [_VP]),
     "hweno_destroy": (ctypes.c_int, [_VP]),
 }
@@ -125,6 +126,16 @@ def _ptr(t: Optional[torch.Tensor]):
 
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def measure_fp64_peak() -> float:
+    """hweno_measure_fp64_peak: FP64 TFLOP/s of a DFMA-only loop on the
+    current device (the ceiling that FP64-pipe-bound kernels can reach)."""
+    out = ctypes.c_double(0.0)
+    rc = lib.hweno_measure_fp64_peak(ctypes.byref(out), _stream())
+    if rc != OK:
+        raise HwenoError(rc, "hweno_measure_fp64_peak failed")
+    return out.value
 
 
 class Solver:

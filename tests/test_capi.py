@@ -79,6 +79,7 @@ def test_create_rejects_invalid_problems(hw, kw):
 
 def test_null_arguments(hw):
     assert hw.lib.hweno_create(None, 0, None, 1.4, None) == hw.EINVAL
+    assert hw.lib.hweno_measure_fp64_peak(None, None) == hw.EINVAL
     assert hw.lib.hweno_destroy(None) == 0
     assert hw.lib.hweno_last_error(None) == b"null context"
     assert hw.lib.hweno_step(None, None, None, None, None, 1.0, None, None) == hw.EINVAL
