@@ -462,7 +462,11 @@ def run_e2e(args, w, hweno, torch):
     """Same metric through the C ABI's host-buffer entry point: every step
     copies U, V, t from pinned host memory and the result back (in 1D the
     library pipelines the copies of instance chunks with their kernels)."""
-    s = hweno.Solver.from_workload(w, precision=args.precision)
+    # small 1D instances take the cluster step, as in the device-side measurement
+    small1d = (w.dim == 1 and max(w.nx) <= hweno.CLUSTER_MAX_POINTS and
+               working_set_mb(w, args.precision) < 129.0)
+    s = hweno.Solver.from_workload(w, precision=args.precision,
+                                   **({"fused_small": 2} if small1d else {}))
     dt_t = torch.float64 if args.precision == "fp64" else torch.float32
     if w.dim == 1:  # the same tile shape as the device-side measurement
         Ud = torch.from_numpy(w.U).to("cuda", dt_t)
