@@ -205,3 +205,30 @@ def test_fused_boundaries_match_tiled(hw, mode, eq, bc):
     assert float((f[0] - g[0]).abs().max()) <= 1e-13 * K * float(g[0].abs().max())
     assert float((f[1] - g[1]).abs().max()) <= 1e-12 * K * float(g[1].abs().max() + 1.0)
     assert torch.allclose(f[2], g[2], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_fused_steps_in_a_cuda_graph(hw, mode):
+    """hweno_run records the fused or cluster step into a CUDA graph (the
+    first call on a fresh context, so the one-time set-up happens in the
+    recording) and replays it: the bits of the same steps taken one by one."""
+    w = _batch("burgers", MODES[mode], 9)
+    K, t_end = 5, 0.02
+    a = hw.Solver.from_workload(w, fused_small=FUSED[mode])
+    b = hw.Solver.from_workload(w, fused_small=FUSED[mode])
+    U1, V1 = torch.from_numpy(w.U).cuda(), torch.from_numpy(w.V).cuda()
+    U2, V2 = U1.clone(), V1.clone()
+    t1 = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    t2 = t1.clone()
+    for _ in range(K):
+        a.step(U1, V1, None, t1, t_end)
+    a.sync_status()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        steps, pu = b.run_graph(U2, V2, None, t2, t_end, max_steps=K, steps_per_launch=K)
+    torch.cuda.synchronize()
+    b.sync_status()
+    assert steps == K and pu > 0
+    assert torch.equal(U1, U2) and torch.equal(V1, V2) and torch.equal(t1, t2)
+    a.close()
+    b.close()
