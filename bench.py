@@ -557,9 +557,11 @@ def run_adjoint(args, rank, world, dev_index):
     J = sum u(T)^2 dx) and euler2d_adjoint:N (default 512: 2D Euler periodic,
     the density wave plus a seeded 4-mode perturbation, 400 fixed steps of
     T/400, T = 0.25, J = sum rho(T)^2 dx dy). Measured: (a) K adjoint steps,
-    each the reverse of a recorded forward step (replay of stages 1-2 and the
-    reverse stage kernels), timed one by one with CUDA events, L2 flushed
-    between steps; the forward step alone for the ratio; (b) one full
+    each the reverse of a forward step from its step record (the stage
+    states saved by hweno_step_record; the path of the autograd Function),
+    timed one by one with CUDA events, L2 flushed between steps, and the same
+    steps replaying stages 1-2 instead (`replay`); the forward step alone for
+    the ratio; (b) one full
     gradient through the checkpointed autograd Function (checkpoint every 20
     steps), host-timed; (c) --fd-directions seeded smooth directions d: the
     adjoint's <grad J, d> against central differences of the GPU forward
@@ -610,22 +612,38 @@ def run_adjoint(args, rank, world, dev_index):
             e1.record()
             dts.append(dt)
             fwd.append((e0, e1))
-        lam = [2.0 * U * cell, torch.zeros_like(V)] + ([torch.zeros_like(Wd)] if two else [])
+        # the same steps again, untimed, saving their stage states (step records)
+        recs = [s.new_record() for _ in range(Wm + K)]
+        for k in range(Wm + K):
+            Uc, Vc = states[k][0].clone(), states[k][1].clone()
+            Wc = states[k][2].clone() if two else None
+            s.step_record(Uc, Vc, Wc, states[k][3].clone(), t_end, recs[k])
+        lam0 = [2.0 * U * cell, torch.zeros_like(V)] + ([torch.zeros_like(Wd)] if two else [])
         if two:
-            lam[0][npts:] = 0.0
-        adj = []
-        for k in range(Wm + K - 1, -1, -1):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            s.adjoint_step(states[k][0], states[k][1], states[k][2], dts[k], lam[0], lam[1],
-                           lam[2] if two else None, t=states[k][3])
-            e1.record()
-            adj.append((e0, e1))
+            lam0[0][npts:] = 0.0
+
+        def adjoint_pass(recorded):
+            lam = [x.clone() for x in lam0]
+            ev = []
+            for k in range(Wm + K - 1, -1, -1):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.adjoint_step(states[k][0], states[k][1], states[k][2], dts[k], lam[0], lam[1],
+                               lam[2] if two else None, t=states[k][3],
+                               record=recs[k] if recorded else None)
+                e1.record()
+                ev.append((e0, e1))
+            return ev
+
+        adj = adjoint_pass(True)  # the path of the autograd Function
         launches = s.launches_last_call
+        adj_rp = adjoint_pass(False)  # replaying stages 1-2 inside the adjoint step
         torch.cuda.synchronize()
         s.sync_status()
         adj_ms = sum(a.elapsed_time(b) for a, b in adj[Wm:])  # skip the warm-up steps
+        replay_ms = sum(a.elapsed_time(b) for a, b in adj_rp[Wm:])
+        del recs
         fwd_ms = sum(a.elapsed_time(b) for a, b in fwd[Wm:])
         if two:
             active = float(K * npts)
@@ -684,6 +702,9 @@ def run_adjoint(args, rank, world, dev_index):
                       "timing": "CUDA events around each hweno_adjoint_step"},
            "forward_ms_per_step": round(fwd_ms / K, 4),
            "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
+           "replay": {"ms_per_step": round(replay_ms / K, 4),
+                      "note": "hweno_adjoint_step without a step record: stages 1-2 "
+                              "replayed inside the adjoint step"},
            "full_gradient": {"seconds": round(grad_s, 3), "checkpoint_every": 20,
                              "note": "forward run + checkpointed backward, host-timed"},
            "clocks": clk.summary(), "gpu_launches": launches * K}

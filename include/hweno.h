@@ -300,6 +300,24 @@ int hweno_adjoint_step(hweno_ctx* ctx, const void* U, const void* V, const void*
                        const double* t, const double* dt, void* lamU, void* lamV, void* lamW,
                        void* stream);
 
+/* Step records: the same forward step and adjoint without the adjoint's
+ * replay of stages 1 and 2. hweno_step_record takes one hweno_step (same
+ * arguments and results) and then copies that step's stage states (U, V
+ * [, W] after stages 1 and 2) and per-stage wave speeds into `record`, a
+ * device buffer of hweno_adjoint_record_bytes(ctx) bytes owned by the caller
+ * (for 2D Euler 6 x 4 x points doubles). hweno_adjoint_step_recorded is
+ * hweno_adjoint_step for that step reading the stages from its record instead
+ * of recomputing them: the same results (the record holds the bits the
+ * replay would produce when the forward step ran the tiled kernels), two
+ * fewer stages of work. FP64 states only (else HWENO_ENOTSUP); a null record
+ * is HWENO_EINVAL. hweno_adjoint_record_bytes returns -1 for a null ctx. */
+long long hweno_adjoint_record_bytes(const hweno_ctx* ctx);
+int hweno_step_record(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
+                      double* dt_used, void* record, void* stream);
+int hweno_adjoint_step_recorded(hweno_ctx* ctx, const void* U, const void* V, const void* W,
+                                const void* record, const double* t, const double* dt,
+                                void* lamU, void* lamV, void* lamW, void* stream);
+
 /* Synchronise `stream`, read the device status word and return the latched
  * device error (HWENO_OK if none); clears the latch. */
 int hweno_sync_status(hweno_ctx* ctx, void* stream);

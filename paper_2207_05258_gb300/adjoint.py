@@ -46,19 +46,25 @@ class RunToTime(torch.autograd.Function):
         solver, two = ctx.solver, ctx.two
         lam = [g.detach().clone().contiguous() for g in grads]
         bounds = [c[0] for c in ctx.checkpoints] + [ctx.steps]
+        seg_len = max(bounds[i + 1] - bounds[i] for i in range(len(bounds) - 1))
+        records = [solver.new_record(lam[0].device) for _ in range(seg_len)]
         for seg in range(len(ctx.checkpoints) - 1, -1, -1):
             k0, U, V, W, t = ctx.checkpoints[seg]
             k1 = bounds[seg + 1]
             U, V, t = U.clone(), V.clone(), t.clone()
             W = W.clone() if two else None
             states = []
-            for k in range(k0, k1):  # replay the segment, keeping each step's input
+            # replay the segment, keeping each step's input and its stage
+            # states (a step record), so that the adjoint steps replay nothing
+            for k in range(k0, k1):
+                rec = records[k - k0]
                 states.append((U.clone(), V.clone(), W.clone() if two else None))
-                solver.step(U, V, W, t, ctx.t_end)
+                solver.step_record(U, V, W, t, ctx.t_end, rec)
             for k in range(k1 - 1, k0 - 1, -1):
                 Uk, Vk, Wk = states[k - k0]
                 solver.adjoint_step(Uk, Vk, Wk, ctx.dts[k], lam[0], lam[1],
-                                    lam[2] if two else None, t=ctx.ts[k])
+                                    lam[2] if two else None, t=ctx.ts[k],
+                                    record=records[k - k0])
         solver.sync_status()
         return (lam[0], lam[1], lam[2] if two else None, None, None, None, None, None)
 
@@ -67,5 +73,6 @@ def run_to_time(U0, V0, solver, t_end, checkpoint_every=20, max_steps=1 << 30, c
                 W0=None):
     """Differentiable run of an FP64 `solver` from (U0, V0[, W0]) at t = 0 to
     t_end; returns (U(T), V(T)[, W(T)]). Memory: one state per checkpoint
-    plus one segment of states during the backward pass."""
+    plus, during the backward pass, one segment of states and step records
+    (the stage states of each step: two more states per step)."""
     return RunToTime.apply(U0, V0, W0, solver, t_end, checkpoint_every, max_steps, check_every)

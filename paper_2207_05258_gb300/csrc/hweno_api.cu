@@ -1121,30 +1121,34 @@ double* adj_field(hweno_ctx* c, int f) {
 }
 
 int adjoint_1d(hweno_ctx* c, const void* U, const void* V, const double* dt, double* lU,
-               double* lV, cudaStream_t s) {
+               double* lV, bool replay, cudaStream_t s) {
   cudaError_t e;
   // 1. replay stages 1 and 2 of the forward step with its dt; alpha of each
-  //    stage input lands in slots 0, 1, 2 (frozen in the adjoint)
-  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)))
-    return cuda_fail(c, e, "memset");
-  Args1D a = base_args_1d(c);
-  a.t = c->d_ht;  // unused with skip_done = 0
-  a.t_end = 0.0;
-  a.skip_done = 0;
-  a.dt = c->d_dt;
-  a.lands = c->d_lands;
-  a.dt_in = dt;
-  a.U = U;
-  a.alpha_out = slot(c, 0);
-  if ((e = launch_alpha_1d(c->eq, false, c->variant, a, c->ntiles, s))) return cuda_fail(c, e, "alpha");
-  a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
-  a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
-  if ((e = launch_stage_1d(c->eq, false, c->variant, MODE_STAGE1, a, c->ntiles, s)))
-    return cuda_fail(c, e, "replay stage 1");
-  a.U = c->d_U1; a.V = c->d_V1; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = c->d_U2; a.Vout = c->d_V2;
-  a.Vt0out = nullptr; a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
-  if ((e = launch_stage_1d(c->eq, false, c->variant, MODE_STAGE2, a, c->ntiles, s)))
-    return cuda_fail(c, e, "replay stage 2");
+  //    stage input lands in slots 0, 1, 2 (frozen in the adjoint). Without
+  //    replay the stage states and slots come from a record.
+  if (replay) {
+    if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)))
+      return cuda_fail(c, e, "memset");
+    Args1D a = base_args_1d(c);
+    a.t = c->d_ht;  // unused with skip_done = 0
+    a.t_end = 0.0;
+    a.skip_done = 0;
+    a.dt = c->d_dt;
+    a.lands = c->d_lands;
+    a.dt_in = dt;
+    a.U = U;
+    a.alpha_out = slot(c, 0);
+    if ((e = launch_alpha_1d(c->eq, false, c->variant, a, c->ntiles, s)))
+      return cuda_fail(c, e, "alpha");
+    a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
+    a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
+    if ((e = launch_stage_1d(c->eq, false, c->variant, MODE_STAGE1, a, c->ntiles, s)))
+      return cuda_fail(c, e, "replay stage 1");
+    a.U = c->d_U1; a.V = c->d_V1; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = c->d_U2; a.Vout = c->d_V2;
+    a.Vt0out = nullptr; a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
+    if ((e = launch_stage_1d(c->eq, false, c->variant, MODE_STAGE2, a, c->ntiles, s)))
+      return cuda_fail(c, e, "replay stage 2");
+  }
   // 2. reverse stages 3, 2, 1 (the adjoint kernels use the default tiles)
   double *aU2 = adj_field(c, 0), *aV2 = adj_field(c, 1), *aU1 = adj_field(c, 3),
          *aV1 = adj_field(c, 4), *acU = adj_field(c, 6), *acV = adj_field(c, 7);
@@ -1171,39 +1175,43 @@ int adjoint_1d(hweno_ctx* c, const void* U, const void* V, const double* dt, dou
   g.accOutU = nullptr; g.accOutVt = nullptr;
   g.outU = lU; g.outV = lV;
   if ((e = launch_adjoint_1d(c->eq, g, c->ntiles0, s))) return cuda_fail(c, e, "adjoint 1");
-  c->launches = 6;
+  c->launches = replay ? 6 : 3;
   return HWENO_OK;
 }
 
 int adjoint_2d(hweno_ctx* c, const void* U, const void* V, const void* W, const double* t,
-               const double* dt, double* lU, double* lV, double* lW, cudaStream_t s) {
+               const double* dt, double* lU, double* lV, double* lW, bool replay,
+               cudaStream_t s) {
   cudaError_t e;
-  // 1. replay stages 1 and 2 with the recorded dt (alpha slots 0, 1, 2)
-  if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 6, s)))
-    return cuda_fail(c, e, "memset");
+  // 1. replay stages 1 and 2 with the recorded dt (alpha slots 0, 1, 2);
+  //    without replay the stage states and slots come from a record
   Args2D a = base_args_2d(c);
-  a.t = t;
-  a.t_end = 0.0;
-  a.skip_done = 0;
-  a.dt_in = dt;
-  a.U = U;
-  a.alpha_out = c->d_alpha;
-  if ((e = launch_alpha_2d(c->eq, false, a, s))) return cuda_fail(c, e, "alpha");
-  struct Stage { const void *u, *v, *w; void *uo, *vo, *wo, *vt; double sc; };
-  const Stage st[2] = {{U, V, W, c->d_U1, c->d_V1, c->d_W1, c->d_Vt0, 0.0},
-                       {c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_VT, 1.0}};
-  for (int k = 0; k < 2; ++k) {
-    const int mode = MODE_STAGE1 + k;
-    a.U = st[k].u; a.V = st[k].v; a.W = st[k].w;
-    a.U0 = U; a.Vt0 = c->d_Vt0; a.Wt0 = c->d_Wt0;
-    a.Uout = st[k].uo; a.Vout = st[k].vo; a.Wout = st[k].wo;
-    a.Wt0out = k == 0 ? c->d_Wt0 : nullptr;
-    a.VT = st[k].vt;
-    a.stage_c = st[k].sc;
-    a.alpha_in = reinterpret_cast<const double*>(c->d_alpha + 2 * k);
-    a.alpha_out = c->d_alpha + 2 * (k + 1);
-    if ((e = launch_xsweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay x");
-    if ((e = launch_ysweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay y");
+  if (replay) {
+    if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 6, s)))
+      return cuda_fail(c, e, "memset");
+    a.t = t;
+    a.t_end = 0.0;
+    a.skip_done = 0;
+    a.dt_in = dt;
+    a.U = U;
+    a.alpha_out = c->d_alpha;
+    if ((e = launch_alpha_2d(c->eq, false, a, s))) return cuda_fail(c, e, "alpha");
+    struct Stage { const void *u, *v, *w; void *uo, *vo, *wo, *vt; double sc; };
+    const Stage st[2] = {{U, V, W, c->d_U1, c->d_V1, c->d_W1, c->d_Vt0, 0.0},
+                         {c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_VT, 1.0}};
+    for (int k = 0; k < 2; ++k) {
+      const int mode = MODE_STAGE1 + k;
+      a.U = st[k].u; a.V = st[k].v; a.W = st[k].w;
+      a.U0 = U; a.Vt0 = c->d_Vt0; a.Wt0 = c->d_Wt0;
+      a.Uout = st[k].uo; a.Vout = st[k].vo; a.Wout = st[k].wo;
+      a.Wt0out = k == 0 ? c->d_Wt0 : nullptr;
+      a.VT = st[k].vt;
+      a.stage_c = st[k].sc;
+      a.alpha_in = reinterpret_cast<const double*>(c->d_alpha + 2 * k);
+      a.alpha_out = c->d_alpha + 2 * (k + 1);
+      if ((e = launch_xsweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay x");
+      if ((e = launch_ysweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay y");
+    }
   }
   // 2. reverse stages 3, 2, 1: an x sweep into `part`, then a y sweep
   AdjArgs2D g{};
@@ -1242,16 +1250,46 @@ int adjoint_2d(hweno_ctx* c, const void* U, const void* V, const void* W, const 
     if ((e = launch_adjoint_2d(c->eq, 0, g, s))) return cuda_fail(c, e, "adjoint x");
     if ((e = launch_adjoint_2d(c->eq, 1, g, s))) return cuda_fail(c, e, "adjoint y");
   }
-  c->launches = 11;
+  c->launches = replay ? 11 : 6;
   return HWENO_OK;
 }
 
-}  // namespace
+// A step record: the stage states x1 = (U1, V1 [, W1]) and x2 = (U2, V2
+// [, W2]) of one forward step and its wave-speed slots, so that the adjoint
+// of that step needs no replay.
+int record_fields(const hweno_ctx* c) { return c->dim == 2 ? 6 : 4; }
+size_t record_alpha_bytes(const hweno_ctx* c) {
+  return sizeof(unsigned long long) * (c->dim == 2 ? 6 : 3 * (size_t)c->batch);
+}
+size_t record_bytes(const hweno_ctx* c) {
+  const size_t b = record_fields(c) * c->elems * sizeof(double) + record_alpha_bytes(c);
+  return (b + 255) / 256 * 256;
+}
 
-int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W,
-                       const double* t, const double* dt, void* lamU, void* lamV, void* lamW,
-                       void* stream) {
-  if (!c) return HWENO_EINVAL;
+// Copy the context's stage states and slots into a record, or back.
+int record_copy(hweno_ctx* c, void* rec, bool to_record, cudaStream_t s) {
+  void* bufs[6] = {c->d_U1, c->d_V1, c->d_U2, c->d_V2, c->d_W1, c->d_W2};
+  const size_t fb = c->elems * sizeof(double);
+  char* r = static_cast<char*>(rec);
+  const int nf = record_fields(c);
+  cudaError_t e;
+  for (int i = 0; i < nf; ++i) {
+    void* dst = to_record ? static_cast<void*>(r + i * fb) : bufs[i];
+    const void* src = to_record ? bufs[i] : static_cast<const void*>(r + i * fb);
+    if ((e = cudaMemcpyAsync(dst, src, fb, cudaMemcpyDeviceToDevice, s)))
+      return cuda_fail(c, e, "record copy");
+  }
+  void* ra = r + nf * fb;
+  if ((e = cudaMemcpyAsync(to_record ? ra : static_cast<void*>(c->d_alpha),
+                           to_record ? static_cast<const void*>(c->d_alpha) : ra,
+                           record_alpha_bytes(c), cudaMemcpyDeviceToDevice, s)))
+    return cuda_fail(c, e, "record copy");
+  return HWENO_OK;
+}
+
+// Checks shared by the adjoint entry points; HWENO_OK when the call may run.
+int adjoint_check(hweno_ctx* c, const void* U, const void* V, const void* W, const double* dt,
+                  const void* lamU, const void* lamV, const void* lamW) {
   if (c->fp32) return fail(c, HWENO_ENOTSUP, "adjoint built for FP64 states");
   if (c->eq == HWENO_BUCKLEY)
     return fail(c, HWENO_ENOTSUP, "adjoint built for Burgers and Euler");
@@ -1264,11 +1302,22 @@ int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W
   for (int d = 0; d < c->dim; ++d)
     if ((bcs[2 * d] == HWENO_BC_PERIODIC) != (bcs[2 * d + 1] == HWENO_BC_PERIODIC))
       return fail(c, HWENO_ENOTSUP, "adjoint needs both ends of a direction periodic or neither");
+  return adjoint_scratch(c);
+}
+
+// The adjoint of one step, with the stage states replayed (record null) or
+// taken from a record.
+int adjoint_any(hweno_ctx* c, const void* U, const void* V, const void* W, const double* t,
+                const double* dt, void* lamU, void* lamV, void* lamW, const void* record,
+                cudaStream_t s) {
   int rc;
-  if ((rc = adjoint_scratch(c)) != HWENO_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!two)
-    return adjoint_1d(c, U, V, dt, static_cast<double*>(lamU), static_cast<double*>(lamV), s);
+  if ((rc = adjoint_check(c, U, V, W, dt, lamU, lamV, lamW)) != HWENO_OK) return rc;
+  if (record && (rc = record_copy(c, const_cast<void*>(record), false, s)) != HWENO_OK)
+    return rc;
+  const bool replay = record == nullptr;
+  if (c->dim == 1)
+    return adjoint_1d(c, U, V, dt, static_cast<double*>(lamU), static_cast<double*>(lamV),
+                      replay, s);
   const double* tt = t;
   if (!tt) {  // no boundary time given: the boundaries must not depend on it
     if (c->bc.yhi == HWENO_BC_DMR_TOP)
@@ -1278,7 +1327,41 @@ int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W
     tt = c->d_ht;
   }
   return adjoint_2d(c, U, V, W, tt, dt, static_cast<double*>(lamU), static_cast<double*>(lamV),
-                    static_cast<double*>(lamW), s);
+                    static_cast<double*>(lamW), replay, s);
+}
+
+}  // namespace
+
+int hweno_adjoint_step(hweno_ctx* c, const void* U, const void* V, const void* W,
+                       const double* t, const double* dt, void* lamU, void* lamV, void* lamW,
+                       void* stream) {
+  if (!c) return HWENO_EINVAL;
+  return adjoint_any(c, U, V, W, t, dt, lamU, lamV, lamW, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+long long hweno_adjoint_record_bytes(const hweno_ctx* c) {
+  if (!c) return -1;
+  return (long long)record_bytes(c);
+}
+
+int hweno_step_record(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end,
+                      double* dt_used, void* record, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!record) return fail(c, HWENO_EINVAL, "null record");
+  if (c->fp32) return fail(c, HWENO_ENOTSUP, "records are built for FP64 states");
+  int rc = hweno_step(c, U, V, W, t, t_end, dt_used, stream);
+  if (rc != HWENO_OK) return rc;
+  return record_copy(c, record, true, static_cast<cudaStream_t>(stream));
+}
+
+int hweno_adjoint_step_recorded(hweno_ctx* c, const void* U, const void* V, const void* W,
+                                const void* record, const double* t, const double* dt,
+                                void* lamU, void* lamV, void* lamW, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (!record) return fail(c, HWENO_EINVAL, "null record");
+  return adjoint_any(c, U, V, W, t, dt, lamU, lamV, lamW, record,
+                     static_cast<cudaStream_t>(stream));
 }
 
 int hweno_sync_status(hweno_ctx* c, void* stream) {

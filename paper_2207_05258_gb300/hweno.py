@@ -91,6 +91,10 @@ SIGNATURES = {
                                              ctypes.POINTER(Options), _VP, _VP, _VP,
                                              ctypes.c_double, _VP, _VP]),
     "hweno_measure_fp64_peak": (ctypes.c_int, [_DP, _VP]),
+    "hweno_adjoint_record_bytes": (ctypes.c_longlong, [_VP]),
+    "hweno_step_record": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP,
+                                         _VP]),
+    "hweno_adjoint_step_recorded": (ctypes.c_int, [_VP] * 11),
     "hweno_last_error": (ctypes.c_char_p, [_VP]),
     "hweno_destroy": (ctypes.c_int, [_VP]),
 }
@@ -238,12 +242,34 @@ class Solver:
         self._check(lib.hweno_totals(self.h, _ptr(U), _ptr(out), _stream()))
         return out
 
-    def adjoint_step(self, U, V, W, dt, lamU, lamV, lamW=None, t=None):
+    def adjoint_step(self, U, V, W, dt, lamU, lamV, lamW=None, t=None, record=None):
         """hweno_adjoint_step: lamU, lamV (, lamW) (in: d J / d output of the
         step taken from U, V (, W) at time t with time steps dt) become
-        d J / d input, in place."""
-        self._check(lib.hweno_adjoint_step(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t), _ptr(dt),
-                                           _ptr(lamU), _ptr(lamV), _ptr(lamW), _stream()))
+        d J / d input, in place. With `record` (from step_record of that
+        step): hweno_adjoint_step_recorded, no replay of the stages."""
+        if record is None:
+            self._check(lib.hweno_adjoint_step(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t),
+                                               _ptr(dt), _ptr(lamU), _ptr(lamV), _ptr(lamW),
+                                               _stream()))
+        else:
+            self._check(lib.hweno_adjoint_step_recorded(
+                self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(record), _ptr(t), _ptr(dt), _ptr(lamU),
+                _ptr(lamV), _ptr(lamW), _stream()))
+
+    @property
+    def record_bytes(self) -> int:
+        """hweno_adjoint_record_bytes: size of one step record."""
+        return int(lib.hweno_adjoint_record_bytes(self.h))
+
+    def new_record(self, device="cuda"):
+        """A device buffer for one step record."""
+        return torch.empty(self.record_bytes, dtype=torch.uint8, device=device)
+
+    def step_record(self, U, V, W, t, t_end, record, dt_used=None):
+        """hweno_step_record: hweno_step that also saves the stage states and
+        wave speeds of the step into `record` (see new_record)."""
+        self._check(lib.hweno_step_record(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t),
+                                          float(t_end), _ptr(dt_used), _ptr(record), _stream()))
 
     def active_instances(self) -> int:
         n = lib.hweno_active_instances(self.h, _stream())

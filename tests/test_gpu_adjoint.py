@@ -412,3 +412,73 @@ def test_frozen_weights_2d_euler(hw):
     w = rough_2d("euler", 40, 30, "periodic", "outflow", 64)
     r = _dot_check_2d(hw, w, 65, 1e-11, adj_frozen_weights=1)
     print("2D frozen weights: relative mismatch %.2e" % r)
+
+
+# ---------------------------------------------------------------------------
+# step records (hweno_step_record / hweno_adjoint_step_recorded): the adjoint
+# without its replay gives the bits of the replaying adjoint
+# ---------------------------------------------------------------------------
+def _recorded_vs_replayed(hw, w, steps, t_end, two):
+    s = hw.Solver.from_workload(w)
+    dev = lambda x: torch.from_numpy(x.copy()).cuda()
+    U, V = dev(w.U), dev(w.V)
+    Wd = dev(w.W) if two else None
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    for _ in range(steps):  # move away from the initial data
+        s.step(U, V, Wd, t, t_end)
+    U0, V0 = U.clone(), V.clone()
+    W0 = Wd.clone() if two else None
+    t0 = t.clone()
+    dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+    rec = s.new_record()
+    s.step_record(U, V, Wd, t, t_end, rec, dt)
+    rng = np.random.default_rng(5)
+    lam = [torch.from_numpy(rng.standard_normal(w.U.size)).cuda() for _ in range(3 if two else 2)]
+    a = [x.clone() for x in lam]
+    b = [x.clone() for x in lam]
+    s.adjoint_step(U0, V0, W0, dt, *a[:2], a[2] if two else None, t=t0)
+    assert s.launches_last_call == (11 if two else 6)
+    s.adjoint_step(U0, V0, W0, dt, *b[:2], b[2] if two else None, t=t0, record=rec)
+    assert s.launches_last_call == (6 if two else 3)
+    s.sync_status()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    s.close()
+
+
+def test_recorded_adjoint_1d_burgers(hw):
+    w = rough_batch([40, 123, 124, 125, 300], "periodic", 61)
+    _recorded_vs_replayed(hw, w, 2, 0.05, False)
+
+
+def test_recorded_adjoint_1d_euler_with_finished_instances(hw):
+    w = euler_rough_batch([40, 200, 130], "outflow", 62)
+    _recorded_vs_replayed(hw, w, 3, 0.01, False)  # the 40-point instance lands on t_end early
+
+
+@pytest.mark.parametrize("case", [("euler", 130, 128, "periodic", "periodic"),
+                                  ("euler", 40, 36, "reflective", "outflow"),
+                                  ("burgers", 30, 40, "periodic", "periodic")])
+def test_recorded_adjoint_2d(hw, case):
+    eq, nx, ny, bcx, bcy = case
+    w = rough_2d(eq, nx, ny, bcx, bcy, 63)
+    _recorded_vs_replayed(hw, w, 2, 1.0, True)
+
+
+def test_record_arguments(hw):
+    w = rough_batch([64], "periodic", 64)
+    s = hw.Solver.from_workload(w)
+    assert s.record_bytes >= 4 * 64 * 8 and s.record_bytes % 256 == 0
+    U = torch.from_numpy(w.U.copy()).cuda()
+    V = torch.from_numpy(w.V.copy()).cuda()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(hw.HwenoError) as e:
+        s.step_record(U, V, None, t, 1.0, None)
+    assert e.value.code == hw.EINVAL
+    s.close()
+    f = hw.Solver.from_workload(w, precision="fp32")
+    rec = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hw.HwenoError) as e:
+        f.step_record(U.float(), V.float(), None, t, 1.0, rec)
+    assert e.value.code == hw.ENOTSUP
+    f.close()
