@@ -27,8 +27,9 @@
  *  - The library allocates the scratch of a step (stage buffers, the stored
  *    limited derivative, per-instance wave speeds and time steps, a status
  *    word) in hweno_create and frees everything in hweno_destroy. Only
- *    hweno_adjoint_step, hweno_run_persistent and the pipelined
- *    hweno_step_host allocate more, once, on their first call.
+ *    hweno_adjoint_step (and its recorded form), hweno_run_persistent and
+ *    the pipelined hweno_step_host allocate more, once, on their first call;
+ *    hweno_measure_fp64_peak allocates and frees a small buffer.
  *  - Every call returns an int status: HWENO_OK (0) or a negative code; a
  *    readable message is kept in the context (hweno_last_error). Errors the
  *    device detects (a non-finite wave speed) are latched into the context's
