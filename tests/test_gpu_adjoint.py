@@ -482,3 +482,28 @@ def test_record_arguments(hw):
         f.step_record(U.float(), V.float(), None, t, 1.0, rec)
     assert e.value.code == hw.ENOTSUP
     f.close()
+
+
+def test_recorded_adjoint_after_a_cluster_step(hw):
+    """A record taken by the cluster step (fused_small = 2) holds the stage
+    states that step computed; its adjoint matches the replaying adjoint
+    (which recomputes them with the tiled kernels) to rounding."""
+    w = rough_batch([40, 123, 300], "periodic", 65)
+    s = hw.Solver.from_workload(w, fused_small=2)
+    U = torch.from_numpy(w.U.copy()).cuda()
+    V = torch.from_numpy(w.V.copy()).cuda()
+    t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+    U0, V0, t0 = U.clone(), V.clone(), t.clone()
+    dt = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+    rec = s.new_record()
+    s.step_record(U, V, None, t, 0.05, rec, dt)
+    rng = np.random.default_rng(6)
+    lam = [torch.from_numpy(rng.standard_normal(w.U.size)).cuda() for _ in range(2)]
+    a = [x.clone() for x in lam]
+    b = [x.clone() for x in lam]
+    s.adjoint_step(U0, V0, None, dt, a[0], a[1], t=t0)
+    s.adjoint_step(U0, V0, None, dt, b[0], b[1], t=t0, record=rec)
+    s.sync_status()
+    for x, y in zip(a, b):
+        assert float((x - y).abs().max()) <= 1e-12 * float(x.abs().max())
+    s.close()
