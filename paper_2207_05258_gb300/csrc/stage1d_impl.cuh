@@ -152,6 +152,140 @@ __device__ __forceinline__ StageIO io_of(const Args1D& a) {
   return StageIO{a.U, a.V, a.U0, a.Vt0, a.Uout, a.Vout, a.Vt0out, a.alpha_in, a.alpha_out};
 }
 
+// Point g of a tile starting at s (instance point s - 2 + g; ghosts by the
+// boundary conditions): stores u, v, the split fluxes f^+-, H^+- (H = dx h)
+// and, for Euler, sqrt(rho), u, H and c^2 in shared memory.
+template <int EQ, class Real, int NP>
+__device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const Real* V, int n,
+                                           int s, int g, Real alpha, Real hdx, Real gam, Real gm1,
+                                           Real (*sU)[NP], Real (*sV)[NP], Real (*sFp)[NP],
+                                           Real (*sFm)[NP], Real (*sHp)[NP], Real (*sHm)[NP],
+                                           Real (*sE)[NP]) {
+  constexpr int M = Dim1<EQ>::M;
+  int kind;
+  const int src = map_1d(s - 2 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
+  Real u[M], v[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    if (kind == 2) {
+      u[c] = Real(a.sp.inflow[c]);
+      v[c] = Real(0);
+    } else {
+      u[c] = U[(long long)c * n + src];
+      v[c] = V[(long long)c * n + src];
+      if (kind == 1) { const Real sg = Real(refl_sign<EQ>(c)); u[c] *= sg; v[c] *= -sg; }
+    }
+    sU[c][g] = u[c];
+    sV[c][g] = v[c];
+  }
+  Real F[M], H[M];
+  if constexpr (EQ == HWENO_BURGERS) {
+    F[0] = Real(0.5) * u[0] * u[0];
+    H[0] = u[0] * v[0];
+  } else if constexpr (EQ == HWENO_BUCKLEY) {
+    Real df;
+    buckley_f(u[0], F[0], df);
+    H[0] = df * v[0];
+  } else {
+    // 1/rho and sqrt(rho) from one reciprocal square root
+    const Real rr = rsq(u[0]);
+    const Real ir = rr * rr;
+    const Real vel = u[1] * ir;
+    const Real p = gm1 * (u[2] - Real(0.5) * u[1] * vel);
+    const Real Ep = u[2] + p;
+    F[0] = u[1];
+    F[1] = u[1] * vel + p;
+    F[2] = Ep * vel;
+    const Real dvel = (v[1] - vel * v[0]) * ir;
+    const Real dp = gm1 * (v[2] - vel * v[1] + Real(0.5) * vel * vel * v[0]);
+    H[0] = v[1];
+    H[1] = v[1] * vel + u[1] * dvel + dp;
+    H[2] = (v[2] + dp) * vel + Ep * dvel;
+    sE[0][g] = u[0] * rr;
+    sE[1][g] = vel;
+    sE[2][g] = Ep * ir;
+    sE[3][g] = gam * p * ir;
+  }
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
+    sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
+    sHp[c][g] = hdx * (H[c] + alpha * v[c]);
+    sHm[c][g] = hdx * (H[c] - alpha * v[c]);
+  }
+}
+
+// The limited derivative v~ at loaded point g (Sec. 2.2): v unchanged with
+// the limiter off, component-wise, or (Euler) on the characteristic fields
+// of the eigenvectors at U_g.
+template <int EQ, class Real, int NP>
+__device__ __forceinline__ void limited_point(const Args1D& a, int g, Real dx, Real idx, Real gm1,
+                                              const Weights<Real>& w, Real (*sU)[NP],
+                                              Real (*sV)[NP], Real (*sE)[NP], Real* vt) {
+  constexpr int M = Dim1<EQ>::M;
+  constexpr bool EUL = EQ == HWENO_EULER;
+  if (a.sp.limiter == 0) {
+#pragma unroll
+    for (int c = 0; c < M; ++c) vt[c] = sV[c][g];
+  } else if (!EUL || a.sp.limiter == 2) {
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+      vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
+                                 dx * sV[c][g + 1], w) * idx;
+  } else if constexpr (EUL) {
+    Real cg, icg;
+    sound_speed(sE[3][g], cg, icg);
+    Eigen<Real, 3> e;
+    euler_eigen<Real, 3>(0, sE[1][g], Real(0), sE[2][g], cg, icg, gm1, e);
+    Frac<Real> zr[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const Real l0 = e.L[q][0], l1q = e.L[q][1], l2q = e.L[q][2];
+      auto pj = [&](Real (*A)[NP], int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
+      zr[q] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
+                                      dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
+    }
+    Real z[3];
+    resolve2(zr[0], zr[1], z[0], z[1]);
+    z[2] = resolve1(zr[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      vt[c] = (e.R[c][0] * z[0] + e.R[c][1] * z[1] + e.R[c][2] * z[2]) * idx;
+  }
+}
+
+// The SSP-RK3 combination of one stage at instance point q (component
+// stride n) from the stage input u, the right-hand sides l1, l2 and v~:
+// writes U, V of the stage output (stage 1 also v~^n) and returns U in un.
+template <int EQ, class Real, int MODE>
+__device__ __forceinline__ void stage_update(const StageIO& io, long long base, long long n,
+                                             const Real* u, const Real* l1, const Real* l2,
+                                             const Real* vt, Real rdt, Real* un) {
+  constexpr int M = Dim1<EQ>::M;
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    const long long q = base + (long long)c * n;
+    Real vn;
+    if constexpr (MODE == MODE_STAGE1) {
+      un[c] = u[c] + rdt * l1[c];
+      vn = vt[c] + rdt * l2[c];
+      static_cast<Real*>(io.Vt0out)[q] = vt[c];
+    } else if constexpr (MODE == MODE_STAGE2) {
+      const Real u0 = static_cast<const Real*>(io.U0)[q];
+      const Real v0 = static_cast<const Real*>(io.Vt0)[q];
+      un[c] = Real(0.75) * u0 + Real(0.25) * (u[c] + rdt * l1[c]);
+      vn = Real(0.75) * v0 + Real(0.25) * (vt[c] + rdt * l2[c]);
+    } else {
+      const Real u0 = static_cast<const Real*>(io.U0)[q];
+      const Real v0 = static_cast<const Real*>(io.Vt0)[q];
+      un[c] = Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * (u[c] + rdt * l1[c]);
+      vn = Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * (vt[c] + rdt * l2[c]);
+    }
+    static_cast<Real*>(io.Uout)[q] = un[c];
+    static_cast<Real*>(io.Vout)[q] = vn;
+  }
+}
+
 // One stage on the tile of instance k starting at point s (the whole CTA;
 // contains barriers, so every thread calls it with the same k, s).
 template <int EQ, class Real, int MODE, int NT, int PPT>
@@ -206,59 +340,9 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
     const Real* U = static_cast<const Real*>(io.U) + off;
     const Real* V = static_cast<const Real*>(io.V) + off;
     const Real hdx = Real(0.5) * dx;
-    for (int g = threadIdx.x; g < np + 4; g += blockDim.x) {
-      int kind;
-      const int src = map_1d(s - 2 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
-      Real u[M], v[M];
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        if (kind == 2) {
-          u[c] = Real(a.sp.inflow[c]);
-          v[c] = Real(0);
-        } else {
-          u[c] = U[(long long)c * n + src];
-          v[c] = V[(long long)c * n + src];
-          if (kind == 1) { const Real sg = Real(refl_sign<EQ>(c)); u[c] *= sg; v[c] *= -sg; }
-        }
-        sU[c][g] = u[c];
-        sV[c][g] = v[c];
-      }
-      Real F[M], H[M];
-      if constexpr (EQ == HWENO_BURGERS) {
-        F[0] = Real(0.5) * u[0] * u[0];
-        H[0] = u[0] * v[0];
-      } else if constexpr (EQ == HWENO_BUCKLEY) {
-        Real df;
-        buckley_f(u[0], F[0], df);
-        H[0] = df * v[0];
-      } else {
-        // 1/rho and sqrt(rho) from one reciprocal square root
-        const Real rr = rsq(u[0]);
-        const Real ir = rr * rr;
-        const Real vel = u[1] * ir;
-        const Real p = gm1 * (u[2] - Real(0.5) * u[1] * vel);
-        const Real Ep = u[2] + p;
-        F[0] = u[1];
-        F[1] = u[1] * vel + p;
-        F[2] = Ep * vel;
-        const Real dvel = (v[1] - vel * v[0]) * ir;
-        const Real dp = gm1 * (v[2] - vel * v[1] + Real(0.5) * vel * vel * v[0]);
-        H[0] = v[1];
-        H[1] = v[1] * vel + u[1] * dvel + dp;
-        H[2] = (v[2] + dp) * vel + Ep * dvel;
-        sE[0][g] = u[0] * rr;
-        sE[1][g] = vel;
-        sE[2][g] = Ep * ir;
-        sE[3][g] = gam * p * ir;
-      }
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
-        sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
-        sHp[c][g] = hdx * (H[c] + alpha * v[c]);
-        sHm[c][g] = hdx * (H[c] - alpha * v[c]);
-      }
-    }
+    for (int g = threadIdx.x; g < np + 4; g += blockDim.x)
+      tile_point<EQ, Real, NP>(a, U, V, n, s, g, alpha, hdx, gam, gm1, sU, sV, sFp, sFm, sHp,
+                               sHm, sE);
   }
   __syncthreads();
 
@@ -328,34 +412,7 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
       l1[c] = -(sF[c][j + 1] - sF[c][j]) * idx;
       l2[c] = -(sD[c][j + 1] - sD[c][j]) * idx2;
     }
-    if (a.sp.limiter == 0) {
-#pragma unroll
-      for (int c = 0; c < M; ++c) vt[c] = sV[c][g];
-    } else if (!EUL || a.sp.limiter == 2) {
-#pragma unroll
-      for (int c = 0; c < M; ++c)
-        vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
-                                   dx * sV[c][g + 1], w) * idx;
-    } else if constexpr (EUL) {
-      Real cg, icg;
-      sound_speed(sE[3][g], cg, icg);
-      Eigen<Real, 3> e;
-      euler_eigen<Real, 3>(0, sE[1][g], Real(0), sE[2][g], cg, icg, gm1, e);
-      Frac<Real> zr[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const Real l0 = e.L[q][0], l1q = e.L[q][1], l2q = e.L[q][2];
-        auto pj = [&](Real (*A)[NP], int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
-        zr[q] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
-                                        dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
-      }
-      Real z[3];
-      resolve2(zr[0], zr[1], z[0], z[1]);
-      z[2] = resolve1(zr[2]);
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        vt[c] = (e.R[c][0] * z[0] + e.R[c][1] * z[1] + e.R[c][2] * z[2]) * idx;
-    }
+    limited_point<EQ, Real, NP>(a, g, dx, idx, gm1, w, sU, sV, sE, vt);
 
     const long long base = off + s + j;
     if constexpr (MODE == MODE_RHS) {
@@ -366,28 +423,10 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
         if (a.Vlim) static_cast<Real*>(a.Vlim)[base + (long long)c * n] = vt[c];
       }
     } else {
-      Real un[M], vn[M];
+      Real u[M], un[M];
 #pragma unroll
-      for (int c = 0; c < M; ++c) {
-        const long long q = base + (long long)c * n;
-        if constexpr (MODE == MODE_STAGE1) {
-          un[c] = sU[c][g] + rdt * l1[c];
-          vn[c] = vt[c] + rdt * l2[c];
-          static_cast<Real*>(io.Vt0out)[q] = vt[c];
-        } else if constexpr (MODE == MODE_STAGE2) {
-          const Real u0 = static_cast<const Real*>(io.U0)[q];
-          const Real v0 = static_cast<const Real*>(io.Vt0)[q];
-          un[c] = Real(0.75) * u0 + Real(0.25) * (sU[c][g] + rdt * l1[c]);
-          vn[c] = Real(0.75) * v0 + Real(0.25) * (vt[c] + rdt * l2[c]);
-        } else {
-          const Real u0 = static_cast<const Real*>(io.U0)[q];
-          const Real v0 = static_cast<const Real*>(io.Vt0)[q];
-          un[c] = Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * (sU[c][g] + rdt * l1[c]);
-          vn[c] = Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * (vt[c] + rdt * l2[c]);
-        }
-        static_cast<Real*>(io.Uout)[q] = un[c];
-        static_cast<Real*>(io.Vout)[q] = vn[c];
-      }
+      for (int c = 0; c < M; ++c) u[c] = sU[c][g];
+      stage_update<EQ, Real, MODE>(io, base, n, u, l1, l2, vt, rdt, un);
       if (want_alpha) {
         const Real sp = wave_speed<EQ>(un, gam, pick<Real>(a.sp.wd, a.sp.wf)[10]);
         bad |= !(sp <= real_max<Real>());
@@ -803,62 +842,10 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
 
   // A (warp 0): the tile with ghosts, point fluxes and splitting; lane g is
   // point s - 2 + g
-  if (warp == 0 && lane < np + 4) {
-    const Real* U = static_cast<const Real*>(io.U) + off;
-    const Real* V = static_cast<const Real*>(io.V) + off;
-    const Real hdx = Real(0.5) * dx;
-    const int g = lane;
-    int kind;
-    const int src = map_1d(s - 2 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
-    Real u[M], v[M];
-#pragma unroll
-    for (int c = 0; c < M; ++c) {
-      if (kind == 2) {
-        u[c] = Real(a.sp.inflow[c]);
-        v[c] = Real(0);
-      } else {
-        u[c] = U[(long long)c * n + src];
-        v[c] = V[(long long)c * n + src];
-        if (kind == 1) { const Real sg = Real(refl_sign<EQ>(c)); u[c] *= sg; v[c] *= -sg; }
-      }
-      sU[c][g] = u[c];
-      sV[c][g] = v[c];
-    }
-    Real F[M], H[M];
-    if constexpr (EQ == HWENO_BURGERS) {
-      F[0] = Real(0.5) * u[0] * u[0];
-      H[0] = u[0] * v[0];
-    } else if constexpr (EQ == HWENO_BUCKLEY) {
-      Real df;
-      buckley_f(u[0], F[0], df);
-      H[0] = df * v[0];
-    } else {
-      const Real rr = rsq(u[0]);
-      const Real ir = rr * rr;
-      const Real vel = u[1] * ir;
-      const Real p = gm1 * (u[2] - Real(0.5) * u[1] * vel);
-      const Real Ep = u[2] + p;
-      F[0] = u[1];
-      F[1] = u[1] * vel + p;
-      F[2] = Ep * vel;
-      const Real dvel = (v[1] - vel * v[0]) * ir;
-      const Real dp = gm1 * (v[2] - vel * v[1] + Real(0.5) * vel * vel * v[0]);
-      H[0] = v[1];
-      H[1] = v[1] * vel + u[1] * dvel + dp;
-      H[2] = (v[2] + dp) * vel + Ep * dvel;
-      sE[0][g] = u[0] * rr;
-      sE[1][g] = vel;
-      sE[2][g] = Ep * ir;
-      sE[3][g] = gam * p * ir;
-    }
-#pragma unroll
-    for (int c = 0; c < M; ++c) {
-      sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
-      sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
-      sHp[c][g] = hdx * (H[c] + alpha * v[c]);
-      sHm[c][g] = hdx * (H[c] - alpha * v[c]);
-    }
-  }
+  if (warp == 0 && lane < np + 4)
+    tile_point<EQ, Real, NP>(a, static_cast<const Real*>(io.U) + off,
+                             static_cast<const Real*>(io.V) + off, n, s, lane, alpha,
+                             Real(0.5) * dx, gam, gm1, sU, sV, sFp, sFm, sHp, sHm, sE);
   __syncthreads();
 
   // B: warps 0 / 1 the "+" / "-" side of interface x_{s+j-1/2}, j = lane
@@ -908,34 +895,7 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
     const int j = lane, g = j + 2;
     if (j < np) {
       Real vt[M];
-      if (a.sp.limiter == 0) {
-#pragma unroll
-        for (int c = 0; c < M; ++c) vt[c] = sV[c][g];
-      } else if (!EUL || a.sp.limiter == 2) {
-#pragma unroll
-        for (int c = 0; c < M; ++c)
-          vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
-                                     dx * sV[c][g + 1], w) * idx;
-      } else if constexpr (EUL) {
-        Real cg, icg;
-        sound_speed(sE[3][g], cg, icg);
-        Eigen<Real, 3> el;
-        euler_eigen<Real, 3>(0, sE[1][g], Real(0), sE[2][g], cg, icg, gm1, el);
-        Frac<Real> zr[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const Real l0 = el.L[q][0], l1q = el.L[q][1], l2q = el.L[q][2];
-          auto pj = [&](Real (*A)[NP], int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
-          zr[q] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
-                                          dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
-        }
-        Real z[3];
-        resolve2(zr[0], zr[1], z[0], z[1]);
-        z[2] = resolve1(zr[2]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          vt[c] = (el.R[c][0] * z[0] + el.R[c][1] * z[1] + el.R[c][2] * z[2]) * idx;
-      }
+      limited_point<EQ, Real, NP>(a, g, dx, idx, gm1, w, sU, sV, sE, vt);
 #pragma unroll
       for (int c = 0; c < M; ++c) sVt[c][j] = vt[c];
     }
@@ -984,30 +944,10 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
       l1[c] = -(sF[c][j + 1] - sF[c][j]) * idx;
       l2[c] = -(sD[c][j + 1] - sD[c][j]) * idx2;
     }
-    const long long base_q = off + s + j;
-    Real un[M], vn[M];
+    Real u[M], vt[M], un[M];
 #pragma unroll
-    for (int c = 0; c < M; ++c) {
-      const long long q = base_q + (long long)c * n;
-      const Real vt = sVt[c][j];
-      if constexpr (MODE == MODE_STAGE1) {
-        un[c] = sU[c][g] + rdt * l1[c];
-        vn[c] = vt + rdt * l2[c];
-        static_cast<Real*>(io.Vt0out)[q] = vt;
-      } else if constexpr (MODE == MODE_STAGE2) {
-        const Real u0 = static_cast<const Real*>(io.U0)[q];
-        const Real v0 = static_cast<const Real*>(io.Vt0)[q];
-        un[c] = Real(0.75) * u0 + Real(0.25) * (sU[c][g] + rdt * l1[c]);
-        vn[c] = Real(0.75) * v0 + Real(0.25) * (vt + rdt * l2[c]);
-      } else {
-        const Real u0 = static_cast<const Real*>(io.U0)[q];
-        const Real v0 = static_cast<const Real*>(io.Vt0)[q];
-        un[c] = Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * (sU[c][g] + rdt * l1[c]);
-        vn[c] = Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * (vt + rdt * l2[c]);
-      }
-      static_cast<Real*>(io.Uout)[q] = un[c];
-      static_cast<Real*>(io.Vout)[q] = vn[c];
-    }
+    for (int c = 0; c < M; ++c) { u[c] = sU[c][g]; vt[c] = sVt[c][j]; }
+    stage_update<EQ, Real, MODE>(io, off + s + j, n, u, l1, l2, vt, rdt, un);
     if (want_alpha) {
       const Real sp = wave_speed<EQ>(un, gam, pick<Real>(a.sp.wd, a.sp.wf)[10]);
       bad = !(sp <= real_max<Real>());
