@@ -67,6 +67,11 @@ MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 100.5, "fp32": 40.3}
 # an ncu capture (profiles/k_run_1d_euler_fp64_riemann_batch.md); None until
 # taken for the kernel as it stands.
 MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.5, "fp32": None}
+# DRAM bytes per point of one 2D stage (x-sweep + y-sweep launches) on the
+# smooth periodic problem at 2048^2, from an ncu capture
+# (profiles/k_sweeps_2d_euler_fp64_smooth.md); applied to grids whose working
+# set exceeds the L2 (smaller grids keep part of it in L2).
+MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {"fp64": 627.8, "fp32": 306.6}
 
 
 def parse():
@@ -377,7 +382,10 @@ def run_ours(args, rank, world, dev_index):
     achieved = flop_stage * pts_per_stage / stage_time / 1e12
     peak = PEAK_TFLOPS[args.precision]
     traffic = (MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
-               if args.workload == "riemann_batch" else None)  # None: not yet re-captured
+               if args.workload == "riemann_batch" else
+               MEASURED_STAGE_TRAFFIC_2D_PER_POINT.get(args.precision)
+               if args.workload.startswith("euler2d_smooth") and not small
+               else None)  # None: not captured for this workload
     if use_clus:  # the headline kernel: one cluster launch per step
         achieved = ALGO_FLOPS_PER_POINT_STEP[(w.equation, w.dim)] * clus[1] / (clus[3] * 1e-3) / 1e12
     if use_pers:  # the headline kernel: K steps in one persistent launch
