@@ -270,9 +270,8 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
   const bool periodic = a.sp.bc[2 * DIR] == HWENO_BC_PERIODIC;  // both ends (host checks)
   const int lim = a.sp.limiter;
   const double ts = __dadd_rn(a.t[0], __dmul_rn(a.stage_c, dt));
-  const double xc = DIR == 1 ? __dadd_rn(a.x0, __dmul_rn((double)line + 0.5, a.dx)) : 0.0;
   auto src_of = [&](int p) {
-    return DIR == 0 ? map_x(p, nx, a.sp) : map_y(p, ny, xc, a.y0, a.dy, ts, a.sp);
+    return DIR == 0 ? map_x(p, nx, a.sp) : map_y(p, ny, line, a.x0, a.dx, a.y0, a.dy, ts, a.sp);
   };
   // the line's normal and tangential derivative fields and their cotangents
   const double* Nf = DIR == 0 ? a.V : a.W;

@@ -88,21 +88,19 @@ __device__ __forceinline__ Src map_x(int i, int n, const SchemeParams& sp) {
   return r;
 }
 
-// y ghosts of column x (cell centre) at stage time ts; the DMR bottom wall
-// starts at dmr_x0 and the top carries the exact shock position at the
-// ghost's height (reading of Example 3.11).
-__device__ __forceinline__ Src map_y(int j, int n, double x, double y0, double dy, double ts,
-                                     const SchemeParams& sp) {
+// y ghost rows that take an imposed state or, on the double-Mach bottom,
+// depend on x: column i (cell centre x = x0 + (i + 1/2) dx) at stage time
+// ts. Out of line, so that the FP64 arithmetic of the shock position runs
+// for these ghosts only and not, speculated, for every loaded point.
+static __device__ __noinline__ Src map_y_imposed(int j, int n, int b, int i, double x0, double dx,
+                                          double y0, double dy, double ts,
+                                          const SchemeParams& sp) {
   Src r{j, 0, 0};
-  if (j >= 0 && j < n) return r;
-  const int b = j < 0 ? sp.bc[2] : sp.bc[3];
-  if (b == HWENO_BC_PERIODIC) r.idx = j < 0 ? j + n : j - n;
-  else if (b == HWENO_BC_OUTFLOW) r.idx = j < 0 ? 0 : n - 1;
-  else if (b == HWENO_BC_REFLECTIVE ||
-           (b == HWENO_BC_DMR_BOTTOM && !(x < sp.dmr_x0))) {
+  const double x = __dadd_rn(x0, __dmul_rn((double)i + 0.5, dx));
+  if (b == HWENO_BC_DMR_BOTTOM && !(x < sp.dmr_x0)) {  // the wall
     r.kind = 1;
     r.idx = j < 0 ? -j - 1 : 2 * n - 1 - j;
-  } else if (b == HWENO_BC_DMR_TOP) {
+  } else if (b == HWENO_BC_DMR_TOP) {  // the exact shock at the ghost's height
     const double yg = __dadd_rn(y0, __dmul_rn((double)j + 0.5, dy));
     const double xs = __dadd_rn(__dadd_rn(sp.dmr_x0, __ddiv_rn(yg, sp.dmr_tan)),
                                 __ddiv_rn(__dmul_rn(sp.dmr_speed, ts), sp.dmr_sin));
@@ -110,6 +108,25 @@ __device__ __forceinline__ Src map_y(int j, int n, double x, double y0, double d
     r.pre = x < xs ? 0 : 1;
   } else {
     r.kind = 2;  // inflow, or the DMR bottom left of the wall
+  }
+  return r;
+}
+
+// y ghosts of column i at stage time ts; the DMR bottom wall starts at
+// dmr_x0 and the top carries the exact shock position at the ghost's height
+// (reading of Example 3.11).
+__device__ __forceinline__ Src map_y(int j, int n, int i, double x0, double dx, double y0,
+                                     double dy, double ts, const SchemeParams& sp) {
+  Src r{j, 0, 0};
+  if (j >= 0 && j < n) return r;
+  const int b = j < 0 ? sp.bc[2] : sp.bc[3];
+  if (b == HWENO_BC_PERIODIC) r.idx = j < 0 ? j + n : j - n;
+  else if (b == HWENO_BC_OUTFLOW) r.idx = j < 0 ? 0 : n - 1;
+  else if (b == HWENO_BC_REFLECTIVE) {
+    r.kind = 1;
+    r.idx = j < 0 ? -j - 1 : 2 * n - 1 - j;
+  } else {
+    r = map_y_imposed(j, n, b, i, x0, dx, y0, dy, ts, sp);
   }
   return r;
 }

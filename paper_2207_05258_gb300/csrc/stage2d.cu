@@ -411,9 +411,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
       const int r = k / C, col = k % C;
       if (col >= ncol || r >= nrow + 4) continue;
       const int i = i0 + col, jj = j0 - 2 + r;
-      // cell-centre x, needed only by the double-Mach maps of ghost rows
-      const double xc = jj < 0 || jj >= ny ? __dadd_rn(a.x0, __dmul_rn((double)i + 0.5, a.dx)) : 0.0;
-      const Src s = map_y(jj, ny, xc, a.y0, a.dy, ts, a.sp);
+      const Src s = map_y(jj, ny, i, a.x0, a.dx, a.y0, a.dy, ts, a.sp);
       Real u[M], v[M], ww[M];
 #pragma unroll
       for (int c = 0; c < M; ++c) {
