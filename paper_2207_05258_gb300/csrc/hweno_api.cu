@@ -203,7 +203,12 @@ SchemeParams scheme_params(const hweno_ctx* c) {
   sp.adj_frozen = c->opt.adj_frozen_weights;
   sp.gas_gamma = c->gamma;
   sp.bc[0] = c->bc.xlo; sp.bc[1] = c->bc.xhi; sp.bc[2] = c->bc.ylo; sp.bc[3] = c->bc.yhi;
-  for (int i = 0; i < 4; ++i) { sp.inflow[i] = c->bc.inflow[i]; sp.pre[i] = c->bc.pre[i]; }
+  for (int i = 0; i < 4; ++i) {
+    sp.inflow[i] = c->bc.inflow[i];
+    sp.pre[i] = c->bc.pre[i];
+    sp.inflowf[i] = (float)c->bc.inflow[i];
+    sp.pref[i] = (float)c->bc.pre[i];
+  }
   sp.dmr_x0 = c->bc.dmr_x0;
   sp.dmr_speed = c->bc.dmr_speed;
   sp.dmr_angle = c->bc.dmr_angle;

@@ -163,7 +163,12 @@ extern "C" int hweno_step_1d_noalloc(int equation, int nx, double x0, double x1,
   sp.eig_avg = o.eig_avg;
   sp.gas_gamma = gamma;
   sp.bc[0] = bc->xlo; sp.bc[1] = bc->xhi; sp.bc[2] = bc->ylo; sp.bc[3] = bc->yhi;
-  for (int i = 0; i < 4; ++i) { sp.inflow[i] = bc->inflow[i]; sp.pre[i] = bc->pre[i]; }
+  for (int i = 0; i < 4; ++i) {
+    sp.inflow[i] = bc->inflow[i];
+    sp.pre[i] = bc->pre[i];
+    sp.inflowf[i] = (float)bc->inflow[i];
+    sp.pref[i] = (float)bc->pre[i];
+  }
   const double tab[11] = {o.lin_w[0], o.lin_w[1], o.lin_w[2], o.lim_d[0], o.lim_d[1],
                           o.lim_d[2], o.eps, 1.0 / o.lin_w[0], 1.0 / o.lim_d[0], gamma, 0.0};
   for (int i = 0; i < 11; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }

@@ -52,6 +52,7 @@ struct SchemeParams {
   double gas_gamma;
   int bc[4];
   double inflow[4], pre[4];
+  float inflowf[4], pref[4];  // the same in FP32 (the 1D loads read these)
   double dmr_x0, dmr_speed, dmr_angle;
   double dmr_tan, dmr_sin;  // tan and sin of dmr_angle, evaluated on the host
   // constants in both precisions, converted once on the host:

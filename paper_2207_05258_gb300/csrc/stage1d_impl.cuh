@@ -168,7 +168,7 @@ __device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const
 #pragma unroll
   for (int c = 0; c < M; ++c) {
     if (kind == 2) {
-      u[c] = Real(a.sp.inflow[c]);
+      u[c] = pick<Real>(a.sp.inflow, a.sp.inflowf)[c];
       v[c] = Real(0);
     } else {
       u[c] = U[(long long)c * n + src];
