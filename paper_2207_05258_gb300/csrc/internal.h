@@ -314,6 +314,7 @@ constexpr int kClusterMax = 8;
 constexpr size_t kClusterSmem = 116 * 1024;
 // Latency form of the cluster step: 28-point tiles, up to 16 CTAs per cluster
 constexpr int kSplitTile = 28, kSplitMax = 16;
+static_assert(kSplitMax <= 32 && kClusterMax <= 32, "one lane per CTA in the cluster's alpha");
 static_assert(kClusterMax * kTile1D == HWENO_CLUSTER_MAX_POINTS, "cluster step size");
 cudaError_t launch_step_cluster_1d_f64(int eq, const Args1D& a, const FusedArgs& f, int max_n,
                                        cudaStream_t s);

@@ -1020,12 +1020,15 @@ k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ Fuse
       if (threadIdx.x == 0) part = (double)amax;
     }
     cl.sync();
-    if (live && rank == 0 && threadIdx.x == 0) {  // the instance's alpha; stage slots from zero
-      double m = 0.0;
-      for (int r = 0; r < C; ++r) m = fmax(m, *cl.map_shared_rank(&part, r));
-      s0[k] = (unsigned long long)__double_as_longlong(m);
-      s1[k] = 0ull;
-      s2[k] = 0ull;
+    if (live && rank == 0 && threadIdx.x < 32) {  // the instance's alpha; stage slots from zero
+      // one lane per CTA of the cluster (C <= 16) reads its partial, in parallel
+      double m = (int)threadIdx.x < C ? *cl.map_shared_rank(&part, (int)threadIdx.x) : 0.0;
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (threadIdx.x == 0) {
+        s0[k] = (unsigned long long)__double_as_longlong(m);
+        s1[k] = 0ull;
+        s2[k] = 0ull;
+      }
     }
     cl.sync();
     StageIO io = io_of(a);
