@@ -792,7 +792,8 @@ __device__ __forceinline__ Frac<Real> sides_sum(Real na, Real da, Real nb, Real 
 
 template <int EQ, class Real, int MODE>
 __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO& io, const int k,
-                                                 const int s) {
+                                                 const int s, const double alpha_in,
+                                                 const double dt, double* part_out) {
   using Lay = SplitLayout<EQ, Real>;
   constexpr int M = Lay::M;
   constexpr int NP = Lay::NP;
@@ -813,32 +814,17 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
   Real(*sD)[NF] = reinterpret_cast<Real(*)[NF]>(sSd + 2);
   Real(*sF)[NF] = sD + M;
   Real(*sVt)[P] = reinterpret_cast<Real(*)[P]>(sF + M);
-  __shared__ double s_dt;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.inst_n[k];
-  if (a.skip_done && !(a.t[k] < a.t_end)) return;
   const int np = min(P, n - s);
   const long long off = a.inst_off[k] * M;
   const Real* geo = pick<Real>(a.inst_geo, a.inst_geof) + 3 * k;
   const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
-  const Real alpha = Real(io.alpha_in[k]);
+  const Real alpha = Real(alpha_in);
   const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
   const Real gm1 = gam - Real(1);
   const Weights<Real> w = weights_from(pick<Real>(a.sp.wd, a.sp.wf));
-
-  if (threadIdx.x == 0) {  // time step (as stage_tile)
-    double dt = 0.0;
-    if constexpr (MODE == MODE_STAGE1) {
-      int lands = 0;
-      dt = a.dt_in ? a.dt_in[k]
-                   : time_step(a.sp, io.alpha_in[k], a.inst_hx[k], a.t[k], a.t_end, lands);
-      if (s == 0) { a.dt[k] = dt; a.lands[k] = lands; }
-    } else {
-      dt = a.dt[k];
-    }
-    s_dt = dt;
-  }
 
   // A (warp 0): the tile with ghosts, point fluxes and splitting; lane g is
   // point s - 2 + g
@@ -931,8 +917,8 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
     }
   }
   __syncwarp();
-  const Real rdt = Real(s_dt);
-  const bool want_alpha = io.alpha_out != nullptr;  // uniform
+  const Real rdt = Real(dt);
+  const bool want_alpha = part_out != nullptr;  // uniform
   Real amax = Real(0);
   bool bad = false;
   const int j = lane;
@@ -959,7 +945,7 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
       if (bad) atomicOr(a.status, STATUS_NONFINITE);
-      atomicMax(&io.alpha_out[k], (unsigned long long)__double_as_longlong((double)amax));
+      *part_out = (double)amax;  // this CTA's share of the stage output's wave speed
     }
   }
 }
@@ -976,18 +962,12 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
 // Every CTA passes the same six barriers per step whatever its share of the
 // instance.
 // ---------------------------------------------------------------------------
-template <int EQ, class Real, int MODE, bool SPLIT>
-__device__ __forceinline__ void cluster_stage(const Args1D& a, const StageIO& io, int k, int s) {
-  if constexpr (SPLIT) stage_tile_split<EQ, Real, MODE>(a, io, k, s);
-  else stage_tile<EQ, Real, MODE, kThreads1D, 1>(a, io, k, s);
-}
-
-template <int EQ, class Real, bool SPLIT>
+template <int EQ, class Real>
 __global__ void __launch_bounds__(kThreads1D)
 k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ FusedArgs f) {
   namespace cg = cooperative_groups;
   constexpr int M = Dim1<EQ>::M;
-  constexpr int P = SPLIT ? kSplitTile : kTile1D;
+  constexpr int P = kTile1D;
   __shared__ Real red[kThreads1D / 32];
   __shared__ double part;
   cg::cluster_group cl = cg::this_cluster();
@@ -1034,16 +1014,16 @@ k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ Fuse
     StageIO io = io_of(a);
     io.Uout = f.U1; io.Vout = f.V1; io.Vt0out = f.Vt0;
     io.alpha_in = reinterpret_cast<const double*>(s0); io.alpha_out = s1;
-    if (has) cluster_stage<EQ, Real, MODE_STAGE1, SPLIT>(a, io, k, s);
+    if (has) stage_tile<EQ, Real, MODE_STAGE1, kThreads1D, 1>(a, io, k, s);
     cl.sync();
     io.U = f.U1; io.V = f.V1; io.U0 = a.U; io.Vt0 = f.Vt0; io.Uout = f.U2; io.Vout = f.V2;
     io.Vt0out = nullptr;
     io.alpha_in = reinterpret_cast<const double*>(s1); io.alpha_out = s2;
-    if (has) cluster_stage<EQ, Real, MODE_STAGE2, SPLIT>(a, io, k, s);
+    if (has) stage_tile<EQ, Real, MODE_STAGE2, kThreads1D, 1>(a, io, k, s);
     cl.sync();
     io.U = f.U2; io.V = f.V2; io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V);
     io.alpha_in = reinterpret_cast<const double*>(s2); io.alpha_out = nullptr;
-    if (has) cluster_stage<EQ, Real, MODE_STAGE3, SPLIT>(a, io, k, s);
+    if (has) stage_tile<EQ, Real, MODE_STAGE3, kThreads1D, 1>(a, io, k, s);
     cl.sync();  // every CTA is past its reads of t[k]
     if (rank == 0 && threadIdx.x == 0) {
       if (!live) {  // finished: nothing moves (as k_finalize)
@@ -1063,6 +1043,113 @@ k_step_cluster_1d(const __grid_constant__ Args1D a, const __grid_constant__ Fuse
   }
 }
 
+// The latency form of the cluster step (instances of at most kSplitMax *
+// kSplitTile points, stage_tile_split). Every CTA keeps the instance's time,
+// wave speeds and time step itself (the same arithmetic on the same values in
+// every CTA); each stage leaves its CTA's share of the output's wave speed in
+// shared memory, and after the stage's cluster barrier every CTA reduces the
+// shares through distributed shared memory. A step thus takes one cluster
+// barrier per stage, and the K steps of a launch one more before the first.
+// Rank 0 publishes t, dt, lands, the wave speeds (the alpha slots a step
+// record copies), the counters and dt_used.
+template <int EQ, class Real>
+__global__ void __launch_bounds__(kThreads1D)
+k_step_cluster_split_1d(const __grid_constant__ Args1D a, const __grid_constant__ FusedArgs f) {
+  namespace cg = cooperative_groups;
+  constexpr int M = Dim1<EQ>::M;
+  constexpr int P = kSplitTile;
+  __shared__ Real red[kThreads1D / 32];
+  __shared__ double part[4];  // shares: alpha of U^n and of the three stage outputs
+  __shared__ double s_alpha, s_dt;
+  __shared__ int s_lands;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int k = blockIdx.x / C;
+  const int n = a.inst_n[k];
+  const int s = rank * P;
+  const bool mine = s < n;
+  if (threadIdx.x < 4) part[threadIdx.x] = 0.0;
+  double t = a.t[k];  // rank 0 writes t[k] only after the first step's barriers
+  // the cluster's maximum of share q (after a cluster barrier), to every thread
+  auto cluster_alpha = [&](int q) -> double {
+    if (threadIdx.x < 32) {
+      double m = (int)threadIdx.x < C ? cl.map_shared_rank(part, (int)threadIdx.x)[q] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (threadIdx.x == 0) s_alpha = m;
+    }
+    __syncthreads();
+    return s_alpha;
+  };
+  {  // alpha(U^n) of this tile's points
+    Real amax = Real(0);
+    if (mine && t < a.t_end) {
+      const Real* U = static_cast<const Real*>(a.U) + a.inst_off[k] * M;
+      const Real gam = pick<Real>(a.sp.wd, a.sp.wf)[9];
+      const Real a01 = pick<Real>(a.sp.wd, a.sp.wf)[10];
+      const int e = min(s + P, n);
+      for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
+        Real u[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) u[c] = U[(long long)c * n + j];
+        amax = fmax(amax, wave_speed<EQ>(u, gam, a01));
+      }
+    }
+    amax = block_max_t(amax, red);
+    if (threadIdx.x == 0) part[0] = (double)amax;
+  }
+  cl.sync();
+  double alpha = cluster_alpha(0);
+  for (int step = 0; step < f.steps; ++step) {
+    const bool live = t < a.t_end;  // the same in every CTA
+    const bool has = live && mine;
+    double dt = 0.0;
+    int lands = 0;
+    if (live) {
+      if (threadIdx.x == 0) {
+        s_dt = a.dt_in ? a.dt_in[k] : time_step(a.sp, alpha, a.inst_hx[k], t, a.t_end, s_lands);
+        if (a.dt_in) s_lands = 0;
+      }
+      __syncthreads();
+      dt = s_dt;
+      lands = s_lands;
+    }
+    StageIO io = io_of(a);
+    io.Uout = f.U1; io.Vout = f.V1; io.Vt0out = f.Vt0;
+    if (has) stage_tile_split<EQ, Real, MODE_STAGE1>(a, io, k, s, alpha, dt, &part[1]);
+    cl.sync();
+    const double a1 = cluster_alpha(1);
+    io.U = f.U1; io.V = f.V1; io.U0 = a.U; io.Vt0 = f.Vt0; io.Uout = f.U2; io.Vout = f.V2;
+    io.Vt0out = nullptr;
+    if (has) stage_tile_split<EQ, Real, MODE_STAGE2>(a, io, k, s, a1, dt, &part[2]);
+    cl.sync();
+    const double a2 = cluster_alpha(2);
+    io.U = f.U2; io.V = f.V2; io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V);
+    const bool more = step + 1 < f.steps;  // stage 3 also gives alpha of U^{n+1}
+    if (has) stage_tile_split<EQ, Real, MODE_STAGE3>(a, io, k, s, a2, dt, more ? &part[3] : nullptr);
+    cl.sync();
+    if (live) {
+      const double tn = lands ? a.t_end : t + dt;
+      if (rank == 0 && threadIdx.x == 0) {
+        const_cast<double*>(a.t)[k] = tn;
+        a.dt[k] = dt;
+        a.lands[k] = lands;
+        f.alpha[k] = (unsigned long long)__double_as_longlong(alpha);
+        f.alpha[f.batch + k] = (unsigned long long)__double_as_longlong(a1);
+        f.alpha[2 * f.batch + k] = (unsigned long long)__double_as_longlong(a2);
+        if (!(alpha <= DBL_MAX)) atomicOr(a.status, STATUS_NONFINITE);
+        if (f.pu) atomicAdd(f.pu, (unsigned long long)n);
+        if (f.dt_used) f.dt_used[k] = dt;
+        if (!more && tn < a.t_end) atomicAdd(f.active, 1);
+      }
+      t = tn;
+    } else if (rank == 0 && threadIdx.x == 0 && f.dt_used) {
+      f.dt_used[k] = 0.0;  // finished: nothing moves
+    }
+    if (more) alpha = cluster_alpha(3);
+  }
+}
+
 // Launch on clusters of C CTAs; returns cudaErrorNotSupported (nothing
 // launched) when the device cannot hold such a cluster.
 template <int EQ, class Real, bool SPLIT>
@@ -1070,7 +1157,7 @@ cudaError_t step_cluster_try(const Args1D& a, const FusedArgs& f, int C, cudaStr
   constexpr size_t tile =
       SPLIT ? SplitLayout<EQ, Real>::bytes : Layout1D<EQ, Real, kThreads1D, 1>::bytes;
   constexpr size_t bytes = tile > kClusterSmem ? tile : kClusterSmem;
-  auto kern = k_step_cluster_1d<EQ, Real, SPLIT>;
+  auto kern = SPLIT ? k_step_cluster_split_1d<EQ, Real> : k_step_cluster_1d<EQ, Real>;
   static unsigned configured = 0;  // devices whose limit is raised
   if (const cudaError_t e = ensure_smem_limit(kern, bytes, configured)) return e;
   static unsigned nonportable = 0;  // devices allowed clusters above 8
