@@ -101,18 +101,16 @@ __device__ __forceinline__ Cand<Real> candidates(Real fm, Real f0, Real fp, Real
   const Real e1 = a1 + Real(0.25) * a3 + Real(0.0625) * a5;
   const Real e2 = a2 + Real(63.0 / 130.0) * a4;
   const Real e3 = a3 + Real(8825.0 / 10934.0) * a5;
-  const Real beta0 = e1 * e1 + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * e3 * e3 +
-                     Real(1421461.0 / 2275.0) * a4 * a4 +
-                     Real(21520059541.0 / 1377684.0) * a5 * a5;
+  // beta_l + eps accumulated directly (eps enters each sum once, so no
+  // separate addition); tau from the differences, where eps cancels
+  c.b0 = e1 * e1 + eps + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * e3 * e3 +
+         Real(1421461.0 / 2275.0) * a4 * a4 + Real(21520059541.0 / 1377684.0) * a5 * a5;
   const Real s1 = H0 - f0 + fm, s2 = H0 + f0 - fp;  // beta_2 uses f_{i+1}
-  const Real h2 = H0 * H0;
-  const Real beta1 = h2 + Real(13.0 / 3.0) * s1 * s1;
-  const Real beta2 = h2 + Real(13.0 / 3.0) * s2 * s2;
-  const Real t = fabs(beta0 - beta1) + fabs(beta0 - beta2);
+  const Real h2e = H0 * H0 + eps;
+  c.b1 = h2e + Real(13.0 / 3.0) * s1 * s1;
+  c.b2 = h2e + Real(13.0 / 3.0) * s2 * s2;
+  const Real t = fabs(c.b0 - c.b1) + fabs(c.b0 - c.b2);
   c.tau = Real(0.25) * t * t;
-  c.b0 = beta0 + eps;
-  c.b1 = beta1 + eps;
-  c.b2 = beta2 + eps;
   return c;
 }
 
@@ -235,12 +233,12 @@ __device__ __forceinline__ Frac<Real> limited_derivative_frac(Real um, Real u0, 
   const Real a4 = Real(-0.25) * dV - Real(0.5) * lap;
   const Real e1 = q0 + Real(0.25) * a3;
   const Real e2 = a2 + Real(63.0 / 130.0) * a4;
-  const Real beta0 = e1 * e1 + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * a3 * a3 +
-                     Real(1421461.0 / 2275.0) * a4 * a4;
-  const Real beta1 = q1 * q1, beta2 = q2 * q2;
-  const Real t = fabs(beta0 - beta1) + fabs(beta0 - beta2);
+  // beta_l + eps accumulated directly, as in candidates()
+  const Real b0 = e1 * e1 + w.eps + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * a3 * a3 +
+                  Real(1421461.0 / 2275.0) * a4 * a4;
+  const Real b1 = q1 * q1 + w.eps, b2 = q2 * q2 + w.eps;
+  const Real t = fabs(b0 - b1) + fabs(b0 - b2);
   const Real tau = Real(0.25) * t * t;
-  const Real b0 = beta0 + w.eps, b1 = beta1 + w.eps, b2 = beta2 + w.eps;
   if constexpr (std::is_same<Real, double>::value) {
     const Real b12 = b1 * b2, b02 = b0 * b2, b01 = b0 * b1;
     const Real L0 = (b0 + tau) * b12;
