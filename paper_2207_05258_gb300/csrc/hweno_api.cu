@@ -214,11 +214,8 @@ SchemeParams scheme_params(const hweno_ctx* c) {
   sp.dmr_angle = c->bc.dmr_angle;
   sp.dmr_tan = std::tan(c->bc.dmr_angle);
   sp.dmr_sin = std::sin(c->bc.dmr_angle);
-  const double tab[11] = {c->opt.lin_w[0], c->opt.lin_w[1], c->opt.lin_w[2], c->opt.lim_d[0],
-                          c->opt.lim_d[1], c->opt.lim_d[2], c->opt.eps, 1.0 / c->opt.lin_w[0],
-                          1.0 / c->opt.lim_d[0], c->gamma,
-                          c->eq == HWENO_BUCKLEY ? buckley_alpha01() : 0.0};
-  for (int i = 0; i < 11; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
+  fill_constant_table(sp, c->opt.lin_w, c->opt.lim_d, c->opt.eps, c->gamma,
+                      c->eq == HWENO_BUCKLEY ? buckley_alpha01() : 0.0);
   return sp;
 }
 

@@ -26,6 +26,7 @@ struct Weights {
   Real d0, d1, d2;       // limiter linear weights d_l (Sec. 2.2)
   Real eps;
   Real ig0, id0;         // 1/gamma_0, 1/d_0
+  Real rm, r0, rp, rH;   // p0 - g1 p1 - g2 p2 in f_{i-1}, f_i, f_{i+1}, H_i
 };
 
 // Largest finite value of the state precision.
@@ -50,6 +51,7 @@ __device__ __forceinline__ Weights<Real> weights_from(const Real* v) {
   w.eps = v[6];
   w.ig0 = v[7];
   w.id0 = v[8];
+  w.rm = v[11]; w.r0 = v[12]; w.rp = v[13]; w.rH = v[14];
   return w;
 }
 
@@ -70,43 +72,59 @@ __device__ __forceinline__ T block_max_t(T v, T* red) {
 }
 
 // Quantities of one "+" reconstruction (Sec. 2.1) from f^+ and H = dx h^+ on
-// the stencil {i-1, i, i+1}: the three candidate values at x_{i+1/2}, the
-// smoothness indicators and the scaled derivative flux D = dx p_0'.
+// the stencil {i-1, i, i+1}: the candidate values at x_{i+1/2} (p0 only
+// through r = p0 - g1 p1 - g2 p2, its share of the nonlinear combination),
+// the smoothness indicators and tau.
 template <class Real>
 struct Cand {
-  Real p0, p1, p2;
+  Real r, p1, p2;
   Real b0, b1, b2;  // beta_l + eps
   Real tau;
-  Real D;
 };
 
 template <class Real>
 __device__ __forceinline__ Cand<Real> candidates(Real fm, Real f0, Real fp, Real Hm, Real H0,
-                                                 Real Hp, Real eps) {
+                                                 Real Hp, const Weights<Real>& w) {
+  const Real eps = w.eps;
   Cand<Real> c;
   const Real sHp = Hm + Hp, dHp = Hm - Hp;
   const Real lap = fm - Real(2) * f0 + fp;  // f_{i-1} - 2 f_i + f_{i+1}
   const Real dif = fm - fp;
-  c.p0 = Real(11.0 / 60.0) * (fm + fp) + Real(19.0 / 30.0) * f0 + Real(0.05) * dHp + Real(0.5) * H0;
+  // p0 = 11/60 (f_{i-1} + f_{i+1}) + 19/30 f_i + (H_{i-1} - H_{i+1})/20 + H_i/2
   c.p1 = Real(1.0 / 6.0) * fm + Real(5.0 / 6.0) * f0 + Real(2.0 / 3.0) * H0;
   c.p2 = Real(5.0 / 6.0) * f0 + Real(1.0 / 6.0) * fp + Real(1.0 / 3.0) * H0;
-  c.D = Real(0.25) * (fm - Real(8) * f0 + Real(7) * fp) +
-        Real(1.0 / 12.0) * (Hm - Real(2) * H0 - Real(5) * Hp);
-  // a_1..a_5 of Eq. GHYZP (dx absorbed into H)
-  const Real a1 = Real(19.0 / 192.0) * sHp + Real(79.0 / 48.0) * H0 + Real(27.0 / 64.0) * dif;
-  const Real a2 = Real(0.375) * dHp + Real(1.25) * lap;
-  const Real a3 = -(Real(11.0 / 24.0) * sHp + Real(17.0 / 6.0) * H0) - Real(1.875) * dif;
-  const Real a4 = Real(-0.25) * dHp - Real(0.5) * lap;
+  if constexpr (std::is_same<Real, double>::value) {  // r as one linear form
+    c.r = w.rm * fm + w.r0 * f0 + w.rp * fp + Real(0.05) * dHp + w.rH * H0;
+  } else {  // FP32: no further constants held (the kernels are register capped)
+    const Real p0 = Real(11.0 / 60.0) * (fm + fp) + Real(19.0 / 30.0) * f0 + Real(0.05) * dHp +
+                    Real(0.5) * H0;
+    c.r = p0 - w.g1 * c.p1 - w.g2 * c.p2;
+  }
+  // beta_0 of Eq. GHYZP as a sum of squares of the quintic's coefficients
+  // a_1..a_5 (dx absorbed into H): e1^2 + 13/3 e2^2 + 781/20 e3^2 +
+  // 1421461/2275 a4^2 + 21520059541/1377684 a5^2 with e1 = a1 + a3/4 + a5/16,
+  // e2 = a2 + 63/130 a4, e3 = a3 + 8825/10934 a5. In the stencil values a1 and
+  // a3 enter only e1 and e3, and e1 reduces to H_i exactly (the sHp and dif
+  // terms cancel, the H_i coefficients sum to 1); e2 and e3 are taken
+  // straight from sHp, dHp, H_i, lap, dif:
+  //   a2 = 3/8 dHp + 5/4 lap, a3 = -11/24 sHp - 17/6 H_i - 15/8 dif,
+  //   e2 = 33/130 dHp + 131/130 lap,
+  //   e3 = -16831/65604 sHp - 33232/16401 H_i - 27765/21868 dif,
+  //   a4 = -1/4 dHp - 1/2 lap, a5 = 1/4 sHp + H_i + 3/4 dif.
+  // The weights of the first three squares ride on the coefficients (their
+  // square roots times the coefficients above, to 20 digits):
+  // E2 = sqrt(13/3) e2, E3 = sqrt(781/20) e3, A4 = sqrt(1421461/2275) a4.
+  const Real E2 = Real(0.52842290755678754049) * dHp + Real(2.0976788148466414486) * lap;
+  const Real E3 = Real(-1.6032089149031235916) * sHp + Real(-12.661835579599691806) * H0 +
+                  Real(-7.9341267047029694945) * dif;
+  const Real A4 = Real(-6.2490900436484649542) * dHp + Real(-12.498180087296929908) * lap;
   const Real a5 = Real(0.25) * sHp + H0 + Real(0.75) * dif;
-  const Real e1 = a1 + Real(0.25) * a3 + Real(0.0625) * a5;
-  const Real e2 = a2 + Real(63.0 / 130.0) * a4;
-  const Real e3 = a3 + Real(8825.0 / 10934.0) * a5;
   // beta_l + eps accumulated directly (eps enters each sum once, so no
-  // separate addition); tau from the differences, where eps cancels
-  c.b0 = e1 * e1 + eps + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * e3 * e3 +
-         Real(1421461.0 / 2275.0) * a4 * a4 + Real(21520059541.0 / 1377684.0) * a5 * a5;
-  const Real s1 = H0 - f0 + fm, s2 = H0 + f0 - fp;  // beta_2 uses f_{i+1}
+  // separate addition; e1^2 + eps = H_i^2 + eps is shared with beta_1 and
+  // beta_2); tau from the differences, where eps cancels
   const Real h2e = H0 * H0 + eps;
+  c.b0 = h2e + E2 * E2 + E3 * E3 + A4 * A4 + Real(21520059541.0 / 1377684.0) * a5 * a5;
+  const Real s1 = H0 - f0 + fm, s2 = H0 + f0 - fp;  // beta_2 uses f_{i+1}
   c.b1 = h2e + Real(13.0 / 3.0) * s1 * s1;
   c.b2 = h2e + Real(13.0 / 3.0) * s2 * s2;
   const Real t = fabs(c.b0 - c.b1) + fabs(c.b0 - c.b2);
@@ -117,14 +135,17 @@ __device__ __forceinline__ Cand<Real> candidates(Real fm, Real f0, Real fp, Real
 // Numerator and denominator of f-hat over the common factor b0 b1 b2:
 // f-hat = num / den, num = (b0+tau) b1 b2 (p0 - g1 p1 - g2 p2)
 //   + g1 (b1+tau) b0 b2 p1 + g2 (b2+tau) b0 b1 p2, den = g0 (b0+tau) b1 b2 + ...
+// Each (b_l + tau) prod_{m != l} b_m is formed as P + tau prod_{m != l} b_m,
+// P = b0 b1 b2.
 template <class Real>
 __device__ __forceinline__ void combine_nd(const Cand<Real>& c, const Weights<Real>& w, Real& num,
                                            Real& den) {
   const Real b12 = c.b1 * c.b2, b02 = c.b0 * c.b2, b01 = c.b0 * c.b1;
-  const Real W0 = (c.b0 + c.tau) * b12;
-  const Real W1 = w.g1 * (c.b1 + c.tau) * b02;
-  const Real W2 = w.g2 * (c.b2 + c.tau) * b01;
-  num = W0 * (c.p0 - w.g1 * c.p1 - w.g2 * c.p2) + W1 * c.p1 + W2 * c.p2;
+  const Real P = c.b0 * b12;
+  const Real W0 = P + c.tau * b12;
+  const Real W1 = w.g1 * (P + c.tau * b02);
+  const Real W2 = w.g2 * (P + c.tau * b01);
+  num = W0 * c.r + W1 * c.p1 + W2 * c.p2;
   den = w.g0 * W0 + W1 + W2;
 }
 
@@ -142,7 +163,7 @@ __device__ __forceinline__ Real combine_direct(const Cand<Real>& c, const Weight
   const Real o0 = w.g0 + w.g0 * qdiv(c.tau, c.b0);
   const Real o1 = w.g1 + w.g1 * qdiv(c.tau, c.b1);
   const Real o2 = w.g2 + w.g2 * qdiv(c.tau, c.b2);
-  const Real num = o0 * w.ig0 * (c.p0 - w.g1 * c.p1 - w.g2 * c.p2) + o1 * c.p1 + o2 * c.p2;
+  const Real num = o0 * w.ig0 * c.r + o1 * c.p1 + o2 * c.p2;
   return qdiv(num, o0 + o1 + o2);
 }
 
@@ -184,8 +205,8 @@ __device__ __forceinline__ Frac<Real> interface_flux_frac(Real fpm, Real fp0, Re
                                                           Real Hp0, Real Hpp, Real fm0, Real fm1,
                                                           Real fm2, Real Hm0, Real Hm1, Real Hm2,
                                                           const Weights<Real>& w) {
-  const Cand<Real> a = candidates(fpm, fp0, fpp, Hpm, Hp0, Hpp, w.eps);
-  const Cand<Real> b = candidates(fm2, fm1, fm0, -Hm2, -Hm1, -Hm0, w.eps);  // mirror
+  const Cand<Real> a = candidates(fpm, fp0, fpp, Hpm, Hp0, Hpp, w);
+  const Cand<Real> b = candidates(fm2, fm1, fm0, -Hm2, -Hm1, -Hm0, w);  // mirror
   if constexpr (std::is_same<Real, double>::value) {
     Real na, da, nb, db;
     combine_nd(a, w, na, da);
@@ -241,9 +262,10 @@ __device__ __forceinline__ Frac<Real> limited_derivative_frac(Real um, Real u0, 
   const Real tau = Real(0.25) * t * t;
   if constexpr (std::is_same<Real, double>::value) {
     const Real b12 = b1 * b2, b02 = b0 * b2, b01 = b0 * b1;
-    const Real L0 = (b0 + tau) * b12;
-    const Real L1 = w.d1 * (b1 + tau) * b02;
-    const Real L2 = w.d2 * (b2 + tau) * b01;
+    const Real P = b0 * b12;  // as in combine_nd
+    const Real L0 = P + tau * b12;
+    const Real L1 = w.d1 * (P + tau * b02);
+    const Real L2 = w.d2 * (P + tau * b01);
     const Real num = L0 * (q0 - w.d1 * q1 - w.d2 * q2) + L1 * q1 + L2 * q2;
     return Frac<Real>{num, w.d0 * L0 + L1 + L2};
   } else {

@@ -169,9 +169,7 @@ extern "C" int hweno_step_1d_noalloc(int equation, int nx, double x0, double x1,
     sp.inflowf[i] = (float)bc->inflow[i];
     sp.pref[i] = (float)bc->pre[i];
   }
-  const double tab[11] = {o.lin_w[0], o.lin_w[1], o.lin_w[2], o.lim_d[0], o.lim_d[1],
-                          o.lim_d[2], o.eps, 1.0 / o.lin_w[0], 1.0 / o.lim_d[0], gamma, 0.0};
-  for (int i = 0; i < 11; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
+  fill_constant_table(sp, o.lin_w, o.lim_d, o.eps, gamma, 0.0);
   a.t = t;
   a.t_end = t_end;
   a.skip_done = 1;

@@ -45,6 +45,8 @@ constexpr int kThreads1D = 128;
 constexpr int kTile1D = tile_points(0);
 constexpr int kMinTile1D = 60;  // smallest tile of any variant
 
+constexpr int kConstTable = 15;
+
 struct SchemeParams {
   double lin_w[3], lim_d[3], eps, cfl, dt_fixed;
   int dt_mode, limiter, eig_avg;
@@ -55,12 +57,30 @@ struct SchemeParams {
   float inflowf[4], pref[4];  // the same in FP32 (the 1D loads read these)
   double dmr_x0, dmr_speed, dmr_angle;
   double dmr_tan, dmr_sin;  // tan and sin of dmr_angle, evaluated on the host
-  // constants in both precisions, converted once on the host:
-  // g0, g1, g2, d0, d1, d2, eps, 1/g0, 1/d0, gas gamma, and (Buckley-Leverett)
-  // max |f'| over [0, 1]
-  double wd[11];
-  float wf[11];
+  // constants in both precisions, converted once on the host
+  // (fill_constant_table): g0, g1, g2, d0, d1, d2, eps, 1/g0, 1/d0, gas
+  // gamma, (Buckley-Leverett) max |f'| over [0, 1], and the coefficients of
+  // p0 - g1 p1 - g2 p2 in f_{i-1}, f_i, f_{i+1}, H_i
+  double wd[kConstTable];
+  float wf[kConstTable];
 };
+
+// The constant table of SchemeParams. p0 - g1 p1 - g2 p2 (the quintic's
+// share of the nonlinear combination, Sec. 2.1) is a fixed linear form in
+// the stencil values once the linear weights are known: with p0, p1, p2 of
+// Sec. 2.1 its coefficients are 11/60 - g1/6 (f_{i-1}), 19/30 - 5 (g1 + g2)/6
+// (f_i), 11/60 - g2/6 (f_{i+1}), 1/2 - 2 g1/3 - g2/3 (H_i) and 1/20
+// (H_{i-1} - H_{i+1}, a literal in the kernels).
+inline void fill_constant_table(SchemeParams& sp, const double g[3], const double d[3],
+                                double eps, double gas_gamma, double bl_alpha) {
+  const double tab[kConstTable] = {g[0], g[1], g[2], d[0], d[1], d[2], eps, 1.0 / g[0],
+                                   1.0 / d[0], gas_gamma, bl_alpha,
+                                   11.0 / 60.0 - g[1] / 6.0,
+                                   19.0 / 30.0 - 5.0 * (g[1] + g[2]) / 6.0,
+                                   11.0 / 60.0 - g[2] / 6.0,
+                                   0.5 - 2.0 * g[1] / 3.0 - g[2] / 3.0};
+  for (int i = 0; i < kConstTable; ++i) { sp.wd[i] = tab[i]; sp.wf[i] = (float)tab[i]; }
+}
 
 // Arguments of one 1D launch (all instances of the batch).
 struct Args1D {

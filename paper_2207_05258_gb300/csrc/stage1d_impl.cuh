@@ -773,7 +773,7 @@ template <class Real>
 __device__ __forceinline__ Frac<Real> side_frac(int sd, Real f0, Real f1, Real f2, Real H0,
                                                Real H1, Real H2, const Weights<Real>& w) {
   const Cand<Real> c = candidates(sd ? f2 : f0, f1, sd ? f0 : f2, sd ? -H2 : H0, sd ? -H1 : H1,
-                                  sd ? -H0 : H2, w.eps);
+                                  sd ? -H0 : H2, w);
   if constexpr (std::is_same<Real, double>::value) {
     Real n, d;
     combine_nd(c, w, n, d);
