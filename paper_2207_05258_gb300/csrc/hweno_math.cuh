@@ -88,16 +88,18 @@ __device__ __forceinline__ Cand<Real> candidates(Real fm, Real f0, Real fp, Real
   const Real eps = w.eps;
   Cand<Real> c;
   const Real sHp = Hm + Hp, dHp = Hm - Hp;
-  const Real lap = fm - Real(2) * f0 + fp;  // f_{i-1} - 2 f_i + f_{i+1}
-  const Real dif = fm - fp;
+  const Real d1 = fm - f0, d2 = f0 - fp;  // the two one-sided differences
+  const Real lap = d1 - d2;               // f_{i-1} - 2 f_i + f_{i+1}
+  const Real dif = d1 + d2;               // f_{i-1} - f_{i+1}
+  // p1 = 1/6 f_{i-1} + 5/6 f_i + 2/3 H_i, p2 = 5/6 f_i + 1/6 f_{i+1} + 1/3 H_i
+  c.p1 = f0 + Real(1.0 / 6.0) * d1 + Real(2.0 / 3.0) * H0;
+  c.p2 = f0 - Real(1.0 / 6.0) * d2 + Real(1.0 / 3.0) * H0;
   // p0 = 11/60 (f_{i-1} + f_{i+1}) + 19/30 f_i + (H_{i-1} - H_{i+1})/20 + H_i/2
-  c.p1 = Real(1.0 / 6.0) * fm + Real(5.0 / 6.0) * f0 + Real(2.0 / 3.0) * H0;
-  c.p2 = Real(5.0 / 6.0) * f0 + Real(1.0 / 6.0) * fp + Real(1.0 / 3.0) * H0;
+  //    = f_i + 11/60 lap + dHp/20 + H_i/2
   if constexpr (std::is_same<Real, double>::value) {  // r as one linear form
     c.r = w.rm * fm + w.r0 * f0 + w.rp * fp + Real(0.05) * dHp + w.rH * H0;
   } else {  // FP32: no further constants held (the kernels are register capped)
-    const Real p0 = Real(11.0 / 60.0) * (fm + fp) + Real(19.0 / 30.0) * f0 + Real(0.05) * dHp +
-                    Real(0.5) * H0;
+    const Real p0 = f0 + Real(11.0 / 60.0) * lap + Real(0.05) * dHp + Real(0.5) * H0;
     c.r = p0 - w.g1 * c.p1 - w.g2 * c.p2;
   }
   // beta_0 of Eq. GHYZP as a sum of squares of the quintic's coefficients
@@ -124,9 +126,13 @@ __device__ __forceinline__ Cand<Real> candidates(Real fm, Real f0, Real fp, Real
   // beta_2); tau from the differences, where eps cancels
   const Real h2e = H0 * H0 + eps;
   c.b0 = h2e + E2 * E2 + E3 * E3 + A4 * A4 + Real(21520059541.0 / 1377684.0) * a5 * a5;
-  const Real s1 = H0 - f0 + fm, s2 = H0 + f0 - fp;  // beta_2 uses f_{i+1}
-  c.b1 = h2e + Real(13.0 / 3.0) * s1 * s1;
-  c.b2 = h2e + Real(13.0 / 3.0) * s2 * s2;
+  // beta_1 = H_i^2 + 13/3 (H_i + d1)^2, beta_2 = H_i^2 + 13/3 (H_i + d2)^2,
+  // with sqrt(13/3) on the inner sums (S_l = sqrt(13/3) (H_i + d_l))
+  const Real kH = Real(2.0816659994661327353) * H0;
+  const Real S1 = kH + Real(2.0816659994661327353) * d1;
+  const Real S2 = kH + Real(2.0816659994661327353) * d2;
+  c.b1 = h2e + S1 * S1;
+  c.b2 = h2e + S2 * S2;
   const Real t = fabs(c.b0 - c.b1) + fabs(c.b0 - c.b2);
   c.tau = Real(0.25) * t * t;
   return c;
@@ -231,12 +237,13 @@ template <class Real>
 __device__ __forceinline__ Real derivative_flux(Real fpm, Real fp0, Real fpp, Real Hpm, Real Hp0,
                                                 Real Hpp, Real fm0, Real fm1, Real fm2, Real Hm0,
                                                 Real Hm1, Real Hm2) {
-  const Real Dp = Real(0.25) * (fpm - Real(8) * fp0 + Real(7) * fpp) +
-                  Real(1.0 / 12.0) * (Hpm - Real(2) * Hp0 - Real(5) * Hpp);
-  // mirror: -(0.25 (f2 - 8 f1 + 7 f0) + (-H2 + 2 H1 + 5 H0)/12)
-  const Real Dm = Real(-0.25) * (fm2 - Real(8) * fm1 + Real(7) * fm0) +
-                  Real(1.0 / 12.0) * (Hm2 - Real(2) * Hm1 - Real(5) * Hm0);
-  return Dp + Dm;
+  // "+" side: 0.25 (f_{i-1} - 8 f_i + 7 f_{i+1}) + (H_{i-1} - 2 H_i - 5 H_{i+1})/12;
+  // "-" side (mirror): -(0.25 (f2 - 8 f1 + 7 f0) + (-H2 + 2 H1 + 5 H0)/12);
+  // their sum as one linear form of the twelve values
+  return Real(0.25) * fpm - Real(2) * fp0 + Real(1.75) * fpp - Real(1.75) * fm0 +
+         Real(2) * fm1 - Real(0.25) * fm2 + Real(1.0 / 12.0) * Hpm - Real(1.0 / 6.0) * Hp0 -
+         Real(5.0 / 12.0) * Hpp - Real(5.0 / 12.0) * Hm0 - Real(1.0 / 6.0) * Hm1 +
+         Real(1.0 / 12.0) * Hm2;
 }
 
 // HWENO limiter (Sec. 2.2) in scaled form: point values um, u0, up and
@@ -245,18 +252,22 @@ template <class Real>
 __device__ __forceinline__ Frac<Real> limited_derivative_frac(Real um, Real u0, Real up, Real Vm,
                                                               Real Vp, const Weights<Real>& w) {
   const Real sV = Vm + Vp, dV = Vm - Vp;
-  const Real lap = um - Real(2) * u0 + up;
-  const Real q0 = Real(0.75) * (up - um) - Real(0.25) * sV;  // dx q_0'(x_i) = a_1
   const Real q1 = u0 - um;                                    // dx q_1'
   const Real q2 = up - u0;                                    // dx q_2'
-  const Real a2 = Real(0.25) * dV + lap;
-  const Real a3 = Real(0.25) * sV - Real(0.25) * (up - um);
-  const Real a4 = Real(-0.25) * dV - Real(0.5) * lap;
-  const Real e1 = q0 + Real(0.25) * a3;
-  const Real e2 = a2 + Real(63.0 / 130.0) * a4;
+  const Real lap = q2 - q1;                                   // um - 2 u0 + up
+  const Real du = q1 + q2;                                    // up - um
+  const Real q0 = Real(0.75) * du - Real(0.25) * sV;          // dx q_0'(x_i) = a_1
+  // beta_0 = e1^2 + 13/3 e2^2 + 781/20 a3^2 + 1421461/2275 a4^2 with
+  // a2 = dV/4 + lap, a3 = (sV - du)/4, a4 = -dV/4 - lap/2, e1 = a1 + a3/4,
+  // e2 = a2 + 63/130 a4 = 67/520 dV + 197/260 lap; the weights of the last
+  // three squares ride on the coefficients (square roots, to 20 digits):
+  // E2 = sqrt(13/3) e2, A3 = sqrt(781/20) a3, A4 = sqrt(1421461/2275) a4.
+  const Real E2 = Real(0.26821465762352094858) * dV + Real(1.5772623149801082648) * lap;
+  const Real A3 = Real(1.5622499799967993599) * (sV - du);
+  const Real A4 = Real(-6.2490900436484649542) * dV + Real(-12.498180087296929908) * lap;
+  const Real e1 = q0 + Real(0.040006401536409714721) * A3;  // a3 / 4 = A3 / (4 sqrt(781/20))
   // beta_l + eps accumulated directly, as in candidates()
-  const Real b0 = e1 * e1 + w.eps + Real(13.0 / 3.0) * e2 * e2 + Real(781.0 / 20.0) * a3 * a3 +
-                  Real(1421461.0 / 2275.0) * a4 * a4;
+  const Real b0 = e1 * e1 + w.eps + E2 * E2 + A3 * A3 + A4 * A4;
   const Real b1 = q1 * q1 + w.eps, b2 = q2 * q2 + w.eps;
   const Real t = fabs(b0 - b1) + fabs(b0 - b2);
   const Real tau = Real(0.25) * t * t;
