@@ -63,17 +63,17 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # (dram__bytes_read.sum + dram__bytes_write.sum over points;
 # profiles/k_stage_1d_euler_fp{64,32}_riemann_batch.md). An entry is removed
 # whenever the kernel changes after its capture.
-MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 99.0, "fp32": 38.7}
+MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 99.3, "fp32": 38.4}
 # DRAM bytes per point-step of the persistent kernel (all three stages), from
 # an ncu capture (profiles/k_run_1d_euler_fp64_riemann_batch.md); None until
 # taken for the kernel as it stands (FP32: the 1024-instance capture batch
 # fits in L2, so its counters do not scale to the larger batch).
-MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.9, "fp32": None}
+MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.7, "fp32": None}
 # DRAM bytes per point of one 2D stage (x-sweep + y-sweep launches) on the
 # smooth periodic problem at 2048^2, from an ncu capture
 # (profiles/k_sweeps_2d_euler_fp64_smooth.md); applied to grids whose working
 # set exceeds the L2 (smaller grids keep part of it in L2).
-MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {"fp64": 627.8, "fp32": 306.7}
+MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {"fp64": 627.3, "fp32": 306.6}
 
 
 def parse():
