@@ -111,9 +111,14 @@ typedef struct hweno_grid {
  * dt_mode = 0, limiter = 1, eig_avg = 0, tile_variant = 0, fused_small = 0
  * and adj_frozen_weights = 0. */
 typedef struct hweno_options {
-  double lin_w[3]; /* gamma_0..2 of the reconstruction: > 0, sum 1 (Sec. 2.1) */
-  double lim_d[3]; /* d_0..2 of the limiter: > 0, sum 1 (Sec. 2.2) */
-  double eps;      /* epsilon of the nonlinear weights, > 0 */
+  double lin_w[3]; /* gamma_0..2 of the reconstruction: >= 1e-6 each, sum 1 (Sec. 2.1) */
+  double lim_d[3]; /* d_0..2 of the limiter: >= 1e-6 each, sum 1 (Sec. 2.2) */
+  double eps;      /* epsilon of the nonlinear weights, in [1e-20, 1e6]. The
+                      kernels resolve the nonlinear weights of several fields
+                      over one common denominator, a product of up to twelve
+                      factors of the size of beta + eps; the bounds on eps and
+                      the linear weights keep it inside the FP64 range. Other
+                      values are HWENO_EINVAL. */
   double cfl;      /* CFL number, > 0 */
   int dt_mode;     /* 0: dt = cfl / sum(alpha_d / h_d) with h = dx;
                       1: h = dx^{5/3} (accuracy runs); 2: dt = dt_fixed.

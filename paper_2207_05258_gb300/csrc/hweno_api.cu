@@ -114,13 +114,14 @@ int cuda_fail(hweno_ctx* c, cudaError_t e, const char* what) {
 }
 
 bool weights_ok(const double* w) {
-  return w[0] > 0 && w[1] > 0 && w[2] > 0 && std::fabs(w[0] + w[1] + w[2] - 1.0) <= 1e-12;
+  return w[0] >= kWeightMin && w[1] >= kWeightMin && w[2] >= kWeightMin &&
+         std::fabs(w[0] + w[1] + w[2] - 1.0) <= 1e-12;
 }
 
 int check_options(const hweno_options* o, std::string& why) {
-  if (!weights_ok(o->lin_w)) { why = "lin_w must be positive and sum to 1"; return HWENO_EINVAL; }
-  if (!weights_ok(o->lim_d)) { why = "lim_d must be positive and sum to 1"; return HWENO_EINVAL; }
-  if (!(o->eps > 0)) { why = "eps must be > 0"; return HWENO_EINVAL; }
+  if (!weights_ok(o->lin_w)) { why = "lin_w must be >= 1e-6 each and sum to 1"; return HWENO_EINVAL; }
+  if (!weights_ok(o->lim_d)) { why = "lim_d must be >= 1e-6 each and sum to 1"; return HWENO_EINVAL; }
+  if (!(o->eps >= kEpsMin && o->eps <= kEpsMax)) { why = "eps must lie in [1e-20, 1e6]"; return HWENO_EINVAL; }
   if (!(o->cfl > 0)) { why = "cfl must be > 0"; return HWENO_EINVAL; }
   if (o->dt_mode < 0 || o->dt_mode > 2) { why = "dt_mode must be 0, 1 or 2"; return HWENO_EINVAL; }
   if (o->dt_mode == 2 && !(o->dt_fixed > 0)) { why = "dt_fixed must be > 0"; return HWENO_EINVAL; }

@@ -89,11 +89,13 @@ __global__ void k_noalloc_setup(unsigned char* base, int ntiles, int n, double d
 }
 
 bool weights_valid(const double* w) {
-  return w[0] > 0 && w[1] > 0 && w[2] > 0 && std::fabs(w[0] + w[1] + w[2] - 1.0) <= 1e-12;
+  return w[0] >= kWeightMin && w[1] >= kWeightMin && w[2] >= kWeightMin &&
+         std::fabs(w[0] + w[1] + w[2] - 1.0) <= 1e-12;
 }
 
 bool options_valid(const hweno_options* o) {
-  return weights_valid(o->lin_w) && weights_valid(o->lim_d) && o->eps > 0 && o->cfl > 0 &&
+  return weights_valid(o->lin_w) && weights_valid(o->lim_d) && o->eps >= kEpsMin &&
+         o->eps <= kEpsMax && o->cfl > 0 &&
          o->dt_mode >= 0 && o->dt_mode <= 2 && (o->dt_mode != 2 || o->dt_fixed > 0) &&
          o->limiter >= 0 && o->limiter <= 2 && o->eig_avg >= 0 && o->eig_avg <= 1 &&
          o->tile_variant == 0;

@@ -47,6 +47,14 @@ constexpr int kMinTile1D = 60;  // smallest tile of any variant
 
 constexpr int kConstTable = 15;
 
+// Bounds of the options that enter the deferred quotients. The kernels
+// resolve quotients whose denominators are products of up to twelve factors
+// of the size of beta + eps (the nonlinear weights of two sides of two
+// fields over a common denominator) times powers of the linear weights.
+// Within these bounds, and for data of moderate size, those products stay
+// inside the FP64 range: eps^12 g^4 >= 1e-264 even where beta = 0.
+constexpr double kEpsMin = 1e-20, kEpsMax = 1e6, kWeightMin = 1e-6;
+
 struct SchemeParams {
   double lin_w[3], lim_d[3], eps, cfl, dt_fixed;
   int dt_mode, limiter, eig_avg;

@@ -95,3 +95,28 @@ def test_valid_create_without_gpu_fails_cleanly(hw):
 def test_binding_refuses_cpu_tensors(hw):
     with pytest.raises(ValueError):
         hw._ptr(torch.zeros(4))
+
+
+@pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", 1e-30), ("eps", 1e7),
+                                         ("lin_w", (1 - 2e-7, 1e-7, 1e-7)),
+                                         ("lim_d", (0.5, 0.5 - 1e-9, 1e-9)),
+                                         ("lin_w", (0.5, 0.3, 0.3))])
+def test_out_of_range_options_are_rejected_before_any_cuda_call(hw, field, value):
+    """The allocation-free step checks its options before it touches a device
+    pointer: eps outside [1e-20, 1e6], a linear weight below 1e-6 or weights
+    that do not sum to 1 are HWENO_EINVAL (host buffers stand in for the
+    device ones, which are never read)."""
+    import numpy as np
+    o = hw.default_options()
+    if field == "eps":
+        o.eps = value
+    else:
+        for i, x in enumerate(value):
+            getattr(o, field)[i] = x
+    n = 32
+    U = np.zeros(3 * n); V = np.zeros(3 * n); t = np.zeros(1)
+    bc = hw.Bc(1, 1, 0, 0)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+    rc = hw.lib.hweno_step_1d_noalloc(hw.EULER, n, 0.0, 1.0, 1.4, ctypes.byref(bc),
+                                      ctypes.byref(o), ptr(U), ptr(V), ptr(t), 1.0, None, None)
+    assert rc == hw.EINVAL

@@ -342,7 +342,9 @@ def test_fp32_error_against_fp64_oracle(hw, record_property):
 
 @pytest.mark.parametrize("opts", [dict(fused_small=3), dict(fused_small=-1), dict(tile_variant=5),
                                   dict(adj_frozen_weights=2), dict(limiter=3), dict(dt_mode=3),
-                                  dict(eig_avg=2), dict(cfl=0.0), dict(eps=-1.0)])
+                                  dict(eig_avg=2), dict(cfl=0.0), dict(eps=-1.0), dict(eps=1e-30),
+                                  dict(eps=1e7), dict(lin_w=(1 - 2e-7, 1e-7, 1e-7)),
+                                  dict(lim_d=(0.5, 0.5 - 1e-9, 1e-9))])
 def test_invalid_options_are_rejected(hw, opts):
     w = euler_batch([64], 43, "riemann")
     with pytest.raises(hw.HwenoError) as e:
