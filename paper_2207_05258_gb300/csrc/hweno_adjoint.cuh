@@ -2,7 +2,11 @@
 // blocks of the L-HWENO stage (Zhang & Zhao, arXiv:2207.05258, Sec. 2.1-2.2),
 // written by hand from the forward formulas. They differentiate the functions
 // themselves (the per-weight form of the nonlinear weights), not the folded
-// arrangement used by the forward kernels; the |.| in tau keeps the sign of
+// arrangement used by the forward kernels; beta_0 of the reconstruction is
+// taken in the forward kernels' rewritten form (equal in exact arithmetic to
+// Eq. GHYZP, with e1 = H_i and the square weights in the coefficients of the
+// squared sums), which also keeps the cotangents of a1, a3 and e1 from
+// cancelling in floating point; the |.| in tau keeps the sign of
 // its argument at the point of evaluation (the branch of the forward run).
 // With `frozen` the nonlinear weights count as constants: only the
 // candidates' (linear) dependence on the data is propagated.
@@ -13,11 +17,17 @@
 namespace hweno {
 
 namespace adj {
-constexpr double A1s = 19.0 / 192.0, A1h = 79.0 / 48.0, A1d = 27.0 / 64.0;
-constexpr double A3s = 11.0 / 24.0, A3h = 17.0 / 6.0;
-constexpr double K6 = 63.0 / 130.0, K7 = 8825.0 / 10934.0, K8 = 13.0 / 3.0, K9 = 781.0 / 20.0;
+constexpr double K6 = 63.0 / 130.0, K8 = 13.0 / 3.0, K9 = 781.0 / 20.0;
 constexpr double K10 = 1421461.0 / 2275.0, K11 = 21520059541.0 / 1377684.0;
 constexpr double C11 = 11.0 / 60.0, C19 = 19.0 / 30.0;
+// beta_0 of the reconstruction as H_i^2 + E2^2 + E3^2 + A4^2 + K11 a5^2 (the
+// forward kernels' form; e1 = a1 + a3/4 + a5/16 reduces to H_i): E2 =
+// sqrt(13/3) e2, E3 = sqrt(781/20) e3, A4 = sqrt(1421461/2275) a4 in the
+// stencil sums (square roots times the exact coefficients, to 20 digits)
+constexpr double E2d = 0.52842290755678754049, E2l = 2.0976788148466414486;
+constexpr double E3s = -1.6032089149031235916, E3h = -12.661835579599691806,
+                 E3d = -7.9341267047029694945;
+constexpr double A4d = -6.2490900436484649542, A4l = -12.498180087296929908;
 }  // namespace adj
 
 // Source of point p of an instance with n points (maybe a ghost): kind 0
@@ -47,15 +57,14 @@ __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, doub
   const double p0 = C11 * (fm + fp) + C19 * f0 + 0.05 * dHp + 0.5 * H0;
   const double p1 = fm / 6.0 + 5.0 * f0 / 6.0 + 2.0 * H0 / 3.0;
   const double p2 = 5.0 * f0 / 6.0 + fp / 6.0 + H0 / 3.0;
-  const double a1 = A1s * sHp + A1h * H0 + A1d * dif;
-  const double a2 = 0.375 * dHp + 1.25 * lap;
-  const double a3 = -A3s * sHp - A3h * H0 - 1.875 * dif;
-  const double a4 = -0.25 * dHp - 0.5 * lap;
+  const double E2 = E2d * dHp + E2l * lap;
+  const double E3 = E3s * sHp + E3h * H0 + E3d * dif;
+  const double A4 = A4d * dHp + A4l * lap;
   const double a5 = 0.25 * sHp + H0 + 0.75 * dif;
-  const double e1 = a1 + 0.25 * a3 + 0.0625 * a5, e2 = a2 + K6 * a4, e3 = a3 + K7 * a5;
-  const double be0 = e1 * e1 + K8 * e2 * e2 + K9 * e3 * e3 + K10 * a4 * a4 + K11 * a5 * a5;
+  const double h2 = H0 * H0;
+  const double be0 = h2 + E2 * E2 + E3 * E3 + A4 * A4 + K11 * a5 * a5;
   const double s1 = H0 - f0 + fm, s2 = H0 + f0 - fp;
-  const double be1 = H0 * H0 + K8 * s1 * s1, be2 = H0 * H0 + K8 * s2 * s2;
+  const double be1 = h2 + K8 * s1 * s1, be2 = h2 + K8 * s2 * s2;
   const double d1 = be0 - be1, d2 = be0 - be2;
   const double t = fabs(d1) + fabs(d2), tau = 0.25 * t * t;
   const double b0 = be0 + w.eps, b1 = be1 + w.eps, b2 = be2 + w.eps;
@@ -82,18 +91,15 @@ __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, doub
   const double gt = 0.5 * t * gtau;
   const double gd1 = gt * sgn(d1), gd2 = gt * sgn(d2);
   const double gbe0 = gb0 + gd1 + gd2, gbe1 = gb1 - gd1, gbe2 = gb2 - gd2;
-  double gH0 = 2.0 * H0 * (gbe1 + gbe2);
   const double gs1 = 2.0 * K8 * s1 * gbe1, gs2 = 2.0 * K8 * s2 * gbe2;
-  const double ge1 = 2.0 * e1 * gbe0, ge2 = 2.0 * K8 * e2 * gbe0, ge3 = 2.0 * K9 * e3 * gbe0;
-  double ga4 = 2.0 * K10 * a4 * gbe0, ga5 = 2.0 * K11 * a5 * gbe0;
-  const double ga1 = ge1, ga2 = ge2, ga3 = 0.25 * ge1 + ge3;
-  ga5 += 0.0625 * ge1 + K7 * ge3;
-  ga4 += K6 * ge2;
-  double gsHp = A1s * ga1 - A3s * ga3 + 0.25 * ga5;
-  double gdHp = 0.375 * ga2 - 0.25 * ga4 + 0.05 * gp0;
-  const double glap = 1.25 * ga2 - 0.5 * ga4;
-  const double gdif = A1d * ga1 - 1.875 * ga3 + 0.75 * ga5;
-  gH0 += A1h * ga1 - A3h * ga3 + ga5 + 0.5 * gp0 + 2.0 / 3.0 * gp1 + 1.0 / 3.0 * gp2 + gs1 + gs2;
+  const double tg = 2.0 * gbe0;
+  const double gE2 = tg * E2, gE3 = tg * E3, gA4 = tg * A4, ga5 = K11 * a5 * tg;
+  const double gsHp = E3s * gE3 + 0.25 * ga5;
+  const double gdHp = E2d * gE2 + A4d * gA4 + 0.05 * gp0;
+  const double glap = E2l * gE2 + A4l * gA4;
+  const double gdif = E3d * gE3 + 0.75 * ga5;
+  const double gH0 = 2.0 * H0 * (gbe0 + gbe1 + gbe2) + E3h * gE3 + ga5 + 0.5 * gp0 +
+                     2.0 / 3.0 * gp1 + 1.0 / 3.0 * gp2 + gs1 + gs2;
   g[0] += C11 * gp0 + gp1 / 6.0 + glap + gdif + gs1;
   g[1] += C19 * gp0 + 5.0 / 6.0 * (gp1 + gp2) - 2.0 * glap - gs1 + gs2;
   g[2] += C11 * gp0 + gp2 / 6.0 + glap - gdif - gs2;
