@@ -120,3 +120,18 @@ def test_derivative_flux_is_the_sum_of_the_two_sides():
         num = sympy.nsimplify(coef.replace(" ", ""))
         total += (-1 if sign == "-" else 1) * num * names[var]
     assert expand(total - (Dp + Dm)) == 0
+
+
+def test_adjoint_uses_the_same_indicator_constants():
+    """The reverse passes take beta_0 in the same rewritten form; their named
+    constants equal the exact values as well."""
+    path = os.path.join(os.path.dirname(SRC), "hweno_adjoint.cuh")
+    with open(path) as f:
+        text = f.read()
+    K2, K3, K4 = sqrt(R(13, 3)), sqrt(R(781, 20)), sqrt(R(1421461, 2275))
+    want = dict(E2d=K2 * R(33, 130), E2l=K2 * R(131, 130), E3s=K3 * R(-16831, 65604),
+                E3h=K3 * R(-33232, 16401), E3d=K3 * R(-27765, 21868), A4d=-K4 / 4, A4l=-K4 / 2)
+    for name, exact in want.items():
+        m = re.search(r"\b%s = (-?[0-9.]+)" % name, text)
+        assert m, name
+        close(m.group(1), exact, 19)
