@@ -64,3 +64,31 @@ def test_cpu_baseline_all_cores_on_a_small_sample():
     r = bench.cpu_baseline(w, budget_s=0.6, sample=6, processes=2)
     assert r["cores"] == 2 and r["kind"] == "oracle"
     assert r["value"] > 0 and r["single_thread"] > 0
+
+
+def _reference_arm(rank, world):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--gpus", str(world)], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=300)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    return r.returncode, [json.loads(l) for l in lines]
+
+
+def test_reference_arm_rank0_prints_one_line_other_ranks_nothing():
+    """The reference arm (the oracle on a bounded sample of the batch) runs on
+    rank 0 alone and prints one JSON line with the contract's keys; any other
+    rank exits 0 without work or output."""
+    rc, out = _reference_arm(0, 2)
+    assert rc == 0 and len(out) == 1
+    d = out[0]
+    assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
+    assert d["metric"] == bench.METRIC and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    rc, out = _reference_arm(1, 2)
+    assert rc == 0 and out == []
