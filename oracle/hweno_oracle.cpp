@@ -202,10 +202,13 @@ R p0_prime(const R f[3], const R h[3], double dx) {
 }
 
 // freeze_w: the nonlinear weights enter as constants (their tangent is
-// dropped), for the frozen-weights derivative of the scheme.
+// dropped), for the frozen-weights derivative of the scheme. with_dp0 = false
+// skips p_0' (hhat, dp0 stay 0): the characteristic-wise Euler flux uses only
+// fhat of each characteristic field, its derivative flux being taken
+// component by component (remarks after the 1D and 2D schemes).
 template <class R>
 Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
-                   double eps, bool freeze_w = false) {
+                   double eps, bool freeze_w = false, bool with_dp0 = true) {
   Face<R> o;
   const R fm = f[0], f0 = f[1], fp = f[2];
   const R hm = h[0], h0 = h[1], hp = h[2];
@@ -215,7 +218,7 @@ Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
            (dx / 20.0) * (hm + 10.0 * h0 - hp);
   o.p[1] = (1.0 / 6.0) * fm + (5.0 / 6.0) * f0 + (2.0 / 3.0) * dx * h0;
   o.p[2] = (5.0 / 6.0) * f0 + (1.0 / 6.0) * fp + (1.0 / 3.0) * dx * h0;
-  o.dp0 = p0_prime(f, h, dx);
+  o.dp0 = with_dp0 ? p0_prime(f, h, dx) : R(0.0);
 
   // a_1..a_5 and the smoothness indicators (Eq. GHYZP).
   const R a1 = dx * ((19.0 / 192.0) * hm + (79.0 / 48.0) * h0 + (19.0 / 192.0) * hp) +
@@ -259,10 +262,10 @@ Face<R> hweno_plus(const R f[3], const R h[3], double dx, const double g[3],
 // derivative flux reflects back with a sign change.
 template <class R>
 Face<R> hweno_minus(const R f[3], const R h[3], double dx, const double g[3],
-                    double eps, bool freeze_w = false) {
+                    double eps, bool freeze_w = false, bool with_dp0 = true) {
   const R fr[3] = {f[2], f[1], f[0]};
   const R hr[3] = {-h[2], -h[1], -h[0]};
-  Face<R> o = hweno_plus(fr, hr, dx, g, eps, freeze_w);
+  Face<R> o = hweno_plus(fr, hr, dx, g, eps, freeze_w, with_dp0);
   o.hhat = -o.hhat;
   o.dp0 = -o.dp0;
   return o;
@@ -548,8 +551,8 @@ void sweep_line(const or_problem& P, int dir, int n, double dx, R alpha,
         const R h3p[3] = {whp[0][s], whp[1][s], whp[2][s]};
         const R f3m[3] = {wfm[0][s], wfm[1][s], wfm[2][s]};
         const R h3m[3] = {whm[0][s], whm[1][s], whm[2][s]};
-        const Face<R> a = hweno_plus(f3p, h3p, dx, gw, P.eps, P.freeze_weights != 0);
-        const Face<R> b = hweno_minus(f3m, h3m, dx, gw, P.eps, P.freeze_weights != 0);
+        const Face<R> a = hweno_plus(f3p, h3p, dx, gw, P.eps, P.freeze_weights != 0, false);
+        const Face<R> b = hweno_minus(f3m, h3m, dx, gw, P.eps, P.freeze_weights != 0, false);
         fchar[s] = a.fhat + b.fhat;
       }
       matvec(m, Rm, fchar, fh);
