@@ -24,12 +24,18 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy stream); all
  *    work is enqueued on it and the calls return without synchronising,
  *    except hweno_sync_status and hweno_step_host.
- *  - The library allocates the scratch of a step (stage buffers, the stored
- *    limited derivative, per-instance wave speeds and time steps, a status
- *    word) in hweno_create and frees everything in hweno_destroy. Only
- *    hweno_adjoint_step (and its recorded form), hweno_run_persistent and
- *    the pipelined hweno_step_host allocate more, once, on their first call;
- *    hweno_measure_fp64_peak allocates and frees a small buffer.
+ *  - The library allocates all of its device scratch in hweno_create and
+ *    frees it in hweno_destroy: the stage buffers, the stored limited
+ *    derivative, per-instance wave speeds and time steps, a status word, the
+ *    persistent run's counters (1D), the device copies, streams and events of
+ *    hweno_step_host, and (FP64 Burgers and Euler contexts) the adjoint's
+ *    scratch. No other call allocates device memory, so the calls that only
+ *    enqueue work (hweno_rhs, hweno_step, hweno_run_persistent without a
+ *    point-update count, hweno_totals, hweno_adjoint_step and the record
+ *    calls) can be recorded into a CUDA graph by the caller. hweno_run
+ *    instantiates a graph of its own (driver objects), hweno_profile_start
+ *    creates events, and hweno_measure_fp64_peak allocates and frees a small
+ *    buffer of its own (no context).
  *  - Every call returns an int status: HWENO_OK (0) or a negative code; a
  *    readable message is kept in the context (hweno_last_error). Errors the
  *    device detects (a non-finite wave speed) are latched into the context's
@@ -114,11 +120,17 @@ typedef struct hweno_options {
   double lin_w[3]; /* gamma_0..2 of the reconstruction: >= 1e-6 each, sum 1 (Sec. 2.1) */
   double lim_d[3]; /* d_0..2 of the limiter: >= 1e-6 each, sum 1 (Sec. 2.2) */
   double eps;      /* epsilon of the nonlinear weights, in [1e-20, 1e6]. The
-                      kernels resolve the nonlinear weights of several fields
-                      over one common denominator, a product of up to twelve
-                      factors of the size of beta + eps; the bounds on eps and
-                      the linear weights keep it inside the FP64 range. Other
-                      values are HWENO_EINVAL. */
+                      FP64 kernels resolve the nonlinear weights of two sides
+                      and two fields over one common denominator, a product
+                      of up to sixteen factors of the size of beta + eps; the
+                      bounds on eps and the linear weights keep it above the
+                      FP64 underflow limit. Large data (beta grows like the
+                      square of the split-flux jumps) push it past the
+                      overflow limit; the kernels then divide per side and
+                      per field, which holds for split-flux jumps up to about
+                      1e35 (tested against the CPU oracle with Euler states
+                      scaled by 1e6, 1e12, 1e20 and Burgers by 1e4, 1e8).
+                      Other eps values are HWENO_EINVAL. */
   double cfl;      /* CFL number, > 0 */
   int dt_mode;     /* 0: dt = cfl / sum(alpha_d / h_d) with h = dx;
                       1: h = dx^{5/3} (accuracy runs); 2: dt = dt_fixed.
@@ -186,7 +198,11 @@ int hweno_default_options(hweno_options* opt);
 int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double gamma,
                  const hweno_bc* bc);
 
-/* Replace the scheme options (validated; HWENO_EINVAL leaves them unchanged). */
+/* Replace the scheme options (validated; HWENO_EINVAL leaves them unchanged).
+ * A graph that hweno_run recorded is dropped, so that the next hweno_run
+ * records the new options. No device memory is written: the tile tables of
+ * every tile variant and the step sizes of every dt_mode are made by
+ * hweno_create, so work still running on any stream is not disturbed. */
 int hweno_set_options(hweno_ctx* ctx, const hweno_options* opt);
 
 /* Spatial operator of one stage (Eq. odeH in 1D, Eq. ode2H in 2D):
@@ -230,8 +246,8 @@ int hweno_run(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end
  * instances with about equal points, each copied in, stepped and copied out
  * on a library stream of its own, so that the copies of one range overlap
  * the kernels of the others; the results are those of hweno_step bit for bit
- * and hweno_active_instances counts after the call. The first such call
- * creates the streams and events. */
+ * and hweno_active_instances counts after the call. The device copies, the
+ * streams and their events are made by hweno_create. */
 int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double t_end,
                     int nsteps, void* stream);
 
@@ -247,9 +263,14 @@ int hweno_step_host(hweno_ctx* ctx, void* U, void* V, void* W, double* t, double
  * place. If point_updates (host) is not NULL the call synchronises `stream`
  * and stores the point-updates of stepping instances there, then returns the
  * latched device status; otherwise it returns after enqueueing. Waits are
- * bounded (about two seconds); a wait that gives up latches HWENO_ETIMEOUT.
- * 1D only (2D: HWENO_ENOTSUP). Library scratch: counters and alpha slots,
- * allocated by the first call. With fused_small = 2 and instances within
+ * bounded (about two seconds); a wait that gives up latches HWENO_ETIMEOUT,
+ * and every CTA then stops: tiles whose inputs were ready have run, the rest
+ * have not, so after HWENO_ETIMEOUT the contents of U, V and t are
+ * undefined. 1D only (2D: HWENO_ENOTSUP). Library scratch (counters, alpha
+ * slots, tiles per instance of every tile variant) is made by hweno_create;
+ * with point_updates NULL the
+ * call only enqueues work, so it can be recorded into a CUDA graph and
+ * replayed (each replay resets the counters first). With fused_small = 2 and instances within
  * HWENO_CLUSTER_MAX_POINTS, the steps run instead as one launch of the
  * cluster step (one cluster per instance, cluster barriers between stages and
  * steps); it gives the bits of `steps` calls of hweno_step with that option. */
@@ -260,16 +281,17 @@ int hweno_run_persistent(hweno_ctx* ctx, void* U, void* V, double* t, double t_e
  * the next hweno_run_persistent expects one tile too many for instance 0, so
  * the waits for that instance cannot be satisfied; they give up after about
  * two seconds, every CTA then stops, and the call returns HWENO_ETIMEOUT
- * (latched status). The context stays usable: the following calls rebuild
- * the tile counts. kind = 0 clears a pending injection. Nothing faults or
- * hangs the device. */
+ * (latched status). The injection travels as an argument of that one
+ * launch; the context stays usable and the following runs are normal.
+ * kind = 0 clears a pending injection. Nothing faults or hangs the device. */
 int hweno_test_inject(hweno_ctx* ctx, int kind);
 
 /* Tile-shape autotuner (1D): times the fused stage kernel of every tile
  * variant (CTA sizes 64, 128, 256 threads, one or two points per thread) on
  * the given state U, V at times t (device) with t_end, and keeps the fastest
  * for the following calls of this context. Only library scratch is written
- * (U, V, W, t are read). Synchronises `stream`. *chosen (host, nullable)
+ * (U, V, W, t are read). Synchronises `stream` and drops a graph that
+ * hweno_run recorded for another variant. *chosen (host, nullable)
  * receives the variant index (0 = the default 128 x 1; variants 1..4 are
  * 64 x 1, 256 x 1, 128 x 2 and 64 x 2, threads x points per thread);
  * ms (host, nullable, HWENO_TILE_VARIANTS doubles) the best measured time of
@@ -300,8 +322,9 @@ int hweno_totals(hweno_ctx* ctx, const void* U, double* totals, void* stream);
  * boundaries periodic or neither (else HWENO_ENOTSUP). 1D: W and lamW must be
  * NULL and t is not read (may be NULL). 2D: W and lamW are required; t is
  * read by the double-Mach top boundary and may be NULL otherwise. Library
- * scratch holds the replayed stages (allocated on the first call: 12 fields
- * of m x points doubles). */
+ * scratch holds the replayed stages and the stage cotangents (made by
+ * hweno_create for FP64 Burgers and Euler contexts: 6 fields of m x points
+ * doubles in 1D, 12 in 2D). */
 int hweno_adjoint_step(hweno_ctx* ctx, const void* U, const void* V, const void* W,
                        const double* t, const double* dt, void* lamU, void* lamV, void* lamW,
                        void* stream);

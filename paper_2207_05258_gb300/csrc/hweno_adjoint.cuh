@@ -68,8 +68,8 @@ __device__ __forceinline__ double side_vjp(double fm, double f0, double fp, doub
   const double d1 = be0 - be1, d2 = be0 - be2;
   const double t = fabs(d1) + fabs(d2), tau = 0.25 * t * t;
   const double b0 = be0 + w.eps, b1 = be1 + w.eps, b2 = be2 + w.eps;
-  // 1/b0, 1/b1, 1/b2 from one division (b ~ beta + eps stays far from the
-  // FP64 range limits)
+  // 1/b0, 1/b1, 1/b2 from one division: b0 b1 b2 stays inside the FP64
+  // range while beta < 1e100 (split-flux jumps below about 1e48)
   const double b12 = b1 * b2, inv = 1.0 / (b0 * b12);
   const double ib0 = b12 * inv, ib1 = b0 * b2 * inv, ib2 = b0 * b1 * inv;
   const double r0 = tau * ib0, r1 = tau * ib1, r2 = tau * ib2;

@@ -32,12 +32,20 @@ struct hweno_ctx {
   hweno_options opt{};
   long long npts = 0;
   size_t elems = 0, esize = 8;
-  // 1D batch tables (for the current tile variant)
+  // 1D batch tables of every tile variant, made in create: (instance, first
+  // point) per tile and tiles per instance. Choosing a variant only switches
+  // the pointers below, so it never writes device memory that kernels still
+  // in flight on a caller's stream may read. 2D: one entry in variant 0.
+  int* d_vt_inst[kNumVariants1D] = {};
+  int* d_vt_start[kNumVariants1D] = {};
+  int* d_vt_tiles[kNumVariants1D] = {};
+  int vt_ntiles[kNumVariants1D] = {};
+  // the current variant (aliases of the arrays above)
   int ntiles = 0;
   int variant = 0;
   int tile = kTile1D;
-  int tiles_cap = 0;  // capacity of the tile tables (smallest tile)
-  int* d_tile0_inst = nullptr;   // default-variant table kept for the adjoint
+  int tiles_cap = 0;  // largest table (smallest tile)
+  int* d_tile0_inst = nullptr;   // variant 0, used by the adjoint
   int* d_tile0_start = nullptr;
   int ntiles0 = 0;
   int* d_tile_inst = nullptr;
@@ -45,7 +53,8 @@ struct hweno_ctx {
   int* d_inst_n = nullptr;
   long long* d_inst_off = nullptr;
   double* d_inst_dx = nullptr;
-  double* d_inst_hx = nullptr;
+  double* d_hx[2] = {};            // h of the time-step rule: dx, dx^{5/3} (made in create)
+  double* d_inst_hx = nullptr;     // the one dt_mode selects (alias)
   double* d_inst_geo = nullptr;   // per instance dx, 1/dx, 1/dx^2
   float* d_inst_geof = nullptr;   // the same in FP32
   std::vector<double> inst_dx;
@@ -60,21 +69,21 @@ struct hweno_ctx {
   void* d_U2 = nullptr; void* d_V2 = nullptr; void* d_W2 = nullptr;
   void* d_Vt0 = nullptr; void* d_Wt0 = nullptr;
   void* d_LX = nullptr; void* d_VT = nullptr;  // 2D: x-sweep results
-  // adjoint scratch (FP64, allocated by the first hweno_adjoint_step): the
+  // adjoint scratch (FP64 Burgers / Euler contexts, allocated in create): the
   // adjoints of the stage-2 and stage-1 outputs, the base-term cotangents and
   // (2D) the x-sweep part, each m x points doubles per field
   double* d_adj = nullptr;
-  // persistent run (allocated by the first hweno_run_persistent)
+  // persistent run (1D, allocated in create)
   unsigned long long* d_next = nullptr;  // ticket counter, then done[batch], done3[batch]
   unsigned* d_done = nullptr;
   unsigned* d_done3 = nullptr;
   unsigned long long* d_palpha = nullptr;  // 2 x 3 x batch alpha slots
-  int* d_inst_tiles = nullptr;
-  int persist_variant = -1;  // tile variant d_inst_tiles was built for
-  int persist_ctas = 0;
+  int* d_inst_tiles = nullptr;  // tiles per instance of the current variant (alias)
+  int persist_ctas = 0;          // resident CTAs of the current variant's persistent kernel
   int max_n = 0;  // largest instance (1D)
   int inject = 0;  // hweno_test_inject: 1 = the next persistent run waits in vain
-  // pipelined host-buffer steps (1D): streams, events and per-chunk counters
+  // pipelined host-buffer steps (1D batches, created in create): streams,
+  // events and per-chunk counters
   static constexpr int kChunks = 8;
   cudaStream_t cs[kChunks] = {};
   cudaEvent_t ce[kChunks] = {};
@@ -95,6 +104,7 @@ struct hweno_ctx {
   double g_tend = 0.0;
   int g_k = 0;
   bool capturing = false;
+  cudaEvent_t tune_ev[2] = {};  // hweno_autotune's timing events
   // kernel timing (hweno_profile_start / hweno_profile_read)
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
@@ -141,6 +151,18 @@ int check_options(const hweno_options* o, std::string& why) {
 
 bool bc_ok_1d(int b) { return b >= HWENO_BC_PERIODIC && b <= HWENO_BC_INFLOW; }
 
+// Adjoint scratch (hweno_adjoint_step), allocated in create for the contexts
+// the adjoint is built for (FP64 Burgers and Euler). Fields: 0-2 lambda of
+// the stage-2 output (U, V, W), 3-5 of the stage-1 output, 6-8 the base-term
+// cotangents, 9-11 the 2D x-sweep part (of U, V and W); each m x points
+// doubles. 1D has no W fields and no x-sweep part, so its six fields are
+// stored back to back.
+bool adjoint_applies(const hweno_ctx* c) { return !c->fp32 && c->eq != HWENO_BUCKLEY; }
+int adjoint_fields(const hweno_ctx* c) { return c->dim == 2 ? 12 : 6; }
+size_t adjoint_scratch_bytes(const hweno_ctx* c) {
+  return sizeof(double) * (size_t)c->m * (size_t)c->npts * (size_t)adjoint_fields(c);
+}
+
 template <class T>
 int dalloc(hweno_ctx* c, T** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -156,13 +178,20 @@ int dalloc(hweno_ctx* c, T** p, size_t bytes) {
 void free_all(hweno_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
-  void* ptrs[] = {c->d_pu, c->d_partial, c->d_tile0_inst, c->d_tile0_start, c->d_tile_inst, c->d_tile_start, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
-                  c->d_inst_hx, c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt, c->d_lands, c->d_active, c->d_status,
+  void* ptrs[] = {c->d_pu, c->d_partial, c->d_inst_n, c->d_inst_off, c->d_inst_dx,
+                  c->d_hx[0], c->d_hx[1], c->d_inst_geo, c->d_inst_geof, c->d_alpha, c->d_dt,
+                  c->d_lands, c->d_active, c->d_status,
                   c->d_U1, c->d_V1, c->d_W1, c->d_U2, c->d_V2, c->d_W2, c->d_Vt0, c->d_Wt0,
                   c->d_LX, c->d_VT, c->d_hU, c->d_hV, c->d_hW, c->d_ht,
-                  c->d_adj, c->d_next, c->d_palpha, c->d_inst_tiles, c->d_chunk_active};
+                  c->d_adj, c->d_next, c->d_palpha, c->d_chunk_active};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int v = 0; v < kNumVariants1D; ++v) {
+    void* vp[] = {c->d_vt_inst[v], c->d_vt_start[v], c->d_vt_tiles[v]};
+    for (void* p : vp)
+      if (p) cudaFree(p);
+    c->d_vt_inst[v] = c->d_vt_start[v] = c->d_vt_tiles[v] = nullptr;
+  }
   for (int i = 0; i < hweno_ctx::kChunks; ++i) {
     if (c->cs[i]) cudaStreamDestroy(c->cs[i]);
     if (c->ce[i]) cudaEventDestroy(c->ce[i]);
@@ -171,6 +200,10 @@ void free_all(hweno_ctx* c) {
   }
   if (c->ce0) cudaEventDestroy(c->ce0);
   c->ce0 = nullptr;
+  for (cudaEvent_t& ev : c->tune_ev) {
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  }
 }
 
 // Buckley-Leverett alpha over the admissible states (Example 3.4): with
@@ -230,32 +263,32 @@ void tile_table(const std::vector<int>& nx, int tile, std::vector<int>& tinst,
     for (int s = 0; s < nx[k]; s += tile) { tinst.push_back((int)k); tstart.push_back(s); }
 }
 
-// Upload the tile table of variant v (1D) and make it current.
+// Make the tables of variant v (1D, made in create) current and size the
+// persistent grid for it. A graph recorded by hweno_run for another variant
+// is dropped (it holds the old launch shapes). No device memory is written.
 int use_variant(hweno_ctx* c, int v) {
-  std::vector<int> tinst, tstart;
-  tile_table(c->nx, tile_points(v), tinst, tstart);
-  if ((int)tinst.size() > c->tiles_cap) return fail(c, HWENO_EINVAL, "tile table capacity");
+  int dev = 0, sms = 0;
   cudaError_t e;
-  if ((e = cudaMemcpy(c->d_tile_inst, tinst.data(), sizeof(int) * tinst.size(),
-                      cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(c->d_tile_start, tstart.data(), sizeof(int) * tstart.size(),
-                      cudaMemcpyHostToDevice)))
-    return cuda_fail(c, e, "upload tile table");
+  if ((e = cudaGetDevice(&dev)) ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+    return cuda_fail(c, e, "device attributes");
+  const int per_sm = run_1d_ctas_per_sm(c->eq, c->fp32, v);
+  if (per_sm < 1) return fail(c, HWENO_ECUDA, "persistent kernel does not fit on an SM");
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
   c->variant = v;
   c->tile = tile_points(v);
-  c->ntiles = (int)tinst.size();
+  c->d_tile_inst = c->d_vt_inst[v];
+  c->d_tile_start = c->d_vt_start[v];
+  c->d_inst_tiles = c->d_vt_tiles[v];
+  c->ntiles = c->vt_ntiles[v];
+  c->persist_ctas = sms * per_sm;
   return HWENO_OK;
 }
 
-// Per-instance h of the time-step rule (dx, or dx^{5/3} for dt_mode 1).
-int upload_hx(hweno_ctx* c) {
-  std::vector<double> hx(c->batch);
-  for (int k = 0; k < c->batch; ++k)
-    hx[k] = c->opt.dt_mode == 1 ? std::pow(c->inst_dx[k], 5.0 / 3.0) : c->inst_dx[k];
-  const cudaError_t e = cudaMemcpy(c->d_inst_hx, hx.data(), sizeof(double) * c->batch,
-                                   cudaMemcpyHostToDevice);
-  return e == cudaSuccess ? HWENO_OK : cuda_fail(c, e, "upload hx");
-}
+// Per-instance h of the time-step rule: dx (dt_mode 0, 2) or dx^{5/3}
+// (dt_mode 1), both made in create.
+void select_hx(hweno_ctx* c) { c->d_inst_hx = c->d_hx[c->opt.dt_mode == 1 ? 1 : 0]; }
 
 Args1D base_args_1d(const hweno_ctx* c) {
   Args1D a{};
@@ -624,8 +657,7 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
         (equation != HWENO_EULER || !(std::sin(bc->dmr_angle) > 0) || !(std::tan(bc->dmr_angle) > 0)))
       return bad("dmr");
   }
-  // sizes and (1D) tile tables: capacity for the smallest tile of any variant
-  std::vector<int> tinst, tstart;
+  // sizes and tile tables: every 1D variant's table; 2D one entry
   std::vector<long long> off(c->batch);
   c->inst_dx.resize(c->batch);
   long long acc = 0;
@@ -634,34 +666,41 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
     acc += c->nx[k];
     c->inst_dx[k] = (c->x1 - c->x0) / c->nx[k];
   }
-  if (grid->dim == 1) {
-    tile_table(c->nx, kMinTile1D, tinst, tstart);
-    c->tiles_cap = (int)tinst.size();
-    tile_table(c->nx, kTile1D, tinst, tstart);
-  } else {
-    acc = (long long)c->nx[0] * c->ny;
-    tinst.push_back(0);
-    tstart.push_back(0);
-    c->tiles_cap = 1;
+  const int nvar = grid->dim == 1 ? kNumVariants1D : 1;
+  std::vector<int> tinst[kNumVariants1D], tstart[kNumVariants1D], ntk[kNumVariants1D];
+  for (int v = 0; v < nvar; ++v) {
+    if (grid->dim == 1) {
+      const int tp = tile_points(v);
+      tile_table(c->nx, tp, tinst[v], tstart[v]);
+      for (int k = 0; k < c->batch; ++k) ntk[v].push_back((c->nx[k] + tp - 1) / tp);
+    } else {
+      tinst[v] = {0};
+      tstart[v] = {0};
+      ntk[v] = {1};
+    }
+    c->vt_ntiles[v] = (int)tinst[v].size();
+    c->tiles_cap = std::max(c->tiles_cap, c->vt_ntiles[v]);
   }
+  if (grid->dim == 2) acc = (long long)c->nx[0] * c->ny;
   c->npts = acc;
   c->elems = (size_t)c->m * (size_t)acc;
-  c->ntiles = (int)tinst.size();
   c->ntiles_tot = grid->dim == 1 ? c->tiles_cap
                                  : ((c->nx[0] + kTileX2D - 1) / kTileX2D) * c->ny;
 
   int rc = HWENO_OK;
   const size_t fb = c->elems * c->esize;
   const size_t B = (size_t)c->batch;
-  c->ntiles0 = (int)tinst.size();
-  if ((rc = dalloc(c, &c->d_tile_inst, sizeof(int) * c->tiles_cap)) ||
-      (rc = dalloc(c, &c->d_tile_start, sizeof(int) * c->tiles_cap)) ||
-      (rc = dalloc(c, &c->d_tile0_inst, sizeof(int) * c->ntiles0)) ||
-      (rc = dalloc(c, &c->d_tile0_start, sizeof(int) * c->ntiles0)) ||
+  for (int v = 0; v < nvar && rc == HWENO_OK; ++v)
+    if ((rc = dalloc(c, &c->d_vt_inst[v], sizeof(int) * tinst[v].size())) ||
+        (rc = dalloc(c, &c->d_vt_start[v], sizeof(int) * tstart[v].size())) ||
+        (rc = dalloc(c, &c->d_vt_tiles[v], sizeof(int) * ntk[v].size())))
+      break;
+  if (rc != HWENO_OK ||
       (rc = dalloc(c, &c->d_inst_n, sizeof(int) * B)) ||
       (rc = dalloc(c, &c->d_inst_off, sizeof(long long) * B)) ||
       (rc = dalloc(c, &c->d_inst_dx, sizeof(double) * B)) ||
-      (rc = dalloc(c, &c->d_inst_hx, sizeof(double) * B)) ||
+      (rc = dalloc(c, &c->d_hx[0], sizeof(double) * B)) ||
+      (rc = dalloc(c, &c->d_hx[1], sizeof(double) * B)) ||
       (rc = dalloc(c, &c->d_inst_geo, sizeof(double) * 3 * B)) ||
       (rc = dalloc(c, &c->d_inst_geof, sizeof(float) * 3 * B)) ||
       (rc = dalloc(c, &c->d_alpha, sizeof(unsigned long long) * 3 * B * 2)) ||
@@ -678,28 +717,59 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
       (c->dim == 2 &&
        ((rc = dalloc(c, &c->d_W1, fb)) || (rc = dalloc(c, &c->d_W2, fb)) ||
         (rc = dalloc(c, &c->d_Wt0, fb)) || (rc = dalloc(c, &c->d_LX, 3 * fb)) ||
-        (rc = dalloc(c, &c->d_VT, fb)) || (rc = dalloc(c, &c->d_hW, fb))))) {
+        (rc = dalloc(c, &c->d_VT, fb)) || (rc = dalloc(c, &c->d_hW, fb)))) ||
+      (c->dim == 1 &&
+       ((rc = dalloc(c, &c->d_next, sizeof(unsigned long long) + 2 * sizeof(unsigned) * B)) ||
+        (rc = dalloc(c, &c->d_palpha, sizeof(unsigned long long) * 6 * B)) ||
+        (rc = dalloc(c, &c->d_chunk_active, sizeof(int) * hweno_ctx::kChunks)))) ||
+      (adjoint_applies(c) && (rc = dalloc(c, &c->d_adj, adjoint_scratch_bytes(c))))) {
     free_all(c);
     delete c;
     return rc;
   }
-  std::vector<double> geo(3 * B);
+  if (c->dim == 1) {
+    c->d_done = reinterpret_cast<unsigned*>(c->d_next + 1);
+    c->d_done3 = c->d_done + B;
+  }
+  // events and (1D batches) the streams of the pipelined host-buffer step
+  bool made = cudaEventCreate(&c->tune_ev[0]) == cudaSuccess &&
+              cudaEventCreate(&c->tune_ev[1]) == cudaSuccess;
+  if (made && c->dim == 1 && c->batch > 1) {
+    made = cudaEventCreateWithFlags(&c->ce0, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < hweno_ctx::kChunks && made; ++i)
+      made = cudaStreamCreateWithFlags(&c->cs[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ce[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!made) {
+    free_all(c);
+    delete c;
+    return HWENO_ECUDA;
+  }
+  std::vector<double> geo(3 * B), hx53(B);
   std::vector<float> geof(3 * B);
   for (size_t k = 0; k < B; ++k) {
     const double d = c->inst_dx[k];
     const double g3[3] = {d, 1.0 / d, 1.0 / (d * d)};
     for (int i = 0; i < 3; ++i) { geo[3 * k + i] = g3[i]; geof[3 * k + i] = (float)g3[i]; }
+    hx53[k] = std::pow(d, 5.0 / 3.0);
   }
-  const bool copy_failed =
+  bool copy_failed = false;
+  for (int v = 0; v < nvar && !copy_failed; ++v)
+    copy_failed =
+        cudaMemcpy(c->d_vt_inst[v], tinst[v].data(), sizeof(int) * tinst[v].size(),
+                   cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->d_vt_start[v], tstart[v].data(), sizeof(int) * tstart[v].size(),
+                   cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->d_vt_tiles[v], ntk[v].data(), sizeof(int) * ntk[v].size(),
+                   cudaMemcpyHostToDevice);
+  copy_failed = copy_failed ||
       cudaMemcpy(c->d_inst_geo, geo.data(), sizeof(double) * 3 * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_geof, geof.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(c->d_tile_inst, tinst.data(), sizeof(int) * tinst.size(), cudaMemcpyHostToDevice) ||
-      cudaMemcpy(c->d_tile0_inst, tinst.data(), sizeof(int) * tinst.size(), cudaMemcpyHostToDevice) ||
-      cudaMemcpy(c->d_tile0_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice) ||
-      cudaMemcpy(c->d_tile_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_n, c->nx.data(), sizeof(int) * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_off, off.data(), sizeof(long long) * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_dx, c->inst_dx.data(), sizeof(double) * B, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_hx[0], c->inst_dx.data(), sizeof(double) * B, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(c->d_hx[1], hx53.data(), sizeof(double) * B, cudaMemcpyHostToDevice) ||
       cudaMemset(c->d_status, 0, sizeof(unsigned)) ||
       cudaMemset(c->d_pu, 0, sizeof(unsigned long long));
   if (copy_failed) {
@@ -707,7 +777,13 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
     delete c;
     return HWENO_ECUDA;
   }
-  if ((rc = upload_hx(c)) != HWENO_OK) {
+  // variant 0 (also the adjoint's table) and the paper's dt rule
+  c->d_tile0_inst = c->d_tile_inst = c->d_vt_inst[0];
+  c->d_tile0_start = c->d_tile_start = c->d_vt_start[0];
+  c->d_inst_tiles = c->d_vt_tiles[0];
+  c->ntiles0 = c->ntiles = c->vt_ntiles[0];
+  select_hx(c);
+  if (c->dim == 1 && (rc = use_variant(c, 0)) != HWENO_OK) {
     free_all(c);
     delete c;
     return rc;
@@ -722,10 +798,13 @@ int hweno_set_options(hweno_ctx* c, const hweno_options* o) {
   if (check_options(o, why) != HWENO_OK) return fail(c, HWENO_EINVAL, why);
   const hweno_options old = c->opt;
   c->opt = *o;
-  int rc = upload_hx(c);
-  if (rc == HWENO_OK && c->dim == 1 && o->tile_variant != c->variant)
-    rc = use_variant(c, o->tile_variant);
+  int rc = HWENO_OK;
+  if (c->dim == 1 && o->tile_variant != c->variant) rc = use_variant(c, o->tile_variant);
   if (rc != HWENO_OK) c->opt = old;
+  select_hx(c);
+  // a graph recorded by hweno_run holds the old scheme parameters
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
   return rc;
 }
 
@@ -818,7 +897,6 @@ int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end
     return fail(c, HWENO_EINVAL, "too many steps for one launch");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  int rc;
   if (c->opt.fused_small == 2 && c->max_n <= kClusterMax * kTile1D) {
     // small instances: the K steps as one launch of the cluster step
     if ((e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)) ||
@@ -854,32 +932,8 @@ int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end
     // no such cluster here: the tiled persistent kernel below
   }
   const size_t B = c->batch;
-  if (!c->d_next) {
-    // counters: next (8 B), done, done3 (4 B per instance each), one allocation
-    if ((rc = dalloc(c, &c->d_next, sizeof(unsigned long long) + 2 * sizeof(unsigned) * B)) ||
-        (rc = dalloc(c, &c->d_palpha, sizeof(unsigned long long) * 6 * B)) ||
-        (rc = dalloc(c, &c->d_inst_tiles, sizeof(int) * B)))
-      return rc;
-    c->d_done = reinterpret_cast<unsigned*>(c->d_next + 1);
-    c->d_done3 = c->d_done + B;
-  }
-  if (c->persist_variant != c->variant || c->inject == 1) {
-    const int tp = tile_points(c->variant);
-    std::vector<int> nt(B);
-    for (size_t k = 0; k < B; ++k) nt[k] = (c->nx[k] + tp - 1) / tp;
-    if (c->inject == 1) nt[0] += 1;  // instance 0 then waits for a tile that does not exist
-    if ((e = cudaMemcpy(c->d_inst_tiles, nt.data(), sizeof(int) * B, cudaMemcpyHostToDevice)))
-      return cuda_fail(c, e, "copy tile counts");
-    int dev = 0, sms = 0;
-    if ((e = cudaGetDevice(&dev)) ||
-        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
-      return cuda_fail(c, e, "device attributes");
-    const int per_sm = run_1d_ctas_per_sm(c->eq, c->fp32, c->variant);
-    if (per_sm < 1) return fail(c, HWENO_ECUDA, "persistent kernel does not fit on an SM");
-    c->persist_ctas = sms * per_sm;
-    c->persist_variant = c->inject == 1 ? -1 : c->variant;  // a corrupted table is rebuilt next time
-    c->inject = 0;
-  }
+  const unsigned wait_extra = c->inject == 1 ? 1u : 0u;  // hweno_test_inject
+  c->inject = 0;
   if ((e = cudaMemsetAsync(c->d_next, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned) * B, s)) ||
       (e = cudaMemsetAsync(c->d_palpha, 0, sizeof(unsigned long long) * 6 * B, s)) ||
       (e = cudaMemsetAsync(c->d_active, 0, sizeof(int), s)) ||
@@ -905,6 +959,7 @@ int hweno_run_persistent(hweno_ctx* c, void* U, void* V, double* t, double t_end
   p.U1 = c->d_U1; p.V1 = c->d_V1; p.U2 = c->d_U2; p.V2 = c->d_V2; p.Vt0 = c->d_Vt0;
   p.active = c->d_active; p.pu = c->d_pu;
   p.steps = steps; p.ntiles = c->ntiles; p.batch = c->batch;
+  p.wait_extra = wait_extra;
   prof_begin(c, s);
   if ((e = launch_run_1d(c->eq, c->fp32, c->variant, a, p, c->persist_ctas, s)))
     return cuda_fail(c, e, "persistent run");
@@ -932,16 +987,6 @@ int step_host_1d_pipelined(hweno_ctx* c, void* U, void* V, double* t, double t_e
                            cudaStream_t s) {
   cudaError_t e;
   const int C = std::min(hweno_ctx::kChunks, c->batch);
-  if (!c->ce0) {
-    if ((e = cudaEventCreateWithFlags(&c->ce0, cudaEventDisableTiming)))
-      return cuda_fail(c, e, "event");
-    for (int i = 0; i < hweno_ctx::kChunks; ++i)
-      if ((e = cudaStreamCreateWithFlags(&c->cs[i], cudaStreamNonBlocking)) ||
-          (e = cudaEventCreateWithFlags(&c->ce[i], cudaEventDisableTiming)))
-        return cuda_fail(c, e, "stream");
-    int rc;
-    if ((rc = dalloc(c, &c->d_chunk_active, sizeof(int) * hweno_ctx::kChunks))) return rc;
-  }
   // ranges of instances and of tiles
   const int tp = tile_points(c->variant);
   std::vector<long long> first_tile(c->batch + 1, 0), first_pt(c->batch + 1, 0);
@@ -1047,9 +1092,7 @@ int hweno_autotune(hweno_ctx* c, const void* U, const void* V, const void* W, co
   }
   (void)W;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, HWENO_ECUDA, "event");
-  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(c, HWENO_ECUDA, "event"); }
+  cudaEvent_t e0 = c->tune_ev[0], e1 = c->tune_ev[1];
   int best = 0;
   float best_ms = 1e30f;
   int rc = HWENO_OK;
@@ -1083,8 +1126,6 @@ int hweno_autotune(hweno_ctx* c, const void* U, const void* V, const void* W, co
     if (ms) ms[v] = tv;
     if (tv < best_ms) { best_ms = tv; best = v; }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (rc != HWENO_OK) {
     use_variant(c, 0);
     return rc;
@@ -1111,16 +1152,9 @@ int hweno_totals(hweno_ctx* c, const void* U, double* totals, void* stream) {
 
 namespace {
 
-// Adjoint scratch fields: 0-2 lambda of the stage-2 output (U, V, W), 3-5 of
-// the stage-1 output, 6-8 base-term cotangents, 9-11 the 2D x-sweep part.
-int adjoint_scratch(hweno_ctx* c) {
-  if (c->d_adj) return HWENO_OK;
-  const size_t field = sizeof(double) * (size_t)c->m * (size_t)c->npts;
-  return dalloc(c, &c->d_adj, field * 12);
-}
-
 double* adj_field(hweno_ctx* c, int f) {
-  return c->d_adj + (size_t)f * (size_t)c->m * (size_t)c->npts;
+  const int slot = c->dim == 2 ? f : (f / 3) * 2 + f % 3;  // 1D: 0 1 3 4 6 7 -> 0..5
+  return c->d_adj + (size_t)slot * (size_t)c->m * (size_t)c->npts;
 }
 
 int adjoint_1d(hweno_ctx* c, const void* U, const void* V, const double* dt, double* lU,
@@ -1305,7 +1339,8 @@ int adjoint_check(hweno_ctx* c, const void* U, const void* V, const void* W, con
   for (int d = 0; d < c->dim; ++d)
     if ((bcs[2 * d] == HWENO_BC_PERIODIC) != (bcs[2 * d + 1] == HWENO_BC_PERIODIC))
       return fail(c, HWENO_ENOTSUP, "adjoint needs both ends of a direction periodic or neither");
-  return adjoint_scratch(c);
+  if (!c->d_adj) return fail(c, HWENO_ENOTSUP, "no adjoint scratch in this context");
+  return HWENO_OK;
 }
 
 // The adjoint of one step, with the stage states replayed (record null) or

@@ -181,19 +181,51 @@ struct Frac {
   Real n, d;
 };
 
-// n0/d0 and n1/d1 with one division: r = 1/(d0 d1). Both denominators lie in
-// [1e-40, 1e120] for any data the scheme meets (products of smoothness
-// indicators >= eps), so the product stays far inside the FP64 range.
+// Range checks of the deferred quotients, on the biased exponent (integer
+// operations, off the FP64 pipe). A denominator is a product of up to
+// sixteen factors of the size of beta + eps (beta grows like the square of
+// the split-flux jumps), so for large data it leaves the FP64 range: each
+// deferred form below then falls back to separate divisions, whose
+// intermediates are only as large as beta itself.
+__device__ __forceinline__ int biased_exponent(double x) {
+  return (__double2hiint(x) >> 20) & 0x7ff;
+}
+// d > 0 with 1/d normal and some headroom: 2^-1019 <= d < 2^1020
+__device__ __forceinline__ bool denominator_ok(double d) {
+  return (unsigned)(biased_exponent(d) - 4) < 2039u;
+}
+__device__ __forceinline__ bool finite_value(double x) { return biased_exponent(x) != 0x7ff; }
+
+// n0/d0 and n1/d1 with one division: r = 1/(d0 d1), unless d0 d1 or the
+// cross products leave the range, where each quotient is divided alone.
 template <class Real>
 __device__ __forceinline__ void resolve2(const Frac<Real>& a, const Frac<Real>& b, Real& qa,
                                          Real& qb) {
   if constexpr (std::is_same<Real, double>::value) {
-    const Real r = Real(1) / (a.d * b.d);
+    const Real dd = a.d * b.d;
+    const Real r = Real(1) / dd;
     qa = a.n * b.d * r;
     qb = b.n * a.d * r;
+    if (!(denominator_ok(dd) & finite_value(qa) & finite_value(qb))) {
+      qa = a.n / a.d;
+      qb = b.n / b.d;
+    }
   } else {
     qa = a.n;
     qb = b.n;
+  }
+}
+
+// The sum of two deferred quotients na/da + nb/db as one deferred quotient,
+// or (out of range) as a final value.
+template <class Real>
+__device__ __forceinline__ Frac<Real> sum_frac(Real na, Real da, Real nb, Real db) {
+  if constexpr (std::is_same<Real, double>::value) {
+    const Frac<Real> f{na * db + nb * da, da * db};
+    if (denominator_ok(f.d) & finite_value(f.n)) return f;
+    return Frac<Real>{na / da + nb / db, Real(1)};
+  } else {
+    return Frac<Real>{na + nb, Real(1)};
   }
 }
 
@@ -217,7 +249,7 @@ __device__ __forceinline__ Frac<Real> interface_flux_frac(Real fpm, Real fp0, Re
     Real na, da, nb, db;
     combine_nd(a, w, na, da);
     combine_nd(b, w, nb, db);
-    return Frac<Real>{na * db + nb * da, da * db};
+    return sum_frac(na, da, nb, db);
   } else {
     return Frac<Real>{combine_direct(a, w) + combine_direct(b, w), Real(1)};
   }
@@ -278,7 +310,7 @@ __device__ __forceinline__ Frac<Real> limited_derivative_frac(Real um, Real u0, 
     const Real L1 = w.d1 * (P + tau * b02);
     const Real L2 = w.d2 * (P + tau * b01);
     const Real num = L0 * (q0 - w.d1 * q1 - w.d2 * q2) + L1 * q1 + L2 * q2;
-    return Frac<Real>{num, w.d0 * L0 + L1 + L2};
+    return Frac<Real>{num, w.d0 * L0 + L1 + L2};  // about b^4: in range (resolve2 checks)
   } else {
     const Real l0 = w.d0 + w.d0 * qdiv(tau, b0);
     const Real l1 = w.d1 + w.d1 * qdiv(tau, b1);

@@ -48,11 +48,13 @@ constexpr int kMinTile1D = 60;  // smallest tile of any variant
 constexpr int kConstTable = 15;
 
 // Bounds of the options that enter the deferred quotients. The kernels
-// resolve quotients whose denominators are products of up to twelve factors
-// of the size of beta + eps (the nonlinear weights of two sides of two
-// fields over a common denominator) times powers of the linear weights.
-// Within these bounds, and for data of moderate size, those products stay
-// inside the FP64 range: eps^12 g^4 >= 1e-264 even where beta = 0.
+// resolve quotients whose denominators are products of factors of the size
+// of beta + eps (the nonlinear weights of two sides of two fields over a
+// common denominator) times powers of the linear weights. Within these
+// bounds those products stay above the FP64 underflow limit: where beta = 0
+// (constant data, where tau = 0 too) they are eps^12 g^4 >= 1e-264. Large
+// beta (large data) is handled in the kernels: out of range, they divide
+// per side and per field (hweno_math.cuh, resolve2 / sum_frac).
 constexpr double kEpsMin = 1e-20, kEpsMax = 1e6, kWeightMin = 1e-6;
 
 struct SchemeParams {
@@ -306,6 +308,7 @@ struct PersistArgs {
   int* active;                // instances with t < t_end after the last step
   unsigned long long* pu;     // point-updates of stepping instances (nullable)
   int steps, ntiles, batch;
+  unsigned wait_extra;        // test hook: tiles of instance 0 wait for this many more
 };
 
 // Fused step of small instances (stage1d_impl.cuh, k_step_small_1d): one CTA

@@ -542,7 +542,7 @@ template <int EQ, class Real, int NT, int PPT>
 __global__ void __launch_bounds__(NT, (MinBlocks1D<Real, NT>::value))
 k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p) {
   __shared__ long long s_ticket;
-  __shared__ int s_stop;
+  __shared__ int s_stop, s_gave_up;
   const long long per_step = 3LL * p.ntiles;
   const long long total = per_step * p.steps;
   for (;;) {
@@ -560,8 +560,12 @@ k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p
     const int b = r - stage * p.ntiles;
     const int k = a.tile_inst[b], s = a.tile_start[b];
     const unsigned ntk = (unsigned)p.inst_tiles[k];
-    if (threadIdx.x == 0) wait_count(&p.done[k], (unsigned)(3 * n + stage) * ntk, a.status);
+    if (threadIdx.x == 0) {
+      const unsigned need = (unsigned)(3 * n + stage) * ntk + (k == 0 ? p.wait_extra : 0u);
+      s_gave_up = !wait_count(&p.done[k], need, a.status);
+    }
     __syncthreads();
+    if (s_gave_up) break;  // this tile's inputs are not ready: leave it untouched
     const int par = n & 1;
     unsigned long long* slot0 = p.alpha + (size_t)(par * 3) * p.batch;  // this step's slots
     StageIO io = io_of(a);
@@ -786,8 +790,7 @@ __device__ __forceinline__ Frac<Real> side_frac(int sd, Real f0, Real f1, Real f
 // The two sides of one field summed as in interface_flux_frac.
 template <class Real>
 __device__ __forceinline__ Frac<Real> sides_sum(Real na, Real da, Real nb, Real db) {
-  if constexpr (std::is_same<Real, double>::value) return Frac<Real>{na * db + nb * da, da * db};
-  else return Frac<Real>{na + nb, Real(1)};
+  return sum_frac(na, da, nb, db);
 }
 
 template <int EQ, class Real, int MODE>

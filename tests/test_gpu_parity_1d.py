@@ -350,3 +350,34 @@ def test_invalid_options_are_rejected(hw, opts):
     with pytest.raises(hw.HwenoError) as e:
         hw.Solver.from_workload(w, **opts)
     assert e.value.code == hw.EINVAL
+
+
+def _scaled(w, k):
+    return W.Workload(w.name, w.equation, 1, w.nx, 1, w.x0, w.x1, w.y0, w.y1, w.t_end, w.bc,
+                      w.U * k, w.V * k, gas_gamma=w.gas_gamma,
+                      inflow=tuple(k * np.asarray(w.inflow)))
+
+
+@pytest.mark.parametrize("k", [1e6, 1e12, 1e20])
+def test_large_euler_data(hw, k):
+    """Conserved variables in large (dimensional) units: rho, rho u, E scaled
+    by k keep the velocities and sound speeds, so the split fluxes and their
+    jumps grow by k and the smoothness indicators by k^2. The products of
+    indicators that the kernels divide by once per pair of fields then leave
+    the FP64 range (from k ~ 1e6 on these data); the kernels then divide per
+    field and still match the oracle (which divides per weight)."""
+    w = _scaled(euler_batch(SIZES, 21, "riemann"), k)
+    check_rhs(hw, w)
+    compare_runs(w, gpu_run(hw, w, 1.0, steps=1), oracle_run(w, 1.0, steps=1), 1e-13, 1e-12)
+    w = _scaled(euler_batch(SIZES, 24, "smooth", ("periodic", "periodic")), k)
+    check_rhs(hw, w)
+
+
+@pytest.mark.parametrize("k", [1e4, 1e8])
+def test_large_burgers_data(hw, k):
+    """Burgers with u scaled by k: f = u^2/2 grows by k^2, the indicators by
+    k^4 (range fallback as above); the wave speed and the time step scale
+    with it."""
+    w = _scaled(burgers_batch(SIZES, 22, "periodic"), k)
+    check_rhs(hw, w)
+    compare_runs(w, gpu_run(hw, w, 1.0, steps=1), oracle_run(w, 1.0, steps=1), 1e-13, 1e-12)
