@@ -51,6 +51,14 @@ ALGO_FLOPS_PER_POINT_STEP = {
     ("euler", 2): 14555.81,
     ("burgers", 2): 2484.84,
 }
+# Algorithmic operations per grid point of one adjoint step: the op count of
+# the oracle's forward-mode (dual-number) step, values and tangents together,
+# on the adjoint workloads; one reverse step computes the same
+# Jacobian-vector arithmetic transposed, plus the forward values it needs.
+ALGO_ADJOINT_FLOPS_PER_POINT_STEP = {
+    ("euler", 2): 45603.16,
+    ("burgers", 1): 3722.17,
+}
 # Compulsory state traffic per point-step and component (words): 1D reads
 # U^n,V^n / U1,V1,U^n,V~^n / U2,V2,U^n,V~^n and writes U1,V1,V~^n / U2,V2 /
 # U^{n+1},V^{n+1}: 10 + 7 = 17.
@@ -64,17 +72,17 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # (dram__bytes_read.sum + dram__bytes_write.sum over points;
 # profiles/k_stage_1d_euler_fp{64,32}_riemann_batch.md). An entry is removed
 # whenever the kernel changes after its capture.
-MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": 99.3, "fp32": 38.4}
+MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": None, "fp32": None}
 # DRAM bytes per point-step of the persistent kernel (all three stages), from
 # an ncu capture (profiles/k_run_1d_euler_fp64_riemann_batch.md); None until
 # taken for the kernel as it stands (FP32: the 1024-instance capture batch
 # fits in L2, so its counters do not scale to the larger batch).
-MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.7, "fp32": None}
+MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": None, "fp32": None}
 # DRAM bytes per point of one 2D stage (x-sweep + y-sweep launches) on the
 # smooth periodic problem at 2048^2, from an ncu capture
 # (profiles/k_sweeps_2d_euler_fp64_smooth.md); applied to grids whose working
 # set exceeds the L2 (smaller grids keep part of it in L2).
-MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {"fp64": 627.3, "fp32": 306.6}
+MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {"fp64": None, "fp32": None}
 
 
 def parse():
@@ -94,7 +102,7 @@ def parse():
     ap.add_argument("--fd-directions", type=int, default=16,
                     help="adjoint workloads: seeded directions checked by central differences")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the e2e, fp32 and cpu_baseline legs")
+                    help="skip the e2e, fp32 and cpu_baseline legs and the other workloads")
     return ap.parse_args()
 
 
@@ -451,10 +459,25 @@ def run_ours(args, rank, world, dev_index):
     if not args.no_extras:
         # FP32 variant of the same workload (state and reconstruction in FP32)
         if args.precision == "fp64":
-            ms32, pu32, prof32, _, _, _ = timed("fp32", args.steps, args.warmup, True)
+            ms32, pu32, prof32, _, _, pu32_ng = timed("fp32", args.steps, args.warmup, True)
+            st32 = prof32["stage"][0] / prof32["stage"][1] * launches_per_stage * 1e-3
+            ach32 = flop_stage * (pu32_ng / args.steps) / st32 / 1e12
             out["fp32"] = {"value": round(pu32 / (ms32 * 1e-3) / 1e6, 3),
                            "ms_per_step": round(ms32 / args.steps, 4),
-                           "stage_kernel_ms": round(prof32["stage"][0] / prof32["stage"][1], 4)}
+                           "stage_kernel_ms": round(prof32["stage"][0] / prof32["stage"][1], 4),
+                           "roofline": {
+                               "bound": "alu", "achieved": round(ach32, 4),
+                               "peak": round(PEAK_TFLOPS["fp32"], 2), "unit": "TFLOP/s",
+                               "frac": round(ach32 / PEAK_TFLOPS["fp32"], 4),
+                               "traffic": (None if MEASURED_STAGE_TRAFFIC_PER_POINT["fp32"] is None
+                                           or args.workload != "riemann_batch" else
+                                           MEASURED_STAGE_TRAFFIC_PER_POINT["fp32"] *
+                                           pu32_ng / args.steps),
+                               "kernel": ("k_stage_1d<%s,fp32>" % w.equation if w.dim == 1 else
+                                          "k_xsweep_2d + k_ysweep_2d <%s,fp32>" % w.equation),
+                               "flops_per_point_stage": round(flop_stage, 2),
+                               "peak_source": "unit counts (recipe): 152 SM x 128 FP32 lanes x "
+                                              "2 flop x 2.07 GHz"}}
             p32 = timed.pers
             if p32 is not None and p32[1] > 0:  # the same K steps as one persistent launch
                 out["fp32"]["persistent"] = {"value": round(p32[1] / (p32[0] * 1e-3) / 1e6, 3),
@@ -661,49 +684,19 @@ def run_adjoint(args, rank, world, dev_index):
         else:
             active = float(sum(float((d > 0).double().sum().item()) for d in dts[:K])) * n
         del states
-        # (b) full gradient with checkpoints
-        U0, V0 = cuda(w.U).requires_grad_(True), cuda(w.V).requires_grad_(True)
-        W0 = cuda(w.W).requires_grad_(True) if two else None
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        out = run_to_time(U0, V0, s, t_end, 20, max_steps=max_steps, W0=W0)
-        J = jfun(out[0])
-        J.backward()
-        torch.cuda.synchronize()
-        grad_s = time.perf_counter() - t0
-        g = [U0.grad, V0.grad] + ([W0.grad] if two else [])
-        # (c) central differences along seeded smooth directions
-        fd = []
-        rng = W.SplitMix64(1234 + rank)
-        for _ in range(args.fd_directions):
-            if two:  # a perturbation of the initial density alone (and its derivatives)
-                f, fx, fy = W.fourier_2d(rng, n, n, 0.0, 2.0, 1e-2)
-                z = np.zeros(3 * npts)
-                d = [np.concatenate([g.ravel(), z]) for g in (f, fx, fy)]
-            else:
-                x = W.centers(0.0, 2.0, n)
-                du = np.concatenate([1e-2 * np.sin(np.pi * x * (1 + int(rng.uniform(0, 4))) +
-                                                   rng.uniform(0, 6.3)) for _ in range(count)])
-                d = [du, np.zeros_like(du)]
-            dg = [cuda(x) for x in d]
-            adj_dJ = float(sum((gi * di).sum().item() for gi, di in zip(g, dg)))
-            scale = math.sqrt(sum(float((gi * gi).sum().item()) for gi in g) *
-                              sum(float((di * di).sum().item()) for di in dg))
-            eps = 1e-6
-            Js = []
-            for sg in (1.0, -1.0):
-                Ue = cuda(w.U) + sg * eps * dg[0]
-                Ve = cuda(w.V) + sg * eps * dg[1]
-                We = cuda(w.W) + sg * eps * dg[2] if two else None
-                te = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
-                s.run(Ue, Ve, We, te, t_end, max_steps=max_steps)
-                Js.append(float(jfun(Ue).item()))
-            fdv = (Js[0] - Js[1]) / (2 * eps)
-            fd.append({"adjoint": adj_dJ, "fd": fdv,
-                       "rel_to_cs_scale": abs(adj_dJ - fdv) / scale})
+        light = getattr(args, "light", False)
+        g, fd, grad_s = None, [], None
+    if not light:
+        with ClockSampler(dev_index), torch.cuda.stream(stream):
+            g, fd, grad_s = _adjoint_gradient_checks(args, w, s, two, n, npts, count if not two
+                                                     else 1, t_end, max_steps, jfun, cuda,
+                                                     rank, W, run_to_time, torch)
     if world > 1:
         adj_ms, active = reduce_over_ranks(adj_ms, active, "cuda")
     value = active / (adj_ms * 1e-3) / 1e6
+    key = ("euler", 2) if two else ("burgers", 1)
+    ach = ALGO_ADJOINT_FLOPS_PER_POINT_STEP[key] * active / (adj_ms * 1e-3) / 1e12
+    fp64_loop = hweno.measure_fp64_peak()
     out = {"metric": "Mpoint-updates/s per adjoint RK step", "value": round(value, 3),
            "unit": "Mpoint-updates/s", "n_gpus": world, "steps": K, "warmup": Wm,
            "ms_per_step": round(adj_ms / K, 4), "higher_is_better": True, "scaling": "weak",
@@ -716,9 +709,20 @@ def run_adjoint(args, rank, world, dev_index):
            "replay": {"ms_per_step": round(replay_ms / K, 4),
                       "note": "hweno_adjoint_step without a step record: stages 1-2 "
                               "replayed inside the adjoint step"},
-           "full_gradient": {"seconds": round(grad_s, 3), "checkpoint_every": 20,
-                             "note": "forward run + checkpointed backward, host-timed"},
+           "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": PEAK_TFLOPS["fp64"],
+                        "unit": "TFLOP/s", "frac": round(ach / PEAK_TFLOPS["fp64"], 4),
+                        "dfma_loop_tflops": round(fp64_loop, 4),
+                        "frac_of_dfma_loop": round(ach / fp64_loop, 4), "traffic": None,
+                        "kernel": "hweno_adjoint_step (reverse stages 3, 2, 1; %d launches)"
+                                  % launches,
+                        "flops_per_point_step": ALGO_ADJOINT_FLOPS_PER_POINT_STEP[key],
+                        "flops_source": "op count of the oracle's dual-number step (values "
+                                        "and tangents)",
+                        "peak_source": "nominal (recipe): FP64 1.25 TFLOP/s"},
            "clocks": clk.summary(), "gpu_launches": launches * K}
+    if grad_s is not None:
+        out["full_gradient"] = {"seconds": round(grad_s, 3), "checkpoint_every": 20,
+                                "note": "forward run + checkpointed backward, host-timed"}
     if fd:
         out["fd_check"] = {"directions": len(fd), "eps": 1e-6,
                            "max_rel_to_cs_scale": max(f["rel_to_cs_scale"] for f in fd),
@@ -726,6 +730,54 @@ def run_adjoint(args, rank, world, dev_index):
                                                 for f in fd),
                            "first": fd[0]}
     return out
+
+
+def _adjoint_gradient_checks(args, w, s, two, n, npts, count, t_end, max_steps, jfun, cuda,
+                             rank, W, run_to_time, torch):
+    """(b) one full gradient through the checkpointed autograd Function,
+    host-timed; (c) central differences along --fd-directions seeded smooth
+    directions against the adjoint's <grad J, d>."""
+    # (b) full gradient with checkpoints
+    U0, V0 = cuda(w.U).requires_grad_(True), cuda(w.V).requires_grad_(True)
+    W0 = cuda(w.W).requires_grad_(True) if two else None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = run_to_time(U0, V0, s, t_end, 20, max_steps=max_steps, W0=W0)
+    J = jfun(out[0])
+    J.backward()
+    torch.cuda.synchronize()
+    grad_s = time.perf_counter() - t0
+    g = [U0.grad, V0.grad] + ([W0.grad] if two else [])
+    # (c) central differences along seeded smooth directions
+    fd = []
+    rng = W.SplitMix64(1234 + rank)
+    for _ in range(args.fd_directions):
+        if two:  # a perturbation of the initial density alone (and its derivatives)
+            f, fx, fy = W.fourier_2d(rng, n, n, 0.0, 2.0, 1e-2)
+            z = np.zeros(3 * npts)
+            d = [np.concatenate([g.ravel(), z]) for g in (f, fx, fy)]
+        else:
+            x = W.centers(0.0, 2.0, n)
+            du = np.concatenate([1e-2 * np.sin(np.pi * x * (1 + int(rng.uniform(0, 4))) +
+                                               rng.uniform(0, 6.3)) for _ in range(count)])
+            d = [du, np.zeros_like(du)]
+        dg = [cuda(x) for x in d]
+        adj_dJ = float(sum((gi * di).sum().item() for gi, di in zip(g, dg)))
+        scale = math.sqrt(sum(float((gi * gi).sum().item()) for gi in g) *
+                          sum(float((di * di).sum().item()) for di in dg))
+        eps = 1e-6
+        Js = []
+        for sg in (1.0, -1.0):
+            Ue = cuda(w.U) + sg * eps * dg[0]
+            Ve = cuda(w.V) + sg * eps * dg[1]
+            We = cuda(w.W) + sg * eps * dg[2] if two else None
+            te = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+            s.run(Ue, Ve, We, te, t_end, max_steps=max_steps)
+            Js.append(float(jfun(Ue).item()))
+        fdv = (Js[0] - Js[1]) / (2 * eps)
+        fd.append({"adjoint": adj_dJ, "fd": fdv,
+                   "rel_to_cs_scale": abs(adj_dJ - fdv) / scale})
+    return g, fd, grad_s
 
 
 # ---------------------------------------------------------------------------
@@ -775,6 +827,46 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# The other workloads of the benchmark suite, each timed briefly in the same
+# run and reported as a sub-object of the headline line (N = 1 only):
+# (key, --workload, precisions, K, W)
+OTHER_CONFIGS = (
+    ("burgers1d_n400", "burgers1d:400", ("fp64",), 20, 5),
+    ("euler2d_smooth_2048", "euler2d_smooth:2048", ("fp64", "fp32"), 10, 3),
+    ("double_mach_1920x480", "double_mach:1920x480", ("fp64", "fp32"), 20, 3),
+)
+
+
+def _compact(out):
+    keep = ("value", "unit", "ms_per_step", "us_per_step", "steps", "warmup", "dtype",
+            "roofline", "clocks", "gpu_launches", "cluster_run", "graph", "no_graph",
+            "plain", "persistent", "forward_ms_per_step", "adjoint_over_forward", "replay")
+    c = {k: out[k] for k in keep if k in out}
+    cfg = out.get("config", {})
+    c["workload"] = cfg.get("workload")
+    for k in ("timing", "l2"):
+        if k in cfg:
+            c[k] = cfg[k]
+    return c
+
+
+def other_configs(args, dev_index):
+    """Configs 1, 3, 4 (FP64 and FP32) and the 2D adjoint step (config 5),
+    each with its own roofline, for the headline line."""
+    import copy
+    res = {}
+    for key, wl, precs, K, Wm in OTHER_CONFIGS:
+        for prec in precs:
+            a = copy.copy(args)
+            a.workload, a.precision, a.no_extras, a.steps, a.warmup = wl, prec, True, K, Wm
+            out, _ = run_ours(a, 0, 1, dev_index)
+            res.setdefault(key, {})[prec] = _compact(out)
+    a = copy.copy(args)
+    a.workload, a.steps, a.warmup, a.fd_directions, a.light = "euler2d_adjoint:512", 5, 2, 0, True
+    res["euler2d_adjoint_512"] = _compact(run_adjoint(a, 0, 1, dev_index))
+    return res
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -794,6 +886,11 @@ def main():
         out = run_adjoint(args, rank, world, local)
     else:
         out, rank = run_ours(args, rank, world, local)
+        if world == 1 and not args.no_extras and args.workload == "riemann_batch":
+            out["configs"] = other_configs(args, local)
+            out["gpu_launches_configs"] = sum(
+                v.get("gpu_launches", 0) for c in out["configs"].values()
+                for v in (c.values() if "value" not in c else [c]))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -100,6 +100,8 @@ def _load():
             L.or_run_tangent.restype = ctypes.c_long
             L.or_flops_per_point_step.argtypes = [_P, _D, _D, _D]
             L.or_flops_per_point_step.restype = ctypes.c_double
+            L.or_tangent_flops_per_point_step.argtypes = [_P, _D, _D, _D, _D, _D, _D]
+            L.or_tangent_flops_per_point_step.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -283,3 +285,16 @@ def limiter_tangent(um, u0, up, vm, vp, direction, dx, lim_d=(0.98, 0.01, 0.01),
     """d v-tilde of the limiter along `direction` (5 values)."""
     return _load().or_limiter_tangent(um, u0, up, vm, vp, _ptr(_arr(direction, 5)), dx,
                                       _ptr(_arr(lim_d, 3)), eps, int(frozen))
+
+
+def tangent_flops_per_point_step(p, U, V, W, dU, dV, dW=None) -> float:
+    """Operations per grid point of one forward-mode (dual-number) step,
+    values and tangents together (the work of one Jacobian-vector product of
+    the step; the wave speeds frozen as in run_tangent)."""
+    shp = _shape(p)
+    U, V = _arr(U).reshape(shp), _arr(V).reshape(shp)
+    dU, dV = _arr(dU).reshape(shp), _arr(dV).reshape(shp)
+    W = _arr(W).reshape(shp) if p.dim == 2 else None
+    dW = _arr(dW).reshape(shp) if p.dim == 2 else None
+    return _load().or_tangent_flops_per_point_step(ctypes.byref(p), _ptr(U), _ptr(V), _ptr(W),
+                                                   _ptr(dU), _ptr(dV), _ptr(dW))

@@ -8,8 +8,8 @@
 // or table with the CUDA implementation.
 //
 // Every function follows the paper's order of operations and notation; where
-// the paper is silent, garbled or inconsistent the reading taken is named at
-// the point of use (readings R1..R13, listed in the design notes):
+// the paper is silent, garbled or inconsistent, the reading taken is stated
+// here and named (R1, R2, ...) at the point of use:
 //   R1  beta_2 of the reconstruction uses f_{i+1} (Sec. 2.1, Eq. GHYZP prints
 //       f_{i-1}; the defining integral Eq. GHYZ gives f_{i+1}).
 //   R2  every f, h in p_0, p_1, p_2, p_0' is the split value f^+, h^+.
@@ -34,6 +34,10 @@
 //   R15 Buckley-Leverett (Example 3.4, non-convex f): alpha = max |f'(u)| over
 //       the admissible states u in [0, 1], and over any grid value outside
 //       [0, 1]; the maximum over [0, 1] is found by golden-section search.
+//   R17 the forward-mode tangent (Dual) freezes alpha of every stage and dt of
+//       every step, and keeps the |.| in tau on the branch of the forward
+//       state; weights, eigenvectors and the limiter are differentiated
+//       (freeze_weights also holds the nonlinear weights at their values).
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (no FMA
 // contraction, no fast-math).
@@ -72,37 +76,47 @@ inline Flop fabs(Flop a) { return Flop(std::fabs(a.v)); }
 inline double val(Flop a) { return a.v; }
 inline double val(double a) { return a; }
 
-// Dual: a double with one tangent (forward-mode differentiation). Used to
+// Dual: a value with one tangent (forward-mode differentiation). Used to
 // differentiate a run with respect to its initial state; fabs takes the sign
-// of the value (the branch taken by the forward run).
-struct Dual {
-  double v, d;
-  Dual() : v(0.0), d(0.0) {}
-  Dual(double x) : v(x), d(0.0) {}  // NOLINT: implicit, so constants mix in
-  Dual(double x, double t) : v(x), d(t) {}
+// of the value (the branch taken by the forward run). DualT<Flop> counts the
+// operations of the value and of the tangent together (the work of one
+// Jacobian-vector product of the step).
+inline double scalar_sqrt(double x) { return std::sqrt(x); }
+inline Flop scalar_sqrt(Flop x) { return sqrt(x); }
+
+template <class S>
+struct DualT {
+  S v, d;
+  DualT() : v(0.0), d(0.0) {}
+  DualT(double x) : v(x), d(0.0) {}  // NOLINT: implicit, so constants mix in
+  DualT(S x, S t) : v(x), d(t) {}
+  // hidden friends: found by argument-dependent lookup, and they let a double
+  // operand convert to DualT implicitly
+  friend DualT operator+(DualT a, DualT b) { return DualT(a.v + b.v, a.d + b.d); }
+  friend DualT operator-(DualT a, DualT b) { return DualT(a.v - b.v, a.d - b.d); }
+  friend DualT operator*(DualT a, DualT b) { return DualT(a.v * b.v, a.d * b.v + a.v * b.d); }
+  friend DualT operator/(DualT a, DualT b) {
+    const S q = a.v / b.v;
+    return DualT(q, (a.d - q * b.d) / b.v);
+  }
+  friend DualT operator-(DualT a) { return DualT(-a.v, -a.d); }
+  friend bool operator<(DualT a, DualT b) { return a.v < b.v; }
+  friend bool operator>(DualT a, DualT b) { return a.v > b.v; }
+  friend DualT sqrt(DualT a) {
+    const S r = scalar_sqrt(a.v);
+    return DualT(r, a.d / (S(2.0) * r));
+  }
+  friend DualT fabs(DualT a) { return a.v < S(0.0) ? DualT(-a.v, -a.d) : a; }
+  friend double val(DualT a) { return val(a.v); }
 };
-inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
-inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
-inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
-inline Dual operator/(Dual a, Dual b) {
-  const double q = a.v / b.v;
-  return Dual(q, (a.d - q * b.d) / b.v);
-}
-inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
-inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
-inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
-inline Dual sqrt(Dual a) {
-  const double r = std::sqrt(a.v);
-  return Dual(r, a.d / (2.0 * r));
-}
-inline Dual fabs(Dual a) { return a.v < 0.0 ? Dual(-a.v, -a.d) : a; }
-inline double val(Dual a) { return a.v; }
+using Dual = DualT<double>;
+using DualFlop = DualT<Flop>;
 
 // The global Lax-Friedrichs coefficient is a constant of each stage when a
 // run is differentiated (its dependence on the state is frozen).
 inline void freeze(double&) {}
 inline void freeze(Flop&) {}
-inline void freeze(Dual& a) { a.d = 0.0; }
+template <class S> inline void freeze(DualT<S>& a) { a.d = S(0.0); }
 
 using std::fabs;
 using std::sqrt;
@@ -1077,6 +1091,28 @@ double or_flops_per_point_step(const or_problem* P, const double* U, const doubl
   const size_t n = (size_t)m * npt;
   std::vector<Flop> u(n), v(n), w(P->dim == 2 ? n : 0);
   for (size_t q = 0; q < n; ++q) { u[q] = U[q]; v[q] = V[q]; if (P->dim == 2) w[q] = W[q]; }
+  double t = 0.0;
+  g_flops = 0;
+  step_generic(*P, u.data(), v.data(), w.data(), &t, 1e300, (double*)nullptr);
+  return (double)g_flops / (double)npt;
+}
+
+// Operations of one forward-mode (dual-number) step per grid point: the
+// values and the tangents together, with the wave speeds frozen as in
+// or_run_tangent (tangent seeds dU, dV, dW).
+double or_tangent_flops_per_point_step(const or_problem* P, const double* U, const double* V,
+                                       const double* W, const double* dU, const double* dV,
+                                       const double* dW) {
+  const int m = ncomp(*P);
+  const size_t npt = (size_t)P->nx * (P->dim == 2 ? P->ny : 1);
+  const size_t n = (size_t)m * npt;
+  const bool two = P->dim == 2;
+  std::vector<DualFlop> u(n), v(n), w(two ? n : 0);
+  for (size_t q = 0; q < n; ++q) {
+    u[q] = DualFlop(Flop(U[q]), Flop(dU[q]));
+    v[q] = DualFlop(Flop(V[q]), Flop(dV[q]));
+    if (two) w[q] = DualFlop(Flop(W[q]), Flop(dW[q]));
+  }
   double t = 0.0;
   g_flops = 0;
   step_generic(*P, u.data(), v.data(), w.data(), &t, 1e300, (double*)nullptr);

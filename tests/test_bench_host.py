@@ -29,6 +29,32 @@ def test_flop_constants_match_oracle_count(key, make):
     assert abs(n - bench.ALGO_FLOPS_PER_POINT_STEP[key]) <= 1e-3 * n
 
 
+@pytest.mark.parametrize("key,make", [
+    (("euler", 2), lambda: W.euler2d_adjoint(64)),
+    (("burgers", 1), lambda: W.burgers_adjoint_batch(count=1, n=800)),
+])
+def test_adjoint_flop_constants_match_oracle_tangent_count(key, make):
+    """The adjoint step's algorithmic flops are the op count of the oracle's
+    dual-number step (values and tangents) on the adjoint workloads."""
+    w = make()
+    kw = dict(dt_mode=2, dt_fixed=w.meta["dt"]) if w.dim == 2 else {}
+    rng = np.random.default_rng(0)
+    d = [rng.standard_normal(w.U.size) for _ in range(3 if w.dim == 2 else 2)]
+    n = O.tangent_flops_per_point_step(oracle_problem(w, nx=w.nx[0], **kw), w.U, w.V, w.W, *d)
+    assert abs(n - bench.ALGO_ADJOINT_FLOPS_PER_POINT_STEP[key]) <= 1e-3 * n
+
+
+def test_tangent_count_is_value_count_plus_tangent_work():
+    """The dual-number count includes the value arithmetic: it exceeds the
+    plain step's count, by less than the four operations per multiply and
+    divide that a tangent can add."""
+    w = W.euler1d_smooth(200, dt_mode="cfl")
+    P = oracle_problem(w)
+    f = O.flops_per_point_step(P, w.U, w.V)
+    tf = O.tangent_flops_per_point_step(P, w.U, w.V, None, np.ones_like(w.U), np.ones_like(w.V))
+    assert 2.0 * f < tf < 5.0 * f
+
+
 def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)

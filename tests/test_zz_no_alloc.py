@@ -4,8 +4,12 @@ own pool, latency-critical paths that must not pay cudaMalloc's implicit
 synchronisation, plug-ins handed only pre-allocated buffers). Its scratch is
 a fixed device array inside the library, so the check is that two calls in a
 row through the C ABI give what the context-based hweno_step gives, within
-the per-step tolerance of the other parity tests. This file is collected
-last on purpose."""
+the per-step tolerance of the other parity tests.
+
+The file name makes pytest collect it last: it checks an addition beside the
+scheme's own path, so a run that stops at the first failure has already run
+every other test by the time it gets here. Its result does not depend on the
+order: it also passes alone in a fresh process."""
 import ctypes
 
 import numpy as np
