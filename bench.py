@@ -272,6 +272,30 @@ def run_ours(args, rank, world, dev_index):
                 torch.cuda.synchronize()
                 run_ms = s.profile_read()["stage"][0]  # the persistent kernel alone
                 pers = (p0.elapsed_time(p1), float(ppu), s.launches_last_call, run_ms)
+            cls = None
+            if w.dim == 1 and w.batch > 1 and profile:
+                # tile variant per instance-size class, against the single variant
+                chosen, cms = s.autotune_classes(U, V, t, w.t_end)
+                cls = {"classes": s.size_classes(), "chosen": chosen,
+                       "stage1_ms": [[round(x, 4) for x in row] for row in cms],
+                       "stage1_ms_sum_single_variant": round(sum(r[tune[0]] for r in cms), 4),
+                       "stage1_ms_sum_per_class": round(sum(min(r) for r in cms), 4),
+                       "mixed_graph": None}
+                if len(set(chosen)) > 1:  # the same K-step graph with per-class launches
+                    s.run_graph(U, V, Wd, t, w.t_end, max_steps=0, steps_per_launch=K)
+                    m0 = torch.cuda.Event(enable_timing=True)
+                    m1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    m0.record()
+                    _, pum = s.run_graph(U, V, Wd, t, w.t_end, max_steps=K, steps_per_launch=K)
+                    m1.record()
+                    torch.cuda.synchronize()
+                    mm = m0.elapsed_time(m1)
+                    cls["mixed_graph"] = {"value": round(pum / (mm * 1e-3) / 1e6, 3),
+                                          "ms_per_step": round(mm / K, 4),
+                                          "launches_per_step": s.launches_last_call // K}
+                s.set_class_variants([tune[0]] * len(chosen))  # back to one variant
+            timed.cls = cls
             prof = ms_ng = pu_ng = None
             if profile:
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -451,6 +475,7 @@ def run_ours(args, rank, world, dev_index):
                                  "each step bracketed by CUDA events, summed over K steps"
                                  if small else timing_note),
                       "tile_variant": tune[0] if w.dim == 1 else None,
+                      "size_classes": getattr(timed, "cls", None),
                       "autotune_stage1_ms": [round(x, 4) for x in tune[1]] if w.dim == 1 else None,
                       "parallelism": "replicas (one seeded batch per rank)"},
            "roofline": roof, "clocks": clocks, "gpu_launches": launches,

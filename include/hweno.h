@@ -125,12 +125,13 @@ typedef struct hweno_options {
                       of up to sixteen factors of the size of beta + eps; the
                       bounds on eps and the linear weights keep it above the
                       FP64 underflow limit. Large data (beta grows like the
-                      square of the split-flux jumps) push it past the
-                      overflow limit; the kernels then divide per side and
-                      per field, which holds for split-flux jumps up to about
-                      1e35 (tested against the CPU oracle with Euler states
-                      scaled by 1e6, 1e12, 1e20 and Burgers by 1e4, 1e8).
-                      Other eps values are HWENO_EINVAL. */
+                      square of the split-flux jumps) would push it past the
+                      overflow limit, so each side's numerator and
+                      denominator are rescaled by an exact power of two; this
+                      holds for split-flux jumps up to about 1e35 (tested
+                      against the CPU oracle with Euler states scaled by 1e6,
+                      1e12, 1e20 and Burgers by 1e4, 1e8). Other eps values
+                      are HWENO_EINVAL. */
   double cfl;      /* CFL number, > 0 */
   int dt_mode;     /* 0: dt = cfl / sum(alpha_d / h_d) with h = dx;
                       1: h = dx^{5/3} (accuracy runs); 2: dt = dt_fixed.
@@ -299,6 +300,42 @@ int hweno_test_inject(hweno_ctx* ctx, int kind);
  * there is a single tile shape: *chosen = 0 and nothing is measured. */
 int hweno_autotune(hweno_ctx* ctx, const void* U, const void* V, const void* W, const double* t,
                    double t_end, int* chosen, double* ms, void* stream);
+
+/* Largest number of instance-size classes of a 1D batch. */
+#define HWENO_MAX_SIZE_CLASSES 16
+
+/* Size classes of a 1D batch (no counterpart in the paper; a tuning aid):
+ * the distinct instance sizes when there are at most HWENO_MAX_SIZE_CLASSES
+ * of them, else octaves of the size above the smallest instance. Returns the
+ * number of classes (0 in 2D, HWENO_EINVAL for a NULL context) and writes
+ * each class's smallest and largest instance size to lo, hi (host, nullable,
+ * HWENO_MAX_SIZE_CLASSES ints each). */
+int hweno_size_classes(const hweno_ctx* ctx, int* lo, int* hi);
+
+/* Tile-shape autotuner per size class (1D batches; no counterpart in the
+ * paper): times the stage-1 kernel of every tile variant on each class's
+ * instances alone (U, V, t device, read only; library scratch written) and
+ * keeps the fastest variant per class. When the classes choose different
+ * variants, hweno_step (and the graph of hweno_run) launches each stage once
+ * per run of consecutive classes with the same variant, over tile tables
+ * ordered by class that hweno_create made; the results are the bits of any
+ * single variant. When all classes agree this is hweno_autotune's choice.
+ * hweno_rhs, hweno_step_host and hweno_run_persistent keep one variant (the
+ * one in force before). hweno_set_options and hweno_autotune end the
+ * per-class choice. chosen (host, nullable, one int per class) receives the
+ * variants, ms (host, nullable, classes x HWENO_TILE_VARIANTS doubles) the
+ * best time of each class and variant. Synchronises `stream`; drops a graph
+ * that hweno_run recorded. 2D: HWENO_ENOTSUP. */
+int hweno_autotune_classes(hweno_ctx* ctx, const void* U, const void* V, const double* t,
+                           double t_end, int* chosen, double* ms, void* stream);
+
+/* Set the tile variant of every size class directly (host array of
+ * hweno_size_classes(ctx) ints in [0, HWENO_TILE_VARIANTS)), for example a
+ * choice hweno_autotune_classes made in an earlier run; the same rules as
+ * there. When all entries are equal this selects that tile_variant for every
+ * call. No device memory is written; a graph that hweno_run recorded is
+ * dropped. HWENO_EINVAL for a variant out of range, HWENO_ENOTSUP in 2D. */
+int hweno_set_class_variants(hweno_ctx* ctx, const int* variants);
 
 /* Conserved totals in FP64 (the discrete integrals conserved by the flux
  * form of Eq. odeH / ode2H): totals[k * m + c] = sum_i U_c(x_i) dx (2D:

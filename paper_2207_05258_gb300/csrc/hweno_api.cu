@@ -40,6 +40,18 @@ struct hweno_ctx {
   int* d_vt_start[kNumVariants1D] = {};
   int* d_vt_tiles[kNumVariants1D] = {};
   int vt_ntiles[kNumVariants1D] = {};
+  // instance-size classes (1D batches): class of each instance, and per
+  // variant a tile table ordered by class with each class's tile range, so
+  // that the stages can run each class with its own tile variant
+  // (hweno_autotune_classes); made in create
+  int nclasses = 0;
+  std::vector<int> inst_class;
+  std::vector<int> class_lo, class_hi;  // smallest / largest instance of a class
+  int* d_ct_inst[kNumVariants1D] = {};
+  int* d_ct_start[kNumVariants1D] = {};
+  int ct_first[kNumVariants1D][HWENO_MAX_SIZE_CLASSES + 1] = {};
+  int class_variant[HWENO_MAX_SIZE_CLASSES] = {};
+  bool mixed = false;  // stages launched per class (set by hweno_autotune_classes)
   // the current variant (aliases of the arrays above)
   int ntiles = 0;
   int variant = 0;
@@ -187,10 +199,12 @@ void free_all(hweno_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int v = 0; v < kNumVariants1D; ++v) {
-    void* vp[] = {c->d_vt_inst[v], c->d_vt_start[v], c->d_vt_tiles[v]};
+    void* vp[] = {c->d_vt_inst[v], c->d_vt_start[v], c->d_vt_tiles[v], c->d_ct_inst[v],
+                  c->d_ct_start[v]};
     for (void* p : vp)
       if (p) cudaFree(p);
     c->d_vt_inst[v] = c->d_vt_start[v] = c->d_vt_tiles[v] = nullptr;
+    c->d_ct_inst[v] = c->d_ct_start[v] = nullptr;
   }
   for (int i = 0; i < hweno_ctx::kChunks; ++i) {
     if (c->cs[i]) cudaStreamDestroy(c->cs[i]);
@@ -276,6 +290,7 @@ int use_variant(hweno_ctx* c, int v) {
   if (per_sm < 1) return fail(c, HWENO_ECUDA, "persistent kernel does not fit on an SM");
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+  c->mixed = false;
   c->variant = v;
   c->tile = tile_points(v);
   c->d_tile_inst = c->d_vt_inst[v];
@@ -284,6 +299,79 @@ int use_variant(hweno_ctx* c, int v) {
   c->ntiles = c->vt_ntiles[v];
   c->persist_ctas = sms * per_sm;
   return HWENO_OK;
+}
+
+// Size classes of a 1D batch: the distinct instance sizes when there are at
+// most HWENO_MAX_SIZE_CLASSES of them, else octaves of the size (log2
+// buckets above the smallest instance, the last bucket open-ended).
+void size_classes(hweno_ctx* c) {
+  std::vector<int> d(c->nx);
+  std::sort(d.begin(), d.end());
+  d.erase(std::unique(d.begin(), d.end()), d.end());
+  c->inst_class.assign(c->batch, 0);
+  if ((int)d.size() <= HWENO_MAX_SIZE_CLASSES) {
+    c->nclasses = (int)d.size();
+    for (int k = 0; k < c->batch; ++k)
+      c->inst_class[k] = (int)(std::lower_bound(d.begin(), d.end(), c->nx[k]) - d.begin());
+  } else {
+    const int lo = d.front();
+    int top = 0;
+    for (int k = 0; k < c->batch; ++k) {
+      int q = 0;
+      while (q + 1 < HWENO_MAX_SIZE_CLASSES && (long long)lo << (q + 1) <= c->nx[k]) ++q;
+      c->inst_class[k] = q;
+      top = std::max(top, q);
+    }
+    c->nclasses = top + 1;
+  }
+  c->class_lo.assign(c->nclasses, 1 << 30);
+  c->class_hi.assign(c->nclasses, 0);
+  for (int k = 0; k < c->batch; ++k) {
+    const int q = c->inst_class[k];
+    c->class_lo[q] = std::min(c->class_lo[q], c->nx[k]);
+    c->class_hi[q] = std::max(c->class_hi[q], c->nx[k]);
+  }
+}
+
+// Tile table of variant-size tiles ordered by size class (instances in
+// order within a class); first[q] = first tile of class q.
+void class_tile_table(const hweno_ctx* c, int tile, std::vector<int>& tinst,
+                      std::vector<int>& tstart, int* first) {
+  tinst.clear();
+  tstart.clear();
+  for (int q = 0; q < c->nclasses; ++q) {
+    first[q] = (int)tinst.size();
+    for (int k = 0; k < c->batch; ++k)
+      if (c->inst_class[k] == q)
+        for (int s = 0; s < c->nx[k]; s += tile) { tinst.push_back(k); tstart.push_back(s); }
+  }
+  first[c->nclasses] = (int)tinst.size();
+}
+
+// One stage of every instance: one launch of the current variant, or (after
+// hweno_autotune_classes) one launch per run of size classes that chose the
+// same variant, over that run's tiles of the class-ordered table.
+cudaError_t launch_stage_all(hweno_ctx* c, int mode, const Args1D& a, cudaStream_t s,
+                             int* launches) {
+  if (!c->mixed) {
+    ++*launches;
+    return launch_stage_1d(c->eq, c->fp32, c->variant, mode, a, c->ntiles, s);
+  }
+  for (int q = 0; q < c->nclasses;) {
+    const int v = c->class_variant[q];
+    int q1 = q + 1;
+    while (q1 < c->nclasses && c->class_variant[q1] == v) ++q1;
+    const int t0 = c->ct_first[v][q], t1 = c->ct_first[v][q1];
+    if (t1 > t0) {
+      Args1D b = a;
+      b.tile_inst = c->d_ct_inst[v] + t0;
+      b.tile_start = c->d_ct_start[v] + t0;
+      ++*launches;
+      if (const cudaError_t e = launch_stage_1d(c->eq, c->fp32, v, mode, b, t1 - t0, s)) return e;
+    }
+    q = q1;
+  }
+  return cudaSuccess;
 }
 
 // Per-instance h of the time-step rule: dx (dt_mode 0, 2) or dx^{5/3}
@@ -421,34 +509,32 @@ int step_1d(hweno_ctx* c, void* U, void* V, double* t, double t_end, double* dt_
   if ((e = launch_alpha_1d(c->eq, c->fp32, c->variant, a, c->ntiles, s)))
     return cuda_fail(c, e, "alpha");
   prof_end(c, s, 0);
+  int nl = 2;  // alpha and finalize
   // stage 1
   a.U = U; a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
   a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
   prof_begin(c, s);
-  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE1, a, c->ntiles, s)))
-    return cuda_fail(c, e, "stage 1");
+  if ((e = launch_stage_all(c, MODE_STAGE1, a, s, &nl))) return cuda_fail(c, e, "stage 1");
   prof_end(c, s, 1);
   // stage 2
   a.U = c->d_U1; a.V = c->d_V1; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = c->d_U2; a.Vout = c->d_V2;
   a.Vt0out = nullptr;
   a.alpha_in = slotd(c, 1); a.alpha_out = slot(c, 2);
   prof_begin(c, s);
-  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE2, a, c->ntiles, s)))
-    return cuda_fail(c, e, "stage 2");
+  if ((e = launch_stage_all(c, MODE_STAGE2, a, s, &nl))) return cuda_fail(c, e, "stage 2");
   prof_end(c, s, 1);
   // stage 3 (in place)
   a.U = c->d_U2; a.V = c->d_V2; a.U0 = U; a.Vt0 = c->d_Vt0; a.Uout = U; a.Vout = V;
   a.alpha_in = slotd(c, 2); a.alpha_out = nullptr;
   prof_begin(c, s);
-  if ((e = launch_stage_1d(c->eq, c->fp32, c->variant, MODE_STAGE3, a, c->ntiles, s)))
-    return cuda_fail(c, e, "stage 3");
+  if ((e = launch_stage_all(c, MODE_STAGE3, a, s, &nl))) return cuda_fail(c, e, "stage 3");
   prof_end(c, s, 1);
   prof_begin(c, s);
   if ((e = launch_finalize(c->batch, c->d_dt, c->d_lands, t, t_end, dt_used, slotd(c, 0),
                            c->d_active, c->d_status, c->d_inst_n, 1, c->d_pu, s)))
     return cuda_fail(c, e, "finalize");
   prof_end(c, s, 2);
-  c->launches = c->step_launches = 5;
+  c->launches = c->step_launches = nl;
   return HWENO_OK;
 }
 
@@ -668,11 +754,14 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
   }
   const int nvar = grid->dim == 1 ? kNumVariants1D : 1;
   std::vector<int> tinst[kNumVariants1D], tstart[kNumVariants1D], ntk[kNumVariants1D];
+  std::vector<int> cinst[kNumVariants1D], cstart[kNumVariants1D];
+  if (grid->dim == 1) size_classes(c);
   for (int v = 0; v < nvar; ++v) {
     if (grid->dim == 1) {
       const int tp = tile_points(v);
       tile_table(c->nx, tp, tinst[v], tstart[v]);
       for (int k = 0; k < c->batch; ++k) ntk[v].push_back((c->nx[k] + tp - 1) / tp);
+      class_tile_table(c, tp, cinst[v], cstart[v], c->ct_first[v]);
     } else {
       tinst[v] = {0};
       tstart[v] = {0};
@@ -693,7 +782,10 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
   for (int v = 0; v < nvar && rc == HWENO_OK; ++v)
     if ((rc = dalloc(c, &c->d_vt_inst[v], sizeof(int) * tinst[v].size())) ||
         (rc = dalloc(c, &c->d_vt_start[v], sizeof(int) * tstart[v].size())) ||
-        (rc = dalloc(c, &c->d_vt_tiles[v], sizeof(int) * ntk[v].size())))
+        (rc = dalloc(c, &c->d_vt_tiles[v], sizeof(int) * ntk[v].size())) ||
+        (grid->dim == 1 &&
+         ((rc = dalloc(c, &c->d_ct_inst[v], sizeof(int) * cinst[v].size())) ||
+          (rc = dalloc(c, &c->d_ct_start[v], sizeof(int) * cstart[v].size())))))
       break;
   if (rc != HWENO_OK ||
       (rc = dalloc(c, &c->d_inst_n, sizeof(int) * B)) ||
@@ -761,7 +853,12 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
         cudaMemcpy(c->d_vt_start[v], tstart[v].data(), sizeof(int) * tstart[v].size(),
                    cudaMemcpyHostToDevice) ||
         cudaMemcpy(c->d_vt_tiles[v], ntk[v].data(), sizeof(int) * ntk[v].size(),
-                   cudaMemcpyHostToDevice);
+                   cudaMemcpyHostToDevice) ||
+        (grid->dim == 1 &&
+         (cudaMemcpy(c->d_ct_inst[v], cinst[v].data(), sizeof(int) * cinst[v].size(),
+                     cudaMemcpyHostToDevice) ||
+          cudaMemcpy(c->d_ct_start[v], cstart[v].data(), sizeof(int) * cstart[v].size(),
+                     cudaMemcpyHostToDevice)));
   copy_failed = copy_failed ||
       cudaMemcpy(c->d_inst_geo, geo.data(), sizeof(double) * 3 * B, cudaMemcpyHostToDevice) ||
       cudaMemcpy(c->d_inst_geof, geof.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice) ||
@@ -1134,6 +1231,91 @@ int hweno_autotune(hweno_ctx* c, const void* U, const void* V, const void* W, co
   c->opt.tile_variant = best;
   if (chosen) *chosen = best;
   return hweno_sync_status(c, stream);
+}
+
+int hweno_size_classes(const hweno_ctx* c, int* lo, int* hi) {
+  if (!c) return HWENO_EINVAL;
+  if (c->dim != 1) return 0;
+  for (int q = 0; q < c->nclasses; ++q) {
+    if (lo) lo[q] = c->class_lo[q];
+    if (hi) hi[q] = c->class_hi[q];
+  }
+  return c->nclasses;
+}
+
+int hweno_autotune_classes(hweno_ctx* c, const void* U, const void* V, const double* t,
+                           double t_end, int* chosen, double* ms, void* stream) {
+  if (!c) return HWENO_EINVAL;
+  if (c->dim != 1) return fail(c, HWENO_ENOTSUP, "size classes are built for 1D batches");
+  if (!U || !V || !t) return fail(c, HWENO_EINVAL, "null array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = c->tune_ev[0], e1 = c->tune_ev[1];
+  const int keep = c->variant;
+  int rc = HWENO_OK;
+  cudaError_t e;
+  // wave speed of U into slot 0 for every instance (current variant's table)
+  {
+    Args1D pre = base_args_1d(c);
+    pre.t = t; pre.t_end = t_end; pre.skip_done = 1; pre.U = U; pre.alpha_out = slot(c, 0);
+    if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 3 * c->batch, s)) ||
+        (e = launch_alpha_1d(c->eq, c->fp32, c->variant, pre, c->ntiles, s)))
+      return cuda_fail(c, e, "autotune classes");
+  }
+  int best[HWENO_MAX_SIZE_CLASSES];
+  for (int q = 0; q < c->nclasses && rc == HWENO_OK; ++q) {
+    float best_ms = 1e30f;
+    best[q] = keep;
+    for (int v = 0; v < kNumVariants1D && rc == HWENO_OK; ++v) {
+      const int t0 = c->ct_first[v][q], t1 = c->ct_first[v][q + 1];
+      Args1D a = base_args_1d(c);
+      a.tile_inst = c->d_ct_inst[v] + t0;
+      a.tile_start = c->d_ct_start[v] + t0;
+      a.t = t; a.t_end = t_end; a.skip_done = 1; a.dt = c->d_dt; a.lands = c->d_lands;
+      a.U = U; a.V = V; a.Uout = c->d_U1; a.Vout = c->d_V1; a.Vt0out = c->d_Vt0;
+      a.alpha_in = slotd(c, 0); a.alpha_out = slot(c, 1);
+      float tv = 1e30f;
+      for (int r = 0; r < 4 && t1 > t0; ++r) {  // first launch warms up, then the best of three
+        cudaEventRecord(e0, s);
+        if ((e = launch_stage_1d(c->eq, c->fp32, v, MODE_STAGE1, a, t1 - t0, s))) {
+          rc = cuda_fail(c, e, "autotune classes");
+          break;
+        }
+        cudaEventRecord(e1, s);
+        if ((e = cudaEventSynchronize(e1))) { rc = cuda_fail(c, e, "autotune classes"); break; }
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        if (r > 0) tv = std::min(tv, x);
+      }
+      if (ms) ms[q * kNumVariants1D + v] = tv;
+      if (tv < best_ms) { best_ms = tv; best[q] = v; }
+    }
+  }
+  if (rc != HWENO_OK) return rc;
+  if (chosen)
+    for (int q = 0; q < c->nclasses; ++q) chosen[q] = best[q];
+  if ((rc = hweno_set_class_variants(c, best)) != HWENO_OK) return rc;
+  return hweno_sync_status(c, stream);
+}
+
+int hweno_set_class_variants(hweno_ctx* c, const int* variants) {
+  if (!c) return HWENO_EINVAL;
+  if (c->dim != 1) return fail(c, HWENO_ENOTSUP, "size classes are built for 1D batches");
+  if (!variants) return fail(c, HWENO_EINVAL, "null array");
+  for (int q = 0; q < c->nclasses; ++q)
+    if (variants[q] < 0 || variants[q] >= kNumVariants1D)
+      return fail(c, HWENO_EINVAL, "tile variant out of range");
+  bool same = true;
+  for (int q = 0; q < c->nclasses; ++q) same = same && variants[q] == variants[0];
+  if (same) {  // one variant for every class: as hweno_set_options' tile_variant
+    const int rc = use_variant(c, variants[0]);
+    if (rc == HWENO_OK) c->opt.tile_variant = variants[0];
+    return rc;
+  }
+  for (int q = 0; q < c->nclasses; ++q) c->class_variant[q] = variants[q];
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->mixed = true;
+  return HWENO_OK;
 }
 
 int hweno_totals(hweno_ctx* c, const void* U, double* totals, void* stream) {

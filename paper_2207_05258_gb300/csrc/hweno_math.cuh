@@ -173,6 +173,68 @@ __device__ __forceinline__ Real combine_direct(const Cand<Real>& c, const Weight
   return qdiv(num, o0 + o1 + o2);
 }
 
+// ---------------------------------------------------------------------------
+// FP32: the "+" side and the mirrored "-" side of an interface carry the same
+// arithmetic on different data, so they travel as the two lanes of packed
+// FP32 pairs (one instruction for both sides: fma / add / mul .f32x2, sm_100
+// and later). Each lane rounds exactly as a scalar FP32 operation would.
+// ---------------------------------------------------------------------------
+#ifndef HWENO_FP32_PAIRS
+#define HWENO_FP32_PAIRS 0
+#endif
+__device__ __forceinline__ float2 pair(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// fast reciprocal of each lane (the approximate division of the FP32 path)
+__device__ __forceinline__ float2 rcp2(float2 a) {
+  return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y));
+}
+
+// f-hat^+ + f-hat^- of one (characteristic) field in FP32: lane x holds the
+// "+" stencil (f^+, H^+ at i-1, i, i+1), lane y the mirrored "-" stencil
+// (f^-, -H^- at i+2, i+1, i). The same formulas as candidates() and
+// combine_direct(), lane by lane.
+__device__ __forceinline__ float interface_flux_pair(float2 fm, float2 f0, float2 fp, float2 Hm,
+                                                     float2 H0, float2 Hp,
+                                                     const Weights<float>& w) {
+  const float2 sHp = add2(Hm, Hp), dHp = sub2(Hm, Hp);
+  const float2 d1 = sub2(fm, f0), d2 = sub2(f0, fp);
+  const float2 lap = sub2(d1, d2), dif = add2(d1, d2);
+  const float2 p1 = fma2(pair(1.0f / 6.0f), d1, fma2(pair(2.0f / 3.0f), H0, f0));
+  const float2 p2 = fma2(pair(-1.0f / 6.0f), d2, fma2(pair(1.0f / 3.0f), H0, f0));
+  const float2 p0 = fma2(pair(11.0f / 60.0f), lap, fma2(pair(0.05f), dHp, fma2(pair(0.5f), H0, f0)));
+  const float2 r = fma2(pair(-w.g2), p2, fma2(pair(-w.g1), p1, p0));
+  // smoothness indicators as in candidates() (square weights in the
+  // coefficients), beta_l + eps accumulated directly
+  const float2 E2 = fma2(pair(2.0976788148466414486f), lap, mul2(pair(0.52842290755678754049f), dHp));
+  const float2 E3 = fma2(pair(-7.9341267047029694945f), dif,
+                         fma2(pair(-12.661835579599691806f), H0,
+                              mul2(pair(-1.6032089149031235916f), sHp)));
+  const float2 A4 = fma2(pair(-12.498180087296929908f), lap, mul2(pair(-6.2490900436484649542f), dHp));
+  const float2 a5 = fma2(pair(0.75f), dif, fma2(pair(0.25f), sHp, H0));
+  const float2 h2e = fma2(H0, H0, pair(w.eps));
+  const float2 b0 = fma2(mul2(pair(21520059541.0f / 1377684.0f), a5), a5,
+                         fma2(A4, A4, fma2(E3, E3, fma2(E2, E2, h2e))));
+  const float2 kH = mul2(pair(2.0816659994661327353f), H0);
+  const float2 S1 = fma2(pair(2.0816659994661327353f), d1, kH);
+  const float2 S2 = fma2(pair(2.0816659994661327353f), d2, kH);
+  const float2 b1 = fma2(S1, S1, h2e), b2 = fma2(S2, S2, h2e);
+  const float2 e1 = sub2(b0, b1), e2 = sub2(b0, b2);
+  const float2 t = make_float2(fabsf(e1.x) + fabsf(e2.x), fabsf(e1.y) + fabsf(e2.y));
+  const float2 tau = mul2(pair(0.25f), mul2(t, t));
+  // per-weight form: o_l = g_l (1 + tau / b_l), f-hat = (o0 r / g0 + o1 p1 + o2 p2) / sum o_l
+  const float2 o0 = fma2(pair(w.g0), mul2(tau, rcp2(b0)), pair(w.g0));
+  const float2 o1 = fma2(pair(w.g1), mul2(tau, rcp2(b1)), pair(w.g1));
+  const float2 o2 = fma2(pair(w.g2), mul2(tau, rcp2(b2)), pair(w.g2));
+  const float2 num = fma2(mul2(o0, pair(w.ig0)), r, fma2(o1, p1, mul2(o2, p2)));
+  const float2 q = mul2(num, rcp2(add2(add2(o0, o1), o2)));
+  return q.x + q.y;
+}
+
 // A quotient n / d whose division is deferred, so that the quotients of
 // several fields can share one reciprocal (resolve2). In FP32 the value is
 // already final (d = 1).
@@ -181,49 +243,58 @@ struct Frac {
   Real n, d;
 };
 
-// Range checks of the deferred quotients, on the biased exponent (integer
-// operations, off the FP64 pipe). A denominator is a product of up to
-// sixteen factors of the size of beta + eps (beta grows like the square of
-// the split-flux jumps), so for large data it leaves the FP64 range: each
-// deferred form below then falls back to separate divisions, whose
-// intermediates are only as large as beta itself.
-__device__ __forceinline__ int biased_exponent(double x) {
-  return (__double2hiint(x) >> 20) & 0x7ff;
-}
-// d > 0 with 1/d normal and some headroom: 2^-1019 <= d < 2^1020
-__device__ __forceinline__ bool denominator_ok(double d) {
-  return (unsigned)(biased_exponent(d) - 4) < 2039u;
-}
-__device__ __forceinline__ bool finite_value(double x) { return biased_exponent(x) != 0x7ff; }
+// Scaling of the deferred quotients. A denominator is a product of factors
+// of the size of beta + eps (beta grows like the square of the split-flux
+// jumps): one side of an interface is of degree four in them, a pair of
+// sides eight, a pair of fields sixteen, which leaves the FP64 range for
+// split-flux jumps near 1e8. So each side's numerator and denominator are
+// multiplied by one power of two that brings the denominator into [1, 2),
+// by integer arithmetic on the exponent fields (off the FP64 pipe, no
+// branches). Scaling by a power of two is exact, so the quotients keep the
+// bits they have without it wherever that form stays in range.
 
-// n0/d0 and n1/d1 with one division: r = 1/(d0 d1), unless d0 d1 or the
-// cross products leave the range, where each quotient is divided alone.
+// x 2^k by adding k to the exponent field: exact while x and the result are
+// normal; a zero or subnormal x, or a result below the normal range, gives a
+// zero of x's sign. Callers keep x 2^k below the overflow limit.
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int e = ((hi >> 20) & 0x7ff) + k;
+  const bool keep = ((hi & 0x7ff00000) != 0) & (e > 0);
+  return __hiloint2double(keep ? ((hi & 0x800fffff) | (e << 20)) : (hi & 0x80000000),
+                          keep ? lo : 0);
+}
+
+// n / d (d > 0, normal) as n', d' with d' in [1, 2) and n' / d' = n / d.
+__device__ __forceinline__ void normalize(double& n, double& d) {
+  const int hi = __double2hiint(d);
+  const int k = 1023 - ((hi >> 20) & 0x7ff);
+  d = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(d));
+  n = scale_pow2(n, k);
+}
+
+// n0/d0 and n1/d1 with one division: r = 1/(d0 d1) (the denominators are
+// normalized, so the product lies in [1, 4)).
 template <class Real>
 __device__ __forceinline__ void resolve2(const Frac<Real>& a, const Frac<Real>& b, Real& qa,
                                          Real& qb) {
   if constexpr (std::is_same<Real, double>::value) {
-    const Real dd = a.d * b.d;
-    const Real r = Real(1) / dd;
+    const Real r = Real(1) / (a.d * b.d);
     qa = a.n * b.d * r;
     qb = b.n * a.d * r;
-    if (!(denominator_ok(dd) & finite_value(qa) & finite_value(qb))) {
-      qa = a.n / a.d;
-      qb = b.n / b.d;
-    }
   } else {
     qa = a.n;
     qb = b.n;
   }
 }
 
-// The sum of two deferred quotients na/da + nb/db as one deferred quotient,
-// or (out of range) as a final value.
+// The sum of two deferred quotients na/da + nb/db as one deferred quotient
+// (each side normalized first).
 template <class Real>
 __device__ __forceinline__ Frac<Real> sum_frac(Real na, Real da, Real nb, Real db) {
   if constexpr (std::is_same<Real, double>::value) {
-    const Frac<Real> f{na * db + nb * da, da * db};
-    if (denominator_ok(f.d) & finite_value(f.n)) return f;
-    return Frac<Real>{na / da + nb / db, Real(1)};
+    normalize(na, da);
+    normalize(nb, db);
+    return Frac<Real>{na * db + nb * da, da * db};
   } else {
     return Frac<Real>{na + nb, Real(1)};
   }
@@ -243,14 +314,21 @@ __device__ __forceinline__ Frac<Real> interface_flux_frac(Real fpm, Real fp0, Re
                                                           Real Hp0, Real Hpp, Real fm0, Real fm1,
                                                           Real fm2, Real Hm0, Real Hm1, Real Hm2,
                                                           const Weights<Real>& w) {
-  const Cand<Real> a = candidates(fpm, fp0, fpp, Hpm, Hp0, Hpp, w);
-  const Cand<Real> b = candidates(fm2, fm1, fm0, -Hm2, -Hm1, -Hm0, w);  // mirror
   if constexpr (std::is_same<Real, double>::value) {
+    const Cand<Real> a = candidates(fpm, fp0, fpp, Hpm, Hp0, Hpp, w);
+    const Cand<Real> b = candidates(fm2, fm1, fm0, -Hm2, -Hm1, -Hm0, w);  // mirror
     Real na, da, nb, db;
     combine_nd(a, w, na, da);
     combine_nd(b, w, nb, db);
     return sum_frac(na, da, nb, db);
+  } else if constexpr (HWENO_FP32_PAIRS) {  // both sides at once, the mirror in lane y
+    return Frac<Real>{interface_flux_pair(make_float2(fpm, fm2), make_float2(fp0, fm1),
+                                          make_float2(fpp, fm0), make_float2(Hpm, -Hm2),
+                                          make_float2(Hp0, -Hm1), make_float2(Hpp, -Hm0), w),
+                      Real(1)};
   } else {
+    const Cand<Real> a = candidates(fpm, fp0, fpp, Hpm, Hp0, Hpp, w);
+    const Cand<Real> b = candidates(fm2, fm1, fm0, -Hm2, -Hm1, -Hm0, w);  // mirror
     return Frac<Real>{combine_direct(a, w) + combine_direct(b, w), Real(1)};
   }
 }
@@ -310,7 +388,9 @@ __device__ __forceinline__ Frac<Real> limited_derivative_frac(Real um, Real u0, 
     const Real L1 = w.d1 * (P + tau * b02);
     const Real L2 = w.d2 * (P + tau * b01);
     const Real num = L0 * (q0 - w.d1 * q1 - w.d2 * q2) + L1 * q1 + L2 * q2;
-    return Frac<Real>{num, w.d0 * L0 + L1 + L2};  // about b^4: in range (resolve2 checks)
+    Real n = num, d = w.d0 * L0 + L1 + L2;
+    normalize(n, d);
+    return Frac<Real>{n, d};
   } else {
     const Real l0 = w.d0 + w.d0 * qdiv(tau, b0);
     const Real l1 = w.d1 + w.d1 * qdiv(tau, b1);

@@ -53,8 +53,9 @@ constexpr int kConstTable = 15;
 // common denominator) times powers of the linear weights. Within these
 // bounds those products stay above the FP64 underflow limit: where beta = 0
 // (constant data, where tau = 0 too) they are eps^12 g^4 >= 1e-264. Large
-// beta (large data) is handled in the kernels: out of range, they divide
-// per side and per field (hweno_math.cuh, resolve2 / sum_frac).
+// beta (large data) is handled in the kernels, which rescale each side's
+// numerator and denominator by an exact power of two (hweno_math.cuh,
+// normalize).
 constexpr double kEpsMin = 1e-20, kEpsMax = 1e6, kWeightMin = 1e-6;
 
 struct SchemeParams {

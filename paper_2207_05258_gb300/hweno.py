@@ -22,6 +22,7 @@ BURGERS, EULER, BUCKLEY = 0, 1, 2
 EQUATIONS = dict(burgers=BURGERS, euler=EULER, buckley=BUCKLEY)
 FP64, FP32 = 0, 1
 TILE_VARIANTS = 5  # HWENO_TILE_VARIANTS: 1D tile shapes
+MAX_SIZE_CLASSES = 16  # HWENO_MAX_SIZE_CLASSES
 CLUSTER_MAX_POINTS = 992  # HWENO_CLUSTER_MAX_POINTS: fused_small = 2
 BC = dict(periodic=0, outflow=1, reflective=2, inflow=3, dmr_bottom=4, dmr_top=5)
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
@@ -74,6 +75,11 @@ SIGNATURES = {
                                  ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_longlong), _VP]),
     "hweno_totals": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "hweno_size_classes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "hweno_autotune_classes": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_int), _DP, _VP]),
+    "hweno_set_class_variants": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "hweno_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_int), _DP, _VP]),
     "hweno_adjoint_step": (ctypes.c_int, [_VP] * 10),
@@ -235,6 +241,32 @@ class Solver:
         self._check(lib.hweno_autotune(self.h, _ptr(U), _ptr(V), _ptr(W), _ptr(t), float(t_end),
                                        ctypes.byref(chosen), ms, _stream()))
         return chosen.value, list(ms)
+
+    def size_classes(self):
+        """hweno_size_classes: [(smallest, largest instance size)] per class."""
+        lo = (ctypes.c_int * MAX_SIZE_CLASSES)()
+        hi = (ctypes.c_int * MAX_SIZE_CLASSES)()
+        n = lib.hweno_size_classes(self.h, lo, hi)
+        if n < 0:
+            self._check(n)
+        return [(lo[i], hi[i]) for i in range(n)]
+
+    def autotune_classes(self, U, V, t=None, t_end=float("inf")):
+        """hweno_autotune_classes: returns (variant per class, per class the
+        best ms of each variant)."""
+        t = torch.zeros(self.batch, dtype=torch.float64, device=U.device) if t is None else t
+        nq = len(self.size_classes())
+        chosen = (ctypes.c_int * MAX_SIZE_CLASSES)()
+        ms = (ctypes.c_double * (MAX_SIZE_CLASSES * TILE_VARIANTS))()
+        self._check(lib.hweno_autotune_classes(self.h, _ptr(U), _ptr(V), _ptr(t), float(t_end),
+                                               chosen, ms, _stream()))
+        return ([chosen[q] for q in range(nq)],
+                [[ms[q * TILE_VARIANTS + v] for v in range(TILE_VARIANTS)] for q in range(nq)])
+
+    def set_class_variants(self, variants):
+        """hweno_set_class_variants: the tile variant of each size class."""
+        arr = (ctypes.c_int * MAX_SIZE_CLASSES)(*variants)
+        self._check(lib.hweno_set_class_variants(self.h, arr))
 
     def totals(self, U):
         """FP64 conserved totals, tensor [batch, m] (fixed summation order)."""

@@ -41,6 +41,7 @@ def test_binding_constants_match_the_header(hw):
     value = lambda name: int(defines["HWENO_" + name].strip("()"))
     assert value("TILE_VARIANTS") == hw.TILE_VARIANTS
     assert value("CLUSTER_MAX_POINTS") == hw.CLUSTER_MAX_POINTS
+    assert value("MAX_SIZE_CLASSES") == hw.MAX_SIZE_CLASSES
     for name in ("OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ENOTSUP",
                  "BURGERS", "EULER", "BUCKLEY"):
         assert value(name) == getattr(hw, name), name

@@ -113,3 +113,62 @@ def test_every_tile_variant_gives_the_same_bits(hw, precision):
                             w.t_end)
     assert 0 <= chosen < hw.TILE_VARIANTS and all(m > 0 for m in ms)
     assert ms[chosen] == min(ms)
+
+
+def test_size_classes_of_the_riemann_batch(hw):
+    full = W.riemann_batch(count=64, seed=3)
+    s = hw.Solver.from_workload(full)
+    assert s.size_classes() == [(n, n) for n in sorted(set(full.nx))]
+    # more distinct sizes than classes: octaves above the smallest instance
+    sizes = list(range(60, 60 + 40 * 9, 9))
+    w = W.Workload("oct", "burgers", 1, sizes, 1, 0.0, 2.0, 0.0, 1.0, 1.0, ("periodic",) * 4,
+                   np.ones(sum(sizes)), np.zeros(sum(sizes)))
+    cl = hw.Solver.from_workload(w).size_classes()
+    assert cl[0][0] == 60 and cl[-1][1] == max(sizes)
+    assert all(lo <= hi for lo, hi in cl)
+    assert all(cl[q][1] < cl[q + 1][0] for q in range(len(cl) - 1))
+    assert [(lo, hi) for lo, hi in cl] == [(60, 114), (123, 231), (240, 411)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mixed_tile_variants_per_size_class_give_the_same_bits(hw, precision):
+    """Each size class on its own tile variant (one launch per class and
+    stage): the state bits of a single variant, also through hweno_run's
+    graph; hweno_autotune_classes picks the fastest variant per class."""
+    w = W.riemann_batch(count=40, seed=17)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    nq = len(set(w.nx))
+
+    def run(s, graph):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            U, V = torch.from_numpy(w.U).to("cuda", dt), torch.from_numpy(w.V).to("cuda", dt)
+            t = torch.zeros(w.batch, dtype=torch.float64, device="cuda")
+            if graph:
+                s.run_graph(U, V, None, t, w.t_end, max_steps=3, steps_per_launch=3)
+            else:
+                for _ in range(3):
+                    s.step(U, V, None, t, w.t_end)
+        stream.synchronize()
+        s.sync_status()
+        return U.cpu(), V.cpu(), t.cpu()
+
+    ref = run(hw.Solver.from_workload(w, precision=precision), False)
+    mixed = hw.Solver.from_workload(w, precision=precision)
+    mixed.set_class_variants([q % hw.TILE_VARIANTS for q in range(nq)])
+    for graph in (False, True):
+        out = run(mixed, graph)
+        if not graph:
+            assert mixed.launches_last_call == 2 + 3 * nq
+        for a, b in zip(ref, out):
+            assert torch.equal(a, b)
+    s = hw.Solver.from_workload(w, precision=precision)
+    U, V = torch.from_numpy(w.U).to("cuda", dt), torch.from_numpy(w.V).to("cuda", dt)
+    chosen, ms = s.autotune_classes(U, V, None, w.t_end)
+    assert len(chosen) == nq and all(0 <= v < hw.TILE_VARIANTS for v in chosen)
+    for q in range(nq):
+        assert ms[q][chosen[q]] == min(ms[q]) and all(m > 0 for m in ms[q])
+    for a, b in zip(ref, run(s, False)):
+        assert torch.equal(a, b)
+    with pytest.raises(hw.HwenoError):
+        s.set_class_variants([hw.TILE_VARIANTS] * nq)

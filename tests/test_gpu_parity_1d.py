@@ -363,9 +363,10 @@ def test_large_euler_data(hw, k):
     """Conserved variables in large (dimensional) units: rho, rho u, E scaled
     by k keep the velocities and sound speeds, so the split fluxes and their
     jumps grow by k and the smoothness indicators by k^2. The products of
-    indicators that the kernels divide by once per pair of fields then leave
-    the FP64 range (from k ~ 1e6 on these data); the kernels then divide per
-    field and still match the oracle (which divides per weight)."""
+    indicators that the kernels divide by once per pair of fields would leave
+    the FP64 range (from k ~ 1e6 on these data) without the kernels' exact
+    power-of-two rescaling; with it they match the oracle (which divides per
+    weight)."""
     w = _scaled(euler_batch(SIZES, 21, "riemann"), k)
     check_rhs(hw, w)
     compare_runs(w, gpu_run(hw, w, 1.0, steps=1), oracle_run(w, 1.0, steps=1), 1e-13, 1e-12)
