@@ -103,6 +103,9 @@ def parse():
                     help="adjoint workloads: seeded directions checked by central differences")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, fp32 and cpu_baseline legs and the other workloads")
+    ap.add_argument("--adjoint-steps-only", dest="light", action="store_true",
+                    help="adjoint workloads: time the adjoint steps only (no full gradient, "
+                         "no finite-difference checks)")
     return ap.parse_args()
 
 
@@ -272,6 +275,28 @@ def run_ours(args, rank, world, dev_index):
                 torch.cuda.synchronize()
                 run_ms = s.profile_read()["stage"][0]  # the persistent kernel alone
                 pers = (p0.elapsed_time(p1), float(ppu), s.launches_last_call, run_ms)
+                # the next K steps as that persistent launch recorded into a CUDA graph
+                # and replayed; its point-updates are those of the same steps run
+                # uncaptured on a copy of the state (the steps are deterministic)
+                s.profile_start(0)
+                Uc, Vc, tc = U.clone(), V.clone(), t.clone()
+                gpu_ref = s.run_persistent(Uc, Vc, tc, w.t_end, K)
+                del Uc, Vc
+                cg = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(cg, capture_error_mode="thread_local"):
+                    s.run_persistent(U, V, t, w.t_end, K, count=False)
+                g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                if world > 1:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                g0.record()
+                cg.replay()
+                g1.record()
+                torch.cuda.synchronize()
+                s.sync_status()
+                assert torch.equal(t, tc), "graph replay and direct run took different steps"
+                del tc
+                timed.pgraph = (g0.elapsed_time(g1), float(gpu_ref), 2)
             cls = None
             if w.dim == 1 and w.batch > 1 and profile:
                 # tile variant per instance-size class, against the single variant
@@ -349,6 +374,8 @@ def run_ours(args, rank, world, dev_index):
         s.close()
         timed.tune = tune
         timed.pers = pers
+        if pers is None:
+            timed.pgraph = None
         timed.clus = clus
         if clus is None:
             timed.clus_run = None
@@ -373,10 +400,17 @@ def run_ours(args, rank, world, dev_index):
              "ms_per_step": round(ms_ng / args.steps, 4),
              "note": "same steps launched one by one, L2 flushed between steps"}
     persistent = None
+    pgraph = getattr(timed, "pgraph", None)
     if pers is not None:
         persistent = {"value": round(pers[1] / (pers[0] * 1e-3) / 1e6, 3),
                       "ms_per_step": round(pers[0] / args.steps, 4),
                       "note": "the next K steps as one persistent launch (hweno_run_persistent)"}
+        if pgraph is not None:
+            persistent["graph_replay"] = {
+                "value": round(pgraph[1] / (pgraph[0] * 1e-3) / 1e6, 3),
+                "ms_per_step": round(pgraph[0] / args.steps, 4),
+                "note": "the next K steps: that persistent launch recorded into a CUDA graph "
+                        "and replayed"}
     use_pers = (not small and pers is not None and pers[1] > 0 and
                 pers[1] / pers[0] > pu / ms)
     timing_note = "K steps = one CUDA-graph replay (hweno_run), CUDA events"
@@ -399,6 +433,11 @@ def run_ours(args, rank, world, dev_index):
         ms, pu = ms_ng, pu_ng
     if use_clus:
         ms, pu, launches = clus[0], clus[1], clus[2]
+    elif use_pers and pgraph is not None:
+        ms, pu, launches = pgraph[0], pgraph[1], pgraph[2]
+        timing_note = ("K steps = one persistent launch (hweno_run_persistent) after one "
+                       "wave-speed launch, recorded into a CUDA graph and replayed; CUDA events "
+                       "around the replay")
     elif use_pers:
         ms, pu, launches = pers[0], pers[1], pers[2]
         timing_note = ("K steps = one persistent launch (hweno_run_persistent) after one "
@@ -857,8 +896,12 @@ def run_reference(args, rank, world):
 # (key, --workload, precisions, K, W)
 OTHER_CONFIGS = (
     ("burgers1d_n400", "burgers1d:400", ("fp64",), 20, 5),
+    ("euler2d_smooth_256", "euler2d_smooth:256", ("fp64", "fp32"), 20, 3),
+    ("euler2d_smooth_512", "euler2d_smooth:512", ("fp64", "fp32"), 20, 3),
+    ("euler2d_smooth_1024", "euler2d_smooth:1024", ("fp64", "fp32"), 10, 3),
     ("euler2d_smooth_2048", "euler2d_smooth:2048", ("fp64", "fp32"), 10, 3),
     ("double_mach_1920x480", "double_mach:1920x480", ("fp64", "fp32"), 20, 3),
+    ("double_mach_3840x960", "double_mach:3840x960", ("fp64", "fp32"), 5, 2),
 )
 
 

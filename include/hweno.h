@@ -60,6 +60,8 @@ extern "C" {
 #define HWENO_ENONFINITE (-4) /* a wave speed (alpha) became NaN or Inf */
 #define HWENO_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define HWENO_ENOTSUP (-6)    /* not implemented for this configuration */
+#define HWENO_EBOUNDS (-7)    /* a device-side index check failed (checked builds
+                                 only: compiled with -DHWENO_CHECKS=1) */
 
 /* Equations (Sec. 3: Burgers, Eq. 1dbugers / 2dbugers; Euler, Eq. euler1 /
  * euler2 with E = p/(gamma-1) + rho |u|^2 / 2; Buckley-Leverett, Example 3.4,
@@ -284,7 +286,13 @@ int hweno_run_persistent(hweno_ctx* ctx, void* U, void* V, double* t, double t_e
  * two seconds, every CTA then stops, and the call returns HWENO_ETIMEOUT
  * (latched status). The injection travels as an argument of that one
  * launch; the context stays usable and the following runs are normal.
- * kind = 0 clears a pending injection. Nothing faults or hangs the device. */
+ * kind = 0 clears a pending injection. kind = 2 (builds compiled with
+ * -DHWENO_CHECKS=1, whose kernels check their shared-memory and global
+ * indices): a one-CTA self-test kernel on the legacy stream reads one row
+ * and one column past the end of a checked shared-memory view; the check
+ * redirects both reads to element 0 (nothing outside the array is read) and
+ * latches HWENO_EBOUNDS, which the next hweno_sync_status returns (other
+ * builds: HWENO_ENOTSUP). Nothing faults or hangs the device. */
 int hweno_test_inject(hweno_ctx* ctx, int kind);
 
 /* Tile-shape autotuner (1D): times the fused stage kernel of every tile

@@ -20,6 +20,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhweno.so")
+# checked build (device-side index checks, NaN-filled scratch): for tests
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libhweno.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,10 +43,10 @@ def _deps():
             [os.path.abspath(__file__)])
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
@@ -52,14 +55,18 @@ def flags(extra=()):
             + ARCH + list(extra))
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libhweno.so if any source is newer than it."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile and link libhweno.so if any source is newer than it. With
+    checked=True: the checked library (-DHWENO_CHECKS=1) in _build_checked/."""
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if checked:
+        extra = list(extra) + ["-DHWENO_CHECKS=1"]
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
@@ -73,17 +80,18 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for msg in ex.map(compile_one, zip(srcs, objs)):
             if verbose and msg:
                 sys.stderr.write(msg)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     force = "--force" in sys.argv
     verbose = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(force=force or bool(extra), verbose=verbose or bool(extra), extra=extra))
+    print(build(force=force or bool(extra), verbose=verbose or bool(extra), extra=extra,
+                checked="--checked" in sys.argv))

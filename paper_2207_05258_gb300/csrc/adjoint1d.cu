@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
   const int b = blockIdx.x;
   const int k = a.tile_inst[b], s = a.tile_start[b], n = a.inst_n[k];
   const int np = min(P, n - s);
+  HWENO_CHECK(s >= 0 && np >= 1, a.status);
   const long long off = a.inst_off[k];
   const double dt = a.dt[k];
   if (dt == 0.0) {  // the instance did not step: the stage is the identity
@@ -55,6 +56,7 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
   for (int g = threadIdx.x; g < np + 6; g += blockDim.x) {
     int kind;
     const int src = ghost_src(s - 3 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
+    HWENO_CHECK(kind == 2 || (src >= 0 && src < n), a.status);
     double u, v;
     if (kind == 2) { u = a.sp.inflow[0]; v = 0.0; }
     else {
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
     if (!periodic) {
       // ghosts at walls refer to owned points 0, 1 (left) and n-1, n-2 (right)
       auto add = [&](int jf, int kk, int p) {  // interface item jf, slot kk, point p
+        HWENO_CHECK_RETURN(jf >= 0 && jf < NI, a.status);
         int kind;
         const int src = ghost_src(p, n, a.sp.bc[0], a.sp.bc[1], kind);
         if (kind == 2 || src != i) return;
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(128) k_adjoint_burgers_1d(const __grid_constan
         rv += gv[jf][kk];
       };
       auto addl = [&](int jl, int kk, int p) {  // limiter item jl, slot kk (0 or 2)
+        HWENO_CHECK_RETURN(jl >= 0 && jl < NV, a.status);
         int kind;
         const int src = ghost_src(p, n, a.sp.bc[0], a.sp.bc[1], kind);
         if (kind == 2 || src != i) return;

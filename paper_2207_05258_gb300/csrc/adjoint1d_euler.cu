@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(NT, 2) k_adjoint_euler_1d(const __grid_constan
   for (int g = threadIdx.x; g < np + 6; g += blockDim.x) {
     int kind;
     const int src = ghost_src(s - 3 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
+    HWENO_CHECK(kind == 2 || (src >= 0 && src < n), a.status);
     double u[3], v[3], F[3], H[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -435,6 +436,7 @@ __global__ void __launch_bounds__(NT, 2) k_adjoint_euler_1d(const __grid_constan
         if (p >= 0 && p < n) continue;  // a halo point of another tile, not a ghost
         int kind;
         const int src = ghost_src(p, n, a.sp.bc[0], a.sp.bc[1], kind);
+        HWENO_CHECK(kind == 2 || (src >= 0 && src < n), a.status);
         if (kind == 2 || src != i) continue;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {  // ghost u = S u_src, v = -S v_src (mirror) or copies

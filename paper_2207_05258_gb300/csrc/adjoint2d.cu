@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
   }
   const int s = tile * P;
   const int np = min(P, n - s);
+  HWENO_CHECK(np >= 1 && line >= 0 && line < (DIR == 0 ? ny : nx), a.status);
   auto at = [&](int p) -> long long {
     return DIR == 0 ? (long long)line * nx + p : (long long)p * nx + line;
   };
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constan
       if (sr.kind == 2) {
         u[c] = imposed(a.sp, sr, c); N[c] = 0.0; T[c] = 0.0;
       } else {
+        HWENO_CHECK(sr.idx >= 0 && sr.idx < n, a.status);
         const long long q = c * Ntot + at(sr.idx);
         u[c] = a.U[q]; N[c] = Nf[q]; T[c] = Tf[q];
         if (sr.kind == 1) {

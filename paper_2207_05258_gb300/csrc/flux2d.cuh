@@ -5,6 +5,7 @@
 #pragma once
 
 #include "hweno.h"
+#include "hweno_math.cuh"
 #include "internal.h"
 
 namespace hweno {
@@ -21,7 +22,7 @@ struct Prim2 {
 template <class Real>
 __device__ __forceinline__ Prim2<Real> prim2(const Real* U, Real gm1) {
   Prim2<Real> q;
-  q.ir = Real(1) / U[0];
+  q.ir = recip(U[0]);
   q.u = U[1] * q.ir;
   q.v = U[2] * q.ir;
   q.p = gm1 * (U[3] - Real(0.5) * (U[1] * q.u + U[2] * q.v));

@@ -823,6 +823,24 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
     c->d_done = reinterpret_cast<unsigned*>(c->d_next + 1);
     c->d_done3 = c->d_done + B;
   }
+#if defined(HWENO_CHECKS) && HWENO_CHECKS
+  {  // checked builds: stage scratch starts as NaN, so that a read before a write shows
+    struct Buf { void* p; size_t bytes; };
+    const Buf bufs[] = {{c->d_U1, fb}, {c->d_V1, fb}, {c->d_U2, fb}, {c->d_V2, fb},
+                        {c->d_Vt0, fb}, {c->d_hU, fb}, {c->d_hV, fb}, {c->d_W1, fb},
+                        {c->d_W2, fb}, {c->d_Wt0, fb}, {c->d_LX, 3 * fb}, {c->d_VT, fb},
+                        {c->d_hW, fb}, {c->d_dt, sizeof(double) * B},
+                        {c->d_palpha, sizeof(unsigned long long) * 6 * B},
+                        {c->d_alpha, sizeof(unsigned long long) * 6 * B},
+                        {c->d_adj, c->d_adj ? adjoint_scratch_bytes(c) : 0}};
+    for (const Buf& b : bufs)
+      if (b.p && cudaMemset(b.p, 0xff, b.bytes) != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return HWENO_ECUDA;
+      }
+  }
+#endif
   // events and (1D batches) the streams of the pipelined host-buffer step
   bool made = cudaEventCreate(&c->tune_ev[0]) == cudaSuccess &&
               cudaEventCreate(&c->tune_ev[1]) == cudaSuccess;
@@ -1140,9 +1158,33 @@ int step_host_1d_pipelined(hweno_ctx* c, void* U, void* V, double* t, double t_e
 
 }  // namespace
 
+#if defined(HWENO_CHECKS) && HWENO_CHECKS
+namespace {
+// Self-test of the device-side checks: one row and one column past the end of
+// a checked shared-memory view. The views redirect both reads to element 0,
+// so nothing outside the array is touched, and flag STATUS_BOUNDS.
+__global__ void k_check_selftest(unsigned* status, double* sink) {
+  __shared__ double buf[2][4];
+  const auto v = tile_view(buf, status);
+  buf[threadIdx.x / 4][threadIdx.x % 4] = 1.0;
+  __syncthreads();
+  if (threadIdx.x == 0) *sink = v[2][0] + v[0][4];
+}
+}  // namespace
+#endif
+
 int hweno_test_inject(hweno_ctx* c, int kind) {
   if (!c) return HWENO_EINVAL;
-  if (kind != 0 && kind != 1) return fail(c, HWENO_EINVAL, "unknown injection");
+  if (kind < 0 || kind > 2) return fail(c, HWENO_EINVAL, "unknown injection");
+  if (kind == 2) {
+#if defined(HWENO_CHECKS) && HWENO_CHECKS
+    k_check_selftest<<<1, 8>>>(c->d_status, c->d_dt);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HWENO_OK : cuda_fail(c, e, "check self-test");
+#else
+    return fail(c, HWENO_ENOTSUP, "device-side checks are compiled in checked builds only");
+#endif
+  }
   c->inject = kind;
   return HWENO_OK;
 }
@@ -1374,6 +1416,7 @@ int adjoint_1d(hweno_ctx* c, const void* U, const void* V, const double* dt, dou
   AdjArgs1D g{};
   g.tile_inst = c->d_tile0_inst; g.tile_start = c->d_tile0_start; g.inst_n = c->d_inst_n;
   g.inst_off = c->d_inst_off; g.inst_geo = c->d_inst_geo; g.dt = dt;
+  g.status = c->d_status;
   g.sp = scheme_params(c);
   // stage 3: lambda2 = (2/3) G'(x2)^T lambda^{n+1}
   g.U = static_cast<const double*>(c->d_U2); g.V = static_cast<const double*>(c->d_V2);
@@ -1437,6 +1480,7 @@ int adjoint_2d(hweno_ctx* c, const void* U, const void* V, const void* W, const 
   g.nx = c->nx[0]; g.ny = c->ny; g.dx = a.dx; g.dy = a.dy;
   for (int i = 0; i < 6; ++i) g.geod[i] = a.geod[i];
   g.x0 = c->x0; g.y0 = c->y0; g.t = t; g.dt = dt; g.sp = a.sp;
+  g.status = c->d_status;
   g.part = adj_field(c, 9);
   double* f[9];
   for (int i = 0; i < 9; ++i) f[i] = adj_field(c, i);
@@ -1596,6 +1640,8 @@ int hweno_sync_status(hweno_ctx* c, void* stream) {
     cudaMemset(c->d_status, 0, sizeof(unsigned));
     if (st & STATUS_TIMEOUT)
       return fail(c, HWENO_ETIMEOUT, "a persistent-run wait gave up (dependency not met in ~2 s)");
+    if (st & STATUS_BOUNDS)
+      return fail(c, HWENO_EBOUNDS, "a device-side index check failed (checked build)");
     if (st & STATUS_NONFINITE) return fail(c, HWENO_ENONFINITE, "non-finite wave speed");
   }
   return HWENO_OK;

@@ -179,9 +179,6 @@ __device__ __forceinline__ Real combine_direct(const Cand<Real>& c, const Weight
 // FP32 pairs (one instruction for both sides: fma / add / mul .f32x2, sm_100
 // and later). Each lane rounds exactly as a scalar FP32 operation would.
 // ---------------------------------------------------------------------------
-#ifndef HWENO_FP32_PAIRS
-#define HWENO_FP32_PAIRS 0
-#endif
 __device__ __forceinline__ float2 pair(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
@@ -309,7 +306,11 @@ __device__ __forceinline__ Real resolve1(const Frac<Real>& a) {
 // Full interface flux of one (characteristic) field: f-hat = f-hat^+ + f-hat^-
 // from f^+ at i-1..i+1, f^- at i..i+2 and the scaled derivative data, as a
 // deferred quotient (FP64: both sides over the common denominator).
-template <class Real>
+// Pairs (FP32 only): both sides in packed pairs. Measured: +5.6% for the 2D
+// sweeps (96 registers allowed); in the 1D stage kernels, capped at 64
+// registers for 8 CTAs per SM, the pairs spill and lose 5%, so they keep the
+// scalar form.
+template <class Real, bool Pairs = false>
 __device__ __forceinline__ Frac<Real> interface_flux_frac(Real fpm, Real fp0, Real fpp, Real Hpm,
                                                           Real Hp0, Real Hpp, Real fm0, Real fm1,
                                                           Real fm2, Real Hm0, Real Hm1, Real Hm2,
@@ -321,7 +322,7 @@ __device__ __forceinline__ Frac<Real> interface_flux_frac(Real fpm, Real fp0, Re
     combine_nd(a, w, na, da);
     combine_nd(b, w, nb, db);
     return sum_frac(na, da, nb, db);
-  } else if constexpr (HWENO_FP32_PAIRS) {  // both sides at once, the mirror in lane y
+  } else if constexpr (Pairs) {  // both sides at once, the mirror in lane y
     return Frac<Real>{interface_flux_pair(make_float2(fpm, fm2), make_float2(fp0, fm1),
                                           make_float2(fpp, fm0), make_float2(Hpm, -Hm2),
                                           make_float2(Hp0, -Hm1), make_float2(Hpp, -Hm0), w),
@@ -333,12 +334,12 @@ __device__ __forceinline__ Frac<Real> interface_flux_frac(Real fpm, Real fp0, Re
   }
 }
 
-template <class Real>
+template <class Real, bool Pairs = false>
 __device__ __forceinline__ Real interface_flux(Real fpm, Real fp0, Real fpp, Real Hpm, Real Hp0,
                                                Real Hpp, Real fm0, Real fm1, Real fm2, Real Hm0,
                                                Real Hm1, Real Hm2, const Weights<Real>& w) {
-  return resolve1(interface_flux_frac(fpm, fp0, fpp, Hpm, Hp0, Hpp, fm0, fm1, fm2, Hm0, Hm1,
-                                      Hm2, w));
+  return resolve1(interface_flux_frac<Real, Pairs>(fpm, fp0, fpp, Hpm, Hp0, Hpp, fm0, fm1, fm2,
+                                                   Hm0, Hm1, Hm2, w));
 }
 
 // Scaled derivative flux D = dx (h-hat^+ + h-hat^-) = dx (p_0'^+ + p_0'^-),
@@ -400,10 +401,58 @@ __device__ __forceinline__ Frac<Real> limited_derivative_frac(Real um, Real u0, 
   }
 }
 
+// Two FP32 limited derivatives at once (lanes: two characteristic fields),
+// the per-weight form of limited_derivative_frac lane by lane.
+__device__ __forceinline__ float2 limited_derivative_pair(float2 um, float2 u0, float2 up,
+                                                          float2 Vm, float2 Vp,
+                                                          const Weights<float>& w) {
+  const float2 sV = add2(Vm, Vp), dV = sub2(Vm, Vp);
+  const float2 q1 = sub2(u0, um), q2 = sub2(up, u0);
+  const float2 lap = sub2(q2, q1), du = add2(q1, q2);
+  const float2 q0 = fma2(pair(0.75f), du, mul2(pair(-0.25f), sV));
+  const float2 E2 = fma2(pair(1.5772623149801082648f), lap, mul2(pair(0.26821465762352094858f), dV));
+  const float2 A3 = mul2(pair(1.5622499799967993599f), sub2(sV, du));
+  const float2 A4 = fma2(pair(-12.498180087296929908f), lap, mul2(pair(-6.2490900436484649542f), dV));
+  const float2 e1 = fma2(pair(0.040006401536409714721f), A3, q0);
+  const float2 b0 = fma2(A4, A4, fma2(A3, A3, fma2(E2, E2, fma2(e1, e1, pair(w.eps)))));
+  const float2 b1 = fma2(q1, q1, pair(w.eps)), b2 = fma2(q2, q2, pair(w.eps));
+  const float2 e01 = sub2(b0, b1), e02 = sub2(b0, b2);
+  const float2 t = make_float2(fabsf(e01.x) + fabsf(e02.x), fabsf(e01.y) + fabsf(e02.y));
+  const float2 tau = mul2(pair(0.25f), mul2(t, t));
+  const float2 l0 = fma2(pair(w.d0), mul2(tau, rcp2(b0)), pair(w.d0));
+  const float2 l1 = fma2(pair(w.d1), mul2(tau, rcp2(b1)), pair(w.d1));
+  const float2 l2 = fma2(pair(w.d2), mul2(tau, rcp2(b2)), pair(w.d2));
+  const float2 c0 = fma2(pair(-w.d2), q2, fma2(pair(-w.d1), q1, q0));
+  const float2 num = fma2(mul2(l0, pair(w.id0)), c0, fma2(l1, q1, mul2(l2, q2)));
+  return mul2(num, rcp2(add2(add2(l0, l1), l2)));
+}
+
 template <class Real>
 __device__ __forceinline__ Real limited_derivative(Real um, Real u0, Real up, Real Vm, Real Vp,
                                                    const Weights<Real>& w) {
   return resolve1(limited_derivative_frac(um, u0, up, Vm, Vp, w));
+}
+
+// 1/x: the IEEE division in FP64, the fast approximate reciprocal in FP32
+// (as qdiv).
+template <class Real>
+__device__ __forceinline__ Real recip(Real x) {
+  if constexpr (std::is_same<Real, float>::value) return __fdividef(1.f, x);
+  else return Real(1) / x;
+}
+
+// sqrt(x): IEEE in FP64; in FP32 the approximate square root of PTX
+// (sqrt.approx.f32: NaN for x < 0 or NaN, so a bad state still shows in the
+// wave speed; +0 for +0).
+template <class Real>
+__device__ __forceinline__ Real fast_sqrt(Real x) {
+  if constexpr (std::is_same<Real, float>::value) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  } else {
+    return sqrt(x);
+  }
 }
 
 // Reciprocal square root (FP64: CUDA's rsqrt, within one ulp; FP32: the

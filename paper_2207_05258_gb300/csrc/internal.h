@@ -24,7 +24,80 @@ inline cudaError_t ensure_smem_limit(K* f, size_t bytes, unsigned& done) {
 }
 
 // Status-word bits written by kernels (read by hweno_sync_status).
-enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u };
+// STATUS_BOUNDS: a device-side index check of a checked build failed.
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
+
+// ---------------------------------------------------------------------------
+// Checked builds (compiled with -DHWENO_CHECKS=1; a stand-in for a memory
+// checker). Shared-memory tiles are reached through views whose rows and
+// columns are checked against their extents, and global indices through
+// HWENO_CHECK at the points where they are formed. A failed check sets
+// STATUS_BOUNDS in the context's status word (no trap: the context stays
+// usable) and the access goes to element 0 of the array instead, so nothing
+// outside it is touched. In a normal build the views are the plain arrays
+// and the checks vanish.
+// ---------------------------------------------------------------------------
+#if defined(HWENO_CHECKS) && HWENO_CHECKS
+#define HWENO_CHECK(cond, status)                                     \
+  do {                                                                \
+    if (!(cond)) atomicOr((status), STATUS_BOUNDS);                   \
+  } while (0)
+// the same, leaving the enclosing function (a lambda) when the check fails
+#define HWENO_CHECK_RETURN(cond, status)                              \
+  do {                                                                \
+    if (!(cond)) {                                                    \
+      atomicOr((status), STATUS_BOUNDS);                              \
+      return;                                                         \
+    }                                                                 \
+  } while (0)
+
+template <class T, int C>
+struct CheckedRow {
+  T* p;
+  unsigned* st;
+  __device__ __forceinline__ T& operator[](int i) const {
+    if ((unsigned)i >= (unsigned)C) {
+      atomicOr(st, STATUS_BOUNDS);
+      i = 0;
+    }
+    return p[i];
+  }
+};
+template <class T, int C>
+struct CheckedTile {
+  T* base;
+  int rows;
+  unsigned* st;
+  __device__ __forceinline__ CheckedRow<T, C> operator[](int r) const {
+    if ((unsigned)r >= (unsigned)rows) {
+      atomicOr(st, STATUS_BOUNDS);
+      r = 0;
+    }
+    return CheckedRow<T, C>{base + (size_t)r * C, st};
+  }
+};
+// view of a [rows][C] tile at p (dynamic shared memory)
+template <int C, class T>
+__device__ __forceinline__ CheckedTile<T, C> tile_view(T* p, int rows, unsigned* st) {
+  return CheckedTile<T, C>{p, rows, st};
+}
+// view of a static [R][C] shared array
+template <class T, int R, int C>
+__device__ __forceinline__ CheckedTile<T, C> tile_view(T (&a)[R][C], unsigned* st) {
+  return CheckedTile<T, C>{&a[0][0], R, st};
+}
+#else
+#define HWENO_CHECK(cond, status) ((void)0)
+#define HWENO_CHECK_RETURN(cond, status) ((void)0)
+template <int C, class T>
+__device__ __forceinline__ T (*tile_view(T* p, int, unsigned*))[C] {
+  return reinterpret_cast<T(*)[C]>(p);
+}
+template <class T, int R, int C>
+__device__ __forceinline__ T (*tile_view(T (&a)[R][C], unsigned*))[C] {
+  return a;
+}
+#endif
 
 enum Mode { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE2 = 2, MODE_STAGE3 = 3 };
 
@@ -229,6 +302,7 @@ struct AdjArgs1D {
   const double* inst_geo;
   const double* alpha;   // frozen wave speed of the stage input, per instance
   const double* dt;      // time step per instance (0: the instance did not step)
+  unsigned* status;      // checked builds: STATUS_BOUNDS
   SchemeParams sp;
 };
 
@@ -270,6 +344,7 @@ struct AdjArgs2D {
   double stage_c;       // boundary time of the stage: t + stage_c * dt
   const double* alpha;  // [2] frozen alpha_x, alpha_y of the stage input
   const double* dt;     // [1] (0: the step did not happen)
+  unsigned* status;     // checked builds: STATUS_BOUNDS
   SchemeParams sp;
 };
 

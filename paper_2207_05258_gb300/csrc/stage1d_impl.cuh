@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cfloat>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 #include <cuda/atomic>
@@ -61,10 +62,10 @@ __device__ __forceinline__ Real wave_speed(const Real* u, Real gam, Real a01) {
     buckley_f(u[0], f, df);
     return fmax(a01, fabs(df));
   } else {
-    const Real ir = Real(1) / u[0];
+    const Real ir = recip(u[0]);
     const Real vel = u[1] * ir;
     const Real p = (gam - Real(1)) * (u[2] - Real(0.5) * u[1] * vel);
-    return fabs(vel) + sqrt(gam * p * ir);
+    return fabs(vel) + fast_sqrt(gam * p * ir);
   }
 }
 
@@ -153,17 +154,20 @@ __device__ __forceinline__ StageIO io_of(const Args1D& a) {
 }
 
 // Point g of a tile starting at s (instance point s - 2 + g; ghosts by the
-// boundary conditions): stores u, v, the split fluxes f^+-, H^+- (H = dx h)
-// and, for Euler, sqrt(rho), u, H and c^2 in shared memory.
-template <int EQ, class Real, int NP>
+// boundary conditions): stores u, dx v (the limiter's scaled derivative),
+// the split fluxes f^+-, H^+- (H = dx h) and, for Euler, sqrt(rho), u, H and
+// c^2 in shared memory.
+template <int EQ, class Real, class TV>
 __device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const Real* V, int n,
-                                           int s, int g, Real alpha, Real hdx, Real gam, Real gm1,
-                                           Real (*sU)[NP], Real (*sV)[NP], Real (*sFp)[NP],
-                                           Real (*sFm)[NP], Real (*sHp)[NP], Real (*sHm)[NP],
-                                           Real (*sE)[NP]) {
+                                           int s, int g, Real alpha, Real dx, Real hdx, Real gam,
+                                           Real gm1,
+                                           const TV& sU, const TV& sV, const TV& sFp,
+                                           const TV& sFm, const TV& sHp, const TV& sHm,
+                                           const TV& sE) {
   constexpr int M = Dim1<EQ>::M;
   int kind;
   const int src = map_1d(s - 2 + g, n, a.sp.bc[0], a.sp.bc[1], kind);
+  HWENO_CHECK(kind == 2 || (src >= 0 && src < n), a.status);
   Real u[M], v[M];
 #pragma unroll
   for (int c = 0; c < M; ++c) {
@@ -176,7 +180,7 @@ __device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const
       if (kind == 1) { const Real sg = Real(refl_sign<EQ>(c)); u[c] *= sg; v[c] *= -sg; }
     }
     sU[c][g] = u[c];
-    sV[c][g] = v[c];
+    sV[c][g] = dx * v[c];
   }
   Real F[M], H[M];
   if constexpr (EQ == HWENO_BURGERS) {
@@ -218,20 +222,20 @@ __device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const
 // The limited derivative v~ at loaded point g (Sec. 2.2): v unchanged with
 // the limiter off, component-wise, or (Euler) on the characteristic fields
 // of the eigenvectors at U_g.
-template <int EQ, class Real, int NP>
-__device__ __forceinline__ void limited_point(const Args1D& a, int g, Real dx, Real idx, Real gm1,
-                                              const Weights<Real>& w, Real (*sU)[NP],
-                                              Real (*sV)[NP], Real (*sE)[NP], Real* vt) {
+template <int EQ, class Real, class TV>
+__device__ __forceinline__ void limited_point(const Args1D& a, int g, Real idx, Real gm1,
+                                              const Weights<Real>& w, const TV& sU,
+                                              const TV& sV, const TV& sE, Real* vt) {
   constexpr int M = Dim1<EQ>::M;
   constexpr bool EUL = EQ == HWENO_EULER;
   if (a.sp.limiter == 0) {
 #pragma unroll
-    for (int c = 0; c < M; ++c) vt[c] = sV[c][g];
+    for (int c = 0; c < M; ++c) vt[c] = sV[c][g] * idx;
   } else if (!EUL || a.sp.limiter == 2) {
 #pragma unroll
     for (int c = 0; c < M; ++c)
-      vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], dx * sV[c][g - 1],
-                                 dx * sV[c][g + 1], w) * idx;
+      vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], sV[c][g - 1],
+                                 sV[c][g + 1], w) * idx;
   } else if constexpr (EUL) {
     Real cg, icg;
     sound_speed(sE[3][g], cg, icg);
@@ -241,9 +245,9 @@ __device__ __forceinline__ void limited_point(const Args1D& a, int g, Real dx, R
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const Real l0 = e.L[q][0], l1q = e.L[q][1], l2q = e.L[q][2];
-      auto pj = [&](Real (*A)[NP], int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
+      auto pj = [&](const TV& A, int gg) { return l0 * A[0][gg] + l1q * A[1][gg] + l2q * A[2][gg]; };
       zr[q] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
-                                      dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
+                                      pj(sV, g - 1), pj(sV, g + 1), w);
     }
     Real z[3];
     resolve2(zr[0], zr[1], z[0], z[1]);
@@ -254,32 +258,48 @@ __device__ __forceinline__ void limited_point(const Args1D& a, int g, Real dx, R
   }
 }
 
+// Factors of the SSP-RK3 combination of a stage: x_out = a x0 + b (x + dt L)
+// with L^1 = -dF / dx, L^2 = -dD / dx^2 (dF, dD the flux differences), so
+// x_out = a x0 + b x + k dF with k1 = -b dt / dx for U, k2 = -b dt / dx^2
+// for V (one FMA per component on the difference; the same expression in
+// exact arithmetic).
+template <class Real, int MODE>
+struct RKFactors {
+  Real b, k1, k2;
+  __device__ __forceinline__ RKFactors(Real rdt, Real idx, Real idx2) {
+    b = MODE == MODE_STAGE1 ? Real(1) : MODE == MODE_STAGE2 ? Real(0.25) : Real(2.0 / 3.0);
+    k1 = -(b * rdt) * idx;
+    k2 = -(b * rdt) * idx2;
+  }
+};
+
 // The SSP-RK3 combination of one stage at instance point q (component
-// stride n) from the stage input u, the right-hand sides l1, l2 and v~:
+// stride n) from the stage input u, the flux differences dF, dD and v~:
 // writes U, V of the stage output (stage 1 also v~^n) and returns U in un.
 template <int EQ, class Real, int MODE>
 __device__ __forceinline__ void stage_update(const StageIO& io, long long base, long long n,
-                                             const Real* u, const Real* l1, const Real* l2,
-                                             const Real* vt, Real rdt, Real* un) {
+                                             const Real* u, const Real* dF, const Real* dD,
+                                             const Real* vt, const RKFactors<Real, MODE>& f,
+                                             Real* un) {
   constexpr int M = Dim1<EQ>::M;
 #pragma unroll
   for (int c = 0; c < M; ++c) {
     const long long q = base + (long long)c * n;
     Real vn;
     if constexpr (MODE == MODE_STAGE1) {
-      un[c] = u[c] + rdt * l1[c];
-      vn = vt[c] + rdt * l2[c];
+      un[c] = u[c] + f.k1 * dF[c];
+      vn = vt[c] + f.k2 * dD[c];
       static_cast<Real*>(io.Vt0out)[q] = vt[c];
     } else if constexpr (MODE == MODE_STAGE2) {
       const Real u0 = static_cast<const Real*>(io.U0)[q];
       const Real v0 = static_cast<const Real*>(io.Vt0)[q];
-      un[c] = Real(0.75) * u0 + Real(0.25) * (u[c] + rdt * l1[c]);
-      vn = Real(0.75) * v0 + Real(0.25) * (vt[c] + rdt * l2[c]);
+      un[c] = (Real(0.75) * u0 + Real(0.25) * u[c]) + f.k1 * dF[c];
+      vn = (Real(0.75) * v0 + Real(0.25) * vt[c]) + f.k2 * dD[c];
     } else {
       const Real u0 = static_cast<const Real*>(io.U0)[q];
       const Real v0 = static_cast<const Real*>(io.Vt0)[q];
-      un[c] = Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * (u[c] + rdt * l1[c]);
-      vn = Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * (vt[c] + rdt * l2[c]);
+      un[c] = (Real(1.0 / 3.0) * u0 + Real(2.0 / 3.0) * u[c]) + f.k1 * dF[c];
+      vn = (Real(1.0 / 3.0) * v0 + Real(2.0 / 3.0) * vt[c]) + f.k2 * dD[c];
     }
     static_cast<Real*>(io.Uout)[q] = un[c];
     static_cast<Real*>(io.Vout)[q] = vn;
@@ -298,21 +318,24 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
   constexpr bool EUL = Lay::EUL;
   extern __shared__ __align__(16) unsigned char smem1d[];
   Real* base = reinterpret_cast<Real*>(smem1d);
-  Real(*sU)[NP] = reinterpret_cast<Real(*)[NP]>(base);
-  Real(*sV)[NP] = reinterpret_cast<Real(*)[NP]>(base + 1 * M * NP);
-  Real(*sFp)[NP] = reinterpret_cast<Real(*)[NP]>(base + 2 * M * NP);
-  Real(*sFm)[NP] = reinterpret_cast<Real(*)[NP]>(base + 3 * M * NP);
-  Real(*sHp)[NP] = reinterpret_cast<Real(*)[NP]>(base + 4 * M * NP);
-  Real(*sHm)[NP] = reinterpret_cast<Real(*)[NP]>(base + 5 * M * NP);
-  Real(*sE)[NP] = reinterpret_cast<Real(*)[NP]>(base + 6 * M * NP);
-  Real(*sF)[NF] = reinterpret_cast<Real(*)[NF]>(base + (6 * M + Lay::NE) * NP);
-  Real(*sD)[NF] = reinterpret_cast<Real(*)[NF]>(base + (6 * M + Lay::NE) * NP + M * NF);
+  unsigned* const st = a.status;
+  const auto sU = tile_view<NP>(base, M, st);
+  const auto sV = tile_view<NP>(base + 1 * M * NP, M, st);
+  const auto sFp = tile_view<NP>(base + 2 * M * NP, M, st);
+  const auto sFm = tile_view<NP>(base + 3 * M * NP, M, st);
+  const auto sHp = tile_view<NP>(base + 4 * M * NP, M, st);
+  const auto sHm = tile_view<NP>(base + 5 * M * NP, M, st);
+  const auto sE = tile_view<NP>(base + 6 * M * NP, Lay::NE, st);
+  const auto sF = tile_view<NF>(base + (6 * M + Lay::NE) * NP, M, st);
+  const auto sD = tile_view<NF>(base + (6 * M + Lay::NE) * NP + M * NF, M, st);
+  using TV = std::remove_const_t<decltype(sU)>;
   __shared__ Real red[NT / 32];
   __shared__ double s_dt;
 
   const int n = a.inst_n[k];
   if (a.skip_done && !(a.t[k] < a.t_end)) return;
   const int np = min(Lay::P, n - s);
+  HWENO_CHECK(s >= 0 && np >= 1, st);
   const long long off = a.inst_off[k] * M;
   const Real* geo = pick<Real>(a.inst_geo, a.inst_geof) + 3 * k;
   const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
@@ -341,8 +364,8 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
     const Real* V = static_cast<const Real*>(io.V) + off;
     const Real hdx = Real(0.5) * dx;
     for (int g = threadIdx.x; g < np + 4; g += blockDim.x)
-      tile_point<EQ, Real, NP>(a, U, V, n, s, g, alpha, hdx, gam, gm1, sU, sV, sFp, sFm, sHp,
-                               sHm, sE);
+      tile_point<EQ, Real, TV>(a, U, V, n, s, g, alpha, dx, hdx, gam, gm1, sU, sV, sFp, sFm,
+                               sHp, sHm, sE);
   }
   __syncthreads();
 
@@ -357,7 +380,7 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
       Real uu, HH, cc;
       if (a.sp.eig_avg == 0) {  // Roe average of U_i, U_{i+1}
         const Real sl = sE[0][gl], sr = sE[0][gl + 1];
-        const Real is = Real(1) / (sl + sr);
+        const Real is = recip(sl + sr);
         uu = (sl * sE[1][gl] + sr * sE[1][gl + 1]) * is;
         HH = (sl * sE[2][gl] + sr * sE[2][gl + 1]) * is;
       } else {  // arithmetic mean state
@@ -376,7 +399,7 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const Real l0 = e.L[q][0], l1 = e.L[q][1], l2 = e.L[q][2];
-        auto pj = [&](Real (*A)[NP], int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
+        auto pj = [&](const TV& A, int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
         fr[q] = interface_flux_frac(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1),
                                     pj(sHp, gl - 1), pj(sHp, gl), pj(sHp, gl + 1),
                                     pj(sFm, gl), pj(sFm, gl + 1), pj(sFm, gl + 2),
@@ -400,33 +423,34 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
   __syncthreads();
 
   // 4: points
-  const Real rdt = Real(s_dt);
+  const RKFactors<Real, MODE> rk(Real(s_dt), idx, idx2);
   const bool want_alpha = MODE != MODE_RHS && io.alpha_out != nullptr;  // uniform
   Real amax = Real(0);
   bool bad = false;
   for (int j = threadIdx.x; j < np; j += blockDim.x) {
     const int g = j + 2;
-    Real l1[M], l2[M], vt[M];
+    Real dF[M], dD[M], vt[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-      l1[c] = -(sF[c][j + 1] - sF[c][j]) * idx;
-      l2[c] = -(sD[c][j + 1] - sD[c][j]) * idx2;
+      dF[c] = sF[c][j + 1] - sF[c][j];
+      dD[c] = sD[c][j + 1] - sD[c][j];
     }
-    limited_point<EQ, Real, NP>(a, g, dx, idx, gm1, w, sU, sV, sE, vt);
+    limited_point<EQ, Real, TV>(a, g, idx, gm1, w, sU, sV, sE, vt);
 
+    HWENO_CHECK(s + j < n, st);
     const long long base = off + s + j;
     if constexpr (MODE == MODE_RHS) {
 #pragma unroll
       for (int c = 0; c < M; ++c) {
-        static_cast<Real*>(a.L1)[base + (long long)c * n] = l1[c];
-        static_cast<Real*>(a.L2)[base + (long long)c * n] = l2[c];
+        static_cast<Real*>(a.L1)[base + (long long)c * n] = -dF[c] * idx;
+        static_cast<Real*>(a.L2)[base + (long long)c * n] = -dD[c] * idx2;
         if (a.Vlim) static_cast<Real*>(a.Vlim)[base + (long long)c * n] = vt[c];
       }
     } else {
       Real u[M], un[M];
 #pragma unroll
       for (int c = 0; c < M; ++c) u[c] = sU[c][g];
-      stage_update<EQ, Real, MODE>(io, base, n, u, l1, l2, vt, rdt, un);
+      stage_update<EQ, Real, MODE>(io, base, n, u, dF, dD, vt, rk, un);
       if (want_alpha) {
         const Real sp = wave_speed<EQ>(un, gam, pick<Real>(a.sp.wd, a.sp.wf)[10]);
         bad |= !(sp <= real_max<Real>());
@@ -559,6 +583,7 @@ k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p
     const int stage = r / p.ntiles;
     const int b = r - stage * p.ntiles;
     const int k = a.tile_inst[b], s = a.tile_start[b];
+    HWENO_CHECK(k >= 0 && k < p.batch, a.status);
     const unsigned ntk = (unsigned)p.inst_tiles[k];
     if (threadIdx.x == 0) {
       const unsigned need = (unsigned)(3 * n + stage) * ntk + (k == 0 ? p.wait_extra : 0u);
@@ -805,22 +830,27 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
   constexpr bool EUL = EQ == HWENO_EULER;
   extern __shared__ __align__(16) unsigned char smem1d[];
   Real* base = reinterpret_cast<Real*>(smem1d);
-  Real(*sU)[NP] = reinterpret_cast<Real(*)[NP]>(base);
-  Real(*sV)[NP] = sU + M;
-  Real(*sFp)[NP] = sV + M;
-  Real(*sFm)[NP] = sFp + M;
-  Real(*sHp)[NP] = sFm + M;
-  Real(*sHm)[NP] = sHp + M;
-  Real(*sE)[NP] = sHm + M;
-  Real(*sSn)[M][NF] = reinterpret_cast<Real(*)[M][NF]>(base + (6 * M + Lay::NE) * NP);  // [2]
-  Real(*sSd)[M][NF] = sSn + 2;                                                        // [2]
-  Real(*sD)[NF] = reinterpret_cast<Real(*)[NF]>(sSd + 2);
-  Real(*sF)[NF] = sD + M;
-  Real(*sVt)[P] = reinterpret_cast<Real(*)[P]>(sF + M);
+  unsigned* const st = a.status;
+  const auto sU = tile_view<NP>(base, M, st);
+  const auto sV = tile_view<NP>(base + 1 * M * NP, M, st);
+  const auto sFp = tile_view<NP>(base + 2 * M * NP, M, st);
+  const auto sFm = tile_view<NP>(base + 3 * M * NP, M, st);
+  const auto sHp = tile_view<NP>(base + 4 * M * NP, M, st);
+  const auto sHm = tile_view<NP>(base + 5 * M * NP, M, st);
+  const auto sE = tile_view<NP>(base + 6 * M * NP, Lay::NE, st);
+  using TV = std::remove_const_t<decltype(sU)>;
+  Real* const sides = base + (6 * M + Lay::NE) * NP;  // numerators, denominators [2][M][NF] each
+  const auto sSn0 = tile_view<NF>(sides, M, st), sSn1 = tile_view<NF>(sides + M * NF, M, st);
+  const auto sSd0 = tile_view<NF>(sides + 2 * M * NF, M, st);
+  const auto sSd1 = tile_view<NF>(sides + 3 * M * NF, M, st);
+  const auto sD = tile_view<NF>(sides + 4 * M * NF, M, st);
+  const auto sF = tile_view<NF>(sides + 5 * M * NF, M, st);
+  const auto sVt = tile_view<P>(sides + 6 * M * NF, M, st);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.inst_n[k];
   const int np = min(P, n - s);
+  HWENO_CHECK(s >= 0 && np >= 1, st);
   const long long off = a.inst_off[k] * M;
   const Real* geo = pick<Real>(a.inst_geo, a.inst_geof) + 3 * k;
   const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
@@ -832,8 +862,8 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
   // A (warp 0): the tile with ghosts, point fluxes and splitting; lane g is
   // point s - 2 + g
   if (warp == 0 && lane < np + 4)
-    tile_point<EQ, Real, NP>(a, static_cast<const Real*>(io.U) + off,
-                             static_cast<const Real*>(io.V) + off, n, s, lane, alpha,
+    tile_point<EQ, Real, TV>(a, static_cast<const Real*>(io.U) + off,
+                             static_cast<const Real*>(io.V) + off, n, s, lane, alpha, dx,
                              Real(0.5) * dx, gam, gm1, sU, sV, sFp, sFm, sHp, sHm, sE);
   __syncthreads();
 
@@ -844,18 +874,20 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
   if (warp < 2) {
     const int sd = warp, j = lane, gl = j + 1, b = gl - 1 + sd;  // first stencil point
     if (j <= np) {
-      Real(*SF)[NP] = sd ? sFm : sFp;
-      Real(*SH)[NP] = sd ? sHm : sHp;
+      const TV SF = sd ? sFm : sFp;
+      const TV SH = sd ? sHm : sHp;
+      const auto sSn = sd ? sSn1 : sSn0;
+      const auto sSd = sd ? sSd1 : sSd0;
       if constexpr (!EUL) {
         const Frac<Real> fr = side_frac(sd, SF[0][b], SF[0][b + 1], SF[0][b + 2], SH[0][b],
                                         SH[0][b + 1], SH[0][b + 2], w);
-        sSn[sd][0][j] = fr.n;
-        sSd[sd][0][j] = fr.d;
+        sSn[0][j] = fr.n;
+        sSd[0][j] = fr.d;
       } else {
         Real uu, HH, cc;
         if (a.sp.eig_avg == 0) {  // Roe average of U_i, U_{i+1}
           const Real sl = sE[0][gl], sr = sE[0][gl + 1];
-          const Real is = Real(1) / (sl + sr);
+          const Real is = recip(sl + sr);
           uu = (sl * sE[1][gl] + sr * sE[1][gl + 1]) * is;
           HH = (sl * sE[2][gl] + sr * sE[2][gl + 1]) * is;
         } else {  // arithmetic mean state
@@ -872,11 +904,11 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const Real l0 = e.L[q][0], l1 = e.L[q][1], l2 = e.L[q][2];
-          auto pj = [&](Real (*A)[NP], int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
+          auto pj = [&](const TV& A, int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
           const Frac<Real> fr = side_frac(sd, pj(SF, b), pj(SF, b + 1), pj(SF, b + 2), pj(SH, b),
                                           pj(SH, b + 1), pj(SH, b + 2), w);
-          sSn[sd][q][j] = fr.n;
-          sSd[sd][q][j] = fr.d;
+          sSn[q][j] = fr.n;
+          sSd[q][j] = fr.d;
         }
       }
     }
@@ -884,7 +916,7 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
     const int j = lane, g = j + 2;
     if (j < np) {
       Real vt[M];
-      limited_point<EQ, Real, NP>(a, g, dx, idx, gm1, w, sU, sV, sE, vt);
+      limited_point<EQ, Real, TV>(a, g, idx, gm1, w, sU, sV, sE, vt);
 #pragma unroll
       for (int c = 0; c < M; ++c) sVt[c][j] = vt[c];
     }
@@ -905,12 +937,12 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
     const int j = lane;
     if (j <= np) {
       if constexpr (!EUL) {
-        sF[0][j] = resolve1(sides_sum(sSn[0][0][j], sSd[0][0][j], sSn[1][0][j], sSd[1][0][j]));
+        sF[0][j] = resolve1(sides_sum(sSn0[0][j], sSd0[0][j], sSn1[0][j], sSd1[0][j]));
       } else {
         Frac<Real> fr[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-          fr[q] = sides_sum(sSn[0][q][j], sSd[0][q][j], sSn[1][q][j], sSd[1][q][j]);
+          fr[q] = sides_sum(sSn0[q][j], sSd0[q][j], sSn1[q][j], sSd1[q][j]);
         Real f[3];
         resolve2(fr[0], fr[1], f[0], f[1]);
         f[2] = resolve1(fr[2]);
@@ -920,23 +952,23 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
     }
   }
   __syncwarp();
-  const Real rdt = Real(dt);
+  const RKFactors<Real, MODE> rk(Real(dt), idx, idx2);
   const bool want_alpha = part_out != nullptr;  // uniform
   Real amax = Real(0);
   bool bad = false;
   const int j = lane;
   if (j < np) {
     const int g = j + 2;
-    Real l1[M], l2[M];
+    Real dF[M], dD[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-      l1[c] = -(sF[c][j + 1] - sF[c][j]) * idx;
-      l2[c] = -(sD[c][j + 1] - sD[c][j]) * idx2;
+      dF[c] = sF[c][j + 1] - sF[c][j];
+      dD[c] = sD[c][j + 1] - sD[c][j];
     }
     Real u[M], vt[M], un[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) { u[c] = sU[c][g]; vt[c] = sVt[c][j]; }
-    stage_update<EQ, Real, MODE>(io, off + s + j, n, u, l1, l2, vt, rdt, un);
+    stage_update<EQ, Real, MODE>(io, off + s + j, n, u, dF, dD, vt, rk, un);
     if (want_alpha) {
       const Real sp = wave_speed<EQ>(un, gam, pick<Real>(a.sp.wd, a.sp.wf)[10]);
       bad = !(sp <= real_max<Real>());

@@ -36,7 +36,7 @@ __device__ __forceinline__ void speeds2(const Real* U, Real gam, Real& sx, Real&
     sx = sy = fabs(U[0]);
   } else {
     const Prim2<Real> q = prim2(U, gam - Real(1));
-    const Real c = sqrt(gam * q.p * q.ir);
+    const Real c = fast_sqrt(gam * q.p * q.ir);
     sx = fabs(q.u) + c;
     sy = fabs(q.v) + c;
   }
@@ -136,10 +136,17 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
   constexpr int M = Dim2<EQ>::M;
   constexpr bool EUL = EQ == HWENO_EULER;
   constexpr int NP = kTileX2D + 4, NF = kTileX2D + 1;
-  __shared__ Real sU[M][NP], sV[M][NP];
-  __shared__ Real sFp[M][NP], sFm[M][NP], sHp[M][NP], sHm[M][NP], sEta[M][NP];
-  __shared__ Real sE[EUL ? 5 : 1][EUL ? NP : 1];  // sqrt(rho), u, v, H, c^2
-  __shared__ Real sF[M][NF], sD[M][NF], sN[M][NF];
+  __shared__ Real sU_[M][NP], sV_[M][NP];
+  __shared__ Real sFp_[M][NP], sFm_[M][NP], sHp_[M][NP], sHm_[M][NP], sEta_[M][NP];
+  __shared__ Real sE_[EUL ? 5 : 1][EUL ? NP : 1];  // sqrt(rho), u, v, H, c^2
+  __shared__ Real sF_[M][NF], sD_[M][NF], sN_[M][NF];
+  unsigned* const st = a.status;
+  const auto sU = tile_view(sU_, st), sV = tile_view(sV_, st);
+  const auto sFp = tile_view(sFp_, st), sFm = tile_view(sFm_, st);
+  const auto sHp = tile_view(sHp_, st), sHm = tile_view(sHm_, st);
+  const auto sEta = tile_view(sEta_, st);
+  const auto sE = tile_view(sE_, st);
+  const auto sF = tile_view(sF_, st), sD = tile_view(sD_, st), sN = tile_view(sN_, st);
 
   if (a.skip_done && !(a.t[0] < a.t_end)) return;
   const int nx = a.nx;
@@ -157,6 +164,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
   }
   const int i0 = tile * kTileX2D;
   const int np = min(kTileX2D, nx - i0);
+  HWENO_CHECK(np >= 1 && j >= 0 && j < a.ny, st);
   const long long row = (long long)j * nx;
   const Real* geo = pick<Real>(a.geod, a.geof);
   const Real dx = geo[0], idx = geo[1], idx2 = geo[2];
@@ -179,6 +187,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
     const Real hdx = Real(0.5) * dx;
     for (int g = threadIdx.x; g < np + 4; g += blockDim.x) {
       const Src s = map_x(i0 - 2 + g, nx, a.sp);
+      HWENO_CHECK(s.kind == 2 || (s.idx >= 0 && s.idx < nx), st);
       Real u[M], v[M], ww[M];
 #pragma unroll
       for (int c = 0; c < M; ++c) {
@@ -223,14 +232,14 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
   for (int jf = threadIdx.x; jf <= np; jf += blockDim.x) {
     const int gl = jf + 1;
     if constexpr (!EUL) {
-      sF[0][jf] = interface_flux(sFp[0][gl - 1], sFp[0][gl], sFp[0][gl + 1], sHp[0][gl - 1],
+      sF[0][jf] = interface_flux<Real, true>(sFp[0][gl - 1], sFp[0][gl], sFp[0][gl + 1], sHp[0][gl - 1],
                                  sHp[0][gl], sHp[0][gl + 1], sFm[0][gl], sFm[0][gl + 1],
                                  sFm[0][gl + 2], sHm[0][gl], sHm[0][gl + 1], sHm[0][gl + 2], w);
     } else {
       Real uu, vv, HH;
       if (a.sp.eig_avg == 0) {
         const Real sl = sE[0][gl], sr = sE[0][gl + 1];
-        const Real is = Real(1) / (sl + sr);
+        const Real is = recip(sl + sr);
         uu = (sl * sE[1][gl] + sr * sE[1][gl + 1]) * is;
         vv = (sl * sE[2][gl] + sr * sE[2][gl + 1]) * is;
         HH = (sl * sE[3][gl] + sr * sE[3][gl + 1]) * is;
@@ -246,8 +255,8 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
       Frac<Real> fr[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        auto pj = [&](Real (*A)[NP], int g) { return e.left(r, A[0][g], A[1][g], A[2][g], A[3][g]); };
-        fr[r] = interface_flux_frac(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1),
+        auto pj = [&](const auto& A, int g) { return e.left(r, A[0][g], A[1][g], A[2][g], A[3][g]); };
+        fr[r] = interface_flux_frac<Real, true>(pj(sFp, gl - 1), pj(sFp, gl), pj(sFp, gl + 1),
                                     pj(sHp, gl - 1), pj(sHp, gl), pj(sHp, gl + 1), pj(sFm, gl),
                                     pj(sFm, gl + 1), pj(sFm, gl + 2), pj(sHm, gl),
                                     pj(sHm, gl + 1), pj(sHm, gl + 2), w);
@@ -276,6 +285,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
   Real* VT = static_cast<Real*>(a.VT);
   for (int ip = threadIdx.x; ip < np; ip += blockDim.x) {
     const int g = ip + 2;
+    HWENO_CHECK(i0 + ip < nx, st);
     const long long q = row + i0 + ip;
     Real vt[M];
     if (a.sp.limiter == 0) {
@@ -289,16 +299,30 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
     } else if constexpr (EUL) {
       Char2<Real, 0> e;
       e.init(sE[1][g], sE[2][g], sE[3][g], sE[4][g], gm1);
-      Frac<Real> zr[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        auto pj = [&](Real (*A)[NP], int gg) { return e.left(r, A[0][gg], A[1][gg], A[2][gg], A[3][gg]); };
-        zr[r] = limited_derivative_frac(pj(sU, g - 1), pj(sU, g), pj(sU, g + 1),
-                                        dx * pj(sV, g - 1), dx * pj(sV, g + 1), w);
-      }
       Real z[4];
-      resolve2(zr[0], zr[1], z[0], z[1]);
-      resolve2(zr[2], zr[3], z[2], z[3]);
+      auto pj = [&](int r, const auto& A, int gg) {
+        return e.left(r, A[0][gg], A[1][gg], A[2][gg], A[3][gg]);
+      };
+      if constexpr (std::is_same<Real, float>::value) {  // two fields per packed pair
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r0 = 2 * h, r1 = 2 * h + 1;
+          auto p2 = [&](const auto& A, int gg) { return make_float2(pj(r0, A, gg), pj(r1, A, gg)); };
+          const float2 o = limited_derivative_pair(p2(sU, g - 1), p2(sU, g), p2(sU, g + 1),
+                                                   mul2(pair(dx), p2(sV, g - 1)),
+                                                   mul2(pair(dx), p2(sV, g + 1)), w);
+          z[r0] = o.x;
+          z[r1] = o.y;
+        }
+      } else {
+        Frac<Real> zr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          zr[r] = limited_derivative_frac(pj(r, sU, g - 1), pj(r, sU, g), pj(r, sU, g + 1),
+                                          dx * pj(r, sV, g - 1), dx * pj(r, sV, g + 1), w);
+        resolve2(zr[0], zr[1], z[0], z[1]);
+        resolve2(zr[2], zr[3], z[2], z[3]);
+      }
       e.right(z, vt);
 #pragma unroll
       for (int c = 0; c < 4; ++c) vt[c] *= idx;
@@ -341,11 +365,14 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
   constexpr int C = Lay::C, P = Lay::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
-  // point arrays: index [(q * P) + r * C + col]
-  auto PT = [&](int qty, int c) { return sm + (size_t)(qty * M + c) * P; };
-  Real* sEig = sm + (size_t)7 * M * P;  // 5 x P (Euler)
-  Real* sI = sm + (size_t)Lay::NQ * P;  // interface arrays [3M][RF][C]
-  auto IF = [&](int kind, int c) { return sI + (size_t)(kind * M + c) * Lay::RF * C; };
+  unsigned* const st = a.status;
+  // point arrays [7M][P]: quantity qty of component c at loaded point r * C + col
+  const auto sPts = tile_view<P>(sm, 7 * M, st);
+  auto PT = [&](int qty, int c) { return sPts[qty * M + c]; };
+  const auto sEig = tile_view<P>(sm + (size_t)7 * M * P, EUL ? 5 : 0, st);  // Euler: 5 x P
+  Real* sI = sm + (size_t)Lay::NQ * P;  // interface arrays [3M][RF * C]
+  const auto sIf = tile_view<Lay::RF * C>(sI, 3 * M, st);
+  auto IF = [&](int kind, int c) { return sIf[kind * M + c]; };
   __shared__ Real red[kThreads2D / 32];
   __shared__ double s_dt, s_ts;
 
@@ -357,7 +384,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
   static_assert(kRowsY2D * C <= kThreads2D, "one epilogue point per thread");
   // FP32: start the copies of this thread's epilogue inputs now, so that
   // their latency hides behind the loads and the interface phase
-  Real* sPre = sI + (size_t)Lay::NI * Lay::RF * C;  // [NPRE][PE]
+  const auto sPre = tile_view<Lay::PE>(sI + (size_t)Lay::NI * Lay::RF * C, Lay::NPRE, st);
   if constexpr (Lay::NPRE > 0) {
     const int k = threadIdx.x, r = k / C, col = k % C;
     if (k < Lay::PE && col < ncol && r < nrow) {
@@ -365,7 +392,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
       const Real* LX = static_cast<const Real*>(a.LX);
       const Real* VT = static_cast<const Real*>(a.VT);
       auto cp = [&](int f, const Real* src) {
-        __pipeline_memcpy_async(&sPre[f * Lay::PE + k], src, sizeof(Real));
+        __pipeline_memcpy_async(&sPre[f][k], src, sizeof(Real));
       };
 #pragma unroll
       for (int c = 0; c < M; ++c) {
@@ -412,6 +439,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
       if (col >= ncol || r >= nrow + 4) continue;
       const int i = i0 + col, jj = j0 - 2 + r;
       const Src s = map_y(jj, ny, i, a.x0, a.dx, a.y0, a.dy, ts, a.sp);
+      HWENO_CHECK(s.kind == 2 || (s.idx >= 0 && s.idx < ny && i < nx), st);
       Real u[M], v[M], ww[M];
 #pragma unroll
       for (int c = 0; c < M; ++c) {
@@ -443,11 +471,11 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
         PT(6, c)[k] = X[c];
       }
       if constexpr (EUL) {
-        sEig[0 * P + k] = u[0] * rsq(u[0]);
-        sEig[1 * P + k] = pq.u;
-        sEig[2 * P + k] = pq.v;
-        sEig[3 * P + k] = pq.Ep * pq.ir;
-        sEig[4 * P + k] = gam * pq.p * pq.ir;
+        sEig[0][k] = u[0] * rsq(u[0]);
+        sEig[1][k] = pq.u;
+        sEig[2][k] = pq.v;
+        sEig[3][k] = pq.Ep * pq.ir;
+        sEig[4][k] = gam * pq.p * pq.ir;
       }
     }
   }
@@ -458,9 +486,9 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
     const int r = k / C, col = k % C;
     if (col >= ncol || r > nrow) continue;
     const int gl = r + 1;
-    auto at = [&](const Real* A, int rr) { return A[rr * C + col]; };
+    auto at = [&](const auto& A, int rr) { return A[rr * C + col]; };
     if constexpr (!EUL) {
-      IF(0, 0)[k] = interface_flux(at(PT(2, 0), gl - 1), at(PT(2, 0), gl), at(PT(2, 0), gl + 1),
+      IF(0, 0)[k] = interface_flux<Real, true>(at(PT(2, 0), gl - 1), at(PT(2, 0), gl), at(PT(2, 0), gl + 1),
                                    at(PT(4, 0), gl - 1), at(PT(4, 0), gl), at(PT(4, 0), gl + 1),
                                    at(PT(3, 0), gl), at(PT(3, 0), gl + 1), at(PT(3, 0), gl + 2),
                                    at(PT(5, 0), gl), at(PT(5, 0), gl + 1), at(PT(5, 0), gl + 2), w);
@@ -468,11 +496,11 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
       Real uu, vv, HH;
       const int kl = gl * C + col, kr = (gl + 1) * C + col;
       if (a.sp.eig_avg == 0) {
-        const Real sl = sEig[kl], sr = sEig[kr];
-        const Real is = Real(1) / (sl + sr);
-        uu = (sl * sEig[P + kl] + sr * sEig[P + kr]) * is;
-        vv = (sl * sEig[2 * P + kl] + sr * sEig[2 * P + kr]) * is;
-        HH = (sl * sEig[3 * P + kl] + sr * sEig[3 * P + kr]) * is;
+        const Real sl = sEig[0][kl], sr = sEig[0][kr];
+        const Real is = recip(sl + sr);
+        uu = (sl * sEig[1][kl] + sr * sEig[1][kr]) * is;
+        vv = (sl * sEig[2][kl] + sr * sEig[2][kr]) * is;
+        HH = (sl * sEig[3][kl] + sr * sEig[3][kr]) * is;
       } else {
         Real Um[4];
 #pragma unroll
@@ -489,7 +517,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
           const int kk = g * C + col;
           return e.left(rr, PT(qty, 0)[kk], PT(qty, 1)[kk], PT(qty, 2)[kk], PT(qty, 3)[kk]);
         };
-        fr[rr] = interface_flux_frac(pj(2, gl - 1), pj(2, gl), pj(2, gl + 1), pj(4, gl - 1),
+        fr[rr] = interface_flux_frac<Real, true>(pj(2, gl - 1), pj(2, gl), pj(2, gl + 1), pj(4, gl - 1),
                                      pj(4, gl), pj(4, gl + 1), pj(3, gl), pj(3, gl + 1),
                                      pj(3, gl + 2), pj(5, gl), pj(5, gl + 1), pj(5, gl + 2), w);
       }
@@ -524,10 +552,11 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
     if (col >= ncol || r >= nrow) continue;
     const int g = r + 2;
     const int kc = g * C + col;
+    HWENO_CHECK(j0 + r < ny && i0 + col < nx, st);
     const long long q = (long long)(j0 + r) * nx + i0 + col;
     // an epilogue input: prefetched (FP32) or read here
     auto in = [&](int f, const Real* src) -> Real {
-      if constexpr (Lay::NPRE > 0) return sPre[f * Lay::PE + k];
+      if constexpr (Lay::NPRE > 0) return sPre[f][k];
       else return *src;
     };
     Real l1[M], l2[M], l3[M], vt[M], wt[M], u[M];
@@ -550,19 +579,31 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
                                    dy * PT(1, c)[kc - C], dy * PT(1, c)[kc + C], w) * idy;
     } else if constexpr (EUL) {
       Char2<Real, 1> e;
-      e.init(sEig[P + kc], sEig[2 * P + kc], sEig[3 * P + kc], sEig[4 * P + kc], gm1);
-      Frac<Real> zr[4];
-#pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        auto pj = [&](int qty, int kk) {
-          return e.left(rr, PT(qty, 0)[kk], PT(qty, 1)[kk], PT(qty, 2)[kk], PT(qty, 3)[kk]);
-        };
-        zr[rr] = limited_derivative_frac(pj(0, kc - C), pj(0, kc), pj(0, kc + C),
-                                         dy * pj(1, kc - C), dy * pj(1, kc + C), w);
-      }
+      e.init(sEig[1][kc], sEig[2][kc], sEig[3][kc], sEig[4][kc], gm1);
       Real z[4];
-      resolve2(zr[0], zr[1], z[0], z[1]);
-      resolve2(zr[2], zr[3], z[2], z[3]);
+      auto pj = [&](int rr, int qty, int kk) {
+        return e.left(rr, PT(qty, 0)[kk], PT(qty, 1)[kk], PT(qty, 2)[kk], PT(qty, 3)[kk]);
+      };
+      if constexpr (std::is_same<Real, float>::value) {  // two fields per packed pair
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r0 = 2 * h, r1 = 2 * h + 1;
+          auto p2 = [&](int qty, int kk) { return make_float2(pj(r0, qty, kk), pj(r1, qty, kk)); };
+          const float2 o = limited_derivative_pair(p2(0, kc - C), p2(0, kc), p2(0, kc + C),
+                                                   mul2(pair(dy), p2(1, kc - C)),
+                                                   mul2(pair(dy), p2(1, kc + C)), w);
+          z[r0] = o.x;
+          z[r1] = o.y;
+        }
+      } else {
+        Frac<Real> zr[4];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+          zr[rr] = limited_derivative_frac(pj(rr, 0, kc - C), pj(rr, 0, kc), pj(rr, 0, kc + C),
+                                           dy * pj(rr, 1, kc - C), dy * pj(rr, 1, kc + C), w);
+        resolve2(zr[0], zr[1], z[0], z[1]);
+        resolve2(zr[2], zr[3], z[2], z[3]);
+      }
       e.right(z, wt);
 #pragma unroll
       for (int c = 0; c < 4; ++c) wt[c] *= idy;

@@ -15,9 +15,11 @@ from typing import Optional, Sequence
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libhweno.so")
+# HWENO_LIBRARY selects another build of the library (the checked build of
+# the tests: _build_checked/libhweno.so)
+LIB_PATH = os.environ.get("HWENO_LIBRARY") or os.path.join(_PKG, "_build", "libhweno.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTSUP, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 BURGERS, EULER, BUCKLEY = 0, 1, 2
 EQUATIONS = dict(burgers=BURGERS, euler=EULER, buckley=BUCKLEY)
 FP64, FP32 = 0, 1
@@ -26,7 +28,7 @@ MAX_SIZE_CLASSES = 16  # HWENO_MAX_SIZE_CLASSES
 CLUSTER_MAX_POINTS = 992  # HWENO_CLUSTER_MAX_POINTS: fused_small = 2
 BC = dict(periodic=0, outflow=1, reflective=2, inflow=3, dmr_bottom=4, dmr_top=5)
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
-          ETIMEOUT: "ETIMEOUT", ENOTSUP: "ENOTSUP"}
+          ETIMEOUT: "ETIMEOUT", ENOTSUP: "ENOTSUP", EBOUNDS: "EBOUNDS"}
 
 
 class HwenoError(RuntimeError):
