@@ -67,22 +67,26 @@ ALGO_WORDS_PER_COMPONENT = {1: 17, 2: 26}
 # MEASURED_PEAKS.json): FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flop
 # x 2.07 GHz.
 PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
-# DRAM bytes per point and launch of the fused stage kernel from an ncu
-# capture of a stage-1 launch of the 128-thread, 2-points-per-thread tile
-# (dram__bytes_read.sum + dram__bytes_write.sum over points;
-# profiles/k_stage_1d_euler_fp{64,32}_riemann_batch.md). An entry is removed
-# whenever the kernel changes after its capture.
+# DRAM traffic constants from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over the points it processed) on cases
+# whose working set exceeds the 129 MB L2; the bench scales them by the
+# points of its own launch. An entry is set to None whenever its kernel
+# changes after the capture (profiles/ holds the commands and the raw
+# figures).
+# Stage kernel, per point and launch (FP32: the 2048-instance batch, one
+# graph-replay launch of the chosen tile).
 MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": None, "fp32": None}
-# DRAM bytes per point-step of the persistent kernel (all three stages), from
-# an ncu capture (profiles/k_run_1d_euler_fp64_riemann_batch.md); None until
-# taken for the kernel as it stands (FP32: the 1024-instance capture batch
-# fits in L2, so its counters do not scale to the larger batch).
-MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": None, "fp32": None}
-# DRAM bytes per point of one 2D stage (x-sweep + y-sweep launches) on the
-# smooth periodic problem at 2048^2, from an ncu capture
-# (profiles/k_sweeps_2d_euler_fp64_smooth.md); applied to grids whose working
-# set exceeds the L2 (smaller grids keep part of it in L2).
-MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {"fp64": None, "fp32": None}
+# Persistent kernel, per point-step (all three stages; FP64: 1024 instances,
+# 1 283 400 points, one launch of 2 steps).
+MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.4, "fp32": None}
+# One 2D stage (x-sweep + y-sweep launches of stage 1) per point, per
+# workload and precision (smooth Euler at 1024^2, double Mach at 1920x480);
+# applied to grids whose working set exceeds the L2.
+MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64"): 505.1,
+                                       ("euler2d_smooth", "fp32"): 221.8,
+                                       ("double_mach", "fp64"): 489.7}
+# One 2D Euler adjoint step (six reverse sweeps) per point, 512^2.
+MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP = {("euler", 2): 1858.1}
 
 
 def parse():
@@ -457,8 +461,8 @@ def run_ours(args, rank, world, dev_index):
     peak = PEAK_TFLOPS[args.precision]
     traffic = (MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
                if args.workload == "riemann_batch" else
-               MEASURED_STAGE_TRAFFIC_2D_PER_POINT.get(args.precision)
-               if args.workload.startswith("euler2d_smooth") and not small
+               MEASURED_STAGE_TRAFFIC_2D_PER_POINT.get((w.name, args.precision))
+               if w.dim == 2 and not small
                else None)  # None: not captured for this workload
     if use_clus:  # the headline kernel: one cluster launch per step
         achieved = ALGO_FLOPS_PER_POINT_STEP[(w.equation, w.dim)] * clus[1] / (clus[3] * 1e-3) / 1e12
@@ -776,7 +780,9 @@ def run_adjoint(args, rank, world, dev_index):
            "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": PEAK_TFLOPS["fp64"],
                         "unit": "TFLOP/s", "frac": round(ach / PEAK_TFLOPS["fp64"], 4),
                         "dfma_loop_tflops": round(fp64_loop, 4),
-                        "frac_of_dfma_loop": round(ach / fp64_loop, 4), "traffic": None,
+                        "frac_of_dfma_loop": round(ach / fp64_loop, 4),
+                        "traffic": (None if key not in MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP
+                                    else MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP[key] * npts),
                         "kernel": "hweno_adjoint_step (reverse stages 3, 2, 1; %d launches)"
                                   % launches,
                         "flops_per_point_step": ALGO_ADJOINT_FLOPS_PER_POINT_STEP[key],
@@ -919,8 +925,9 @@ def _compact(out):
 
 
 def other_configs(args, dev_index):
-    """Configs 1, 3, 4 (FP64 and FP32) and the 2D adjoint step (config 5),
-    each with its own roofline, for the headline line."""
+    """Configs 1, 3, 4 (FP64 and FP32) and the adjoint steps of config 5
+    (2D Euler 512^2 and the batch of 256 Burgers problems, N = 800), each
+    with its own roofline, for the headline line."""
     import copy
     res = {}
     for key, wl, precs, K, Wm in OTHER_CONFIGS:
@@ -929,9 +936,11 @@ def other_configs(args, dev_index):
             a.workload, a.precision, a.no_extras, a.steps, a.warmup = wl, prec, True, K, Wm
             out, _ = run_ours(a, 0, 1, dev_index)
             res.setdefault(key, {})[prec] = _compact(out)
-    a = copy.copy(args)
-    a.workload, a.steps, a.warmup, a.fd_directions, a.light = "euler2d_adjoint:512", 5, 2, 0, True
-    res["euler2d_adjoint_512"] = _compact(run_adjoint(a, 0, 1, dev_index))
+    for key, wl, K in (("euler2d_adjoint_512", "euler2d_adjoint:512", 5),
+                       ("burgers_adjoint_256x800", "burgers_adjoint:256x800", 10)):
+        a = copy.copy(args)
+        a.workload, a.steps, a.warmup, a.fd_directions, a.light = wl, K, 2, 0, True
+        res[key] = _compact(run_adjoint(a, 0, 1, dev_index))
     return res
 
 

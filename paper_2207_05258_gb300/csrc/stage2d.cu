@@ -382,10 +382,11 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
   const int i0 = blockIdx.x * C, j0 = blockIdx.y * kRowsY2D;
   const int ncol = min(C, nx - i0), nrow = min(kRowsY2D, ny - j0);
   static_assert(kRowsY2D * C <= kThreads2D, "one epilogue point per thread");
-  // FP32: start the copies of this thread's epilogue inputs now, so that
-  // their latency hides behind the loads and the interface phase
+  // FP32: copies of this thread's epilogue inputs, started asynchronously
+  // after the tile's own loads (below), so that their latency hides behind
+  // the point and interface phases
   const auto sPre = tile_view<Lay::PE>(sI + (size_t)Lay::NI * Lay::RF * C, Lay::NPRE, st);
-  if constexpr (Lay::NPRE > 0) {
+  auto prefetch_epilogue = [&]() {
     const int k = threadIdx.x, r = k / C, col = k % C;
     if (k < Lay::PE && col < ncol && r < nrow) {
       const long long q = (long long)(j0 + r) * nx + i0 + col;
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
       }
     }
     __pipeline_commit();
-  }
+  };
   const Real* geo = pick<Real>(a.geod, a.geof);
   const Real dy = geo[3], idy = geo[4], idy2 = geo[5];
   const Real alpha = Real(a.alpha_in[1]);
@@ -434,20 +435,61 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
     const Real* V = static_cast<const Real*>(a.V);
     const Real* W = static_cast<const Real*>(a.W);
     const Real hdy = Real(0.5) * dy;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    // FP32: every load of the tile is issued first, as asynchronous copies
+    // into the slots the values occupy anyway (U and W in quantities 0 and
+    // 1; V in quantity 6, which this thread overwrites with xi = A_y V of
+    // the same point), so that their latencies overlap; the epilogue inputs
+    // follow. Each thread then reads only the points it copied itself.
+    constexpr int ITER = (P + kThreads2D - 1) / kThreads2D;
+    Src src[ITER];
+    if constexpr (Lay::NPRE > 0) {
+#pragma unroll
+      for (int it = 0; it < ITER; ++it) {
+        const int k = threadIdx.x + it * kThreads2D;
+        const int r = k / C, col = k % C;
+        if (k >= P || col >= ncol || r >= nrow + 4) continue;
+        const int i = i0 + col, jj = j0 - 2 + r;
+        src[it] = map_y(jj, ny, i, a.x0, a.dx, a.y0, a.dy, ts, a.sp);
+        HWENO_CHECK(src[it].kind == 2 || (src[it].idx >= 0 && src[it].idx < ny && i < nx), st);
+        if (src[it].kind != 2) {
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            const long long q = c * N + (long long)src[it].idx * nx + i;
+            __pipeline_memcpy_async(&PT(0, c)[k], U + q, sizeof(Real));
+            __pipeline_memcpy_async(&PT(1, c)[k], W + q, sizeof(Real));
+            __pipeline_memcpy_async(&PT(6, c)[k], V + q, sizeof(Real));
+          }
+        }
+      }
+      __pipeline_commit();
+      prefetch_epilogue();
+      __pipeline_wait_prior(1);  // this thread's tile copies (the epilogue's may still run)
+    }
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+      const int k = threadIdx.x + it * kThreads2D;
       const int r = k / C, col = k % C;
-      if (col >= ncol || r >= nrow + 4) continue;
-      const int i = i0 + col, jj = j0 - 2 + r;
-      const Src s = map_y(jj, ny, i, a.x0, a.dx, a.y0, a.dy, ts, a.sp);
-      HWENO_CHECK(s.kind == 2 || (s.idx >= 0 && s.idx < ny && i < nx), st);
+      if (k >= P || col >= ncol || r >= nrow + 4) continue;
+      const int i = i0 + col;
+      Src s;
+      if constexpr (Lay::NPRE > 0) {
+        s = src[it];
+      } else {
+        s = map_y(j0 - 2 + r, ny, i, a.x0, a.dx, a.y0, a.dy, ts, a.sp);
+        HWENO_CHECK(s.kind == 2 || (s.idx >= 0 && s.idx < ny && i < nx), st);
+      }
       Real u[M], v[M], ww[M];
 #pragma unroll
       for (int c = 0; c < M; ++c) {
         if (s.kind == 2) {
           u[c] = Real(imposed(a.sp, s, c)); v[c] = Real(0); ww[c] = Real(0);
         } else {
-          const long long q = c * N + (long long)s.idx * nx + i;
-          u[c] = U[q]; v[c] = V[q]; ww[c] = W[q];
+          if constexpr (Lay::NPRE > 0) {
+            u[c] = PT(0, c)[k]; v[c] = PT(6, c)[k]; ww[c] = PT(1, c)[k];
+          } else {
+            const long long q = c * N + (long long)s.idx * nx + i;
+            u[c] = U[q]; v[c] = V[q]; ww[c] = W[q];
+          }
           if (s.kind == 1) {
             const Real sg = Real(refl2<EQ, 1>(c));
             u[c] *= sg; ww[c] *= -sg; v[c] *= sg;

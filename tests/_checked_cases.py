@@ -134,6 +134,18 @@ def main():
             s.sync_status()
             assert all(torch.isfinite(x).all() for x in lam)
         s.close()
+        # FP32 (packed pairs, asynchronous tile copies in the y-sweep)
+        s = hw.Solver.from_workload(w, precision="fp32")
+        f32 = lambda x: dev(x).float()
+        U, V, Wd = f32(w.U), f32(w.V), f32(w.W)
+        s.rhs(U, V, Wd)
+        t = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            s.step(U, V, Wd, t, w.t_end)
+        s.sync_status()
+        g = U.double().cpu().numpy().reshape(Uo.shape)
+        assert np.max(np.abs(g - Uo)) <= 1e-4 * np.max(np.abs(Uo)), ("2d fp32", w.name)
+        s.close()
     # the checks are live: the self-test latches HWENO_EBOUNDS, and the
     # context works afterwards
     w = batch_1d("burgers", "periodic", 3)
