@@ -78,13 +78,14 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": None, "fp32": None}
 # Persistent kernel, per point-step (all three stages; FP64: 1024 instances,
 # 1 283 400 points, one launch of 2 steps).
-MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.4, "fp32": None}
-# One 2D stage (x-sweep + y-sweep launches of stage 1) per point, per
-# workload and precision (smooth Euler at 1024^2, double Mach at 1920x480);
-# applied to grids whose working set exceeds the L2.
-MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64"): 505.1,
-                                       ("euler2d_smooth", "fp32"): 221.8,
-                                       ("double_mach", "fp64"): 489.7}
+MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": None, "fp32": None}
+# One 2D stage per point, per workload, precision and stage form (0: the
+# x-sweep + y-sweep launches of stage 1, 1: the fused stage-1 launch; smooth
+# Euler at 1024^2, double Mach at 1920x480); applied to grids whose working
+# set exceeds the L2.
+MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64", 0): None,
+                                       ("euler2d_smooth", "fp32", 0): None,
+                                       ("double_mach", "fp64", 0): None}
 # One 2D Euler adjoint step (six reverse sweeps) per point, 512^2.
 MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP = {("euler", 2): 1858.1}
 
@@ -107,6 +108,9 @@ def parse():
                     help="adjoint workloads: seeded directions checked by central differences")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, fp32 and cpu_baseline legs and the other workloads")
+    ap.add_argument("--stage-2d", choices=["auto", "split", "fused"], default="auto",
+                    help="2D stage form: auto (hweno_autotune times both and keeps the "
+                         "faster), split (x-sweep + y-sweep launches) or fused (one launch)")
     ap.add_argument("--adjoint-steps-only", dest="light", action="store_true",
                     help="adjoint workloads: time the adjoint steps only (no full gradient, "
                          "no finite-difference checks)")
@@ -218,6 +222,18 @@ def describe(w):
             % (w.nx[0], w.ny))
 
 
+def _r4(x):
+    return None if x is None else round(x, 4)
+
+
+def traffic32(w, small, form, pts):
+    """DRAM bytes of one FP32 stage launch (None where not captured)."""
+    per = (MEASURED_STAGE_TRAFFIC_PER_POINT["fp32"] if w.dim == 1 and w.name == "riemann_batch"
+           else MEASURED_STAGE_TRAFFIC_2D_PER_POINT.get((w.name, "fp32", form))
+           if w.dim == 2 and not small else None)
+    return None if per is None else per * pts
+
+
 def working_set_mb(w, precision):
     """State plus library stage buffers touched by one step."""
     fields = 2 + 5 if w.dim == 1 else 3 + 8 + 4  # 2D adds W and the x-sweep scratch
@@ -238,7 +254,10 @@ def run_ours(args, rank, world, dev_index):
         (b) with profile, K more plain steps, each bracketed by CUDA events with
         the kernels timed by the library's events and an L2 flush between
         steps (roofline and the no-graph comparison)."""
-        s = hweno.Solver.from_workload(w, precision=precision)
+        force = (None if w.dim == 1 or args.stage_2d == "auto"
+                 else int(args.stage_2d == "fused"))
+        s = hweno.Solver.from_workload(w, precision=precision,
+                                       **({} if force is None else {"fused_2d": force}))
         dt_t = torch.float64 if precision == "fp64" else torch.float32
         stream = torch.cuda.Stream()
         with torch.cuda.stream(stream):
@@ -250,7 +269,10 @@ def run_ours(args, rank, world, dev_index):
             for _ in range(Wm):
                 s.step(U, V, Wd, t, w.t_end)
             s.sync_status()
-            tune = s.autotune(U, V, Wd, t, w.t_end)  # tile shape (1D); reads the state only
+            # 1D: the tile shape; 2D: the split or the fused stage form (reads the
+            # state only)
+            tune = (s.autotune(U, V, Wd, t, w.t_end) if force is None
+                    else (force, [None, None]))
             s.run_graph(U, V, Wd, t, w.t_end, max_steps=0, steps_per_launch=K)  # record
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             if world > 1:
@@ -454,14 +476,15 @@ def run_ours(args, rank, world, dev_index):
     stage_ms, stage_n = prof["stage"]
     pts_per_stage = pu_ng / args.steps  # points per stage in the profiled pass (this rank)
     flop_stage = ALGO_FLOPS_PER_POINT_STEP[(w.equation, w.dim)] / 3.0
-    # a 2D stage is two launches (x- and y-sweep): time per stage = 2 launches
-    launches_per_stage = 1 if w.dim == 1 else 2
+    # a split 2D stage is two launches (x- and y-sweep), a fused one is one
+    fused2d = w.dim == 2 and tune[0] == 1
+    launches_per_stage = 1 if (w.dim == 1 or fused2d) else 2
     stage_time = stage_ms / stage_n * launches_per_stage * 1e-3
     achieved = flop_stage * pts_per_stage / stage_time / 1e12
     peak = PEAK_TFLOPS[args.precision]
     traffic = (MEASURED_STAGE_TRAFFIC_PER_POINT.get(args.precision)
                if args.workload == "riemann_batch" else
-               MEASURED_STAGE_TRAFFIC_2D_PER_POINT.get((w.name, args.precision))
+               MEASURED_STAGE_TRAFFIC_2D_PER_POINT.get((w.name, args.precision, tune[0]))
                if w.dim == 2 and not small
                else None)  # None: not captured for this workload
     if use_clus:  # the headline kernel: one cluster launch per step
@@ -481,6 +504,8 @@ def run_ours(args, rank, world, dev_index):
                                                                      args.steps) if use_pers else
                        "k_step_cluster_1d<%s,%s>" % (w.equation, args.precision) if use_clus else
                        "k_stage_1d<%s,%s>" % (w.equation, args.precision) if w.dim == 1 else
+                       "k_stage_2d<%s,%s> (fused x and y parts)" % (w.equation, args.precision)
+                       if fused2d else
                        "k_xsweep_2d + k_ysweep_2d <%s,%s>" % (w.equation, args.precision)),
             "kernel_share_of_step": (round(pers[3] / pers[0], 4) if use_pers else
                                      round(clus[3] / clus[0], 4) if use_clus else
@@ -519,7 +544,12 @@ def run_ours(args, rank, world, dev_index):
                                  if small else timing_note),
                       "tile_variant": tune[0] if w.dim == 1 else None,
                       "size_classes": getattr(timed, "cls", None),
-                      "autotune_stage1_ms": [round(x, 4) for x in tune[1]] if w.dim == 1 else None,
+                      "autotune_stage1_ms": ([round(x, 4) for x in tune[1]] if w.dim == 1 else
+                                             {"split": _r4(tune[1][0]),
+                                              "fused": _r4(tune[1][1])}),
+                      **({"stage_form_2d": ("fused" if fused2d else "split") +
+                          (" (autotuned)" if args.stage_2d == "auto" else " (forced)")}
+                         if w.dim == 2 else {}),
                       "parallelism": "replicas (one seeded batch per rank)"},
            "roofline": roof, "clocks": clocks, "gpu_launches": launches,
            "point_updates_timed": pu}
@@ -528,20 +558,24 @@ def run_ours(args, rank, world, dev_index):
         # FP32 variant of the same workload (state and reconstruction in FP32)
         if args.precision == "fp64":
             ms32, pu32, prof32, _, _, pu32_ng = timed("fp32", args.steps, args.warmup, True)
-            st32 = prof32["stage"][0] / prof32["stage"][1] * launches_per_stage * 1e-3
+            f32 = w.dim == 2 and timed.tune[0] == 1  # the form chosen for FP32
+            st32 = prof32["stage"][0] / prof32["stage"][1] * (1 if (w.dim == 1 or f32) else 2) * 1e-3
             ach32 = flop_stage * (pu32_ng / args.steps) / st32 / 1e12
             out["fp32"] = {"value": round(pu32 / (ms32 * 1e-3) / 1e6, 3),
+                           **({"stage_form_2d": "fused" if f32 else "split",
+                               "autotune_stage1_ms": {"split": _r4(timed.tune[1][0]),
+                                                      "fused": _r4(timed.tune[1][1])}}
+                              if w.dim == 2 else {}),
                            "ms_per_step": round(ms32 / args.steps, 4),
                            "stage_kernel_ms": round(prof32["stage"][0] / prof32["stage"][1], 4),
                            "roofline": {
                                "bound": "alu", "achieved": round(ach32, 4),
                                "peak": round(PEAK_TFLOPS["fp32"], 2), "unit": "TFLOP/s",
                                "frac": round(ach32 / PEAK_TFLOPS["fp32"], 4),
-                               "traffic": (None if MEASURED_STAGE_TRAFFIC_PER_POINT["fp32"] is None
-                                           or args.workload != "riemann_batch" else
-                                           MEASURED_STAGE_TRAFFIC_PER_POINT["fp32"] *
-                                           pu32_ng / args.steps),
+                               "traffic": traffic32(w, small, timed.tune[0], pu32_ng / args.steps),
                                "kernel": ("k_stage_1d<%s,fp32>" % w.equation if w.dim == 1 else
+                                          "k_stage_2d<%s,fp32> (fused x and y parts)" % w.equation
+                                          if f32 else
                                           "k_xsweep_2d + k_ysweep_2d <%s,fp32>" % w.equation),
                                "flops_per_point_stage": round(flop_stage, 2),
                                "peak_source": "unit counts (recipe): 152 SM x 128 FP32 lanes x "
@@ -918,8 +952,8 @@ def _compact(out):
     c = {k: out[k] for k in keep if k in out}
     cfg = out.get("config", {})
     c["workload"] = cfg.get("workload")
-    for k in ("timing", "l2"):
-        if k in cfg:
+    for k in ("timing", "l2", "stage_form_2d", "autotune_stage1_ms"):
+        if k in cfg and not (k == "autotune_stage1_ms" and isinstance(cfg[k], list)):
             c[k] = cfg[k]
     return c
 

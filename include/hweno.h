@@ -116,8 +116,8 @@ typedef struct hweno_grid {
 
 /* Scheme options. hweno_default_options fills the paper's values (Sec. 3):
  * lin_w = lim_d = {0.98, 0.01, 0.01}, eps = 1e-6, cfl = 0.6,
- * dt_mode = 0, limiter = 1, eig_avg = 0, tile_variant = 0, fused_small = 0
- * and adj_frozen_weights = 0. */
+ * dt_mode = 0, limiter = 1, eig_avg = 0, tile_variant = 0, fused_small = 0,
+ * adj_frozen_weights = 0 and fused_2d = 0. */
 typedef struct hweno_options {
   double lin_w[3]; /* gamma_0..2 of the reconstruction: >= 1e-6 each, sum 1 (Sec. 2.1) */
   double lim_d[3]; /* d_0..2 of the limiter: >= 1e-6 each, sum 1 (Sec. 2.2) */
@@ -171,6 +171,13 @@ typedef struct hweno_options {
                        nonlinear weights of the reconstruction and the
                        limiter; 1 = hold them at their forward values (the
                        adjoint of the scheme linearised with frozen weights) */
+  int fused_2d;     /* 2D steps: 0 = per stage an x-sweep and a y-sweep launch
+                       (the x parts pass through library scratch); 1 = one
+                       fused launch per stage, one CTA per 16 x 7 block doing
+                       both directions (the x-interfaces on block edges are
+                       computed by both neighbours). Results agree to
+                       rounding; hweno_autotune picks the faster form for the
+                       caller's grid. hweno_rhs always uses the sweeps. */
 } hweno_options;
 
 /* Largest instance of the cluster step (fused_small = 2): 8 tiles of 124. */
@@ -304,8 +311,10 @@ int hweno_test_inject(hweno_ctx* ctx, int kind);
  * receives the variant index (0 = the default 128 x 1; variants 1..4 are
  * 64 x 1, 256 x 1, 128 x 2 and 64 x 2, threads x points per thread);
  * ms (host, nullable, HWENO_TILE_VARIANTS doubles) the best measured time of
- * each variant in milliseconds. In 2D
- * there is a single tile shape: *chosen = 0 and nothing is measured. */
+ * each variant in milliseconds. In 2D the two forms of a stage are timed
+ * instead (the x- and y-sweep launches, and the fused launch; stage 1 on
+ * the given state) and the faster is kept as fused_2d: *chosen receives 0
+ * or 1 and ms[0], ms[1] their times. */
 int hweno_autotune(hweno_ctx* ctx, const void* U, const void* V, const void* W, const double* t,
                    double t_end, int* chosen, double* ms, void* stream);
 

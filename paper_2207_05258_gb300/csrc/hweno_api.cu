@@ -154,6 +154,10 @@ int check_options(const hweno_options* o, std::string& why) {
     why = "adj_frozen_weights must be 0 or 1";
     return HWENO_EINVAL;
   }
+  if (o->fused_2d < 0 || o->fused_2d > 1) {
+    why = "fused_2d must be 0 or 1";
+    return HWENO_EINVAL;
+  }
   if (o->tile_variant < 0 || o->tile_variant >= kNumVariants1D) {
     why = "tile_variant out of range";
     return HWENO_EINVAL;
@@ -563,8 +567,27 @@ Args2D base_args_2d(const hweno_ctx* c) {
   return a;
 }
 
-// One SSP-RK3 step in 2D: alpha(U^n); per stage an x-sweep (x parts of L and
-// v~ into scratch) and a y-sweep (y parts, w~, RK combination, next alpha).
+// One stage of a 2D step: an x-sweep (x parts of L and v~ into scratch) and
+// a y-sweep (y parts, w~, RK combination, next alpha), or the fused stage
+// kernel (fused_2d); each launch bracketed for hweno_profile_*.
+cudaError_t stage_2d(hweno_ctx* c, int mode, const Args2D& a, cudaStream_t s) {
+  cudaError_t e;
+  if (c->opt.fused_2d) {
+    prof_begin(c, s);
+    if ((e = launch_stage_fused_2d(c->eq, c->fp32, mode, a, s))) return e;
+    prof_end(c, s, 1);
+    return cudaSuccess;
+  }
+  prof_begin(c, s);
+  if ((e = launch_xsweep_2d(c->eq, c->fp32, mode, a, s))) return e;
+  prof_end(c, s, 1);
+  prof_begin(c, s);
+  if ((e = launch_ysweep_2d(c->eq, c->fp32, mode, a, s))) return e;
+  prof_end(c, s, 1);
+  return cudaSuccess;
+}
+
+// One SSP-RK3 step in 2D: alpha(U^n); per stage the x and y parts.
 int step_2d(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end, double* dt_used,
             cudaStream_t s) {
   cudaError_t e;
@@ -595,12 +618,7 @@ int step_2d(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end, do
     a.stage_c = st[k].sc;
     a.alpha_in = reinterpret_cast<const double*>(c->d_alpha + 2 * st[k].slot_in);
     a.alpha_out = k < 2 ? c->d_alpha + 2 * (k + 1) : nullptr;
-    prof_begin(c, s);
-    if ((e = launch_xsweep_2d(c->eq, c->fp32, mode, a, s))) return cuda_fail(c, e, "x-sweep");
-    prof_end(c, s, 1);
-    prof_begin(c, s);
-    if ((e = launch_ysweep_2d(c->eq, c->fp32, mode, a, s))) return cuda_fail(c, e, "y-sweep");
-    prof_end(c, s, 1);
+    if ((e = stage_2d(c, mode, a, s))) return cuda_fail(c, e, "stage");
   }
   prof_begin(c, s);
   if ((e = launch_finalize(1, c->d_dt, c->d_lands, t, t_end, dt_used,
@@ -608,7 +626,7 @@ int step_2d(hweno_ctx* c, void* U, void* V, void* W, double* t, double t_end, do
                            c->d_status, c->d_inst_n, c->ny, c->d_pu, s)))
     return cuda_fail(c, e, "finalize");
   prof_end(c, s, 2);
-  c->launches = c->step_launches = 8;
+  c->launches = c->step_launches = c->opt.fused_2d ? 5 : 8;
   return HWENO_OK;
 }
 
@@ -1225,13 +1243,49 @@ int hweno_autotune(hweno_ctx* c, const void* U, const void* V, const void* W, co
                    double t_end, int* chosen, double* ms, void* stream) {
   if (!c) return HWENO_EINVAL;
   if (!U || !V || !t) return fail(c, HWENO_EINVAL, "null array");
-  if (c->dim == 2) {  // one tile shape in 2D
-    if (chosen) *chosen = 0;
-    return HWENO_OK;
-  }
-  (void)W;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0 = c->tune_ev[0], e1 = c->tune_ev[1];
+  if (c->dim == 2) {  // the split and the fused form of a stage
+    if (!W) return fail(c, HWENO_EINVAL, "W required in 2D");
+    Args2D a = base_args_2d(c);
+    a.t = t; a.t_end = t_end; a.skip_done = 1;
+    a.U = U; a.alpha_out = c->d_alpha;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_alpha, 0, sizeof(unsigned long long) * 6, s)) ||
+        (e = launch_alpha_2d(c->eq, c->fp32, a, s)))
+      return cuda_fail(c, e, "autotune");
+    a.V = V; a.W = W; a.U0 = U; a.Vt0 = c->d_Vt0; a.Wt0 = c->d_Wt0;
+    a.Uout = c->d_U1; a.Vout = c->d_V1; a.Wout = c->d_W1; a.Wt0out = c->d_Wt0; a.VT = c->d_Vt0;
+    a.stage_c = 0.0;
+    a.alpha_in = reinterpret_cast<const double*>(c->d_alpha);
+    a.alpha_out = c->d_alpha + 2;
+    const int keep = c->opt.fused_2d;
+    float best_ms[2] = {1e30f, 1e30f};
+    for (int f = 0; f < 2; ++f) {
+      c->opt.fused_2d = f;
+      for (int r = 0; r < 4; ++r) {  // first launch warms up, then the best of three
+        cudaEventRecord(e0, s);
+        if ((e = stage_2d(c, MODE_STAGE1, a, s))) {
+          c->opt.fused_2d = keep;
+          return cuda_fail(c, e, "autotune");
+        }
+        cudaEventRecord(e1, s);
+        if ((e = cudaEventSynchronize(e1))) {
+          c->opt.fused_2d = keep;
+          return cuda_fail(c, e, "autotune");
+        }
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        if (r > 0) best_ms[f] = std::min(best_ms[f], x);
+      }
+      if (ms) ms[f] = best_ms[f];
+    }
+    c->opt.fused_2d = best_ms[1] < best_ms[0] ? 1 : 0;
+    if (c->graph) cudaGraphExecDestroy(c->graph);  // recorded for the other form
+    c->graph = nullptr;
+    if (chosen) *chosen = c->opt.fused_2d;
+    return hweno_sync_status(c, stream);
+  }
   int best = 0;
   float best_ms = 1e30f;
   int rc = HWENO_OK;
@@ -1471,8 +1525,8 @@ int adjoint_2d(hweno_ctx* c, const void* U, const void* V, const void* W, const 
       a.stage_c = st[k].sc;
       a.alpha_in = reinterpret_cast<const double*>(c->d_alpha + 2 * k);
       a.alpha_out = c->d_alpha + 2 * (k + 1);
-      if ((e = launch_xsweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay x");
-      if ((e = launch_ysweep_2d(c->eq, false, mode, a, s))) return cuda_fail(c, e, "replay y");
+      // the same form as the forward step, so that a replay gives a record's bits
+      if ((e = stage_2d(c, mode, a, s))) return cuda_fail(c, e, "replay");
     }
   }
   // 2. reverse stages 3, 2, 1: an x sweep into `part`, then a y sweep
@@ -1513,7 +1567,8 @@ int adjoint_2d(hweno_ctx* c, const void* U, const void* V, const void* W, const 
     if ((e = launch_adjoint_2d(c->eq, 0, g, s))) return cuda_fail(c, e, "adjoint x");
     if ((e = launch_adjoint_2d(c->eq, 1, g, s))) return cuda_fail(c, e, "adjoint y");
   }
-  c->launches = replay ? 11 : 6;
+  // replay: the wave speed and two stages of one (fused) or two launches each
+  c->launches = replay ? 6 + 1 + 2 * (c->opt.fused_2d ? 1 : 2) : 6;
   return HWENO_OK;
 }
 

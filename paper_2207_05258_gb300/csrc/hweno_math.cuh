@@ -284,6 +284,39 @@ __device__ __forceinline__ void resolve2(const Frac<Real>& a, const Frac<Real>& 
   }
 }
 
+// Three or four quotients with one division (all the characteristic fields
+// of an interface or a limiter item): the denominators are normalized, so
+// their product lies in [1, 64) (three) or [1, 256) (four).
+template <class Real>
+__device__ __forceinline__ void resolve3(const Frac<Real>& a, const Frac<Real>& b,
+                                         const Frac<Real>& c, Real& qa, Real& qb, Real& qc) {
+  if constexpr (std::is_same<Real, double>::value) {
+    const Real dbc = b.d * c.d;
+    const Real r = Real(1) / (a.d * dbc);
+    qa = a.n * dbc * r;
+    qb = b.n * (a.d * c.d) * r;
+    qc = c.n * (a.d * b.d) * r;
+  } else {
+    qa = a.n;
+    qb = b.n;
+    qc = c.n;
+  }
+}
+template <class Real>
+__device__ __forceinline__ void resolve4(const Frac<Real>* f, Real* q) {
+  if constexpr (std::is_same<Real, double>::value) {
+    const Real d01 = f[0].d * f[1].d, d23 = f[2].d * f[3].d;
+    const Real r = Real(1) / (d01 * d23);
+    const Real r01 = d23 * r, r23 = d01 * r;  // 1/(d0 d1), 1/(d2 d3)
+    q[0] = f[0].n * f[1].d * r01;
+    q[1] = f[1].n * f[0].d * r01;
+    q[2] = f[2].n * f[3].d * r23;
+    q[3] = f[3].n * f[2].d * r23;
+  } else {
+    for (int i = 0; i < 4; ++i) q[i] = f[i].n;
+  }
+}
+
 // The sum of two deferred quotients na/da + nb/db as one deferred quotient
 // (each side normalized first).
 template <class Real>

@@ -274,6 +274,9 @@ struct Args2D {
 
 cudaError_t launch_alpha_2d(int eq, bool fp32, const Args2D& a, cudaStream_t s);
 cudaError_t launch_xsweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
+// Fused stage (stage2d_fused.cu): the x- and y-parts of one SSP-RK3 stage in
+// one launch, one CTA per kColsY2D x kRowsY2D block (modes STAGE1..3).
+cudaError_t launch_stage_fused_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
 cudaError_t launch_ysweep_2d(int eq, bool fp32, int mode, const Args2D& a, cudaStream_t s);
 
 // Adjoint of one stage of a 1D step (adjoint1d.cu), FP64. With x_k =

@@ -250,8 +250,7 @@ __device__ __forceinline__ void limited_point(const Args1D& a, int g, Real idx, 
                                       pj(sV, g - 1), pj(sV, g + 1), w);
     }
     Real z[3];
-    resolve2(zr[0], zr[1], z[0], z[1]);
-    z[2] = resolve1(zr[2]);
+    resolve3(zr[0], zr[1], zr[2], z[0], z[1], z[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       vt[c] = (e.R[c][0] * z[0] + e.R[c][1] * z[1] + e.R[c][2] * z[2]) * idx;
@@ -406,8 +405,7 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
                                     pj(sHm, gl), pj(sHm, gl + 1), pj(sHm, gl + 2), w);
       }
       Real f[3];
-      resolve2(fr[0], fr[1], f[0], f[1]);
-      f[2] = resolve1(fr[2]);
+      resolve3(fr[0], fr[1], fr[2], f[0], f[1], f[2]);
       Real out[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) out[c] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
@@ -944,8 +942,7 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
         for (int q = 0; q < 3; ++q)
           fr[q] = sides_sum(sSn0[q][j], sSd0[q][j], sSn1[q][j], sSd1[q][j]);
         Real f[3];
-        resolve2(fr[0], fr[1], f[0], f[1]);
-        f[2] = resolve1(fr[2]);
+        resolve3(fr[0], fr[1], fr[2], f[0], f[1], f[2]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) sF[c][j] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
       }

@@ -24,78 +24,12 @@
 
 #include "hweno.h"
 #include "flux2d.cuh"
+#include "stage2d_common.cuh"
 #include "hweno_math.cuh"
 #include "internal.h"
 
 namespace hweno {
 namespace {
-
-template <int EQ, class Real>
-__device__ __forceinline__ void speeds2(const Real* U, Real gam, Real& sx, Real& sy) {
-  if constexpr (EQ == HWENO_BURGERS) {
-    sx = sy = fabs(U[0]);
-  } else {
-    const Prim2<Real> q = prim2(U, gam - Real(1));
-    const Real c = fast_sqrt(gam * q.p * q.ir);
-    sx = fabs(q.u) + c;
-    sy = fabs(q.v) + c;
-  }
-}
-
-// Characteristic system of the 2D Euler flux Jacobian in direction DIR at
-// velocity (u, v), enthalpy H, sound speed c. Rows of L and columns of R in
-// the eigenvalue order un - c, un, shear, un + c; normal velocity un (slot
-// kn = 1 + DIR), tangential ut (slot kt = 2 - DIR). Zeros are skipped.
-template <class Real, int DIR>
-struct Char2 {
-  Real un, ut, H, c, q, b1, b2, ic;
-  // sound speed from c^2 (one reciprocal square root gives c and 1/c)
-  __device__ __forceinline__ void init(Real u, Real v, Real H_, Real c2, Real gm1) {
-    un = DIR == 0 ? u : v;
-    ut = DIR == 0 ? v : u;
-    H = H_;
-    sound_speed(c2, c, ic);
-    q = Real(0.5) * (u * u + v * v);
-    b1 = gm1 * ic * ic;
-    b2 = b1 * q;
-  }
-  // row r of L applied to (x0, x1, x2, x3)
-  __device__ __forceinline__ Real left(int r, Real x0, Real x1, Real x2, Real x3) const {
-    const Real xn = DIR == 0 ? x1 : x2, xt = DIR == 0 ? x2 : x1;
-    if (r == 2) return xt - ut * x0;
-    const Real A = Real(0.5) * (b2 * x0 - b1 * un * xn - b1 * ut * xt + b1 * x3);
-    if (r == 1) return x0 - Real(2) * A;
-    const Real B = Real(0.5) * ic * (un * x0 - xn);
-    return r == 0 ? A + B : A - B;
-  }
-  // R s
-  __device__ __forceinline__ void right(const Real* s, Real* out) const {
-    const Real sum = s[0] + s[1] + s[3], dif = s[3] - s[0];
-    const Real on = un * sum + c * dif;
-    const Real ot = ut * sum + s[2];
-    out[0] = sum;
-    out[DIR == 0 ? 1 : 2] = on;
-    out[DIR == 0 ? 2 : 1] = ot;
-    out[3] = H * (s[0] + s[3]) + q * s[1] + ut * s[2] + un * c * dif;
-  }
-};
-
-__device__ __forceinline__ double time_step2(const Args2D& a, int& lands) {
-  if (a.dt_in) {  // replay of a recorded step
-    lands = 0;
-    return a.dt_in[0];
-  }
-  double dt;
-  if (a.sp.dt_mode == 2) {
-    dt = a.sp.dt_fixed;
-  } else {
-    const double rate = __dadd_rn(__ddiv_rn(a.alpha_in[0], a.hx), __ddiv_rn(a.alpha_in[1], a.hy));
-    dt = rate > 0.0 ? __ddiv_rn(a.sp.cfl, rate) : __longlong_as_double(0x7ff0000000000000LL);
-  }
-  const double rest = a.t_end - a.t[0];
-  lands = dt >= rest;
-  return lands ? rest : dt;
-}
 
 // ---------------------------------------------------------------------------
 template <int EQ, class Real>
@@ -262,8 +196,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
                                     pj(sHm, gl + 1), pj(sHm, gl + 2), w);
       }
       Real fch[4];
-      resolve2(fr[0], fr[1], fch[0], fch[1]);
-      resolve2(fr[2], fr[3], fch[2], fch[3]);
+      resolve4(fr, fch);
       Real out[4];
       e.right(fch, out);
 #pragma unroll
@@ -320,8 +253,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
         for (int r = 0; r < 4; ++r)
           zr[r] = limited_derivative_frac(pj(r, sU, g - 1), pj(r, sU, g), pj(r, sU, g + 1),
                                           dx * pj(r, sV, g - 1), dx * pj(r, sV, g + 1), w);
-        resolve2(zr[0], zr[1], z[0], z[1]);
-        resolve2(zr[2], zr[3], z[2], z[3]);
+        resolve4(zr, z);
       }
       e.right(z, vt);
 #pragma unroll
@@ -564,8 +496,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
                                      pj(3, gl + 2), pj(5, gl), pj(5, gl + 1), pj(5, gl + 2), w);
       }
       Real fch[4];
-      resolve2(fr[0], fr[1], fch[0], fch[1]);
-      resolve2(fr[2], fr[3], fch[2], fch[3]);
+      resolve4(fr, fch);
       Real out[4];
       e.right(fch, out);
 #pragma unroll
@@ -643,8 +574,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
         for (int rr = 0; rr < 4; ++rr)
           zr[rr] = limited_derivative_frac(pj(rr, 0, kc - C), pj(rr, 0, kc), pj(rr, 0, kc + C),
                                            dy * pj(rr, 1, kc - C), dy * pj(rr, 1, kc + C), w);
-        resolve2(zr[0], zr[1], z[0], z[1]);
-        resolve2(zr[2], zr[3], z[2], z[3]);
+        resolve4(zr, z);
       }
       e.right(z, wt);
 #pragma unroll

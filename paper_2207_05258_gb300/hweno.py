@@ -57,7 +57,8 @@ class Options(ctypes.Structure):
                 ("eps", ctypes.c_double), ("cfl", ctypes.c_double), ("dt_mode", ctypes.c_int),
                 ("dt_fixed", ctypes.c_double), ("limiter", ctypes.c_int),
                 ("eig_avg", ctypes.c_int), ("tile_variant", ctypes.c_int),
-                ("fused_small", ctypes.c_int), ("adj_frozen_weights", ctypes.c_int)]
+                ("fused_small", ctypes.c_int), ("adj_frozen_weights", ctypes.c_int),
+                ("fused_2d", ctypes.c_int)]
 
 
 _VP = ctypes.c_void_p

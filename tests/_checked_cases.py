@@ -4,8 +4,8 @@ checks, NaN-filled stage scratch; see tests/test_gpu_checked_build.py).
 Run as a script with HWENO_LIBRARY pointing at the checked library. Every
 kernel family runs on small and ragged grids: the 1D stage kernels (right-hand
 side and steps, every tile variant, Burgers and Euler, every boundary kind),
-the persistent run, the cluster step, the 2D sweeps, the totals and the
-adjoint steps. Results are compared with the oracle where the plain build's
+the persistent run, the cluster step, the 2D sweeps and the fused 2D stage,
+the totals and the adjoint steps. Results are compared with the oracle where the plain build's
 parity tests do, and the context's status must stay clean (a failed check
 would come back as HWENO_EBOUNDS). Prints "CHECKED OK" at the end.
 """
@@ -113,11 +113,11 @@ def main():
             assert np.max(np.abs(g - Uo)) <= 1e-11 * np.max(np.abs(Uo)), ("persistent", fused, n)
         s.close()
     # 2D: smooth periodic, walls and inflow, the double Mach boundaries; rhs,
-    # two steps and one adjoint step
+    # two steps (split and fused stage forms) and one adjoint step
     cases = [W.euler2d_smooth(24, ny=13, t_end=1.0), W.double_mach(40, 12, t_end=1.0),
              W.burgers2d_sine(20)]
-    for w in cases:
-        s = hw.Solver.from_workload(w)
+    for w, fused in [(w, f) for w in cases for f in (0, 1)]:
+        s = hw.Solver.from_workload(w, fused_2d=fused)
         U, V, Wd = dev(w.U), dev(w.V), dev(w.W)
         s.rhs(U, V, Wd)
         t = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -127,7 +127,7 @@ def main():
         s.sync_status()
         Uo = O.run(oracle_problem(w), w.U, w.V, w.W, 0.0, w.t_end, max_steps=2)[0]
         g = U.cpu().numpy().reshape(Uo.shape)
-        assert np.max(np.abs(g - Uo)) <= 1e-11 * np.max(np.abs(Uo)), ("2d", w.name)
+        assert np.max(np.abs(g - Uo)) <= 1e-11 * np.max(np.abs(Uo)), ("2d", w.name, fused)
         if w.bc[0] == "periodic":
             lam = [torch.ones_like(U), torch.ones_like(V), torch.ones_like(Wd)]
             s.adjoint_step(dev(w.U), dev(w.V), dev(w.W), dt, *lam, t=torch.zeros_like(t))
@@ -135,7 +135,7 @@ def main():
             assert all(torch.isfinite(x).all() for x in lam)
         s.close()
         # FP32 (packed pairs, asynchronous tile copies in the y-sweep)
-        s = hw.Solver.from_workload(w, precision="fp32")
+        s = hw.Solver.from_workload(w, precision="fp32", fused_2d=fused)
         f32 = lambda x: dev(x).float()
         U, V, Wd = f32(w.U), f32(w.V), f32(w.W)
         s.rhs(U, V, Wd)
@@ -144,7 +144,7 @@ def main():
             s.step(U, V, Wd, t, w.t_end)
         s.sync_status()
         g = U.double().cpu().numpy().reshape(Uo.shape)
-        assert np.max(np.abs(g - Uo)) <= 1e-4 * np.max(np.abs(Uo)), ("2d fp32", w.name)
+        assert np.max(np.abs(g - Uo)) <= 1e-4 * np.max(np.abs(Uo)), ("2d fp32", w.name, fused)
         s.close()
     # the checks are live: the self-test latches HWENO_EBOUNDS, and the
     # context works afterwards

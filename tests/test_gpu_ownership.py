@@ -86,7 +86,7 @@ def _exercise(hw, s, b, t_end):
     ok(lib.hweno_sync_status(h, st))
 
 
-@pytest.mark.parametrize("case", ["euler1d_batch", "burgers1d", "euler2d"])
+@pytest.mark.parametrize("case", ["euler1d_batch", "burgers1d", "euler2d", "euler2d_fused"])
 def test_no_call_after_create_allocates_device_memory(hw, case):
     """A first context runs every call once (the first launch of a kernel
     loads its module, which takes device memory). A second context of the
@@ -99,11 +99,12 @@ def test_no_call_after_create_allocates_device_memory(hw, case):
         w = W.burgers1d_sine(100000)
     else:
         w = W.euler2d_smooth(160, t_end=1.0)
+    opts = {"fused_2d": 1} if case == "euler2d_fused" else {}
     t_end = float(w.t_end)
-    warm = hw.Solver.from_workload(w)
+    warm = hw.Solver.from_workload(w, **opts)
     bw = _Buffers(warm, w)
     _exercise(hw, warm, bw, t_end)
-    s = hw.Solver.from_workload(w)
+    s = hw.Solver.from_workload(w, **opts)
     b = _Buffers(s, w)
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
@@ -216,3 +217,61 @@ def test_hweno_run_records_again_after_options_change(hw, change):
             r.step(U2, V2, None, t2, w.t_end)
     side.synchronize()
     assert torch.equal(U, U2) and torch.equal(V, V2) and torch.equal(t, t2)
+
+
+@pytest.mark.parametrize("fused_2d", [0, 1])
+def test_2d_step_recorded_into_a_graph_replays_the_same_bits(hw, fused_2d):
+    """hweno_step in 2D (eight launches split, five fused) recorded by the
+    caller into a CUDA graph gives the bits of direct calls."""
+    w = W.euler2d_smooth(96, ny=40, t_end=1.0)
+    dev = lambda x: torch.from_numpy(x.copy()).cuda()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        s = hw.Solver.from_workload(w, fused_2d=fused_2d)
+        U, V, Wd = dev(w.U), dev(w.V), dev(w.W)
+        t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    side.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        s.step(U, V, Wd, t, w.t_end)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    s.sync_status()
+    r = hw.Solver.from_workload(w, fused_2d=fused_2d)
+    U2, V2, W2 = dev(w.U), dev(w.V), dev(w.W)
+    t2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        r.step(U2, V2, W2, t2, w.t_end)
+    torch.cuda.synchronize()
+    assert r.launches_last_call == (5 if fused_2d else 8)
+    assert torch.equal(U, U2) and torch.equal(V, V2) and torch.equal(Wd, W2)
+    assert torch.equal(t, t2)
+
+
+def test_2d_hweno_run_records_again_after_the_stage_form_changes(hw):
+    """hweno_run in 2D: after hweno_set_options switches the stage form the
+    next hweno_run records the fused launches (compared with plain steps
+    that switch at the same point)."""
+    w = W.euler2d_smooth(64, ny=48, t_end=1.0)
+    dev = lambda x: torch.from_numpy(x.copy()).cuda()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        s = hw.Solver.from_workload(w, dt_mode=1)
+        U, V, Wd = dev(w.U), dev(w.V), dev(w.W)
+        t = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.run_graph(U, V, Wd, t, w.t_end, max_steps=2, steps_per_launch=2)
+        s.set_options(dt_mode=1, fused_2d=1)
+        s.run_graph(U, V, Wd, t, w.t_end, max_steps=2, steps_per_launch=2)
+        r = hw.Solver.from_workload(w, dt_mode=1)
+        U2, V2, W2 = dev(w.U), dev(w.V), dev(w.W)
+        t2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            r.step(U2, V2, W2, t2, w.t_end)
+        r.set_options(dt_mode=1, fused_2d=1)
+        for _ in range(2):
+            r.step(U2, V2, W2, t2, w.t_end)
+        assert r.launches_last_call == 5
+    side.synchronize()
+    assert torch.equal(U, U2) and torch.equal(V, V2) and torch.equal(Wd, W2)
+    assert torch.equal(t, t2)
