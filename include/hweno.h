@@ -448,10 +448,9 @@ int hweno_measure_fp64_peak(double* tflops, void* stream);
  * 2 MB, enough for nx <= HWENO_NOALLOC_MAX_POINTS points), present on every
  * GPU that loads the library until the process exits; the call performs no
  * cudaMalloc, cudaFree or other allocation. The first call on a device looks
- * up that array's address for the device (with the device current), so make
- * the first call on each device before any stream capture. The call
- * synchronises `stream` and returns HWENO_ENONFINITE if a wave speed was not
- * finite. HWENO_EINVAL: nx outside [4, HWENO_NOALLOC_MAX_POINTS], an invalid
+ * up that array's address for the device (with the device current). The
+ * call synchronises `stream` and returns HWENO_ENONFINITE if a wave speed was
+ * not finite. HWENO_EINVAL: nx outside [4, HWENO_NOALLOC_MAX_POINTS], an invalid
  * equation, gamma, boundary set or option. Every call shares the one array,
  * so calls whose GPU work overlaps (other streams, other host threads) race:
  * serialise them. */
