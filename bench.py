@@ -89,7 +89,7 @@ MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64", 0): 505.2,
                                        ("euler2d_smooth", "fp32", 1): 90.2,
                                        ("double_mach", "fp64", 0): 490.9}
 # One 2D Euler adjoint step (six reverse sweeps) per point, 512^2.
-MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP = {("euler", 2): 1858.1}
+MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP = {("euler", 2): None}
 
 
 def parse():

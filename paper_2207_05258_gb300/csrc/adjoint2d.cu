@@ -30,7 +30,14 @@
 namespace hweno {
 namespace {
 
-constexpr int NT = 256;     // threads: two per item
+// 128 threads: two CTAs (2 x 99.5 KB of shared memory, 180 registers) per
+// SM, whose barriers overlap; measured 3.7% faster per adjoint step than one
+// CTA of 256 threads with 122-point tiles, despite the wider halo share.
+#ifndef HWENO_ADJ2D_NT
+#define HWENO_ADJ2D_NT 128
+#endif
+constexpr int NT = HWENO_ADJ2D_NT;  // threads: two per item (NT / 2 a power of two)
+static_assert((NT & (NT - 1)) == 0 && NT >= 128, "NT / 2 indexes items with a mask");
 constexpr int NH = NT / 2;  // items per pass
 constexpr int P = NH - 6;   // owned points per tile (the loaded points fill one pass)
 constexpr int NL = P + 6;   // loaded points s-3 .. s+P+2
@@ -205,7 +212,7 @@ __device__ __forceinline__ void jac2_t(const double* U, const double* g, double 
 }
 
 template <int EQ, int DIR>
-__global__ void __launch_bounds__(NT, 1) k_adjoint_sweep_2d(const __grid_constant__ AdjArgs2D a) {
+__global__ void __launch_bounds__(NT, 256 / NT) k_adjoint_sweep_2d(const __grid_constant__ AdjArgs2D a) {
   constexpr int M = Dim2<EQ>::M;
   constexpr bool EUL = EQ == HWENO_EULER;
   constexpr int NS = 5 * M;  // per slot: F+, F-, H+, H- (then gF, gH, gu, gN), E
