@@ -118,3 +118,18 @@ def test_reference_arm_rank0_prints_one_line_other_ranks_nothing():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     rc, out = _reference_arm(1, 2)
     assert rc == 0 and out == []
+
+
+def test_traffic_tables_hold_positive_numbers_or_null():
+    """Every measured-traffic entry is a positive number, or None once its
+    kernel changed after the capture; scaling a None entry gives None."""
+    import bench
+    for table in (bench.MEASURED_STAGE_TRAFFIC_PER_POINT, bench.MEASURED_RUN_TRAFFIC_PER_POINT_STEP,
+                  bench.MEASURED_STAGE_TRAFFIC_2D_PER_POINT,
+                  bench.MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP):
+        for k, v in table.items():
+            assert v is None or (isinstance(v, float) and v > 0), (k, v)
+            got = bench.scaled_traffic(table, k, 1000)
+            assert got is None if v is None else got == v * 1000
+    assert bench.scaled_traffic({"a": None}, "a", 5) is None
+    assert bench.scaled_traffic({}, "a", 5) is None
