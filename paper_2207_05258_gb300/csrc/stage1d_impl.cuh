@@ -159,7 +159,8 @@ __device__ __forceinline__ StageIO io_of(const Args1D& a) {
 // c^2 in shared memory.
 template <int EQ, class Real, class TV>
 __device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const Real* V, int n,
-                                           int s, int g, Real alpha, Real dx, Real hdx, Real gam,
+                                           int s, int g, Real ha, Real hda, Real dx, Real hdx,
+                                           Real gam,
                                            Real gm1,
                                            const TV& sU, const TV& sV, const TV& sFp,
                                            const TV& sFm, const TV& sHp, const TV& sHm,
@@ -211,18 +212,21 @@ __device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const
     sE[3][g] = gam * p * ir;
   }
 #pragma unroll
-  for (int c = 0; c < M; ++c) {
-    sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
-    sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
-    sHp[c][g] = hdx * (H[c] + alpha * v[c]);
-    sHm[c][g] = hdx * (H[c] - alpha * v[c]);
-  }
+  for (int c = 0; c < M; ++c)
+    split_pm(F[c], u[c], H[c], v[c], ha, hda, hdx, sFp[c][g], sFm[c][g], sHp[c][g], sHm[c][g]);
 }
 
 // The limited derivative v~ at loaded point g (Sec. 2.2): v unchanged with
 // the limiter off, component-wise, or (Euler) on the characteristic fields
 // of the eigenvectors at U_g.
-template <int EQ, class Real, class TV>
+// Factored characteristic projections (Char1) in the tiled stage and
+// persistent kernels in FP64; the FP32 kernels, capped at 64 registers, and
+// the 124-point cluster step keep the rows of L applied one by one (the
+// factored form's larger live set spills there).
+template <class Real>
+constexpr bool kFactored = std::is_same<Real, double>::value;
+
+template <int EQ, class Real, class TV, bool FAC = true>
 __device__ __forceinline__ void limited_point(const Args1D& a, int g, Real idx, Real gm1,
                                               const Weights<Real>& w, const TV& sU,
                                               const TV& sV, const TV& sE, Real* vt) {
@@ -236,7 +240,7 @@ __device__ __forceinline__ void limited_point(const Args1D& a, int g, Real idx, 
     for (int c = 0; c < M; ++c)
       vt[c] = limited_derivative(sU[c][g - 1], sU[c][g], sU[c][g + 1], sV[c][g - 1],
                                  sV[c][g + 1], w) * idx;
-  } else if constexpr (EUL) {
+  } else if constexpr (EUL && !FAC) {  // the rows of L applied one by one
     Real cg, icg;
     sound_speed(sE[3][g], cg, icg);
     Eigen<Real, 3> e;
@@ -254,6 +258,29 @@ __device__ __forceinline__ void limited_point(const Args1D& a, int g, Real idx, 
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       vt[c] = (e.R[c][0] * z[0] + e.R[c][1] * z[1] + e.R[c][2] * z[2]) * idx;
+  } else if constexpr (EUL) {  // factored projections (Char1)
+    Real cg, icg;
+    sound_speed(sE[3][g], cg, icg);
+    const Char1<Real> ch(sE[1][g], sE[2][g], cg, icg, gm1);
+    // the five projected vectors (u at g-1, g, g+1; dx v at g-1, g+1) as
+    // (x0, A, B); each field's projection is then one operation
+    Real x0[5], fa[5], fb[5];
+    auto fac = [&](int k, const TV& X, int gg) {
+      x0[k] = X[0][gg];
+      ch.factors(X[0][gg], X[1][gg], X[2][gg], fa[k], fb[k]);
+    };
+    fac(0, sU, g - 1); fac(1, sU, g); fac(2, sU, g + 1); fac(3, sV, g - 1); fac(4, sV, g + 1);
+    Frac<Real> zr[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      auto pj = [&](int k) { return ch.row(q, x0[k], fa[k], fb[k]); };
+      zr[q] = limited_derivative_frac(pj(0), pj(1), pj(2), pj(3), pj(4), w);
+    }
+    Real z[3];
+    resolve3(zr[0], zr[1], zr[2], z[0], z[1], z[2]);
+    ch.right(z, vt);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vt[c] *= idx;
   }
 }
 
@@ -307,7 +334,7 @@ __device__ __forceinline__ void stage_update(const StageIO& io, long long base, 
 
 // One stage on the tile of instance k starting at point s (the whole CTA;
 // contains barriers, so every thread calls it with the same k, s).
-template <int EQ, class Real, int MODE, int NT, int PPT>
+template <int EQ, class Real, int MODE, int NT, int PPT, bool FAC = false>
 __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, const int k,
                                            const int s) {
   using Lay = Layout1D<EQ, Real, NT, PPT>;
@@ -362,8 +389,9 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
     const Real* U = static_cast<const Real*>(io.U) + off;
     const Real* V = static_cast<const Real*>(io.V) + off;
     const Real hdx = Real(0.5) * dx;
+    const Real ha = Real(0.5) * alpha, hda = hdx * alpha;
     for (int g = threadIdx.x; g < np + 4; g += blockDim.x)
-      tile_point<EQ, Real, TV>(a, U, V, n, s, g, alpha, dx, hdx, gam, gm1, sU, sV, sFp, sFm,
+      tile_point<EQ, Real, TV>(a, U, V, n, s, g, ha, hda, dx, hdx, gam, gm1, sU, sV, sFp, sFm,
                                sHp, sHm, sE);
   }
   __syncthreads();
@@ -392,6 +420,7 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
       }
       Real ic;
       sound_speed(gm1 * (HH - Real(0.5) * uu * uu), cc, ic);
+      if constexpr (!FAC) {  // the rows of L applied one by one
       Eigen<Real, 3> e;
       euler_eigen<Real, 3>(0, uu, Real(0), HH, cc, ic, gm1, e);
       Frac<Real> fr[3];
@@ -406,11 +435,38 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
       }
       Real f[3];
       resolve3(fr[0], fr[1], fr[2], f[0], f[1], f[2]);
-      Real out[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[c] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
+      for (int c = 0; c < 3; ++c)
+        sF[c][j] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
+      } else {
+      const Char1<Real> ch(uu, HH, cc, ic, gm1);
+      // the twelve projected vectors (f^+, H^+ at gl-1..gl+1; f^-, H^- at
+      // gl..gl+2) as (x0, A, B); each field's projection is one operation
+      Real x0[12], fa[12], fb[12];
+      auto fac = [&](int k, const TV& X, int g) {
+        x0[k] = X[0][g];
+        ch.factors(X[0][g], X[1][g], X[2][g], fa[k], fb[k]);
+      };
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        fac(d, sFp, gl - 1 + d);
+        fac(3 + d, sHp, gl - 1 + d);
+        fac(6 + d, sFm, gl + d);
+        fac(9 + d, sHm, gl + d);
+      }
+      Frac<Real> fr[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        auto pj = [&](int k) { return ch.row(q, x0[k], fa[k], fb[k]); };
+        fr[q] = interface_flux_frac(pj(0), pj(1), pj(2), pj(3), pj(4), pj(5), pj(6), pj(7),
+                                    pj(8), pj(9), pj(10), pj(11), w);
+      }
+      Real f[3], out[3];
+      resolve3(fr[0], fr[1], fr[2], f[0], f[1], f[2]);
+      ch.right(f, out);
 #pragma unroll
       for (int c = 0; c < 3; ++c) sF[c][j] = out[c];
+      }
     }
 #pragma unroll
     for (int c = 0; c < M; ++c)
@@ -433,7 +489,7 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
       dF[c] = sF[c][j + 1] - sF[c][j];
       dD[c] = sD[c][j + 1] - sD[c][j];
     }
-    limited_point<EQ, Real, TV>(a, g, idx, gm1, w, sU, sV, sE, vt);
+    limited_point<EQ, Real, TV, FAC>(a, g, idx, gm1, w, sU, sV, sE, vt);
 
     HWENO_CHECK(s + j < n, st);
     const long long base = off + s + j;
@@ -469,7 +525,7 @@ __device__ __forceinline__ void stage_tile(const Args1D& a, const StageIO& io, c
 template <int EQ, class Real, int MODE, int NT, int PPT>
 __global__ void __launch_bounds__(NT, (MinBlocks1D<Real, NT>::value))
 k_stage_1d(const __grid_constant__ Args1D a) {
-  stage_tile<EQ, Real, MODE, NT, PPT>(a, io_of(a), a.tile_inst[blockIdx.x],
+  stage_tile<EQ, Real, MODE, NT, PPT, kFactored<Real>>(a, io_of(a), a.tile_inst[blockIdx.x],
                                       a.tile_start[blockIdx.x]);
 }
 
@@ -596,19 +652,19 @@ k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p
       io.Uout = p.U1; io.Vout = p.V1; io.Vt0out = p.Vt0;
       io.alpha_in = reinterpret_cast<const double*>(slot0);
       io.alpha_out = slot0 + p.batch;
-      stage_tile<EQ, Real, MODE_STAGE1, NT, PPT>(a, io, k, s);
+      stage_tile<EQ, Real, MODE_STAGE1, NT, PPT, kFactored<Real>>(a, io, k, s);
     } else if (stage == 1) {
       io.U = p.U1; io.V = p.V1; io.U0 = a.U; io.Vt0 = p.Vt0;
       io.Uout = p.U2; io.Vout = p.V2; io.Vt0out = nullptr;
       io.alpha_in = reinterpret_cast<const double*>(slot0 + p.batch);
       io.alpha_out = slot0 + 2 * p.batch;
-      stage_tile<EQ, Real, MODE_STAGE2, NT, PPT>(a, io, k, s);
+      stage_tile<EQ, Real, MODE_STAGE2, NT, PPT, kFactored<Real>>(a, io, k, s);
     } else {
       io.U = p.U2; io.V = p.V2; io.U0 = a.U; io.Vt0 = p.Vt0;
       io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V); io.Vt0out = nullptr;
       io.alpha_in = reinterpret_cast<const double*>(slot0 + 2 * p.batch);
       io.alpha_out = p.alpha + (size_t)((par ^ 1) * 3) * p.batch;  // alpha(U^{n+1})
-      stage_tile<EQ, Real, MODE_STAGE3, NT, PPT>(a, io, k, s);
+      stage_tile<EQ, Real, MODE_STAGE3, NT, PPT, kFactored<Real>>(a, io, k, s);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -861,14 +917,15 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
   // point s - 2 + g
   if (warp == 0 && lane < np + 4)
     tile_point<EQ, Real, TV>(a, static_cast<const Real*>(io.U) + off,
-                             static_cast<const Real*>(io.V) + off, n, s, lane, alpha, dx,
-                             Real(0.5) * dx, gam, gm1, sU, sV, sFp, sFm, sHp, sHm, sE);
+                             static_cast<const Real*>(io.V) + off, n, s, lane,
+                             Real(0.5) * alpha, Real(0.5) * dx * alpha, dx, Real(0.5) * dx,
+                             gam, gm1, sU, sV, sFp, sFm, sHp, sHm, sE);
   __syncthreads();
 
   // B: warps 0 / 1 the "+" / "-" side of interface x_{s+j-1/2}, j = lane
   // (left point at loaded index j + 1); warp 2 the limited derivative of
   // point j = lane; warp 3 the derivative flux of interface j = lane
-  Eigen<Real, 3> e{};  // Euler: eigenvectors at the interface (warps 0, 1)
+  Char1<Real> ch{};  // Euler: characteristic system at the interface (warps 0, 1)
   if (warp < 2) {
     const int sd = warp, j = lane, gl = j + 1, b = gl - 1 + sd;  // first stencil point
     if (j <= np) {
@@ -898,13 +955,20 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
         }
         Real ic;
         sound_speed(gm1 * (HH - Real(0.5) * uu * uu), cc, ic);
-        euler_eigen<Real, 3>(0, uu, Real(0), HH, cc, ic, gm1, e);
+        ch = Char1<Real>(uu, HH, cc, ic, gm1);
+        // the side's six projected vectors as (x0, A, B)
+        Real x0[6], fa[6], fb[6];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          x0[d] = SF[0][b + d];
+          ch.factors(SF[0][b + d], SF[1][b + d], SF[2][b + d], fa[d], fb[d]);
+          x0[3 + d] = SH[0][b + d];
+          ch.factors(SH[0][b + d], SH[1][b + d], SH[2][b + d], fa[3 + d], fb[3 + d]);
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const Real l0 = e.L[q][0], l1 = e.L[q][1], l2 = e.L[q][2];
-          auto pj = [&](const TV& A, int g) { return l0 * A[0][g] + l1 * A[1][g] + l2 * A[2][g]; };
-          const Frac<Real> fr = side_frac(sd, pj(SF, b), pj(SF, b + 1), pj(SF, b + 2), pj(SH, b),
-                                          pj(SH, b + 1), pj(SH, b + 2), w);
+          auto pj = [&](int k) { return ch.row(q, x0[k], fa[k], fb[k]); };
+          const Frac<Real> fr = side_frac(sd, pj(0), pj(1), pj(2), pj(3), pj(4), pj(5), w);
           sSn[q][j] = fr.n;
           sSd[q][j] = fr.d;
         }
@@ -941,10 +1005,11 @@ __device__ __forceinline__ void stage_tile_split(const Args1D& a, const StageIO&
 #pragma unroll
         for (int q = 0; q < 3; ++q)
           fr[q] = sides_sum(sSn0[q][j], sSd0[q][j], sSn1[q][j], sSd1[q][j]);
-        Real f[3];
+        Real f[3], out[3];
         resolve3(fr[0], fr[1], fr[2], f[0], f[1], f[2]);
+        ch.right(f, out);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) sF[c][j] = e.R[c][0] * f[0] + e.R[c][1] * f[1] + e.R[c][2] * f[2];
+        for (int c = 0; c < 3; ++c) sF[c][j] = out[c];
       }
     }
   }

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
     const Real* V = static_cast<const Real*>(a.V);
     const Real* W = static_cast<const Real*>(a.W);
     const Real hdx = Real(0.5) * dx;
+    const Real ha = Real(0.5) * alpha, hda = hdx * alpha;
     for (int g = threadIdx.x; g < np + 4; g += blockDim.x) {
       const Src s = map_x(i0 - 2 + g, nx, a.sp);
       HWENO_CHECK(s.kind == 2 || (s.idx >= 0 && s.idx < nx), st);
@@ -146,10 +147,8 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
       jvp2<EQ, 0>(u, pq, ww, gm1, E);
 #pragma unroll
       for (int c = 0; c < M; ++c) {
-        sFp[c][g] = Real(0.5) * (F[c] + alpha * u[c]);
-        sFm[c][g] = Real(0.5) * (F[c] - alpha * u[c]);
-        sHp[c][g] = hdx * (H[c] + alpha * v[c]);
-        sHm[c][g] = hdx * (H[c] - alpha * v[c]);
+        split_pm(F[c], u[c], H[c], v[c], ha, hda, hdx, sFp[c][g], sFm[c][g], sHp[c][g],
+                 sHm[c][g]);
         sEta[c][g] = E[c];
       }
       if constexpr (EUL) {
@@ -367,6 +366,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
     const Real* V = static_cast<const Real*>(a.V);
     const Real* W = static_cast<const Real*>(a.W);
     const Real hdy = Real(0.5) * dy;
+    const Real ha = Real(0.5) * alpha, hda = hdy * alpha;
     // FP32: every load of the tile is issued first, as asynchronous copies
     // into the slots the values occupy anyway (U and W in quantities 0 and
     // 1; V in quantity 6, which this thread overwrites with xi = A_y V of
@@ -438,10 +438,8 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
       jvp2<EQ, 1>(u, pq, v, gm1, X);
 #pragma unroll
       for (int c = 0; c < M; ++c) {
-        PT(2, c)[k] = Real(0.5) * (G[c] + alpha * u[c]);
-        PT(3, c)[k] = Real(0.5) * (G[c] - alpha * u[c]);
-        PT(4, c)[k] = hdy * (T[c] + alpha * ww[c]);
-        PT(5, c)[k] = hdy * (T[c] - alpha * ww[c]);
+        split_pm(G[c], u[c], T[c], ww[c], ha, hda, hdy, PT(2, c)[k], PT(3, c)[k], PT(4, c)[k],
+                 PT(5, c)[k]);
         PT(6, c)[k] = X[c];
       }
       if constexpr (EUL) {

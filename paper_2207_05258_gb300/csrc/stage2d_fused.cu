@@ -116,6 +116,7 @@ k_stage_2d(const __grid_constant__ Args2D a) {
     const auto sN = tile_view<Lay::XF>(xi + 2 * M * Lay::XF, M, st);
     const Real alpha = Real(a.alpha_in[0]);
     const Real hdx = Real(0.5) * dx;
+    const Real ha = Real(0.5) * alpha, hda = hdx * alpha;
     // loaded points: row r, column g (point i0 - 2 + g)
     for (int k = threadIdx.x; k < Lay::XP; k += blockDim.x) {
       const int r = k / kXL, g = k % kXL;
@@ -147,10 +148,8 @@ k_stage_2d(const __grid_constant__ Args2D a) {
       jvp2<EQ, 0>(u, pq, ww, gm1, E);
 #pragma unroll
       for (int c = 0; c < M; ++c) {
-        sFp[c][k] = Real(0.5) * (F[c] + alpha * u[c]);
-        sFm[c][k] = Real(0.5) * (F[c] - alpha * u[c]);
-        sHp[c][k] = hdx * (H[c] + alpha * v[c]);
-        sHm[c][k] = hdx * (H[c] - alpha * v[c]);
+        split_pm(F[c], u[c], H[c], v[c], ha, hda, hdx, sFp[c][k], sFm[c][k], sHp[c][k],
+                 sHm[c][k]);
         sEta[c][k] = E[c];
       }
       if constexpr (EUL) {
@@ -284,6 +283,7 @@ k_stage_2d(const __grid_constant__ Args2D a) {
   {
     const Real alpha = Real(a.alpha_in[1]);
     const Real hdy = Real(0.5) * dy;
+    const Real ha = Real(0.5) * alpha, hda = hdy * alpha;
     // FP32: all of the tile's loads as asynchronous copies first (U and W in
     // quantities 0 and 1, V in quantity 6, which the same thread overwrites
     // with xi), then the prefetch of the stage's U^n, v~^n, w~^n
@@ -368,10 +368,8 @@ k_stage_2d(const __grid_constant__ Args2D a) {
       jvp2<EQ, 1>(u, pq, v, gm1, X);
 #pragma unroll
       for (int c = 0; c < M; ++c) {
-        PT(2, c)[k] = Real(0.5) * (G[c] + alpha * u[c]);
-        PT(3, c)[k] = Real(0.5) * (G[c] - alpha * u[c]);
-        PT(4, c)[k] = hdy * (T[c] + alpha * ww[c]);
-        PT(5, c)[k] = hdy * (T[c] - alpha * ww[c]);
+        split_pm(G[c], u[c], T[c], ww[c], ha, hda, hdy, PT(2, c)[k], PT(3, c)[k], PT(4, c)[k],
+                 PT(5, c)[k]);
         PT(6, c)[k] = X[c];
       }
       if constexpr (EUL) {
