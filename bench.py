@@ -75,19 +75,19 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # figures).
 # Stage kernel, per point and launch (FP32: the 2048-instance batch, the
 # mean of the three stage launches of one step, tile 128 x 2).
-MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": None, "fp32": None}
+MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": None, "fp32": 52.4}
 # Persistent kernel, per point-step (all three stages; FP64: 1024 instances,
-# 1 283 400 points, one launch of 2 steps).
-MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": None, "fp32": None}
+# 1 283 400 points, one launch of 2 steps of the autotuned tile).
+MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 395.0, "fp32": None}
 # One 2D stage per point, per workload, precision and stage form (0: the
 # x-sweep + y-sweep launches of stage 1, 1: the fused stage-1 launch; smooth
 # Euler at 1024^2, double Mach at 1920x480); applied to grids whose working
 # set exceeds the L2.
-MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64", 0): None,
-                                       ("euler2d_smooth", "fp32", 0): None,
-                                       ("euler2d_smooth", "fp64", 1): None,
-                                       ("euler2d_smooth", "fp32", 1): None,
-                                       ("double_mach", "fp64", 0): None}
+MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64", 0): 504.8,
+                                       ("euler2d_smooth", "fp32", 0): 222.5,
+                                       ("euler2d_smooth", "fp64", 1): 209.7,
+                                       ("euler2d_smooth", "fp32", 1): 89.8,
+                                       ("double_mach", "fp64", 0): 490.8}
 # One 2D Euler adjoint step (six reverse sweeps, 128-thread CTAs) per point, 512^2.
 MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP = {("euler", 2): 1862.6}
 
@@ -397,8 +397,11 @@ def run_ours(args, rank, world, dev_index):
                 clus = (sum(a.elapsed_time(b) for a, b in evc),
                         float(((histc > 0).double() * nx[None, :]).sum().item()),
                         sc.launches_last_call * K, kern[0])
-                # and the next K steps as one cluster launch (hweno_run_persistent)
+                # and the next K steps as one cluster launch (hweno_run_persistent),
+                # L2 flushed before it; the events also cover the read-back of
+                # the point-update count
                 q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
                 torch.cuda.synchronize()
                 q0.record()
                 cpu = sc.run_persistent(U, V, t, w.t_end, K)
@@ -461,12 +464,19 @@ def run_ours(args, rank, world, dev_index):
         cluster_run = {"value": round(cr[1] / (cr[0] * 1e-3) / 1e6, 3),
                        "ms_per_step": round(cr[0] / args.steps, 4),
                        "note": "the next K steps as one launch on thread-block clusters "
-                               "(hweno_run_persistent with fused_small = 2), no flush inside"}
+                               "(hweno_run_persistent with fused_small = 2), L2 flushed "
+                               "before the launch"}
     use_clus = (small and clus is not None and clus[1] > 0 and
                 clus[1] / clus[0] > pu_ng / ms_ng)
+    # small instances: the K steps in one cluster launch are the headline
+    # where they beat one launch per step
+    use_crun = (small and cluster_run is not None and use_clus and
+                timed.clus_run[1] / timed.clus_run[0] > clus[1] / clus[0])
     if small:
         ms, pu = ms_ng, pu_ng
-    if use_clus:
+    if use_crun:
+        ms, pu, launches = timed.clus_run[0], timed.clus_run[1], 1
+    elif use_clus:
         ms, pu, launches = clus[0], clus[1], clus[2]
     elif use_pers and pgraph is not None:
         ms, pu, launches = pgraph[0], pgraph[1], pgraph[2]
@@ -496,7 +506,9 @@ def run_ours(args, rank, world, dev_index):
                MEASURED_STAGE_TRAFFIC_2D_PER_POINT.get((w.name, args.precision, tune[0]))
                if w.dim == 2 and not small
                else None)  # None: not captured for this workload
-    if use_clus:  # the headline kernel: one cluster launch per step
+    if use_crun:  # the headline kernel: K steps in one cluster launch
+        achieved = ALGO_FLOPS_PER_POINT_STEP[(w.equation, w.dim)] * pu / (ms * 1e-3) / 1e12
+    elif use_clus:  # the headline kernel: one cluster launch per step
         achieved = ALGO_FLOPS_PER_POINT_STEP[(w.equation, w.dim)] * clus[1] / (clus[3] * 1e-3) / 1e12
     if use_pers:  # the headline kernel: K steps in one persistent launch
         run_s = pers[3] * 1e-3
@@ -511,12 +523,16 @@ def run_ours(args, rank, world, dev_index):
                        (None if rtraffic is None else rtraffic * pers[1]),
             "kernel": ("k_run_1d<%s,%s> (K = %d steps per launch)" % (w.equation, args.precision,
                                                                      args.steps) if use_pers else
-                       "k_step_cluster_1d<%s,%s>" % (w.equation, args.precision) if use_clus else
+                       "%s<%s,%s>%s" % ("k_step_cluster_split_1d" if max(w.nx) <= 448 else
+                                        "k_step_cluster_1d", w.equation, args.precision,
+                                        " (K = %d steps per launch)" % args.steps
+                                        if use_crun else "") if use_clus else
                        "k_stage_1d<%s,%s>" % (w.equation, args.precision) if w.dim == 1 else
                        "k_stage_2d<%s,%s> (fused x and y parts)" % (w.equation, args.precision)
                        if fused2d else
                        "k_xsweep_2d + k_ysweep_2d <%s,%s>" % (w.equation, args.precision)),
             "kernel_share_of_step": (round(pers[3] / pers[0], 4) if use_pers else
+                                     1.0 if use_crun else
                                      round(clus[3] / clus[0], 4) if use_clus else
                                      round(stage_ms / sum(v[0] for v in prof.values()), 4)),
             "flops_per_point_stage": round(flop_stage, 2),
@@ -524,6 +540,7 @@ def run_ours(args, rank, world, dev_index):
             "hbm_achieved_gbs": round(ALGO_WORDS_PER_COMPONENT[w.dim] * w.m *
                                       (8 if args.precision == "fp64" else 4) *
                                       (pers[1] / (pers[3] * 1e-3) if use_pers else
+                                       pu / (ms * 1e-3) if use_crun else
                                        clus[1] / (clus[3] * 1e-3) if use_clus else
                                        pts_per_stage / 3.0 / stage_time) / 1e9, 1)}
 
@@ -536,18 +553,25 @@ def run_ours(args, rank, world, dev_index):
            ("graph" if small else "no_graph"): graph if small else plain,
            **({"graph": graph, "persistent": persistent} if use_pers else
               ({"persistent": persistent} if persistent else {})),
-           **({"cluster": cluster} if cluster and not use_clus else {}),
-           **({"cluster_run": cluster_run} if cluster_run else {}),
+           **({"cluster": cluster} if cluster and (use_crun or not use_clus) else {}),
+           **({"cluster_run": cluster_run} if cluster_run and not use_crun else {}),
            **({"plain": plain} if use_clus else {}),
            "config": {"workload": describe(w),
                       "instances": w.batch, "points": w.points, "precision": args.precision,
-                      "l2": ("flushed between timed steps (256 MiB write): the working set "
+                      "l2": ("flushed before the timed launch (256 MiB write): the working "
+                             "set (%.1f MB) fits in the 129 MB L2" % working_set_mb(w, args.precision)
+                             if use_crun else
+                             "flushed between timed steps (256 MiB write): the working set "
                              "(%.1f MB) fits in the 129 MB L2" % working_set_mb(w, args.precision)
                              if small else
                              "no flush inside the timed graph of K steps: the per-step working "
                              "set (state + stage buffers, %.0f MB) exceeds the 129 MB L2"
                              % (working_set_mb(w, args.precision))),
-                      "timing": ("each step (one launch on thread-block clusters, fused_small = 2) "
+                      "timing": ("the K steps as one launch on thread-block clusters "
+                                 "(hweno_run_persistent, fused_small = 2) after an L2 flush, "
+                                 "CUDA events around the launch and the read-back of its "
+                                 "point-update count" if use_crun else
+                                 "each step (one launch on thread-block clusters, fused_small = 2) "
                                  "bracketed by CUDA events, summed over K steps" if use_clus else
                                  "each step bracketed by CUDA events, summed over K steps"
                                  if small else timing_note),
@@ -956,7 +980,7 @@ OTHER_CONFIGS = (
 
 def _compact(out):
     keep = ("value", "unit", "ms_per_step", "us_per_step", "steps", "warmup", "dtype",
-            "roofline", "clocks", "gpu_launches", "cluster_run", "graph", "no_graph",
+            "roofline", "clocks", "gpu_launches", "cluster", "cluster_run", "graph", "no_graph",
             "plain", "persistent", "forward_ms_per_step", "adjoint_over_forward", "replay")
     c = {k: out[k] for k in keep if k in out}
     cfg = out.get("config", {})
