@@ -992,9 +992,11 @@ def _compact(out):
 
 
 def other_configs(args, dev_index):
-    """Configs 1, 3, 4 (FP64 and FP32) and the adjoint steps of config 5
-    (2D Euler 512^2 and the batch of 256 Burgers problems, N = 800), each
-    with its own roofline, for the headline line."""
+    """The other benchmark workloads, each with its own roofline, for the
+    headline line: 1D Burgers N = 400, the smooth 2D Euler grids 256^2 to
+    2048^2 and the double Mach grids 1920 x 480 and 3840 x 960 (FP64 and
+    FP32), and the adjoint steps of the 2D Euler 512^2 problem and of the
+    batch of 256 Burgers problems with N = 800."""
     import copy
     res = {}
     # a failing sub-configuration is reported in its own entry and does not

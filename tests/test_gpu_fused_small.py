@@ -141,8 +141,8 @@ def test_finished_instances_do_not_move(hw, mode):
 
 
 @pytest.mark.parametrize("mode", [1, 2])
-def test_config_1_to_final_time(hw, mode):  # N = 400: mode 2 takes the latency form
-    """Example 3.1 / config 1 (Burgers N = 400, T = 1.5/pi, shock) through the
+def test_burgers_n400_to_final_time(hw, mode):  # N = 400: mode 2 takes the latency form
+    """Example 3.1 (Burgers N = 400, T = 1.5/pi, shock) through the
     fused paths against the oracle, shocked-run tolerance."""
     w = W.burgers1d_sine(400)
     s = hw.Solver.from_workload(w, fused_small=mode)
