@@ -215,6 +215,13 @@ int hweno_create(hweno_ctx** out, int equation, const hweno_grid* grid, double g
  * hweno_create, so work still running on any stream is not disturbed. */
 int hweno_set_options(hweno_ctx* ctx, const hweno_options* opt);
 
+/* The context's current options into *out (host): those of the last
+ * hweno_set_options, with the tile variant (1D) or the stage form (2D, field
+ * fused_2d) that hweno_autotune, hweno_autotune_classes or
+ * hweno_set_class_variants chose since. A caller changes one option by
+ * reading, editing and setting them back. HWENO_EINVAL for a null pointer. */
+int hweno_get_options(const hweno_ctx* ctx, hweno_options* out);
+
 /* Spatial operator of one stage (Eq. odeH in 1D, Eq. ode2H in 2D):
  * dU = L^1(U, V[, W]), dV = L^2, dW = L^3 (2D), each -(flux difference)/h,
  * with alpha the maximum of |f'(u)| (Euler: |u| + c per direction) over each

@@ -941,6 +941,12 @@ int hweno_set_options(hweno_ctx* c, const hweno_options* o) {
   return rc;
 }
 
+int hweno_get_options(const hweno_ctx* c, hweno_options* out) {
+  if (!c || !out) return HWENO_EINVAL;
+  *out = c->opt;
+  return HWENO_OK;
+}
+
 int hweno_rhs(hweno_ctx* c, const void* U, const void* V, const void* W, void* dU, void* dV,
               void* dW, void* Vlim, void* Wlim, const double* t, void* stream) {
   if (!c) return HWENO_EINVAL;
@@ -1320,7 +1326,7 @@ int hweno_autotune(hweno_ctx* c, const void* U, const void* V, const void* W, co
     if (tv < best_ms) { best_ms = tv; best = v; }
   }
   if (rc != HWENO_OK) {
-    use_variant(c, 0);
+    if (use_variant(c, 0) == HWENO_OK) c->opt.tile_variant = 0;
     return rc;
   }
   if ((rc = use_variant(c, best)) != HWENO_OK) return rc;

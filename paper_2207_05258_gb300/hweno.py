@@ -93,6 +93,7 @@ SIGNATURES = {
     "hweno_num_points": (ctypes.c_longlong, [_VP]),
     "hweno_active_instances": (ctypes.c_int, [_VP, _VP]),
     "hweno_launches_last_call": (ctypes.c_int, [_VP]),
+    "hweno_get_options": (ctypes.c_int, [_VP, ctypes.POINTER(Options)]),
     "hweno_profile_start": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hweno_profile_read": (ctypes.c_int, [_VP, _DP, ctypes.POINTER(ctypes.c_int), _VP]),
     "hweno_step_1d_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -192,12 +193,22 @@ class Solver:
         if rc != OK:
             raise HwenoError(rc, lib.hweno_last_error(self.h).decode())
 
+    def options(self) -> "Options":
+        """hweno_get_options: the context's current options."""
+        o = Options()
+        self._check(lib.hweno_get_options(self.h, ctypes.byref(o)))
+        return o
+
     def set_options(self, **kw):
-        o = default_options()
+        """Change the named options; the others keep their current values
+        (including a tile variant or 2D stage form chosen by the autotuner)."""
+        o = self.options()
         for k, v in kw.items():
             if k in ("lin_w", "lim_d"):
                 getattr(o, k)[:] = list(v)
             else:
+                if not hasattr(o, k):
+                    raise AttributeError("unknown option %r" % k)
                 setattr(o, k, v)
         self._check(lib.hweno_set_options(self.h, ctypes.byref(o)))
 

@@ -244,3 +244,24 @@ def test_recorded_adjoint_replay_bits(hw, fused):
     for x, y in zip(a, b):
         assert torch.equal(x, y)
     s.close()
+
+
+def test_options_keep_the_autotuned_form(hw):
+    """hweno_get_options reports the stage form the autotuner chose, and
+    set_options changes only the named options."""
+    w = W.euler2d_smooth(64, t_end=1.0)
+    s = hw.Solver.from_workload(w, dt_mode=1)
+    U, V, Wd = dev(w.U), dev(w.V), dev(w.W)
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    chosen, _ = s.autotune(U, V, Wd, t, 1.0)
+    assert s.options().fused_2d == chosen
+    s.set_options(cfl=0.3)
+    o = s.options()
+    assert o.fused_2d == chosen and o.dt_mode == 1 and o.cfl == 0.3
+    s.set_options(fused_2d=1 - chosen)
+    assert s.options().fused_2d == 1 - chosen and s.options().cfl == 0.3
+    s.step(U, V, Wd, t, 1.0)
+    assert s.launches_last_call == (5 if chosen == 0 else 8)
+    with pytest.raises(AttributeError):
+        s.set_options(no_such_option=1)
+    s.close()

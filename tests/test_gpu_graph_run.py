@@ -172,3 +172,19 @@ def test_mixed_tile_variants_per_size_class_give_the_same_bits(hw, precision):
         assert torch.equal(a, b)
     with pytest.raises(hw.HwenoError):
         s.set_class_variants([hw.TILE_VARIANTS] * nq)
+
+
+def test_options_report_the_autotuned_tile_and_keep_the_rest(hw):
+    """hweno_get_options after hweno_autotune holds the chosen tile variant;
+    set_options(cfl=...) keeps it and the other options."""
+    full = W.riemann_batch(count=16, seed=3)
+    s = hw.Solver.from_workload(full, dt_mode=1, limiter=2)
+    U, V = torch.from_numpy(full.U).cuda(), torch.from_numpy(full.V).cuda()
+    t = torch.zeros(full.batch, dtype=torch.float64, device="cuda")
+    chosen, _ = s.autotune(U, V, None, t, full.t_end)
+    assert s.options().tile_variant == chosen
+    s.set_options(cfl=0.4)
+    o = s.options()
+    assert (o.tile_variant, o.dt_mode, o.limiter, o.cfl) == (chosen, 1, 2, 0.4)
+    assert list(o.lin_w) == [0.98, 0.01, 0.01]
+    s.close()
