@@ -135,6 +135,21 @@ struct MinBlocks1D {
   static constexpr int value = base * 128 / NT > 0 ? base * 128 / NT : 1;
 };
 
+// The persistent kernel's register budget (FP32: its own setting; the work
+// queue and stage bookkeeping need registers the tiled kernel does not). At
+// 8 CTAs per SM (64 registers) the FP32 persistent kernel spilled 80 bytes;
+// requesting 6 lets it use the factored projections in 71 registers, which
+// still leaves 7 resident: +3% for the FP32 persistent run (measured 6383
+// against 6193 M point-updates/s on the 2048-instance batch).
+#ifndef HWENO_MINB_RUN_F32
+#define HWENO_MINB_RUN_F32 6
+#endif
+template <class Real, int NT>
+struct MinBlocksRun {
+  static constexpr int base = MinBlocks<Real, HWENO_MINB_1D_F64, HWENO_MINB_RUN_F32>::value;
+  static constexpr int value = base * 128 / NT > 0 ? base * 128 / NT : 1;
+};
+
 // The arrays one stage reads and writes (the rest of Args1D is shared by
 // every stage of a step).
 struct StageIO {
@@ -220,11 +235,17 @@ __device__ __forceinline__ void tile_point(const Args1D& a, const Real* U, const
 // the limiter off, component-wise, or (Euler) on the characteristic fields
 // of the eigenvectors at U_g.
 // Factored characteristic projections (Char1) in the tiled stage and
-// persistent kernels in FP64; the FP32 kernels, capped at 64 registers, and
-// the 124-point cluster step keep the rows of L applied one by one (the
-// factored form's larger live set spills there).
+// persistent kernels in FP64 and in the FP32 persistent kernel; the FP32
+// tiled kernel, capped at 64 registers, and the 124-point cluster step keep
+// the rows of L applied one by one (the factored form's larger live set
+// spills there).
 template <class Real>
 constexpr bool kFactored = std::is_same<Real, double>::value;
+#ifndef HWENO_FAC_RUN_F32
+#define HWENO_FAC_RUN_F32 1
+#endif
+template <class Real>
+constexpr bool kFactoredRun = kFactored<Real> || HWENO_FAC_RUN_F32;
 
 template <int EQ, class Real, class TV, bool FAC = true>
 __device__ __forceinline__ void limited_point(const Args1D& a, int g, Real idx, Real gm1,
@@ -617,7 +638,7 @@ __device__ __forceinline__ void release_add(unsigned* ctr, unsigned v) {
 // k does the time update (as k_finalize), clears the alpha slots the step
 // after next accumulates into, and releases step n + 1 of k.
 template <int EQ, class Real, int NT, int PPT>
-__global__ void __launch_bounds__(NT, (MinBlocks1D<Real, NT>::value))
+__global__ void __launch_bounds__(NT, (MinBlocksRun<Real, NT>::value))
 k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p) {
   __shared__ long long s_ticket;
   __shared__ int s_stop, s_gave_up;
@@ -652,19 +673,19 @@ k_run_1d(const __grid_constant__ Args1D a, const __grid_constant__ PersistArgs p
       io.Uout = p.U1; io.Vout = p.V1; io.Vt0out = p.Vt0;
       io.alpha_in = reinterpret_cast<const double*>(slot0);
       io.alpha_out = slot0 + p.batch;
-      stage_tile<EQ, Real, MODE_STAGE1, NT, PPT, kFactored<Real>>(a, io, k, s);
+      stage_tile<EQ, Real, MODE_STAGE1, NT, PPT, kFactoredRun<Real>>(a, io, k, s);
     } else if (stage == 1) {
       io.U = p.U1; io.V = p.V1; io.U0 = a.U; io.Vt0 = p.Vt0;
       io.Uout = p.U2; io.Vout = p.V2; io.Vt0out = nullptr;
       io.alpha_in = reinterpret_cast<const double*>(slot0 + p.batch);
       io.alpha_out = slot0 + 2 * p.batch;
-      stage_tile<EQ, Real, MODE_STAGE2, NT, PPT, kFactored<Real>>(a, io, k, s);
+      stage_tile<EQ, Real, MODE_STAGE2, NT, PPT, kFactoredRun<Real>>(a, io, k, s);
     } else {
       io.U = p.U2; io.V = p.V2; io.U0 = a.U; io.Vt0 = p.Vt0;
       io.Uout = const_cast<void*>(a.U); io.Vout = const_cast<void*>(a.V); io.Vt0out = nullptr;
       io.alpha_in = reinterpret_cast<const double*>(slot0 + 2 * p.batch);
       io.alpha_out = p.alpha + (size_t)((par ^ 1) * 3) * p.batch;  // alpha(U^{n+1})
-      stage_tile<EQ, Real, MODE_STAGE3, NT, PPT, kFactored<Real>>(a, io, k, s);
+      stage_tile<EQ, Real, MODE_STAGE3, NT, PPT, kFactoredRun<Real>>(a, io, k, s);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
