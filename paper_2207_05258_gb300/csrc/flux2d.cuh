@@ -20,14 +20,27 @@ struct Prim2 {
 };
 
 template <class Real>
-__device__ __forceinline__ Prim2<Real> prim2(const Real* U, Real gm1) {
+__device__ __forceinline__ Prim2<Real> prim2_ir(const Real* U, Real gm1, Real ir) {
   Prim2<Real> q;
-  q.ir = recip(U[0]);
+  q.ir = ir;
   q.u = U[1] * q.ir;
   q.v = U[2] * q.ir;
   q.p = gm1 * (U[3] - Real(0.5) * (U[1] * q.u + U[2] * q.v));
   q.Ep = U[3] + q.p;
   return q;
+}
+
+template <class Real>
+__device__ __forceinline__ Prim2<Real> prim2(const Real* U, Real gm1) {
+  return prim2_ir(U, gm1, recip(U[0]));
+}
+
+// The same with 1/rho as the square of rr = 1/sqrt(rho), which the caller
+// also uses (sqrt(rho) = rho rr for the Roe average).
+template <class Real>
+__device__ __forceinline__ Prim2<Real> prim2_rr(const Real* U, Real gm1, Real& rr) {
+  rr = rsq(U[0]);
+  return prim2_ir(U, gm1, rr * rr);
 }
 
 // Flux in direction DIR and the Jacobian-vector product A_DIR D (Eq. EQ3:

@@ -514,6 +514,16 @@ __device__ __forceinline__ Real rsq(Real x) {
   else return rsqrtf(x);
 }
 
+// c from c^2 for a wave speed: FP32 the approximate square root; FP64
+// c^2 rsqrt(c^2) (one reciprocal square root instead of the longer IEEE
+// square root), 0 at c^2 = 0, NaN for a negative or NaN c^2 as the square
+// root would give.
+template <class Real>
+__device__ __forceinline__ Real speed_from_sq(Real c2) {
+  if constexpr (std::is_same<Real, float>::value) return fast_sqrt(c2);
+  else return c2 * rsq(c2 == Real(0) ? Real(1) : c2);
+}
+
 // c and 1/c from c^2 with one reciprocal square root.
 template <class Real>
 __device__ __forceinline__ void sound_speed(Real c2, Real& c, Real& ic) {

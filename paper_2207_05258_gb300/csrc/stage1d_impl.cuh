@@ -62,10 +62,17 @@ __device__ __forceinline__ Real wave_speed(const Real* u, Real gam, Real a01) {
     buckley_f(u[0], f, df);
     return fmax(a01, fabs(df));
   } else {
-    const Real ir = recip(u[0]);
+    // FP64: 1/rho as the square of one reciprocal square root
+    Real ir;
+    if constexpr (std::is_same<Real, double>::value) {
+      const Real rr = rsq(u[0]);
+      ir = rr * rr;
+    } else {
+      ir = recip(u[0]);
+    }
     const Real vel = u[1] * ir;
     const Real p = (gam - Real(1)) * (u[2] - Real(0.5) * u[1] * vel);
-    return fabs(vel) + fast_sqrt(gam * p * ir);
+    return fabs(vel) + speed_from_sq(gam * p * ir);
   }
 }
 

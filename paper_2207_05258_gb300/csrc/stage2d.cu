@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
         sV[c][g] = v[c];
       }
       Prim2<Real> pq{};
-      if constexpr (EUL) pq = prim2(u, gm1);
+      Real rr = Real(0);  // 1/sqrt(rho)
+      if constexpr (EUL) pq = prim2_rr(u, gm1, rr);
       Real F[M], H[M], E[M];
       flux2<EQ, 0>(u, pq, F);
       jvp2<EQ, 0>(u, pq, v, gm1, H);
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_X_F64,
         sEta[c][g] = E[c];
       }
       if constexpr (EUL) {
-        sE[0][g] = u[0] * rsq(u[0]);
+        sE[0][g] = u[0] * rr;
         sE[1][g] = pq.u;
         sE[2][g] = pq.v;
         sE[3][g] = pq.Ep * pq.ir;
@@ -431,7 +432,8 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
         PT(1, c)[k] = ww[c];
       }
       Prim2<Real> pq{};
-      if constexpr (EUL) pq = prim2(u, gm1);
+      Real rr = Real(0);  // 1/sqrt(rho)
+      if constexpr (EUL) pq = prim2_rr(u, gm1, rr);
       Real G[M], T[M], X[M];
       flux2<EQ, 1>(u, pq, G);
       jvp2<EQ, 1>(u, pq, ww, gm1, T);
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(kThreads2D, (MinBlocks<Real, HWENO_MINB_Y_F64,
         PT(6, c)[k] = X[c];
       }
       if constexpr (EUL) {
-        sEig[0][k] = u[0] * rsq(u[0]);
+        sEig[0][k] = u[0] * rr;
         sEig[1][k] = pq.u;
         sEig[2][k] = pq.v;
         sEig[3][k] = pq.Ep * pq.ir;

@@ -15,8 +15,10 @@ __device__ __forceinline__ void speeds2(const Real* U, Real gam, Real& sx, Real&
   if constexpr (EQ == HWENO_BURGERS) {
     sx = sy = fabs(U[0]);
   } else {
-    const Prim2<Real> q = prim2(U, gam - Real(1));
-    const Real c = fast_sqrt(gam * q.p * q.ir);
+    Real rr;
+    const Prim2<Real> q = std::is_same<Real, double>::value ? prim2_rr(U, gam - Real(1), rr)
+                                                            : prim2(U, gam - Real(1));
+    const Real c = speed_from_sq(gam * q.p * q.ir);
     sx = fabs(q.u) + c;
     sy = fabs(q.v) + c;
   }

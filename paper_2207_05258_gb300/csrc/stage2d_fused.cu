@@ -141,7 +141,8 @@ k_stage_2d(const __grid_constant__ Args2D a) {
         sV[c][k] = v[c];
       }
       Prim2<Real> pq{};
-      if constexpr (EUL) pq = prim2(u, gm1);
+      Real rr = Real(0);  // 1/sqrt(rho)
+      if constexpr (EUL) pq = prim2_rr(u, gm1, rr);
       Real F[M], H[M], E[M];
       flux2<EQ, 0>(u, pq, F);
       jvp2<EQ, 0>(u, pq, v, gm1, H);
@@ -153,7 +154,7 @@ k_stage_2d(const __grid_constant__ Args2D a) {
         sEta[c][k] = E[c];
       }
       if constexpr (EUL) {
-        sE[0][k] = u[0] * rsq(u[0]);
+        sE[0][k] = u[0] * rr;
         sE[1][k] = pq.u;
         sE[2][k] = pq.v;
         sE[3][k] = pq.Ep * pq.ir;
@@ -361,7 +362,8 @@ k_stage_2d(const __grid_constant__ Args2D a) {
         PT(1, c)[k] = ww[c];
       }
       Prim2<Real> pq{};
-      if constexpr (EUL) pq = prim2(u, gm1);
+      Real rr = Real(0);  // 1/sqrt(rho)
+      if constexpr (EUL) pq = prim2_rr(u, gm1, rr);
       Real G[M], T[M], X[M];
       flux2<EQ, 1>(u, pq, G);
       jvp2<EQ, 1>(u, pq, ww, gm1, T);
@@ -373,7 +375,7 @@ k_stage_2d(const __grid_constant__ Args2D a) {
         PT(6, c)[k] = X[c];
       }
       if constexpr (EUL) {
-        sEig[0][k] = u[0] * rsq(u[0]);
+        sEig[0][k] = u[0] * rr;
         sEig[1][k] = pq.u;
         sEig[2][k] = pq.v;
         sEig[3][k] = pq.Ep * pq.ir;
