@@ -74,20 +74,20 @@ PEAK_TFLOPS = {"fp64": 1.25, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 # changes after the capture (profiles/ holds the commands and the raw
 # figures).
 # Stage kernel, per point and launch (FP32: the 2048-instance batch, the
-# mean of the three stage launches of one step, tile 128 x 2).
-MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": None, "fp32": 52.4}
+# mean of the three stage launches of one step of the autotuned tile).
+MEASURED_STAGE_TRAFFIC_PER_POINT = {"fp64": None, "fp32": 52.5}
 # Persistent kernel, per point-step (all three stages; FP64: 1024 instances,
 # 1 283 400 points, one launch of 2 steps of the autotuned tile).
-MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": None, "fp32": None}
+MEASURED_RUN_TRAFFIC_PER_POINT_STEP = {"fp64": 394.3, "fp32": None}
 # One 2D stage per point, per workload, precision and stage form (0: the
 # x-sweep + y-sweep launches of stage 1, 1: the fused stage-1 launch; smooth
 # Euler at 1024^2, double Mach at 1920x480); applied to grids whose working
 # set exceeds the L2.
-MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64", 0): None,
-                                       ("euler2d_smooth", "fp32", 0): None,
-                                       ("euler2d_smooth", "fp64", 1): None,
-                                       ("euler2d_smooth", "fp32", 1): None,
-                                       ("double_mach", "fp64", 0): None}
+MEASURED_STAGE_TRAFFIC_2D_PER_POINT = {("euler2d_smooth", "fp64", 0): 504.1,
+                                       ("euler2d_smooth", "fp32", 0): 222.3,
+                                       ("euler2d_smooth", "fp64", 1): 210.7,
+                                       ("euler2d_smooth", "fp32", 1): 89.7,
+                                       ("double_mach", "fp64", 0): 489.6}
 # One 2D Euler adjoint step (six reverse sweeps, 128-thread CTAs) per point, 512^2.
 MEASURED_ADJOINT_TRAFFIC_PER_POINT_STEP = {("euler", 2): 1862.6}
 
