@@ -121,3 +121,30 @@ def test_out_of_range_options_are_rejected_before_any_cuda_call(hw, field, value
     rc = hw.lib.hweno_step_1d_noalloc(hw.EULER, n, 0.0, 1.0, 1.4, ctypes.byref(bc),
                                       ctypes.byref(o), ptr(U), ptr(V), ptr(t), 1.0, None, None)
     assert rc == hw.EINVAL
+
+
+def test_binding_structs_match_the_header_layout(hw, tmp_path):
+    """The ctypes mirrors of hweno_grid, hweno_bc and hweno_options have the
+    C structs' size and field offsets (a C program compiled against the
+    header prints them)."""
+    structs = {"hweno_grid": hw.Grid, "hweno_bc": hw.Bc, "hweno_options": hw.Options}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "hweno.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                               check=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
